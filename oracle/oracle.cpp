@@ -1,0 +1,488 @@
+// CPU oracle for the maximum common induced subgraph (MCIS) problem.
+//
+// TEST INFRASTRUCTURE ONLY.  Nothing in the product library links, loads or
+// calls this file; only the tests, the package's smoke() check and the CPU
+// baseline leg of the benchmark do.  It shares no code, header, table or
+// helper with the CUDA path.
+//
+// Contents (each function cites the passage it follows):
+//   oracle_verify      definition of a common induced subgraph (Section II-A)
+//   oracle_mcs         sequential recursive McSplit (Section II-B, Algorithm 1,
+//                      Eq. 1), plain vertex-list domains, one vertex pair per
+//                      recursion level
+//   oracle_bruteforce  enumeration of injective partial mappings (definition)
+//   oracle_clique      maximum clique of the modular product graph (textbook
+//                      reduction; independent of McSplit)
+//   oracle_branch_log  oracle_mcs instrumented to record, per branching
+//                      decision, which candidate pairs (v,u) lay on an optimal
+//                      extension (training signal for the ordering network)
+//
+// Readings where the paper is silent (the McSplit publication it cites fixes
+// them; none of them changes the optimum, only the traversal):
+//   * vertices of each graph are renumbered by descending degree (total
+//     in+out degree when directed; Section IV-A), ties by lower original index;
+//   * the branching class minimises max(|L|,|R|), ties to the class holding
+//     the lowest-numbered left vertex; v is the lowest-numbered left vertex of
+//     that class; candidates u are tried in ascending number;
+//   * directed graphs split each class four ways by the pair of bits
+//     (x->v is an arc, v->x is an arc), matched against (y->u, u->y);
+//   * a self-loop is part of a vertex's label;
+//   * the prune test is bound <= |incumbent| (Algorithm 1), not the looser
+//     "smaller than" of the prose around Eq. 1.
+#include <algorithm>
+#include <chrono>
+#include <cstdint>
+#include <cstring>
+#include <utility>
+#include <vector>
+
+namespace {
+
+struct OGraph {
+    int n = 0;
+    std::vector<uint8_t> a;     // a[i*n+j] = 1 iff arc i->j
+    std::vector<int> lab;       // vertex label (0 if unlabelled)
+    bool edge(int i, int j) const { return a[(size_t)i * n + j] != 0; }
+};
+
+OGraph make_graph(int n, const uint8_t* adj, const int32_t* labels) {
+    OGraph g;
+    g.n = n;
+    g.a.assign(adj, adj + (size_t)n * n);
+    g.lab.assign(n, 0);
+    if (labels)
+        for (int i = 0; i < n; ++i) g.lab[i] = labels[i];
+    return g;
+}
+
+// Descending (total) degree order, stable by original index (Section IV-A).
+std::vector<int> degree_order(const OGraph& g, bool directed) {
+    std::vector<int> deg(g.n, 0);
+    for (int i = 0; i < g.n; ++i)
+        for (int j = 0; j < g.n; ++j) {
+            if (i == j) continue;
+            if (g.edge(i, j)) deg[i]++;
+            if (directed && g.edge(j, i)) deg[i]++;
+        }
+    std::vector<int> ord(g.n);
+    for (int i = 0; i < g.n; ++i) ord[i] = i;
+    std::stable_sort(ord.begin(), ord.end(),
+                     [&](int x, int y) { return deg[x] > deg[y]; });
+    return ord;
+}
+
+OGraph relabel(const OGraph& g, const std::vector<int>& ord) {
+    OGraph r;
+    r.n = g.n;
+    r.a.assign((size_t)g.n * g.n, 0);
+    r.lab.assign(g.n, 0);
+    for (int i = 0; i < g.n; ++i) {
+        r.lab[i] = g.lab[ord[i]];
+        for (int j = 0; j < g.n; ++j) r.a[(size_t)i * g.n + j] = g.a[(size_t)ord[i] * g.n + ord[j]];
+    }
+    return r;
+}
+
+// ---------------------------------------------------------------------------
+// McSplit (Section II-B; Algorithm 1 without the thread pool)
+// ---------------------------------------------------------------------------
+struct LabelClass {            // one "bidomain": vertices of G and of H sharing a label
+    std::vector<int> L, R;
+};
+
+struct BranchRecord {          // filled only by the instrumented run
+    int depth;
+    int v;                     // renumbered G vertex chosen at this node
+    std::vector<int> cands;    // renumbered H vertices tried, in order
+    std::vector<int64_t> sub_nodes;   // nodes in each candidate's subtree
+    std::vector<int> sub_best;        // best mapping size found inside each subtree
+};
+
+struct McSplit {
+    const OGraph& G;
+    const OGraph& H;
+    bool directed;
+    int64_t node_limit;
+    double time_limit;
+    std::chrono::steady_clock::time_point t0;
+    int64_t nodes = 0;
+    bool aborted = false;
+    std::vector<std::pair<int, int>> M, best;
+    std::vector<BranchRecord>* log = nullptr;
+    int log_max_depth = 0;
+
+    McSplit(const OGraph& g, const OGraph& h, bool d, int64_t nl, double tl)
+        : G(g), H(h), directed(d), node_limit(nl), time_limit(tl),
+          t0(std::chrono::steady_clock::now()) {}
+
+    // The part of the "label string" a newly mapped vertex adds to x (Table 1):
+    // one bit (adjacent or not) for undirected graphs, two bits when directed.
+    int rel(const OGraph& g, int x, int v) const {
+        int k = g.edge(x, v) ? 1 : 0;
+        if (directed && g.edge(v, x)) k |= 2;
+        return k;
+    }
+
+    bool out_of_budget() {
+        if (node_limit > 0 && nodes > node_limit) return true;
+        if (time_limit > 0 && (nodes & 1023) == 0) {
+            double s = std::chrono::duration<double>(std::chrono::steady_clock::now() - t0).count();
+            if (s > time_limit) return true;
+        }
+        return false;
+    }
+
+    // Eq. 1: |M| + sum over label classes of min(|L|, |R|).
+    int bound(const std::vector<LabelClass>& cl) const {
+        int b = (int)M.size();
+        for (const auto& c : cl) b += (int)std::min(c.L.size(), c.R.size());
+        return b;
+    }
+
+    // filterDomain on both graphs (Algorithm 1): drop v and u,
+    // then split every class by each vertex's relation to v (in G) / u (in H).
+    std::vector<LabelClass> filter(const std::vector<LabelClass>& cl, int v, int u) const {
+        std::vector<LabelClass> out;
+        const int parts = directed ? 4 : 2;
+        for (const auto& c : cl) {
+            std::vector<LabelClass> sub(parts);
+            for (int x : c.L)
+                if (x != v) sub[rel(G, x, v)].L.push_back(x);
+            for (int y : c.R)
+                if (y != u) sub[rel(H, y, u)].R.push_back(y);
+            for (auto& s : sub)
+                if (!s.L.empty() && !s.R.empty()) out.push_back(std::move(s));
+        }
+        return out;
+    }
+
+    // One call = one search node (Algorithm 1, procedure Solve).
+    void solve(std::vector<LabelClass> cl, int depth) {
+        ++nodes;
+        if (aborted || out_of_budget()) { aborted = true; return; }
+        if (M.size() > best.size()) best = M;                 // incumbent (Algorithm 1)
+        if (bound(cl) <= (int)best.size()) return;            // prune (Algorithm 1, Eq. 1)
+        // selectLabelClass (Algorithm 1): smallest max(|L|,|R|), ties to the
+        // class with the lowest-numbered left vertex.
+        int c = -1, ckey = 0, cmin = 0;
+        for (int i = 0; i < (int)cl.size(); ++i) {
+            int key = (int)std::max(cl[i].L.size(), cl[i].R.size());
+            int mn = *std::min_element(cl[i].L.begin(), cl[i].L.end());
+            if (c < 0 || key < ckey || (key == ckey && mn < cmin)) { c = i; ckey = key; cmin = mn; }
+        }
+        const int v = cmin;                                   // selectVertex (Algorithm 1)
+        std::vector<int> cand = cl[c].R;
+        std::sort(cand.begin(), cand.end());
+        BranchRecord* rec = nullptr;
+        size_t rec_idx = 0;
+        if (log && depth < log_max_depth) {
+            rec_idx = log->size();
+            log->push_back(BranchRecord{depth, v, {}, {}, {}});
+        }
+        for (int u : cand) {                                  // try every u of the class
+            std::vector<LabelClass> child = filter(cl, v, u);
+            M.emplace_back(v, u);
+            int64_t before = nodes;
+            int best_before = (int)best.size();
+            solve(std::move(child), depth + 1);
+            M.pop_back();
+            if (log && depth < log_max_depth) {
+                rec = &(*log)[rec_idx];
+                rec->cands.push_back(u);
+                rec->sub_nodes.push_back(nodes - before);
+                rec->sub_best.push_back((int)best.size() > best_before ? (int)best.size() : -1);
+            }
+            if (aborted) return;
+        }
+        // "G = G \ v" (Algorithm 1): v stays unmatched; only this class loses it.
+        auto& L = cl[c].L;
+        L.erase(std::find(L.begin(), L.end(), v));
+        if (L.empty()) cl.erase(cl.begin() + c);
+        solve(std::move(cl), depth);                          // the unmatched-v branch
+    }
+};
+
+std::vector<LabelClass> initial_classes(const OGraph& G, const OGraph& H) {
+    // One class per (label, self-loop) value present in both graphs.
+    std::vector<std::pair<int, int>> keys;
+    auto key = [](const OGraph& g, int i) { return std::make_pair(g.lab[i], g.edge(i, i) ? 1 : 0); };
+    for (int i = 0; i < G.n; ++i) keys.push_back(key(G, i));
+    std::sort(keys.begin(), keys.end());
+    keys.erase(std::unique(keys.begin(), keys.end()), keys.end());
+    std::vector<LabelClass> cl;
+    for (auto& k : keys) {
+        LabelClass c;
+        for (int i = 0; i < G.n; ++i) if (key(G, i) == k) c.L.push_back(i);
+        for (int j = 0; j < H.n; ++j) if (key(H, j) == k) c.R.push_back(j);
+        if (!c.L.empty() && !c.R.empty()) cl.push_back(std::move(c));
+    }
+    return cl;
+}
+
+// ---------------------------------------------------------------------------
+// Brute force over injective partial mappings (definition, Section II-A)
+// ---------------------------------------------------------------------------
+struct Brute {
+    const OGraph& G;
+    const OGraph& H;
+    std::vector<int> mapg;     // mapg[x] = y or -1
+    std::vector<char> used;
+    std::vector<int> dom;      // mapped G vertices in order
+    int best = 0;
+    std::vector<int> best_map;
+    int64_t leaves = 0;
+    Brute(const OGraph& g, const OGraph& h) : G(g), H(h), mapg(g.n, -1), used(h.n, 0) {}
+
+    bool ok(int x, int y) const {
+        if (G.lab[x] != H.lab[y]) return false;
+        if (G.edge(x, x) != H.edge(y, y)) return false;
+        for (int x2 : dom) {
+            int y2 = mapg[x2];
+            if (G.edge(x, x2) != H.edge(y, y2)) return false;
+            if (G.edge(x2, x) != H.edge(y2, y)) return false;
+        }
+        return true;
+    }
+    void dfs(int x) {
+        if (x == G.n) {
+            ++leaves;
+            if ((int)dom.size() > best) { best = (int)dom.size(); best_map = mapg; }
+            return;
+        }
+        // counting bound: even mapping every remaining G vertex cannot beat best
+        if ((int)dom.size() + (G.n - x) <= best) return;
+        for (int y = 0; y < H.n; ++y) {
+            if (used[y] || !ok(x, y)) continue;
+            used[y] = 1; mapg[x] = y; dom.push_back(x);
+            dfs(x + 1);
+            dom.pop_back(); mapg[x] = -1; used[y] = 0;
+        }
+        dfs(x + 1);
+    }
+};
+
+// ---------------------------------------------------------------------------
+// Maximum clique of the modular product graph (Bron-Kerbosch with pivoting)
+// ---------------------------------------------------------------------------
+struct Bits {
+    std::vector<uint64_t> w;
+    explicit Bits(int n = 0) : w((n + 63) / 64, 0) {}
+    void set(int i) { w[i >> 6] |= 1ull << (i & 63); }
+    bool get(int i) const { return (w[i >> 6] >> (i & 63)) & 1; }
+    int count() const { int c = 0; for (auto x : w) c += __builtin_popcountll(x); return c; }
+    bool any() const { for (auto x : w) if (x) return true; return false; }
+};
+
+struct Clique {
+    int N;
+    std::vector<Bits> adj;
+    int best = 0;
+    std::vector<int> cur, best_set;
+
+    void bk(Bits P, Bits X) {
+        int pc = P.count();
+        if (!P.any() && !X.any()) {
+            if ((int)cur.size() > best) { best = (int)cur.size(); best_set = cur; }
+            return;
+        }
+        if ((int)cur.size() + pc <= best) return;
+        // pivot: vertex of P u X with most neighbours in P
+        int piv = -1, pbest = -1;
+        for (size_t k = 0; k < P.w.size(); ++k) {
+            uint64_t m = P.w[k] | X.w[k];
+            while (m) {
+                int i = (int)(k * 64 + __builtin_ctzll(m));
+                m &= m - 1;
+                int c = 0;
+                for (size_t q = 0; q < P.w.size(); ++q) c += __builtin_popcountll(P.w[q] & adj[i].w[q]);
+                if (c > pbest) { pbest = c; piv = i; }
+            }
+        }
+        for (size_t k = 0; k < P.w.size(); ++k) {
+            uint64_t m = P.w[k] & ~adj[piv].w[k];
+            while (m) {
+                int i = (int)(k * 64 + __builtin_ctzll(m));
+                m &= m - 1;
+                if (!P.get(i)) continue;
+                Bits P2(N), X2(N);
+                for (size_t q = 0; q < P.w.size(); ++q) {
+                    P2.w[q] = P.w[q] & adj[i].w[q];
+                    X2.w[q] = X.w[q] & adj[i].w[q];
+                }
+                cur.push_back(i);
+                bk(P2, X2);
+                cur.pop_back();
+                P.w[i >> 6] &= ~(1ull << (i & 63));
+                X.set(i);
+                if ((int)cur.size() + P.count() <= best) return;
+            }
+        }
+    }
+};
+
+}  // namespace
+
+extern "C" {
+
+// Checks that (g_idx[i], h_idx[i]), i < k, is an injective partial map whose
+// image is a common induced subgraph: equal labels, and for every ordered pair
+// (i, j) including i == j, arc g_i->g_j exists iff arc h_i->h_j exists.
+// Returns 1 if valid, otherwise a negative reason code.
+int oracle_verify(int nG, const uint8_t* adjG, const int32_t* labG,
+                  int nH, const uint8_t* adjH, const int32_t* labH,
+                  int k, const int32_t* g_idx, const int32_t* h_idx) {
+    if (k < 0 || k > nG || k > nH) return -1;
+    std::vector<char> ug(nG, 0), uh(nH, 0);
+    for (int i = 0; i < k; ++i) {
+        int x = g_idx[i], y = h_idx[i];
+        if (x < 0 || x >= nG || y < 0 || y >= nH) return -2;    // out of range
+        if (ug[x] || uh[y]) return -3;                          // not injective
+        ug[x] = uh[y] = 1;
+        int lx = labG ? labG[x] : 0, ly = labH ? labH[y] : 0;
+        if (lx != ly) return -4;                                // label mismatch
+    }
+    for (int i = 0; i < k; ++i)
+        for (int j = 0; j < k; ++j) {
+            uint8_t eg = adjG[(size_t)g_idx[i] * nG + g_idx[j]] != 0;
+            uint8_t eh = adjH[(size_t)h_idx[i] * nH + h_idx[j]] != 0;
+            if (eg != eh) return i == j ? -6 : -5;              // loop / edge mismatch
+        }
+    return 1;
+}
+
+// Sequential McSplit.  Returns the size of the best mapping found and writes
+// it (original vertex numbers) to out_g/out_h (capacity min(nG,nH)).
+// *status = 0 when the search completed (optimum proven), 1 when the node or
+// time limit stopped it (then the size is a lower bound).  *nodes = number of
+// calls of the recursive procedure (one per search node, Algorithm 1).
+int oracle_mcs(int nG, const uint8_t* adjG, const int32_t* labG,
+               int nH, const uint8_t* adjH, const int32_t* labH,
+               int directed, int64_t node_limit, double time_limit_s,
+               int32_t* out_g, int32_t* out_h, int64_t* nodes, int* status) {
+    OGraph g0 = make_graph(nG, adjG, labG), h0 = make_graph(nH, adjH, labH);
+    std::vector<int> og = degree_order(g0, directed != 0), oh = degree_order(h0, directed != 0);
+    OGraph G = relabel(g0, og), H = relabel(h0, oh);
+    McSplit s(G, H, directed != 0, node_limit, time_limit_s);
+    s.solve(initial_classes(G, H), 0);
+    int k = (int)s.best.size();
+    for (int i = 0; i < k; ++i) {
+        if (out_g) out_g[i] = og[s.best[i].first];
+        if (out_h) out_h[i] = oh[s.best[i].second];
+    }
+    if (nodes) *nodes = s.nodes;
+    if (status) *status = s.aborted ? 1 : 0;
+    return k;
+}
+
+// Exhaustive enumeration of injective partial maps (with only the trivial
+// counting cut).  For tiny graphs (n <= 9 or so).  Returns the maximum size.
+int oracle_bruteforce(int nG, const uint8_t* adjG, const int32_t* labG,
+                      int nH, const uint8_t* adjH, const int32_t* labH,
+                      int32_t* out_g, int32_t* out_h) {
+    OGraph G = make_graph(nG, adjG, labG), H = make_graph(nH, adjH, labH);
+    Brute b(G, H);
+    b.dfs(0);
+    int k = 0;
+    for (int x = 0; x < nG && !b.best_map.empty(); ++x)
+        if (b.best_map[x] >= 0) {
+            if (out_g) out_g[k] = x;
+            if (out_h) out_h[k] = b.best_map[x];
+            ++k;
+        }
+    return b.best;
+}
+
+// Maximum common induced subgraph size as the maximum clique of the modular
+// product: vertices (x, y) with equal label and equal self-loop bit; (x, y)
+// and (x', y') adjacent iff x != x', y != y' and both arc directions agree.
+int oracle_clique(int nG, const uint8_t* adjG, const int32_t* labG,
+                  int nH, const uint8_t* adjH, const int32_t* labH,
+                  int32_t* out_g, int32_t* out_h) {
+    OGraph G = make_graph(nG, adjG, labG), H = make_graph(nH, adjH, labH);
+    std::vector<std::pair<int, int>> V;
+    for (int x = 0; x < nG; ++x)
+        for (int y = 0; y < nH; ++y)
+            if (G.lab[x] == H.lab[y] && G.edge(x, x) == H.edge(y, y)) V.emplace_back(x, y);
+    Clique c;
+    c.N = (int)V.size();
+    c.adj.assign(c.N, Bits(c.N));
+    for (int p = 0; p < c.N; ++p)
+        for (int q = 0; q < c.N; ++q) {
+            int x = V[p].first, y = V[p].second, x2 = V[q].first, y2 = V[q].second;
+            if (x == x2 || y == y2) continue;
+            if (G.edge(x, x2) == H.edge(y, y2) && G.edge(x2, x) == H.edge(y2, y)) c.adj[p].set(q);
+        }
+    Bits P(c.N), X(c.N);
+    for (int p = 0; p < c.N; ++p) P.set(p);
+    if (c.N) c.bk(P, X);
+    for (int i = 0; i < (int)c.best_set.size(); ++i) {
+        if (out_g) out_g[i] = V[c.best_set[i]].first;
+        if (out_h) out_h[i] = V[c.best_set[i]].second;
+    }
+    return c.best;
+}
+
+// Instrumented McSplit for the ordering network's training signal.  For each
+// branching node at depth < max_depth it records the chosen v and, for every
+// candidate u tried, the nodes spent in (v,u)'s subtree and whether a new
+// incumbent was found inside it.  Records are written as flat int64 rows:
+//   [depth, v, u, sub_nodes, improved_to (or -1), cand_rank]
+// in renumbered (degree-order) vertex ids, plus the two renumberings in
+// perm_g/perm_h (perm[i] = original id of renumbered vertex i).  Returns the
+// number of rows written (at most max_rows); *size gets the optimum.
+int64_t oracle_branch_log(int nG, const uint8_t* adjG, const int32_t* labG,
+                          int nH, const uint8_t* adjH, const int32_t* labH,
+                          int directed, int max_depth, int64_t node_limit,
+                          int64_t* rows, int64_t max_rows,
+                          int32_t* perm_g, int32_t* perm_h, int* size, int* status) {
+    OGraph g0 = make_graph(nG, adjG, labG), h0 = make_graph(nH, adjH, labH);
+    std::vector<int> og = degree_order(g0, directed != 0), oh = degree_order(h0, directed != 0);
+    OGraph G = relabel(g0, og), H = relabel(h0, oh);
+    McSplit s(G, H, directed != 0, node_limit, 0.0);
+    std::vector<BranchRecord> log;
+    s.log = &log;
+    s.log_max_depth = max_depth;
+    s.solve(initial_classes(G, H), 0);
+    int64_t r = 0;
+    for (const auto& rec : log)
+        for (size_t i = 0; i < rec.cands.size() && r < max_rows; ++i, ++r) {
+            int64_t* row = rows + r * 6;
+            row[0] = rec.depth; row[1] = rec.v; row[2] = rec.cands[i];
+            row[3] = rec.sub_nodes[i]; row[4] = rec.sub_best[i]; row[5] = (int64_t)i;
+        }
+    for (int i = 0; i < nG; ++i) if (perm_g) perm_g[i] = og[i];
+    for (int i = 0; i < nH; ++i) if (perm_h) perm_h[i] = oh[i];
+    if (size) *size = (int)s.best.size();
+    if (status) *status = s.aborted ? 1 : 0;
+    return r;
+}
+
+// Applies filterDomain for the pairs (g_seq[t], h_seq[t]), t < k, one after
+// the other, starting from the initial label classes, without renumbering.
+// After each step t it writes Eq. 1's bound to bounds[t] and, for every
+// unmatched vertex, the index of the class holding it (or -1 when its class
+// was dropped) to cls_g[t*nG + x] / cls_h[t*nH + y].  Class indices are
+// positions in the class list, so only the partition is meaningful.  Used to
+// pin the split and the bound against the worked example of Table 1.
+int oracle_split_trace(int nG, const uint8_t* adjG, const int32_t* labG,
+                       int nH, const uint8_t* adjH, const int32_t* labH,
+                       int directed, int k, const int32_t* g_seq, const int32_t* h_seq,
+                       int32_t* bounds, int32_t* cls_g, int32_t* cls_h) {
+    OGraph G = make_graph(nG, adjG, labG), H = make_graph(nH, adjH, labH);
+    McSplit s(G, H, directed != 0, 0, 0.0);
+    std::vector<LabelClass> cl = initial_classes(G, H);
+    for (int t = 0; t < k; ++t) {
+        cl = s.filter(cl, g_seq[t], h_seq[t]);
+        s.M.emplace_back(g_seq[t], h_seq[t]);
+        bounds[t] = s.bound(cl);
+        for (int x = 0; x < nG; ++x) cls_g[(size_t)t * nG + x] = -1;
+        for (int y = 0; y < nH; ++y) cls_h[(size_t)t * nH + y] = -1;
+        for (int c = 0; c < (int)cl.size(); ++c) {
+            for (int x : cl[c].L) cls_g[(size_t)t * nG + x] = c;
+            for (int y : cl[c].R) cls_h[(size_t)t * nH + y] = c;
+        }
+    }
+    return (int)cl.size();
+}
+
+}  // extern "C"

@@ -1,0 +1,228 @@
+"""Pins for the CPU oracle against things other than itself: brute force, the
+modular-product clique reduction, closed forms, invariants and the paper's
+worked example (Table 1, Eq. 1)."""
+import json
+import os
+
+import numpy as np
+import pytest
+
+import oracle
+import synth
+
+HERE = os.path.dirname(os.path.abspath(__file__))
+
+
+def _rand_pair(seed, nG, nH, p, directed=False, k=0):
+    rg, rh = synth.rng_for(900, seed, 0), synth.rng_for(900, seed, 1)
+    f = synth.er_directed if directed else synth.er_undirected
+    a, b = f(nG, p, rg), f(nH, p, rh)
+    la = synth.uniform_labels(nG, k, rg)
+    lb = synth.uniform_labels(nH, k, rh)
+    return a, b, la, lb
+
+
+def _edges(n, e):
+    a = np.zeros((n, n), np.uint8)
+    for i, j in e:
+        a[i, j] = a[j, i] = 1
+    return a
+
+
+def complete(n):
+    a = np.ones((n, n), np.uint8)
+    np.fill_diagonal(a, 0)
+    return a
+
+
+def path(n):
+    return _edges(n, [(i, i + 1) for i in range(n - 1)])
+
+
+def cycle(n):
+    return _edges(n, [(i, (i + 1) % n) for i in range(n)])
+
+
+# --------------------------------------------------------------------------
+# verifier
+# --------------------------------------------------------------------------
+def test_verifier_hand_cases():
+    P3 = path(3)                      # 0-1-2
+    K3 = complete(3)
+    # identity on the path is valid
+    assert oracle.verify(P3, P3, [0, 1, 2], [0, 1, 2]) == 1
+    # path into triangle: edge 0-2 missing in P3 but present in K3 -> induced fails
+    assert oracle.verify(P3, K3, [0, 1, 2], [0, 1, 2]) == -5
+    # two vertices of P3 adjacent map to an edge: fine
+    assert oracle.verify(P3, K3, [0, 1], [2, 0]) == 1
+    # non-injective
+    assert oracle.verify(P3, P3, [0, 1], [1, 1]) == -3
+    # out of range
+    assert oracle.verify(P3, P3, [0, 3], [1, 2]) == -2
+    # labels differ
+    assert oracle.verify(P3, P3, [0], [0], np.array([1, 0, 0], np.int32),
+                         np.array([0, 0, 0], np.int32)) == -4
+    # self-loop on one side only
+    L = P3.copy()
+    L[1, 1] = 1
+    assert oracle.verify(L, P3, [1], [1]) == -6
+    # directed: arc only one way
+    D = np.zeros((2, 2), np.uint8)
+    D[0, 1] = 1
+    E = np.zeros((2, 2), np.uint8)
+    E[1, 0] = 1
+    assert oracle.verify(D, E, [0, 1], [0, 1]) == -5
+    assert oracle.verify(D, E, [0, 1], [1, 0]) == 1
+    # empty mapping is valid
+    assert oracle.verify(P3, K3, [], []) == 1
+
+
+# --------------------------------------------------------------------------
+# brute force (n <= 9) and clique reduction
+# --------------------------------------------------------------------------
+@pytest.mark.parametrize("directed,k", [(False, 0), (True, 0), (False, 3), (True, 2)])
+def test_oracle_vs_bruteforce(directed, k):
+    rs = np.random.default_rng(17 + 31 * k + (1000 if directed else 0))
+    for s in range(150):
+        nG, nH = int(rs.integers(0, 10)), int(rs.integers(0, 10))
+        p = float(rs.uniform(0.1, 0.7))
+        a, b, la, lb = _rand_pair(s + (5000 if directed else 0) + 100 * k, nG, nH, p, directed, k)
+        r = oracle.mcs(a, b, la, lb, directed=directed)
+        kb, bg, bh = oracle.bruteforce(a, b, la, lb)
+        assert r.complete
+        assert r.size == kb, (s, nG, nH, p)
+        assert oracle.verify(a, b, r.g_idx, r.h_idx, la, lb) == 1
+        assert oracle.verify(a, b, bg, bh, la, lb) == 1
+        assert len(bg) == kb
+
+
+def test_oracle_vs_bruteforce_selfloops():
+    rs = np.random.default_rng(5)
+    for s in range(100):
+        nG, nH = int(rs.integers(1, 9)), int(rs.integers(1, 9))
+        a, b, la, lb = _rand_pair(7000 + s, nG, nH, 0.4, directed=bool(s % 2))
+        a[np.diag_indices(nG)] = (rs.random(nG) < 0.3)
+        b[np.diag_indices(nH)] = (rs.random(nH) < 0.3)
+        r = oracle.mcs(a, b, directed=bool(s % 2))
+        assert r.size == oracle.bruteforce(a, b)[0]
+        assert oracle.verify(a, b, r.g_idx, r.h_idx) == 1
+
+
+@pytest.mark.parametrize("directed,k", [(False, 0), (True, 0), (False, 2)])
+def test_oracle_vs_modular_product_clique(directed, k):
+    rs = np.random.default_rng(99 + k + (7 if directed else 0))
+    for s in range(25):
+        nG, nH = int(rs.integers(6, 13)), int(rs.integers(6, 13))
+        p = float(rs.uniform(0.15, 0.6))
+        a, b, la, lb = _rand_pair(9000 + s + 50 * k + (500 if directed else 0), nG, nH, p,
+                                  directed, k)
+        r = oracle.mcs(a, b, la, lb, directed=directed)
+        kc, cg, ch = oracle.clique(a, b, la, lb)
+        assert r.size == kc
+        assert oracle.verify(a, b, cg, ch, la, lb) == 1
+
+
+# --------------------------------------------------------------------------
+# closed forms and invariants
+# --------------------------------------------------------------------------
+def test_closed_forms():
+    for a in range(1, 8):
+        for b in range(1, 8):
+            assert oracle.mcs(complete(a), complete(b)).size == min(a, b)
+            assert oracle.mcs(np.zeros((a, a), np.uint8), complete(b)).size == 1
+            assert oracle.mcs(path(a), path(b)).size == min(a, b)
+    for a in range(3, 9):
+        for b in range(a + 1, 11):
+            assert oracle.mcs(cycle(a), cycle(b)).size == a - 1
+    g = synth.grid(6, 6)
+    assert oracle.mcs(g, g).size == 36
+    assert oracle.mcs(np.zeros((0, 0), np.uint8), complete(3)).size == 0
+
+
+def test_invariants():
+    rs = np.random.default_rng(3)
+    for s in range(40):
+        directed = bool(s % 2)
+        n1, n2 = int(rs.integers(5, 15)), int(rs.integers(5, 15))
+        a, b, _, _ = _rand_pair(12000 + s, n1, n2, float(rs.uniform(0.1, 0.5)), directed)
+        k = oracle.mcs(a, b, directed=directed).size
+        assert oracle.mcs(a, a, directed=directed).size == n1            # MCS(G,G) = |V|
+        assert oracle.mcs(b, a, directed=directed).size == k             # symmetry
+        perm = rs.permutation(n2)
+        assert oracle.mcs(a, b[np.ix_(perm, perm)], directed=directed).size == k
+        perm = rs.permutation(n1)
+        assert oracle.mcs(a[np.ix_(perm, perm)], b, directed=directed).size == k
+        assert 1 <= k <= min(n1, n2)
+        if not directed:                                                  # complements
+            ca, cb = 1 - a, 1 - b
+            np.fill_diagonal(ca, 0)
+            np.fill_diagonal(cb, 0)
+            assert oracle.mcs(ca, cb).size == k
+
+
+def test_planted_core_lower_bound():
+    for s in range(6):
+        rng = synth.rng_for(77, s, 0)
+        p = synth.planted_pair(16, 0.5, 0.3, rng)
+        assert oracle.mcs(p.G.adj, p.H.adj).size >= 8
+
+
+def test_labels_restrict():
+    # identical graphs but labels that disagree everywhere: nothing matches
+    a = complete(5)
+    assert oracle.mcs(a, a, np.zeros(5, np.int32), np.ones(5, np.int32)).size == 0
+    la = np.array([0, 0, 1, 1, 2], np.int32)
+    assert oracle.mcs(a, a, la, la).size == 5
+
+
+# --------------------------------------------------------------------------
+# worked example (Table 1) and Eq. 1
+# --------------------------------------------------------------------------
+def test_table1_split_and_bound():
+    fx = json.load(open(os.path.join(HERE, "golden", "table1.json")))
+    G = _edges(4, fx["G_edges"])
+    H = _edges(4, fx["H_edges"])
+    bounds, cg, ch = oracle.split_trace(G, H, fx["mapping_g"], fx["mapping_h"])
+    assert list(bounds) == fx["bound_after_step_eq1"]
+    for t, lab in enumerate(fx["labels_after_step"]):
+        lg = {int(k): v for k, v in lab["G"].items()}
+        lh = {int(k): v for k, v in lab["H"].items()}
+        common = set(lg.values()) & set(lh.values())
+        # same label string on both sides <=> same class; a label present on one
+        # side only gives no class (its vertices can never be matched)
+        for x in range(4):
+            if x in lg and lg[x] in common:
+                for y in range(4):
+                    if y in lh:
+                        assert (cg[t, x] == ch[t, y]) == (lg[x] == lh[y])
+            else:
+                assert cg[t, x] == -1
+        for y in range(4):
+            if not (y in lh and lh[y] in common):
+                assert ch[t, y] == -1
+
+
+def test_node_counts_tiny_hand_derived():
+    # K1 vs K1: root, child (0,0) pruned at its bound (=1 <= incumbent 1),
+    # then the unmatched-v node with no classes: 3 calls.
+    assert oracle.mcs(complete(1), complete(1)).nodes == 3
+    # K2 vs K2 worked by hand under the bound <= incumbent rule: 6 calls.
+    assert oracle.mcs(complete(2), complete(2)).nodes == 6
+
+
+def test_node_limit_gives_lower_bound():
+    p = synth.config1_pair()
+    r = oracle.mcs(p.G.adj, p.H.adj, node_limit=500)
+    assert not r.complete
+    assert oracle.verify(p.G.adj, p.H.adj, r.g_idx, r.h_idx) == 1
+    assert r.size <= 13
+
+
+def test_config1_golden_matches_generator():
+    import sys
+    sys.path.insert(0, os.path.join(HERE, "golden"))
+    from make_oracle_golden import pair_digest
+    rows = [json.loads(x) for x in open(os.path.join(HERE, "golden", "c1_oracle.jsonl"))]
+    p = synth.config1_pair()
+    assert rows[0]["digest"] == pair_digest(p)
+    assert rows[0]["size"] == oracle.mcs(p.G.adj, p.H.adj).size == 13
