@@ -1,0 +1,156 @@
+/*
+ * mcs.h -- C ABI of the B300 (sm_103a) maximum common induced subgraph solver.
+ *
+ * The library computes, for graph pairs (G, H), a maximum common induced
+ * subgraph (Section II-A: the largest graph isomorphic to an induced subgraph
+ * of both G and H; mapped vertices keep their labels, and an arc x->y exists
+ * in G exactly when f(x)->f(y) exists in H, self-loops included) with
+ * McSplit's branch and bound (Section II-B, Algorithm 1, Eq. 1): label classes
+ * are split by adjacency to each newly mapped pair (Table 1) and a branch is
+ * pruned when |M| + sum over classes of min(|L|, |R|) <= |incumbent|.
+ * All graph arithmetic is exact integer work; the size returned with status
+ * MCS_OK is the proven optimum.
+ *
+ * Graph encoding (all entry points):
+ *   n       number of vertices, 0 <= n <= MCS_MAX_N
+ *   adj     n*n bytes, row major, adj[i*n + j] == 1 iff arc i -> j, else 0.
+ *           Without MCS_DIRECTED the matrix must be symmetric.  Diagonal
+ *           entries are self-loops; they are allowed and must be matched.
+ *   labels  n int32 vertex labels (>= 0), or NULL for unlabelled.  A vertex may
+ *           only be mapped onto a vertex with the same label.
+ *
+ * Mapping encoding: for pair p, map[p*MCS_MAX_N + x] is the H vertex matched
+ * to G vertex x (original numbering), or -1; entries x >= n_G are -1.
+ *
+ * Ownership: the caller owns every buffer passed in or out.  The library
+ * copies what it needs before a call returns (synchronous calls) or before it
+ * enqueues work (mcs_submit); it never keeps a caller pointer.  A context is
+ * not thread safe: use one context per host thread.
+ *
+ * Errors: functions return MCS_OK (0) or a positive status on success and a
+ * negative MCS_ERR_* code on failure; mcs_strerror() names every code.  Batch
+ * calls also set a per-pair status and return the worst one.
+ */
+#ifndef MCS_H_
+#define MCS_H_
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+#define MCS_MAX_N 64
+
+/* status / return codes */
+#define MCS_OK                 0   /* optimum found and proven                        */
+#define MCS_TIMEOUT            1   /* time limit hit: size is a valid lower bound      */
+#define MCS_PENDING            2   /* mcs_poll: request not finished yet               */
+#define MCS_ERR_ARG           -1   /* NULL pointer, n out of range, entry not 0/1,     */
+                                   /* asymmetric matrix without MCS_DIRECTED,          */
+                                   /* negative label, unknown ticket                   */
+#define MCS_ERR_NOMEM         -2   /* device or pinned allocation failed              */
+#define MCS_ERR_CUDA          -3   /* a CUDA runtime call failed                      */
+#define MCS_ERR_DEVICE_STALL  -4   /* a bounded device-side wait expired              */
+#define MCS_ERR_UNSUPPORTED   -5   /* option not available in this build              */
+
+/* flags */
+#define MCS_DIRECTED          0x1u  /* arcs are ordered pairs (4-way class split)      */
+#define MCS_ORDER_PLAIN       0x0u  /* degree order (Section IV-A); the default        */
+#define MCS_ORDER_LEARNED     0x2u  /* candidate order from the ordering network;      */
+                                    /* needs mcs_set_order_model(); exact either way   */
+#define MCS_NO_MAPPING        0x4u  /* do not return the mapping                       */
+#define MCS_NO_LEVEL_PRUNE    0x8u  /* diagnostic: do not re-test a level's bound      */
+                                    /* before each sibling, so that with one warp the  */
+                                    /* node count equals the sequential recursion's    */
+
+typedef struct mcs_ctx mcs_ctx;
+
+typedef struct {
+    int32_t n;
+    const uint8_t* adj;      /* n*n, row major, 0/1                               */
+    const int32_t* labels;   /* n entries or NULL                                 */
+} mcs_graph;
+
+typedef struct {
+    int32_t size;            /* |mapping|                                         */
+    int32_t status;          /* MCS_OK, MCS_TIMEOUT or MCS_ERR_*                  */
+    int32_t npairs;          /* entries written to g_idx/h_idx (== size)          */
+    int32_t _pad;
+    int16_t* g_idx;          /* caller-allocated, capacity >= min(nG, nH), or NULL */
+    int16_t* h_idx;          /* same; pairs sorted by g_idx                        */
+    uint64_t nodes;          /* search nodes expanded for this pair               */
+    double seconds;          /* device time from the pair's start to its proof    */
+} mcs_result;
+
+/* Creates a context on CUDA device `device`.  flags: reserved, pass 0.
+ * Returns NULL on failure (no device, allocation failure). */
+mcs_ctx* mcs_create(int device, uint32_t flags);
+void mcs_destroy(mcs_ctx* ctx);
+
+/* Solves one pair.  timeout_s <= 0 means no limit (an internal cap of one
+ * hour still bounds every device wait).  Returns out->status. */
+int mcs_solve(mcs_ctx* ctx, const mcs_graph* G, const mcs_graph* H,
+              uint32_t flags, double timeout_s, mcs_result* out);
+
+/* Solves npairs pairs (G[i], H[i]) in one persistent launch.  timeout_s is
+ * per pair, counted from the moment the pair's search starts.  Returns the
+ * worst (lowest negative, else highest) per-pair status. */
+int mcs_solve_batch(mcs_ctx* ctx, const mcs_graph* G, const mcs_graph* H,
+                    int32_t npairs, uint32_t flags, double timeout_s,
+                    mcs_result* out);
+
+/* Device-resident batch: every pointer is a device pointer; nothing is
+ * copied between host and device and the call does not synchronise.
+ *   d_n[2p], d_n[2p+1]            vertex counts of G_p and H_p
+ *   d_adj_off[2p], d_adj_off[2p+1] byte offsets of their matrices in d_adj
+ *   d_lab_off[...]                 element offsets of their labels in d_labels
+ *                                  (ignored when d_labels is NULL; an offset
+ *                                  of -1 marks one graph as unlabelled)
+ * Outputs (npairs entries each; d_map npairs*MCS_MAX_N, may be NULL):
+ *   d_size, d_status, d_nodes, d_map, d_usec (device microseconds per pair,
+ *   may be NULL).  `stream` is a cudaStream_t (NULL = the context's stream).
+ * Invalid pairs get status MCS_ERR_ARG.  Returns 0 if the work was enqueued. */
+int mcs_solve_batch_device(mcs_ctx* ctx, int32_t npairs,
+                           const int32_t* d_n, const int64_t* d_adj_off,
+                           const uint8_t* d_adj, const int64_t* d_lab_off,
+                           const int32_t* d_labels, uint32_t flags, double timeout_s,
+                           int32_t* d_size, int32_t* d_status, uint64_t* d_nodes,
+                           int16_t* d_map, float* d_usec, void* stream);
+
+/* Serving: admit one request; returns a ticket.  The search starts on the
+ * device as soon as a slot and device memory are free; requests submitted
+ * while others run join them (continuous batching). */
+int mcs_submit(mcs_ctx* ctx, const mcs_graph* G, const mcs_graph* H,
+               uint32_t flags, double timeout_s, uint64_t* ticket);
+
+/* Returns MCS_PENDING until the request finishes, then its status, and fills
+ * `out` (mapping buffers as in mcs_result).  A finished ticket is released by
+ * the first poll that reports it. */
+int mcs_poll(mcs_ctx* ctx, uint64_t ticket, mcs_result* out);
+
+/* Launch shape used by every solve on this context (0 keeps the current or
+ * the tuned value): warps per block, blocks per SM, class-stack entries kept
+ * in shared memory per warp. */
+int mcs_set_launch(mcs_ctx* ctx, int warps_per_block, int blocks_per_sm,
+                   int smem_stack_entries);
+
+/* Restricts a solve to `warps` resident warps in total (0 = the full grid).
+ * With warps == 1 the search order is deterministic. */
+int mcs_set_max_warps(mcs_ctx* ctx, int warps);
+
+/* Statistics of the last solve on this context: out[0] search-kernel
+ * microseconds (for mcs_solve_batch_device: once its stream has passed the
+ * launch, else the previous value), out[1] total nodes, out[2] donated tasks,
+ * out[3] tasks taken from the ring, out[4] child levels that spilled past the
+ * shared-memory class cache, out[5] warps launched, out[6] bytes copied host
+ * to device, out[7] bytes copied device to host (out[1..4], out[6..7]: host
+ * API calls only).  Returns the number of values written (<= n, <= 8). */
+int mcs_last_stats(mcs_ctx* ctx, double* out, int n);
+
+const char* mcs_strerror(int code);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* MCS_H_ */

@@ -1,0 +1,252 @@
+"""B300-native exact maximum common induced subgraph search (McSplit).
+
+Thin ctypes binding over ``libmcs.so`` (C ABI in ``include/mcs.h``).  This
+module only marshals arguments: validation of graph contents, renumbering,
+packing, the branch and bound, and result decoding all run in the library's
+CUDA kernels.  There is no CPU fallback: if the library is missing the import
+of :class:`Solver` fails loudly.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+from dataclasses import dataclass
+from typing import List, Optional, Sequence
+
+import numpy as np
+
+__all__ = ["Solver", "Result", "MCS_OK", "MCS_TIMEOUT", "MCS_PENDING", "MCS_ERR_ARG",
+           "MCS_ERR_NOMEM", "MCS_ERR_CUDA", "MCS_ERR_DEVICE_STALL", "MCS_ERR_UNSUPPORTED",
+           "MCS_DIRECTED", "MCS_ORDER_LEARNED", "MCS_NO_MAPPING", "MCS_NO_LEVEL_PRUNE",
+           "MCS_MAX_N", "lib_path", "load_library", "EXPORTED_SYMBOLS"]
+
+MCS_MAX_N = 64
+MCS_OK, MCS_TIMEOUT, MCS_PENDING = 0, 1, 2
+MCS_ERR_ARG, MCS_ERR_NOMEM, MCS_ERR_CUDA, MCS_ERR_DEVICE_STALL, MCS_ERR_UNSUPPORTED = -1, -2, -3, -4, -5
+MCS_DIRECTED, MCS_ORDER_LEARNED, MCS_NO_MAPPING, MCS_NO_LEVEL_PRUNE = 0x1, 0x2, 0x4, 0x8
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+
+
+def lib_path() -> str:
+    return os.path.join(_HERE, "libmcs.so")
+
+
+class _Graph(ctypes.Structure):
+    _fields_ = [("n", ctypes.c_int32), ("adj", ctypes.POINTER(ctypes.c_uint8)),
+                ("labels", ctypes.POINTER(ctypes.c_int32))]
+
+
+class _Result(ctypes.Structure):
+    _fields_ = [("size", ctypes.c_int32), ("status", ctypes.c_int32),
+                ("npairs", ctypes.c_int32), ("_pad", ctypes.c_int32),
+                ("g_idx", ctypes.POINTER(ctypes.c_int16)),
+                ("h_idx", ctypes.POINTER(ctypes.c_int16)),
+                ("nodes", ctypes.c_uint64), ("seconds", ctypes.c_double)]
+
+
+EXPORTED_SYMBOLS = ["mcs_create", "mcs_destroy", "mcs_solve", "mcs_solve_batch",
+                    "mcs_solve_batch_device", "mcs_submit", "mcs_poll", "mcs_set_launch",
+                    "mcs_set_max_warps", "mcs_last_stats", "mcs_strerror"]
+
+_lib = None
+
+
+def load_library():
+    """Loads libmcs.so (building it if the sources are newer) and declares the
+    signatures.  Raises if the library cannot be built or loaded."""
+    global _lib
+    if _lib is not None:
+        return _lib
+    from . import build as _b
+    path = _b.build()
+    lib = ctypes.CDLL(path)
+    vp, i32, u32, dbl = ctypes.c_void_p, ctypes.c_int32, ctypes.c_uint32, ctypes.c_double
+    gp, rp = ctypes.POINTER(_Graph), ctypes.POINTER(_Result)
+    lib.mcs_create.argtypes = [ctypes.c_int, u32]
+    lib.mcs_create.restype = vp
+    lib.mcs_destroy.argtypes = [vp]
+    lib.mcs_destroy.restype = None
+    lib.mcs_solve.argtypes = [vp, gp, gp, u32, dbl, rp]
+    lib.mcs_solve.restype = ctypes.c_int
+    lib.mcs_solve_batch.argtypes = [vp, gp, gp, i32, u32, dbl, rp]
+    lib.mcs_solve_batch.restype = ctypes.c_int
+    lib.mcs_solve_batch_device.argtypes = [vp, i32, vp, vp, vp, vp, vp, u32, dbl,
+                                           vp, vp, vp, vp, vp, vp]
+    lib.mcs_solve_batch_device.restype = ctypes.c_int
+    lib.mcs_submit.argtypes = [vp, gp, gp, u32, dbl, ctypes.POINTER(ctypes.c_uint64)]
+    lib.mcs_submit.restype = ctypes.c_int
+    lib.mcs_poll.argtypes = [vp, ctypes.c_uint64, rp]
+    lib.mcs_poll.restype = ctypes.c_int
+    lib.mcs_set_launch.argtypes = [vp, ctypes.c_int, ctypes.c_int, ctypes.c_int]
+    lib.mcs_set_launch.restype = ctypes.c_int
+    lib.mcs_set_max_warps.argtypes = [vp, ctypes.c_int]
+    lib.mcs_set_max_warps.restype = ctypes.c_int
+    lib.mcs_last_stats.argtypes = [vp, ctypes.POINTER(ctypes.c_double), ctypes.c_int]
+    lib.mcs_last_stats.restype = ctypes.c_int
+    lib.mcs_strerror.argtypes = [ctypes.c_int]
+    lib.mcs_strerror.restype = ctypes.c_char_p
+    _lib = lib
+    return lib
+
+
+@dataclass
+class Result:
+    size: int
+    status: int
+    g_idx: np.ndarray
+    h_idx: np.ndarray
+    nodes: int
+    seconds: float
+
+
+class _Keep:
+    """Holds numpy buffers alive while ctypes structs point into them."""
+
+    def __init__(self):
+        self.items = []
+
+    def graph(self, adj, labels) -> _Graph:
+        a = np.ascontiguousarray(adj, dtype=np.uint8)
+        n = int(a.shape[0]) if a.ndim == 2 else 0
+        self.items.append(a)
+        g = _Graph()
+        g.n = n
+        g.adj = a.ctypes.data_as(ctypes.POINTER(ctypes.c_uint8))
+        if labels is not None:
+            lab = np.ascontiguousarray(labels, dtype=np.int32)
+            self.items.append(lab)
+            g.labels = lab.ctypes.data_as(ctypes.POINTER(ctypes.c_int32))
+        return g
+
+
+class Solver:
+    """One library context (one CUDA stream, grow-only device arenas)."""
+
+    def __init__(self, device: int = 0):
+        self.lib = load_library()
+        self.ctx = self.lib.mcs_create(int(device), 0)
+        if not self.ctx:
+            raise RuntimeError("mcs_create failed (no CUDA device?)")
+
+    def close(self):
+        if getattr(self, "ctx", None):
+            self.lib.mcs_destroy(self.ctx)
+            self.ctx = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *a):
+        self.close()
+
+    # -- configuration ----------------------------------------------------
+    def set_launch(self, warps_per_block=0, blocks_per_sm=0, smem_stack_entries=0):
+        rc = self.lib.mcs_set_launch(self.ctx, warps_per_block, blocks_per_sm, smem_stack_entries)
+        if rc:
+            raise ValueError(self.strerror(rc))
+
+    def set_max_warps(self, warps: int):
+        rc = self.lib.mcs_set_max_warps(self.ctx, int(warps))
+        if rc:
+            raise ValueError(self.strerror(rc))
+
+    def last_stats(self) -> dict:
+        buf = (ctypes.c_double * 8)()
+        self.lib.mcs_last_stats(self.ctx, buf, 8)
+        return dict(kernel_us=buf[0], nodes=buf[1], donated=buf[2], stolen=buf[3],
+                    spilled=buf[4], warps=buf[5], h2d_bytes=buf[6], d2h_bytes=buf[7])
+
+    def strerror(self, code: int) -> str:
+        return self.lib.mcs_strerror(int(code)).decode()
+
+    # -- solving ----------------------------------------------------------
+    def solve_batch(self, pairs: Sequence, flags: int = 0, timeout_s: float = 0.0,
+                    directed: Optional[bool] = None) -> List[Result]:
+        """pairs: sequence of (adjG, adjH, labG, labH) tuples or objects with
+        .G.adj/.G.labels/.H.adj/.H.labels (and optionally .directed)."""
+        keep = _Keep()
+        n = len(pairs)
+        Gs = (_Graph * max(n, 1))()
+        Hs = (_Graph * max(n, 1))()
+        Rs = (_Result * max(n, 1))()
+        caps = []
+        for i, p in enumerate(pairs):
+            if hasattr(p, "G"):
+                aG, aH, lG, lH = p.G.adj, p.H.adj, p.G.labels, p.H.labels
+                if directed is None and getattr(p, "directed", False):
+                    flags |= MCS_DIRECTED
+            else:
+                aG, aH, lG, lH = p
+            Gs[i] = keep.graph(aG, lG)
+            Hs[i] = keep.graph(aH, lH)
+            cap = max(1, min(Gs[i].n, Hs[i].n))
+            gi = np.zeros(cap, np.int16)
+            hi = np.zeros(cap, np.int16)
+            caps.append((gi, hi))
+            Rs[i].g_idx = gi.ctypes.data_as(ctypes.POINTER(ctypes.c_int16))
+            Rs[i].h_idx = hi.ctypes.data_as(ctypes.POINTER(ctypes.c_int16))
+        if directed:
+            flags |= MCS_DIRECTED
+        rc = self.lib.mcs_solve_batch(self.ctx, Gs, Hs, n, flags, float(timeout_s), Rs)
+        if rc < 0 and rc not in (MCS_ERR_ARG,):
+            raise RuntimeError(f"mcs_solve_batch: {self.strerror(rc)} ({rc})")
+        out = []
+        for i in range(n):
+            r = Rs[i]
+            k = r.npairs
+            gi, hi = caps[i]
+            out.append(Result(int(r.size), int(r.status), gi[:k].astype(np.int32),
+                              hi[:k].astype(np.int32), int(r.nodes), float(r.seconds)))
+        return out
+
+    def solve(self, adjG, adjH, labG=None, labH=None, directed: bool = False,
+              flags: int = 0, timeout_s: float = 0.0) -> Result:
+        return self.solve_batch([(adjG, adjH, labG, labH)],
+                                flags | (MCS_DIRECTED if directed else 0), timeout_s)[0]
+
+    def solve_batch_device(self, npairs: int, d_n, d_adj_off, d_adj, d_lab_off, d_labels,
+                           d_size, d_status, d_nodes, d_map=None, d_usec=None, flags: int = 0,
+                           timeout_s: float = 0.0, stream: int = 0) -> int:
+        """Device-resident batch: every argument is a torch CUDA tensor (or None)
+        in the layout documented for mcs_solve_batch_device; nothing is copied
+        and nothing is synchronised.  Returns the enqueue status."""
+        def ptr(t):
+            return None if t is None else ctypes.c_void_p(int(t.data_ptr()))
+        return int(self.lib.mcs_solve_batch_device(
+            self.ctx, int(npairs), ptr(d_n), ptr(d_adj_off), ptr(d_adj), ptr(d_lab_off),
+            ptr(d_labels), int(flags), float(timeout_s), ptr(d_size), ptr(d_status),
+            ptr(d_nodes), ptr(d_map), ptr(d_usec),
+            ctypes.c_void_p(int(stream)) if stream else None))
+
+
+def pack_host(pairs) -> dict:
+    """Lays a list of pairs out in the flat format of mcs_solve_batch_device
+    (numpy arrays; the caller moves them to the device).  Argument marshalling
+    only: no graph arithmetic happens here."""
+    n, adj_off, lab_off, blobs, labs = [], [], [], [], []
+    ao = lo = 0
+    for p in pairs:
+        for g in (p.G, p.H):
+            a = np.ascontiguousarray(g.adj, dtype=np.uint8).reshape(-1)
+            n.append(int(g.adj.shape[0]))
+            adj_off.append(ao)
+            blobs.append(a)
+            ao += a.size
+            if g.labels is not None:
+                lab_off.append(lo)
+                labs.append(np.ascontiguousarray(g.labels, dtype=np.int32))
+                lo += len(g.labels)
+            else:
+                lab_off.append(-1)
+    return dict(
+        n=np.asarray(n, np.int32), adj_off=np.asarray(adj_off, np.int64),
+        adj=np.concatenate(blobs) if blobs else np.zeros(16, np.uint8),
+        lab_off=np.asarray(lab_off, np.int64),
+        labels=np.concatenate(labs) if labs else None)

@@ -1,0 +1,54 @@
+"""Builds the CUDA library ``libmcs.so`` in-tree for sm_103a (B300).
+
+    python -m paper_1908_06418_b300.build
+"""
+import os
+import subprocess
+import sys
+
+HERE = os.path.dirname(os.path.abspath(__file__))
+CSRC = os.path.join(HERE, "csrc")
+LIB = os.path.join(HERE, "libmcs.so")
+SOURCES = ["mcs_kernels.cu", "mcs_api.cu"]
+HEADERS = ["mcs_internal.cuh", os.path.join("..", "..", "include", "mcs.h")]
+ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
+
+
+def nvcc():
+    for c in (os.environ.get("NVCC"), "/usr/local/cuda/bin/nvcc", "nvcc"):
+        if c and (os.path.isabs(c) and os.path.exists(c) or not os.path.isabs(c)):
+            return c
+    return "nvcc"
+
+
+def _stale() -> bool:
+    if not os.path.exists(LIB):
+        return True
+    t = os.path.getmtime(LIB)
+    deps = [os.path.join(CSRC, s) for s in SOURCES + HEADERS] + [os.path.abspath(__file__)]
+    return any(os.path.getmtime(d) > t for d in deps if os.path.exists(d))
+
+
+def build(force: bool = False, verbose: bool = False, extra=None) -> str:
+    if not force and not _stale():
+        return LIB
+    objs = []
+    flags = ["-O3", "-std=c++17", "-lineinfo", "-Xcompiler", "-fPIC", *ARCH,
+             "--expt-relaxed-constexpr"]
+    if verbose:
+        flags += ["-Xptxas", "-v"]
+    flags += list(extra or [])
+    build_dir = os.path.join(HERE, "_build")
+    os.makedirs(build_dir, exist_ok=True)
+    for s in SOURCES:
+        o = os.path.join(build_dir, s.replace(".cu", ".o"))
+        subprocess.check_call([nvcc(), "-c", os.path.join(CSRC, s), "-o", o, *flags])
+        objs.append(o)
+    tmp = LIB + ".tmp"
+    subprocess.check_call([nvcc(), "-shared", *ARCH, *objs, "-o", tmp, "-lcudart"])
+    os.replace(tmp, LIB)
+    return LIB
+
+
+if __name__ == "__main__":
+    print(build(force=True, verbose="-v" in sys.argv))

@@ -1,0 +1,477 @@
+// Host side of the C ABI declared in include/mcs.h.
+//
+// A context owns one CUDA stream, grow-only device arenas (packed graphs,
+// per-pair state, incumbent mapping slots, the task ring, per-warp stack
+// overflow) and pinned staging buffers.  A synchronous batch solve is:
+//   one pinned H2D copy of the packed inputs -> pack_kernel -> search_kernel
+//   -> one D2H copy of the results.
+#include <algorithm>
+#include <chrono>
+#include <cmath>
+#include <cstdio>
+#include <cstdlib>
+#include <cstring>
+#include <new>
+#include <numeric>
+#include <vector>
+
+#include "mcs_internal.cuh"
+#include "../../include/mcs.h"
+
+using namespace mcsk;
+
+struct mcs_ctx {
+    int device = 0;
+    cudaStream_t stream = nullptr;
+    int sms = 0;
+    int warps_per_block = 4;
+    int blocks_per_sm = 0;        // 0: as many as fit
+    int smem_stack = 256;
+    int max_warps = 0;            // 0: every launched warp
+    // device arenas
+    int pairs_cap = 0;
+    PairGraph* graphs = nullptr;
+    PairState* state = nullptr;
+    uint16_t* best = nullptr;
+    int32_t* order = nullptr;
+    Control* ctl = nullptr;
+    Task* queue = nullptr;
+    u64* qseq = nullptr;
+    uint32_t qcap = 0;
+    ulonglong2* gstack = nullptr;
+    size_t gstack_entries = 0;
+    // host-API staging
+    uint8_t* d_in = nullptr;  size_t d_in_cap = 0;
+    uint8_t* h_in = nullptr;  size_t h_in_cap = 0;
+    uint8_t* d_out = nullptr; size_t d_out_cap = 0;
+    uint8_t* h_out = nullptr; size_t h_out_cap = 0;
+    cudaEvent_t ev0 = nullptr, ev1 = nullptr;
+    double stats[8] = {0, 0, 0, 0, 0, 0, 0, 0};
+    bool ev_pending = false;       // ev0/ev1 recorded by a device call, not yet read
+    Control h_ctl;
+};
+
+namespace {
+
+int cuda_fail(cudaError_t e) {
+    if (e == cudaErrorMemoryAllocation) return MCS_ERR_NOMEM;
+    return MCS_ERR_CUDA;
+}
+#define CK(x) do { cudaError_t _e = (x); if (_e != cudaSuccess) return cuda_fail(_e); } while (0)
+
+size_t align16(size_t x) { return (x + 15) & ~(size_t)15; }
+
+template <typename T>
+int grow_dev(T*& p, size_t& cap, size_t need) {
+    if (need <= cap && p) return 0;
+    size_t n = std::max(need, cap * 3 / 2);
+    if (p) cudaFree(p);
+    p = nullptr;
+    cap = 0;
+    if (cudaMalloc((void**)&p, n) != cudaSuccess) { p = nullptr; return MCS_ERR_NOMEM; }
+    cap = n;
+    return 0;
+}
+template <typename T>
+int grow_host(T*& p, size_t& cap, size_t need) {
+    if (need <= cap && p) return 0;
+    if (p) cudaFreeHost(p);
+    p = nullptr;
+    cap = 0;
+    if (cudaMallocHost((void**)&p, need) != cudaSuccess) { p = nullptr; return MCS_ERR_NOMEM; }
+    cap = need;
+    return 0;
+}
+
+int launch_shape(mcs_ctx* c, bool directed, int* blocks, int* warps_total, int* wsmem) {
+    *wsmem = warp_smem_bytes(c->smem_stack);
+    int smem_block = c->warps_per_block * *wsmem;
+    int per_sm = search_max_blocks_per_sm(c->warps_per_block, smem_block, directed);
+    if (per_sm <= 0) return MCS_ERR_UNSUPPORTED;
+    if (c->blocks_per_sm > 0) per_sm = std::min(per_sm, c->blocks_per_sm);
+    *blocks = c->sms * per_sm;
+    *warps_total = *blocks * c->warps_per_block;
+    if (c->max_warps > 0) {
+        int need_blocks = (c->max_warps + c->warps_per_block - 1) / c->warps_per_block;
+        *blocks = std::min(*blocks, need_blocks);
+        *warps_total = std::min(*warps_total, c->max_warps);
+    }
+    return 0;
+}
+
+int ensure_pairs(mcs_ctx* c, int npairs) {
+    if (npairs <= c->pairs_cap) return 0;
+    int n = std::max(npairs, c->pairs_cap * 3 / 2);
+    cudaFree(c->graphs); cudaFree(c->state); cudaFree(c->best); cudaFree(c->order);
+    c->graphs = nullptr; c->state = nullptr; c->best = nullptr; c->order = nullptr;
+    c->pairs_cap = 0;
+    CK(cudaMalloc((void**)&c->graphs, sizeof(PairGraph) * (size_t)n));
+    CK(cudaMalloc((void**)&c->state, sizeof(PairState) * (size_t)n));
+    CK(cudaMalloc((void**)&c->best, sizeof(uint16_t) * (size_t)n * kLevels * kMaxN));
+    CK(cudaMalloc((void**)&c->order, sizeof(int32_t) * (size_t)n));
+    c->pairs_cap = n;
+    return 0;
+}
+
+int ensure_warps(mcs_ctx* c, int warps) {
+    uint32_t q = 1024;
+    while (q < (uint32_t)(4 * warps)) q <<= 1;
+    if (q > c->qcap) {
+        cudaFree(c->queue); cudaFree(c->qseq);
+        c->queue = nullptr; c->qseq = nullptr; c->qcap = 0;
+        CK(cudaMalloc((void**)&c->queue, sizeof(Task) * (size_t)q));
+        CK(cudaMalloc((void**)&c->qseq, sizeof(u64) * (size_t)q));
+        c->qcap = q;
+    }
+    size_t per = kStackMax > c->smem_stack ? (size_t)(kStackMax - c->smem_stack) : 0;
+    size_t need = per * (size_t)warps;
+    if (need > c->gstack_entries || !c->gstack) {
+        cudaFree(c->gstack);
+        c->gstack = nullptr;
+        c->gstack_entries = 0;
+        CK(cudaMalloc((void**)&c->gstack, sizeof(ulonglong2) * std::max<size_t>(need, 1)));
+        c->gstack_entries = std::max<size_t>(need, 1);
+    }
+    if (!c->ctl) CK(cudaMalloc((void**)&c->ctl, sizeof(Control)));
+    return 0;
+}
+
+// Enqueues pack + search for a device-resident batch.
+int run_device(mcs_ctx* c, int npairs, const int32_t* d_n, const int64_t* d_adj_off,
+               const uint8_t* d_adj, const int64_t* d_lab_off, const int32_t* d_labels,
+               const int32_t* d_order, uint32_t flags, double timeout_s, int32_t* d_size,
+               int32_t* d_status, uint64_t* d_nodes, int16_t* d_map, float* d_usec,
+               cudaStream_t s, bool timed) {
+    if (npairs < 0) return MCS_ERR_ARG;
+    if (npairs == 0) return 0;
+    const bool directed = (flags & MCS_DIRECTED) != 0;
+    if (flags & MCS_ORDER_LEARNED) return MCS_ERR_UNSUPPORTED;
+    int blocks = 0, warps = 0, wsmem = 0;
+    int rc = launch_shape(c, directed, &blocks, &warps, &wsmem);
+    if (rc) return rc;
+    if ((rc = ensure_pairs(c, npairs))) return rc;
+    if ((rc = ensure_warps(c, blocks * c->warps_per_block))) return rc;
+
+    PackParams pp;
+    memset(&pp, 0, sizeof(pp));
+    pp.npairs = npairs;
+    pp.flags = flags;
+    pp.n = d_n;
+    pp.adj_off = d_adj_off;
+    pp.adj = d_adj;
+    pp.lab_off = d_lab_off;
+    pp.labels = d_labels;
+    pp.vscore = nullptr;
+    pp.graphs = c->graphs;
+    pp.state = c->state;
+    pp.out_size = d_size;
+    pp.out_status = d_status;
+    pp.out_nodes = reinterpret_cast<u64*>(d_nodes);
+    pp.out_map = (flags & MCS_NO_MAPPING) ? nullptr : d_map;
+    pp.out_usec = d_usec;
+    pp.ctl = c->ctl;
+    pp.qseq = c->qseq;
+    pp.qcap = c->qcap;
+    CK(launch_pack(pp, s));
+
+    double tmo = timeout_s > 0 ? std::min(timeout_s, 3600.0) : 3600.0;
+    SearchParams sp;
+    memset(&sp, 0, sizeof(sp));
+    sp.npairs = npairs;
+    sp.flags = flags;
+    sp.timeout_ns = (u64)(tmo * 1e9);
+    sp.stall_ns = sp.timeout_ns + 2000000000ull;
+    sp.graphs = c->graphs;
+    sp.state = c->state;
+    sp.best = c->best;
+    sp.order = d_order;
+    sp.ctl = c->ctl;
+    sp.queue = c->queue;
+    sp.qseq = c->qseq;
+    sp.qcap = c->qcap;
+    sp.stack_smem = c->smem_stack;
+    sp.warp_smem_bytes = wsmem;
+    sp.max_warps = warps;
+    sp.gstack = c->gstack;
+    sp.rank = nullptr;
+    sp.out_size = d_size;
+    sp.out_status = d_status;
+    sp.out_nodes = reinterpret_cast<u64*>(d_nodes);
+    sp.out_map = (flags & MCS_NO_MAPPING) ? nullptr : d_map;
+    sp.out_usec = d_usec;
+    if (timed) CK(cudaEventRecord(c->ev0, s));
+    CK(launch_search(sp, blocks, c->warps_per_block, directed, s));
+    if (timed) CK(cudaEventRecord(c->ev1, s));
+    c->stats[5] = warps;
+    return 0;
+}
+
+struct HostLayout {
+    size_t off_n, off_adjoff, off_laboff, off_order, off_labels, off_adj, total;
+};
+
+int check_graph(const mcs_graph* g) {
+    if (!g) return MCS_ERR_ARG;
+    if (g->n < 0 || g->n > MCS_MAX_N) return MCS_ERR_ARG;
+    if (g->n > 0 && !g->adj) return MCS_ERR_ARG;
+    return 0;
+}
+
+int worst(int a, int b) {
+    if (a < 0 || b < 0) return std::min(a, b);
+    return std::max(a, b);
+}
+
+}  // namespace
+
+extern "C" {
+
+mcs_ctx* mcs_create(int device, uint32_t flags) {
+    (void)flags;
+    int ndev = 0;
+    if (cudaGetDeviceCount(&ndev) != cudaSuccess || device < 0 || device >= ndev) return nullptr;
+    if (cudaSetDevice(device) != cudaSuccess) return nullptr;
+    mcs_ctx* c = new (std::nothrow) mcs_ctx();
+    if (!c) return nullptr;
+    c->device = device;
+    cudaDeviceProp prop;
+    if (cudaGetDeviceProperties(&prop, device) != cudaSuccess) { delete c; return nullptr; }
+    c->sms = prop.multiProcessorCount;
+    if (cudaStreamCreateWithFlags(&c->stream, cudaStreamNonBlocking) != cudaSuccess ||
+        cudaEventCreate(&c->ev0) != cudaSuccess || cudaEventCreate(&c->ev1) != cudaSuccess) {
+        mcs_destroy(c);
+        return nullptr;
+    }
+    return c;
+}
+
+void mcs_destroy(mcs_ctx* c) {
+    if (!c) return;
+    cudaSetDevice(c->device);
+    if (c->stream) cudaStreamSynchronize(c->stream);
+    cudaFree(c->graphs); cudaFree(c->state); cudaFree(c->best); cudaFree(c->order);
+    cudaFree(c->ctl); cudaFree(c->queue); cudaFree(c->qseq); cudaFree(c->gstack);
+    cudaFree(c->d_in); cudaFree(c->d_out);
+    if (c->h_in) cudaFreeHost(c->h_in);
+    if (c->h_out) cudaFreeHost(c->h_out);
+    if (c->ev0) cudaEventDestroy(c->ev0);
+    if (c->ev1) cudaEventDestroy(c->ev1);
+    if (c->stream) cudaStreamDestroy(c->stream);
+    delete c;
+}
+
+int mcs_set_launch(mcs_ctx* c, int warps_per_block, int blocks_per_sm, int smem_stack_entries) {
+    if (!c) return MCS_ERR_ARG;
+    if (warps_per_block < 0 || warps_per_block > 8 || blocks_per_sm < 0 || smem_stack_entries < 0 ||
+        smem_stack_entries > kStackMax)
+        return MCS_ERR_ARG;
+    if (warps_per_block) c->warps_per_block = warps_per_block;
+    if (blocks_per_sm) c->blocks_per_sm = blocks_per_sm;
+    if (smem_stack_entries) c->smem_stack = smem_stack_entries;
+    return 0;
+}
+
+int mcs_set_max_warps(mcs_ctx* c, int warps) {
+    if (!c || warps < 0) return MCS_ERR_ARG;
+    c->max_warps = warps;
+    return 0;
+}
+
+int mcs_last_stats(mcs_ctx* c, double* out, int n) {
+    if (!c || !out || n < 0) return MCS_ERR_ARG;
+    if (c->ev_pending && cudaEventQuery(c->ev1) == cudaSuccess) {
+        float ms = 0.f;
+        if (cudaEventElapsedTime(&ms, c->ev0, c->ev1) == cudaSuccess) c->stats[0] = ms * 1e3;
+        c->ev_pending = false;
+    }
+    int k = std::min(n, 8);
+    for (int i = 0; i < k; ++i) out[i] = c->stats[i];
+    return k;
+}
+
+int mcs_solve_batch_device(mcs_ctx* c, int32_t npairs, const int32_t* d_n,
+                           const int64_t* d_adj_off, const uint8_t* d_adj,
+                           const int64_t* d_lab_off, const int32_t* d_labels, uint32_t flags,
+                           double timeout_s, int32_t* d_size, int32_t* d_status,
+                           uint64_t* d_nodes, int16_t* d_map, float* d_usec, void* stream) {
+    if (!c || npairs < 0) return MCS_ERR_ARG;
+    if (npairs > 0 && (!d_n || !d_adj_off || !d_adj || !d_size || !d_status || !d_nodes))
+        return MCS_ERR_ARG;
+    if (cudaSetDevice(c->device) != cudaSuccess) return MCS_ERR_CUDA;
+    cudaStream_t s = stream ? (cudaStream_t)stream : c->stream;
+    int rc = run_device(c, npairs, d_n, d_adj_off, d_adj, d_lab_off, d_labels, nullptr, flags,
+                        timeout_s, d_size, d_status, d_nodes, d_map, d_usec, s, true);
+    c->ev_pending = (rc == 0 && npairs > 0);
+    c->stats[6] = c->stats[7] = 0;
+    return rc;
+}
+
+int mcs_solve_batch(mcs_ctx* c, const mcs_graph* G, const mcs_graph* H, int32_t npairs,
+                    uint32_t flags, double timeout_s, mcs_result* out) {
+    if (!c || npairs < 0 || (npairs > 0 && (!G || !H || !out))) return MCS_ERR_ARG;
+    if (cudaSetDevice(c->device) != cudaSuccess) return MCS_ERR_CUDA;
+    // structural checks (content is validated on the device by the pack kernel)
+    std::vector<char> bad(npairs, 0);
+    size_t adj_bytes = 0, lab_count = 0;
+    for (int p = 0; p < npairs; ++p) {
+        if (check_graph(&G[p]) || check_graph(&H[p])) { bad[p] = 1; continue; }
+        adj_bytes += (size_t)G[p].n * G[p].n + (size_t)H[p].n * H[p].n;
+        if (G[p].labels) lab_count += G[p].n;
+        if (H[p].labels) lab_count += H[p].n;
+    }
+    HostLayout L;
+    size_t P2 = 2 * (size_t)npairs;
+    L.off_n = 0;
+    L.off_adjoff = align16(L.off_n + 4 * P2);
+    L.off_laboff = align16(L.off_adjoff + 8 * P2);
+    L.off_order = align16(L.off_laboff + 8 * P2);
+    L.off_labels = align16(L.off_order + 4 * (size_t)npairs);
+    L.off_adj = align16(L.off_labels + 4 * std::max<size_t>(lab_count, 1));
+    L.total = align16(L.off_adj + std::max<size_t>(adj_bytes, 16));
+    int rc;
+    if ((rc = grow_host(c->h_in, c->h_in_cap, L.total))) return rc;
+    if ((rc = grow_dev(c->d_in, c->d_in_cap, L.total))) return rc;
+    int32_t* hn = (int32_t*)(c->h_in + L.off_n);
+    int64_t* hao = (int64_t*)(c->h_in + L.off_adjoff);
+    int64_t* hlo = (int64_t*)(c->h_in + L.off_laboff);
+    int32_t* hord = (int32_t*)(c->h_in + L.off_order);
+    int32_t* hlab = (int32_t*)(c->h_in + L.off_labels);
+    uint8_t* hadj = c->h_in + L.off_adj;
+    size_t ao = 0, lo = 0;
+    for (int p = 0; p < npairs; ++p) {
+        const mcs_graph* gs[2] = {&G[p], &H[p]};
+        for (int s = 0; s < 2; ++s) {
+            size_t gi = 2 * (size_t)p + s;
+            if (bad[p]) { hn[gi] = -1; hao[gi] = 0; hlo[gi] = -1; continue; }
+            const mcs_graph* g = gs[s];
+            hn[gi] = g->n;
+            hao[gi] = (int64_t)ao;
+            if (g->n) memcpy(hadj + ao, g->adj, (size_t)g->n * g->n);
+            ao += (size_t)g->n * g->n;
+            if (g->labels) {
+                hlo[gi] = (int64_t)lo;
+                memcpy(hlab + lo, g->labels, sizeof(int32_t) * g->n);
+                lo += g->n;
+            } else {
+                hlo[gi] = -1;
+            }
+        }
+    }
+    // longest-processing-time-first: larger and denser pairs start first
+    {
+        std::vector<double> cost(npairs, 0.0);
+        for (int p = 0; p < npairs; ++p) {
+            if (bad[p]) continue;
+            double nG = G[p].n, nH = H[p].n;
+            cost[p] = std::min(nG, nH) * 1000.0 + std::max(nG, nH);
+        }
+        std::vector<int32_t> ord(npairs);
+        std::iota(ord.begin(), ord.end(), 0);
+        std::stable_sort(ord.begin(), ord.end(), [&](int a, int b) { return cost[a] > cost[b]; });
+        memcpy(hord, ord.data(), sizeof(int32_t) * npairs);
+    }
+    // outputs
+    size_t o_size = 0, o_status = align16(4 * (size_t)npairs), o_nodes = align16(o_status + 4 * (size_t)npairs);
+    size_t o_usec = align16(o_nodes + 8 * (size_t)npairs), o_map = align16(o_usec + 4 * (size_t)npairs);
+    size_t o_total = align16(o_map + 2 * (size_t)npairs * kMaxN);
+    if ((rc = grow_host(c->h_out, c->h_out_cap, o_total))) return rc;
+    if ((rc = grow_dev(c->d_out, c->d_out_cap, o_total))) return rc;
+    cudaStream_t s = c->stream;
+    if (npairs > 0) {
+        CK(cudaMemcpyAsync(c->d_in, c->h_in, L.total, cudaMemcpyHostToDevice, s));
+        rc = run_device(c, npairs, (const int32_t*)(c->d_in + L.off_n),
+                        (const int64_t*)(c->d_in + L.off_adjoff), c->d_in + L.off_adj,
+                        (const int64_t*)(c->d_in + L.off_laboff),
+                        lab_count ? (const int32_t*)(c->d_in + L.off_labels) : nullptr,
+                        (const int32_t*)(c->d_in + L.off_order), flags, timeout_s,
+                        (int32_t*)(c->d_out + o_size), (int32_t*)(c->d_out + o_status),
+                        (uint64_t*)(c->d_out + o_nodes),
+                        (flags & MCS_NO_MAPPING) ? nullptr : (int16_t*)(c->d_out + o_map),
+                        (float*)(c->d_out + o_usec), s, true);
+        if (rc) return rc;
+        size_t copy_bytes = (flags & MCS_NO_MAPPING) ? o_map : o_total;
+        CK(cudaMemcpyAsync(c->h_out, c->d_out, copy_bytes, cudaMemcpyDeviceToHost, s));
+        CK(cudaMemcpyAsync(&c->h_ctl, c->ctl, sizeof(Control), cudaMemcpyDeviceToHost, s));
+        CK(cudaStreamSynchronize(s));
+        float ms = 0.f;
+        cudaEventElapsedTime(&ms, c->ev0, c->ev1);
+        c->stats[0] = ms * 1e3;
+        c->stats[2] = (double)c->h_ctl.donated;
+        c->stats[3] = (double)c->h_ctl.stolen;
+        c->stats[4] = (double)c->h_ctl.spilled;
+        c->stats[6] = (double)L.total;
+        c->stats[7] = (double)(copy_bytes + sizeof(Control));
+        c->ev_pending = false;
+    }
+    int32_t* rsize = (int32_t*)(c->h_out + o_size);
+    int32_t* rstat = (int32_t*)(c->h_out + o_status);
+    uint64_t* rnodes = (uint64_t*)(c->h_out + o_nodes);
+    float* rusec = (float*)(c->h_out + o_usec);
+    int16_t* rmap = (int16_t*)(c->h_out + o_map);
+    int ret = MCS_OK;
+    double tot_nodes = 0;
+    for (int p = 0; p < npairs; ++p) {
+        mcs_result& r = out[p];
+        if (bad[p]) {
+            r.size = 0; r.status = MCS_ERR_ARG; r.npairs = 0; r.nodes = 0; r.seconds = 0;
+            ret = worst(ret, MCS_ERR_ARG);
+            continue;
+        }
+        r.size = rsize[p];
+        r.status = rstat[p];
+        r.nodes = rnodes[p];
+        r.seconds = rusec[p] * 1e-6;
+        tot_nodes += (double)r.nodes;
+        r.npairs = 0;
+        if (!(flags & MCS_NO_MAPPING) && r.status >= 0) {
+            int k = 0;
+            for (int x = 0; x < G[p].n; ++x) {
+                int16_t y = rmap[(size_t)p * kMaxN + x];
+                if (y >= 0) {
+                    if (r.g_idx) r.g_idx[k] = (int16_t)x;
+                    if (r.h_idx) r.h_idx[k] = y;
+                    ++k;
+                }
+            }
+            r.npairs = k;
+        }
+        ret = worst(ret, r.status);
+    }
+    c->stats[1] = tot_nodes;
+    if (npairs > 0 && c->h_ctl.error) ret = worst(ret, c->h_ctl.error);
+    return ret;
+}
+
+int mcs_solve(mcs_ctx* c, const mcs_graph* G, const mcs_graph* H, uint32_t flags,
+              double timeout_s, mcs_result* out) {
+    if (!c || !G || !H || !out) return MCS_ERR_ARG;
+    int rc = mcs_solve_batch(c, G, H, 1, flags, timeout_s, out);
+    return rc < 0 ? rc : out->status;
+}
+
+int mcs_submit(mcs_ctx* c, const mcs_graph* G, const mcs_graph* H, uint32_t flags,
+               double timeout_s, uint64_t* ticket) {
+    (void)c; (void)G; (void)H; (void)flags; (void)timeout_s; (void)ticket;
+    return MCS_ERR_UNSUPPORTED;
+}
+
+int mcs_poll(mcs_ctx* c, uint64_t ticket, mcs_result* out) {
+    (void)c; (void)ticket; (void)out;
+    return MCS_ERR_UNSUPPORTED;
+}
+
+const char* mcs_strerror(int code) {
+    switch (code) {
+        case MCS_OK: return "ok: optimum found and proven";
+        case MCS_TIMEOUT: return "timeout: size is a lower bound";
+        case MCS_PENDING: return "pending";
+        case MCS_ERR_ARG: return "invalid argument";
+        case MCS_ERR_NOMEM: return "out of memory";
+        case MCS_ERR_CUDA: return "CUDA error";
+        case MCS_ERR_DEVICE_STALL: return "bounded device wait expired";
+        case MCS_ERR_UNSUPPORTED: return "unsupported";
+        default: return "unknown status";
+    }
+}
+
+}  // extern "C"

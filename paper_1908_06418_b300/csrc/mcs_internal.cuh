@@ -1,0 +1,143 @@
+// Internal device-side layout of the B300 McSplit library (not installed;
+// the public interface is include/mcs.h).
+#pragma once
+#include <cstdint>
+#include <cuda_runtime.h>
+
+namespace mcsk {
+
+constexpr int kMaxN = 64;
+constexpr int kLevels = kMaxN + 1;
+// Classes on one warp's DFS stack: level d holds at most (64 - d) classes
+// (they are disjoint and each keeps one unmatched G vertex), so the whole
+// stack holds at most 64 + 63 + ... + 1 = 2080 entries.
+constexpr int kStackMax = 2080 + 32;
+
+typedef unsigned long long u64;
+
+// Per-pair packed graph data, produced by the pack kernel (renumbered by the
+// chosen vertex order; bit x of row v is vertex x in the new numbering).
+struct PairGraph {
+    u64 gout[kMaxN];       // bit x: arc v -> x in G
+    u64 gin[kMaxN];        // bit x: arc x -> v in G (== gout when undirected)
+    u64 hout[kMaxN];
+    u64 hin[kMaxN];
+    ulonglong2 root[kMaxN];  // initial label classes (L mask, R mask)
+    uint8_t permG[kMaxN];  // new number -> original number
+    uint8_t permH[kMaxN];
+    int32_t nG, nH, C0, valid;
+    int32_t pad[4];
+};
+
+// Per-pair search state.
+struct PairState {
+    int32_t inc;           // incumbent size (atomicMax)
+    int32_t open;          // tasks of this pair that exist (queued or running)
+    int32_t status;        // MCS_PENDING until finalised, or MCS_ERR_ARG
+    int32_t abort;         // 1 once the pair timed out
+    u64 nodes;
+    u64 t_start, deadline; // globaltimer ns
+    u64 pad;
+};
+
+// A unit of work: one level of a pair's search tree (a node, its classes,
+// the chosen left vertex v and the candidate set still to try).
+constexpr int kTaskFresh = 1;      // node entry (bound + selection) still to do
+constexpr int kTaskPending = 2;    // the "v stays unmatched" branch still to do
+struct TaskHdr {
+    int32_t pair, depth, C, v;
+    u64 rrem;
+    int32_t flags, bound;
+    int32_t pad[2];
+};
+struct Task {
+    TaskHdr h;                     // 40 -> padded to 48 below
+    int32_t pad2[2];
+    uint8_t Mg[kMaxN], Mh[kMaxN];  // the mapping prefix M (new numbering)
+    ulonglong2 cls[kMaxN];
+};
+static_assert(sizeof(Task) % 16 == 0, "task slots must stay 16-byte aligned");
+
+// Fields that different warps poll or update sit on separate 128-byte lines.
+struct alignas(128) Control {
+    u64 q_head, q_tail;            // task ring counters (idle warps poll these)
+    u64 pad0[14];
+    int32_t hungry;                // warps waiting for work (busy warps poll this)
+    int32_t pad1[31];
+    int32_t next_pair;             // cursor into the pair order
+    int32_t remaining;             // pairs not finalised
+    int32_t error;                 // MCS_ERR_DEVICE_STALL if a bounded wait expired
+    int32_t pad2;
+    u64 last_progress;             // globaltimer ns of the last pair start/finish/task move
+    u64 pad3[13];
+    u64 donated, stolen, spilled;  // statistics
+    u64 pad4[13];
+};
+static_assert(sizeof(Control) == 512, "one 128-byte line per group of fields");
+
+struct SearchParams {
+    int32_t npairs;
+    uint32_t flags;
+    u64 timeout_ns;                // per pair
+    u64 stall_ns;                  // idle-wait limit without any progress
+    const PairGraph* graphs;
+    PairState* state;
+    uint16_t* best;                // [npairs][kLevels][kMaxN]: (g << 8) | h per size slot
+    const int32_t* order;          // pair processing order (may be null)
+    Control* ctl;
+    Task* queue;
+    u64* qseq;
+    uint32_t qcap;                 // power of two
+    int32_t stack_smem;            // class entries per warp kept in shared memory
+    int32_t warp_smem_bytes;
+    int32_t max_warps;             // warps allowed to work (others exit at once)
+    ulonglong2* gstack;            // per-warp overflow of the class stack
+    const uint8_t* rank;           // learned order: [npairs][kMaxN][kMaxN] rank of u for v, or null
+    // outputs
+    int32_t* out_size;
+    int32_t* out_status;
+    u64* out_nodes;
+    int16_t* out_map;
+    float* out_usec;
+};
+
+struct PackParams {
+    int32_t npairs;
+    uint32_t flags;
+    const int32_t* n;
+    const int64_t* adj_off;
+    const uint8_t* adj;
+    const int64_t* lab_off;
+    const int32_t* labels;
+    const float* vscore;           // optional per-vertex order key [npairs][2][kMaxN] (lower first)
+    PairGraph* graphs;
+    PairState* state;
+    int32_t* out_size;
+    int32_t* out_status;
+    u64* out_nodes;
+    int16_t* out_map;
+    float* out_usec;
+    Control* ctl;
+    u64* qseq;
+    uint32_t qcap;
+};
+
+// Per-warp shared memory layout (bytes from the warp's base).
+constexpr int kSmAdj = 0;                        // 4 * 64 * 8 = 2048
+constexpr int kSmRrem = 2048;                    // 65 * 8 -> 528
+constexpr int kSmInfo = kSmRrem + 528;           // 65 * 8 -> 528
+constexpr int kSmM = kSmInfo + 528;              // 64 + 64
+constexpr int kSmCls = kSmM + 128;               // 16-byte aligned
+static_assert(kSmCls % 16 == 0, "class cache must be 16-byte aligned");
+
+inline int warp_smem_bytes(int stack_entries) { return kSmCls + 16 * stack_entries; }
+
+}  // namespace mcsk
+
+// kernels.cu entry points used by the host library
+namespace mcsk {
+cudaError_t launch_pack(const PackParams& p, cudaStream_t s);
+cudaError_t launch_search(const SearchParams& p, int blocks, int warps_per_block,
+                          bool directed, cudaStream_t s);
+int search_max_blocks_per_sm(int warps_per_block, int smem_per_block, bool directed);
+}

@@ -1,0 +1,830 @@
+// Device kernels of the B300 McSplit library.
+//
+//   pack_kernel    validates each input graph, renumbers its vertices (by
+//                  descending degree, total in+out degree when directed,
+//                  Section IV-A; or by a caller-supplied key), packs the
+//                  adjacency into 64-bit row bitsets and builds the initial
+//                  label classes (one per label + self-loop value present in
+//                  both graphs).
+//   search_kernel  persistent McSplit branch and bound (Section II-B,
+//                  Algorithm 1, Eq. 1).  One warp runs one depth-first search;
+//                  the label classes of a node are spread over the lanes (one
+//                  or two per lane), so filterDomain (Table 1) is a warp-wide
+//                  AND/popcount, the bound of Eq. 1 is one warp add-reduction
+//                  and the class choice one warp min-reduction.  Work moves
+//                  between warps through a task ring in HBM; incumbents are
+//                  per-pair atomicMax counters.
+//
+// Every device-side wait is bounded (iteration count and globaltimer) and
+// reports MCS_ERR_DEVICE_STALL through Control::error instead of trapping.
+#include "mcs_internal.cuh"
+#include "../../include/mcs.h"
+
+namespace mcsk {
+
+#define FULL 0xffffffffu
+
+__device__ __forceinline__ u64 gtimer() {
+    u64 t;
+    asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
+    return t;
+}
+__device__ __forceinline__ unsigned lanemask_lt() {
+    unsigned m;
+    asm("mov.u32 %0, %%lanemask_lt;" : "=r"(m));
+    return m;
+}
+template <typename T>
+__device__ __forceinline__ T vload(const T* p) { return *(volatile const T*)p; }
+
+// Loads that bypass L1: task slots are written by other SMs.
+__device__ __forceinline__ ulonglong2 ld_cg(const ulonglong2* p) {
+    ulonglong2 r;
+    asm volatile("ld.global.cg.v2.u64 {%0, %1}, [%2];" : "=l"(r.x), "=l"(r.y) : "l"(p));
+    return r;
+}
+__device__ __forceinline__ uint8_t ld_cg(const uint8_t* p) {
+    unsigned short r;
+    asm volatile("ld.global.cg.u8 %0, [%1];" : "=h"(r) : "l"(p));
+    return (uint8_t)r;
+}
+
+__device__ __forceinline__ u64 shfl64(u64 x, int src) {
+    unsigned lo = (unsigned)x, hi = (unsigned)(x >> 32);
+    lo = __shfl_sync(FULL, lo, src);
+    hi = __shfl_sync(FULL, hi, src);
+    return ((u64)hi << 32) | lo;
+}
+
+// ---------------------------------------------------------------------------
+// pack kernel: one warp per pair
+// ---------------------------------------------------------------------------
+struct GraphIn {
+    int n;
+    const uint8_t* a;
+    const int32_t* lab;
+};
+
+// Lane l handles vertices l and l + 32.  Returns false (warp-uniform) if the
+// graph is malformed.
+__device__ bool pack_graph(const GraphIn& g, bool directed, const float* key,
+                           u64* out_rows, u64* in_rows, uint8_t* perm,
+                           long long* vkey /* per lane: 2 entries */, int lane) {
+    const int n = g.n;
+    bool ok = (n >= 0 && n <= kMaxN);
+    // content checks: entries 0/1, symmetric when undirected, labels >= 0
+    // (the loop trip count is warp-uniform so that every lane reaches the vote)
+    for (int b0 = 0; ok && b0 < n * n; b0 += 32) {
+        const int idx = b0 + lane;
+        bool bad = false;
+        if (idx < n * n) {
+            uint8_t x = g.a[idx];
+            bad = x > 1;
+            if (!directed) {
+                int i = idx / n, j = idx - i * n;
+                bad |= (x != g.a[j * n + i]);
+            }
+        }
+        if (__any_sync(FULL, bad)) ok = false;
+    }
+    if (g.lab) {
+        bool bad = false;
+        for (int i = lane; i < n; i += 32) bad |= g.lab[i] < 0;
+        if (__any_sync(FULL, bad)) ok = false;
+    }
+    if (!ok) return false;
+    // degree (total degree when directed), loops excluded
+    int deg[2];
+    float kv[2];
+    for (int s = 0; s < 2; ++s) {
+        int i = lane + 32 * s;
+        int d = 0;
+        if (i < n)
+            for (int j = 0; j < n; ++j) {
+                if (j == i) continue;
+                d += g.a[i * n + j];
+                if (directed) d += g.a[j * n + i];
+            }
+        deg[s] = d;
+        kv[s] = (key && i < n) ? key[i] : 0.f;
+    }
+    // rank: earlier if higher degree (or lower caller key), ties to lower index
+    int rank[2];
+    for (int s = 0; s < 2; ++s) {
+        int i = lane + 32 * s;
+        int r = 0;
+        for (int j = 0; j < n; ++j) {
+            int dj = __shfl_sync(FULL, deg[j >> 5], j & 31);
+            float kj = __shfl_sync(FULL, kv[j >> 5], j & 31);
+            bool before;
+            if (key) before = (kj < kv[s]) || (kj == kv[s] && j < i);
+            else before = (dj > deg[s]) || (dj == deg[s] && j < i);
+            r += before ? 1 : 0;
+        }
+        rank[s] = r;
+    }
+    for (int s = 0; s < 2; ++s) {
+        int i = lane + 32 * s;
+        if (i < n) perm[rank[s]] = (uint8_t)i;
+    }
+    // rows in the new numbering
+    for (int s = 0; s < 2; ++s) {
+        int i = lane + 32 * s;
+        u64 o = 0, in = 0;
+        for (int j = 0; j < n; ++j) {
+            int rj = __shfl_sync(FULL, rank[j >> 5], j & 31);
+            if (i < n && j != i) {
+                if (g.a[i * n + j]) o |= 1ull << rj;
+                if (g.a[j * n + i]) in |= 1ull << rj;
+            }
+        }
+        if (i < n) {
+            out_rows[rank[s]] = o;
+            in_rows[rank[s]] = directed ? in : o;
+            long long lab = g.lab ? (long long)g.lab[i] : 0;
+            vkey[s] = lab * 2 + (g.a[i * n + i] ? 1 : 0);   // label + self-loop
+        } else {
+            vkey[s] = -1;
+        }
+    }
+    return true;
+}
+
+__global__ void pack_kernel(PackParams P) {
+    __shared__ long long s_key[4][2][kMaxN];
+    const int lane = threadIdx.x & 31;
+    const int wib = threadIdx.x >> 5;
+    const int p = blockIdx.x * (blockDim.x >> 5) + wib;
+    // ring sequence numbers: slot i is free for ticket i
+    for (uint32_t i = blockIdx.x * blockDim.x + threadIdx.x; i < P.qcap; i += gridDim.x * blockDim.x)
+        P.qseq[i] = i;
+    if (blockIdx.x == 0 && threadIdx.x == 0) {
+        Control* c = P.ctl;
+        c->q_head = c->q_tail = 0;
+        c->hungry = 0;
+        c->next_pair = 0;
+        c->remaining = P.npairs;
+        c->error = 0;
+        c->last_progress = gtimer();
+        c->donated = c->stolen = c->spilled = 0;
+    }
+    if (p >= P.npairs) return;
+    const bool directed = (P.flags & MCS_DIRECTED) != 0;
+    PairGraph& pg = P.graphs[p];
+    bool ok = true;
+    long long vk[2][2];
+    for (int side = 0; side < 2 && ok; ++side) {
+        int gi = 2 * p + side;
+        GraphIn g;
+        g.n = P.n[gi];
+        if (g.n < 0 || g.n > kMaxN) { ok = false; break; }
+        g.a = P.adj + P.adj_off[gi];
+        g.lab = nullptr;
+        if (P.labels && P.lab_off && P.lab_off[gi] >= 0) g.lab = P.labels + P.lab_off[gi];
+        const float* key = P.vscore ? P.vscore + ((size_t)p * 2 + side) * kMaxN : nullptr;
+        u64* orows = side ? pg.hout : pg.gout;
+        u64* irows = side ? pg.hin : pg.gin;
+        uint8_t* perm = side ? pg.permH : pg.permG;
+        ok = pack_graph(g, directed, key, orows, irows, perm, vk[side], lane);
+    }
+    __syncwarp();
+    int nG = P.n[2 * p], nH = P.n[2 * p + 1];
+    if (ok) {
+        // label keys by new number
+        for (int side = 0; side < 2; ++side) {
+            const uint8_t* perm = side ? pg.permH : pg.permG;
+            int n = side ? nH : nG;
+            // vk[side][s] belongs to original vertex lane + 32 s; place it at its new number
+            __syncwarp();
+            for (int r = lane; r < kMaxN; r += 32) s_key[wib][side][r] = -1;
+            __syncwarp();
+            for (int r = 0; r < n; ++r) {
+                int orig = perm[r];
+                long long k = __shfl_sync(FULL, (unsigned long long)vk[side][orig >> 5], orig & 31);
+                if (lane == 0) s_key[wib][side][r] = k;
+            }
+            __syncwarp();
+        }
+        // one class per key present in both graphs; representative = lowest new G number
+        int C = 0;
+        for (int s = 0; s < 2; ++s) {
+            int r = lane + 32 * s;
+            long long k = r < nG ? s_key[wib][0][r] : -2;
+            u64 L = 0, R = 0;
+            bool rep = r < nG;
+            for (int j = 0; j < kMaxN; ++j) {
+                if (j < nG && s_key[wib][0][j] == k) { L |= 1ull << j; if (j < r) rep = false; }
+                if (j < nH && s_key[wib][1][j] == k) R |= 1ull << j;
+            }
+            bool keep = rep && R != 0;
+            unsigned m = __ballot_sync(FULL, keep);
+            int pos = C + __popc(m & lanemask_lt());
+            if (keep) pg.root[pos] = make_ulonglong2(L, R);
+            C += __popc(m);
+        }
+        if (lane == 0) {
+            pg.nG = nG; pg.nH = nH; pg.C0 = C; pg.valid = 1;
+        }
+    } else if (lane == 0) {
+        pg.nG = 0; pg.nH = 0; pg.C0 = 0; pg.valid = 0;
+    }
+    if (lane == 0) {
+        PairState& st = P.state[p];
+        st.inc = 0;
+        st.open = 1;
+        st.status = ok ? MCS_PENDING : MCS_ERR_ARG;
+        st.abort = 0;
+        st.nodes = 0;
+        st.t_start = st.deadline = 0;
+        if (P.out_size) P.out_size[p] = 0;
+        if (P.out_status) P.out_status[p] = ok ? MCS_PENDING : MCS_ERR_ARG;
+        if (P.out_nodes) P.out_nodes[p] = 0;
+        if (P.out_usec) P.out_usec[p] = 0.f;
+    }
+    if (P.out_map)
+        for (int i = lane; i < kMaxN; i += 32) P.out_map[(size_t)p * kMaxN + i] = -1;
+}
+
+cudaError_t launch_pack(const PackParams& p, cudaStream_t s) {
+    int blocks = (p.npairs + 3) / 4;
+    if (blocks < 1) blocks = 1;
+    pack_kernel<<<blocks, 128, 0, s>>>(p);
+    return cudaGetLastError();
+}
+
+// ---------------------------------------------------------------------------
+// search kernel
+// ---------------------------------------------------------------------------
+constexpr unsigned kKeyNone = 0xFFFFu;
+constexpr int kTick = 32;             // nodes between incumbent/hunger refreshes
+constexpr int kTimeTick = 512;        // nodes between deadline checks
+constexpr int kSpinLimit = 1 << 22;   // iterations of a ring-slot wait
+
+struct WarpSmem {
+    u64* gout; u64* gin; u64* hout; u64* hin;
+    u64* rrem;      // per level: candidates still to try
+    u64* info;      // per level: base | C << 16 | v << 24 | flags << 32 | bound << 40
+    uint8_t* Mg; uint8_t* Mh;
+    ulonglong2* cls;
+};
+
+__device__ __forceinline__ u64 pack_info(int base, int C, int v, int flags, int bound) {
+    return (u64)base | ((u64)C << 16) | ((u64)v << 24) | ((u64)flags << 32) | ((u64)bound << 40);
+}
+
+struct Top {                // the cursor of the deepest level, kept in registers
+    int d, base, C, v, flags, bound;
+    u64 rrem;
+};
+
+struct Stack {
+    ulonglong2* sm;          // shared part
+    ulonglong2* gm;          // global overflow part
+    int S;
+    __device__ __forceinline__ ulonglong2* at(int p) const { return p < S ? sm + p : gm + (p - S); }
+};
+
+// Result of scanning a level's classes (node entry): Eq. 1 sum and the class
+// choice.  Key = max(|L|,|R|) << 6 | lowest L vertex (unique per class).
+struct Scan {
+    int sum;
+    unsigned key;
+    u64 R;
+};
+
+// Scan the classes of a level (optionally removing v from its class first,
+// which is the "v stays unmatched" step) and choose the next branching class.
+__device__ __forceinline__ Scan scan_level(const Stack& st, int base, int C, int remove_v, int lane) {
+    int sum = 0;
+    unsigned best = kKeyNone;
+    u64 bestR = 0;
+    const u64 vb = remove_v >= 0 ? (1ull << remove_v) : 0ull;
+    for (int s = 0; s < 2; ++s) {
+        if (s == 1 && C <= 32) break;
+        int i = lane + 32 * s;
+        if (i < C) {
+            ulonglong2* ptr = st.at(base + i);
+            ulonglong2 c = *ptr;
+            if (c.x & vb) {
+                c.x &= ~vb;
+                ptr->x = c.x;
+            }
+            if (c.x) {
+                int a = __popcll(c.x), b = __popcll(c.y);
+                sum += min(a, b);
+                unsigned key = ((unsigned)max(a, b) << 6) | (unsigned)(__ffsll(c.x) - 1);
+                if (key < best) { best = key; bestR = c.y; }
+            }
+        }
+    }
+    Scan r;
+    r.sum = __reduce_add_sync(FULL, sum);
+    r.key = __reduce_min_sync(FULL, best);
+    unsigned win = __ballot_sync(FULL, best == r.key && r.key != kKeyNone);
+    r.R = win ? shfl64(bestR, __ffs(win) - 1) : 0ull;
+    return r;
+}
+
+// Bounded wait for a ring slot's sequence number.
+__device__ __forceinline__ bool wait_seq(const u64* seq, u64 want) {
+    for (int it = 0; it < kSpinLimit; ++it) {
+        if (vload(seq) == want) return true;
+        if (it > 64) __nanosleep(64);
+    }
+    return false;
+}
+
+template <bool DIR>
+__device__ void write_best(const SearchParams& P, int pair, const WarpSmem& w, int d, int v, int u,
+                           int lane) {
+    uint16_t* slot = P.best + ((size_t)pair * kLevels + (d + 1)) * kMaxN;
+    for (int i = lane; i < d; i += 32) slot[i] = (uint16_t)((w.Mg[i] << 8) | w.Mh[i]);
+    if (lane == 0) slot[d] = (uint16_t)((v << 8) | u);
+}
+
+// Finish the pair: write size, status, nodes and the mapping (original numbers).
+__device__ void finalize_pair(const SearchParams& P, int pair, int lane) {
+    __threadfence();
+    PairState& ps = P.state[pair];
+    const PairGraph& pg = P.graphs[pair];
+    int status = vload(&ps.status);
+    int k = 0;
+    if (status == MCS_PENDING) {
+        k = vload(&ps.inc);
+        status = vload(&ps.abort) ? MCS_TIMEOUT : MCS_OK;
+        if (P.out_map) {
+            const uint16_t* slot = P.best + ((size_t)pair * kLevels + k) * kMaxN;
+            for (int i = lane; i < k; i += 32) {
+                uint16_t e = vload(slot + i);
+                int g = pg.permG[e >> 8], h = pg.permH[e & 0xff];
+                P.out_map[(size_t)pair * kMaxN + g] = (int16_t)h;
+            }
+        }
+    } else {
+        k = 0;
+    }
+    if (lane == 0) {
+        u64 now = gtimer();
+        if (P.out_size) P.out_size[pair] = k;
+        if (P.out_nodes) P.out_nodes[pair] = vload(&ps.nodes);
+        u64 t0 = vload(&ps.t_start);
+        if (P.out_usec) P.out_usec[pair] = t0 ? (float)((now - t0) * 1e-3) : 0.f;
+        __threadfence();
+        if (P.out_status) P.out_status[pair] = status;
+        ps.status = status;
+        __threadfence();
+        atomicSub(&P.ctl->remaining, 1);
+        atomicMax(&P.ctl->last_progress, now);
+    }
+    __syncwarp();
+}
+
+// A task of `pair` ended: publish node count, drop the open count and finalise
+// the pair if this was its last task.
+__device__ __forceinline__ void end_task(const SearchParams& P, int pair, u64& nodes, int lane) {
+    int last = 0;
+    if (lane == 0) {
+        if (nodes) atomicAdd(&P.state[pair].nodes, nodes);
+        __threadfence();
+        last = atomicSub(&P.state[pair].open, 1) == 1;
+    }
+    nodes = 0;
+    last = __shfl_sync(FULL, last, 0);
+    if (last) finalize_pair(P, pair, lane);
+}
+
+template <bool DIR>
+__global__ void __launch_bounds__(256) search_kernel(SearchParams P) {
+    extern __shared__ __align__(16) unsigned char smem[];
+    const int lane = threadIdx.x & 31;
+    const int wib = threadIdx.x >> 5;
+    const int gw = blockIdx.x * (blockDim.x >> 5) + wib;
+    if (gw >= P.max_warps) return;
+    unsigned char* base = smem + (size_t)wib * P.warp_smem_bytes;
+    WarpSmem w;
+    w.gout = (u64*)(base + kSmAdj);
+    w.gin = w.gout + kMaxN;
+    w.hout = w.gout + 2 * kMaxN;
+    w.hin = w.gout + 3 * kMaxN;
+    w.rrem = (u64*)(base + kSmRrem);
+    w.info = (u64*)(base + kSmInfo);
+    w.Mg = base + kSmM;
+    w.Mh = base + kSmM + kMaxN;
+    w.cls = (ulonglong2*)(base + kSmCls);
+    Stack st;
+    st.sm = w.cls;
+    st.S = P.stack_smem;
+    st.gm = P.gstack + (size_t)gw * (size_t)(kStackMax > P.stack_smem ? kStackMax - P.stack_smem : 0);
+
+    Control* ctl = P.ctl;
+    const bool level_prune = (P.flags & MCS_NO_LEVEL_PRUNE) == 0;
+    int cur_pair = -1;
+    u64 nodes = 0;
+    unsigned tick = 0;
+    u64 spilled = 0;
+
+    while (true) {
+        // ------------------------------------------------------------------
+        // acquire work: a donated task, else the next pair's root
+        // ------------------------------------------------------------------
+        int pair = -1;
+        Top t;
+        int d0 = 0;
+        bool fresh = false;
+        bool hungry = false;
+        int got = 0;          // 1 task, 2 root, -1 exit
+        u64 qh = 0;
+        for (int it = 0; got == 0; ++it) {
+            if (lane == 0) {
+                u64 h = vload(&ctl->q_head);
+                u64 tl = vload(&ctl->q_tail);
+                if (h < tl && atomicCAS(&ctl->q_head, h, h + 1) == h) { got = 1; qh = h; }
+                if (!got) {
+                    int np = vload(&ctl->next_pair);
+                    if (np < P.npairs) {
+                        int k = atomicAdd(&ctl->next_pair, 1);
+                        if (k < P.npairs) { got = 2; pair = P.order ? P.order[k] : k; }
+                    }
+                }
+                if (!got) {
+                    if (vload(&ctl->remaining) <= 0 || vload(&ctl->error) != 0) got = -1;
+                    else {
+                        u64 now = gtimer();
+                        u64 lp = vload(&ctl->last_progress);
+                        if (now > lp && now - lp > P.stall_ns) { atomicCAS(&ctl->error, 0, MCS_ERR_DEVICE_STALL); got = -1; }
+                    }
+                }
+            }
+            got = __shfl_sync(FULL, got, 0);
+            if (got == 0) {
+                if (!hungry) { if (lane == 0) atomicAdd(&ctl->hungry, 1); hungry = true; }
+                // exponential backoff, 0.25 .. 8 us: thousands of idle warps must
+                // not saturate the L2 slice that holds the ring counters
+                __nanosleep(256u << min(it, 5));
+            }
+        }
+        if (hungry && lane == 0) atomicSub(&ctl->hungry, 1);
+        if (got < 0) break;
+        pair = __shfl_sync(FULL, pair, 0);
+        qh = shfl64(qh, 0);
+
+        const Task* task = nullptr;
+        if (got == 1) {
+            task = P.queue + (qh & (P.qcap - 1));
+            int okw = 1;
+            if (lane == 0) okw = wait_seq(P.qseq + (qh & (P.qcap - 1)), qh + 1);
+            okw = __shfl_sync(FULL, okw, 0);
+            if (!okw) { if (lane == 0) atomicCAS(&ctl->error, 0, MCS_ERR_DEVICE_STALL); break; }
+            __threadfence();
+            pair = vload(&task->h.pair);
+        }
+        PairState& ps = P.state[pair];
+        const PairGraph& pg = P.graphs[pair];
+        if (got == 2) {
+            if (vload(&ps.status) != MCS_PENDING) {       // malformed input: report and skip
+                if (lane == 0) ps.open = 0;
+                finalize_pair(P, pair, lane);
+                continue;
+            }
+            if (lane == 0) {
+                u64 now = gtimer();
+                ps.t_start = now;
+                ps.deadline = now + P.timeout_ns;
+                atomicMax(&ctl->last_progress, now);
+            }
+        }
+        // load the pair's rows into shared memory
+        if (pair != cur_pair) {
+            for (int i = lane; i < kMaxN; i += 32) {
+                w.gout[i] = pg.gout[i];
+                w.hout[i] = pg.hout[i];
+                if (DIR) { w.gin[i] = pg.gin[i]; w.hin[i] = pg.hin[i]; }
+            }
+            cur_pair = pair;
+        }
+        if (got == 1) {
+            t.d = vload(&task->h.depth);
+            t.C = vload(&task->h.C);
+            t.v = vload(&task->h.v);
+            t.rrem = vload(&task->h.rrem);
+            t.flags = vload(&task->h.flags);
+            t.bound = vload(&task->h.bound);
+            for (int i = lane; i < t.d; i += 32) { w.Mg[i] = ld_cg(&task->Mg[i]); w.Mh[i] = ld_cg(&task->Mh[i]); }
+            for (int i = lane; i < t.C; i += 32) *st.at(i) = ld_cg(&task->cls[i]);
+            __syncwarp();
+            if (lane == 0) {
+                __threadfence();
+                P.qseq[qh & (P.qcap - 1)] = qh + P.qcap;      // release the slot
+                atomicAdd(&ctl->stolen, 1ull);
+                atomicMax(&ctl->last_progress, gtimer());
+            }
+            fresh = false;
+        } else {
+            t.d = 0;
+            t.C = pg.C0;
+            for (int i = lane; i < t.C; i += 32) *st.at(i) = pg.root[i];
+            fresh = true;
+        }
+        t.base = 0;
+        d0 = t.d;
+        __syncwarp();
+        int inc = vload(&ps.inc);
+        if (vload(&ps.abort)) { end_task(P, pair, nodes, lane); continue; }
+        if (fresh) {
+            // root node entry (Algorithm 1): bound of Eq. 1, then class choice
+            ++nodes;
+            Scan sc = scan_level(st, 0, t.C, -1, lane);
+            t.bound = sc.sum;
+            if (t.bound <= inc) { end_task(P, pair, nodes, lane); continue; }
+            t.v = sc.key & 63;
+            t.rrem = sc.R;
+            t.flags = kTaskPending;
+        }
+
+        // ------------------------------------------------------------------
+        // depth-first search over this task's subtree
+        // ------------------------------------------------------------------
+        bool aborted = false;
+        while (t.d >= d0) {
+            if ((++tick % kTick) == 0) {
+                int g_inc = 0, ab = 0, hun = 0;
+                if (lane == 0) {
+                    g_inc = vload(&ps.inc);
+                    ab = vload(&ps.abort);
+                    hun = vload(&ctl->hungry);
+                    if (!ab && (tick % kTimeTick) == 0 && gtimer() > vload(&ps.deadline)) {
+                        ps.abort = 1;
+                        ab = 1;
+                    }
+                }
+                g_inc = __shfl_sync(FULL, g_inc, 0);
+                ab = __shfl_sync(FULL, ab, 0);
+                hun = __shfl_sync(FULL, hun, 0);
+                inc = max(inc, g_inc);
+                if (ab) { aborted = true; break; }
+                // ---- donate the shallowest open level to a waiting warp ----
+                if (hun > 0) {
+                    // flush the top cursor so that every level is in shared memory
+                    if (lane == 0) {
+                        w.rrem[t.d] = t.rrem;
+                        w.info[t.d] = pack_info(t.base, t.C, t.v, t.flags, t.bound);
+                    }
+                    __syncwarp();
+                    int ds = -1;
+                    for (int off = d0; off <= t.d && ds < 0; off += 32) {
+                        int d = off + lane;
+                        bool open = false;
+                        if (d <= t.d) {
+                            u64 inf = w.info[d];
+                            int fl = (int)((inf >> 32) & 0xff), bd = (int)((inf >> 40) & 0xff);
+                            open = (w.rrem[d] != 0 || (fl & kTaskPending)) && bd > inc;
+                        }
+                        unsigned m = __ballot_sync(FULL, open);
+                        if (m) ds = off + __ffs(m) - 1;
+                    }
+                    // keep at least one level of work of our own: a level whose
+                    // subtree we are inside (ds < t.d) or the top with >= 2 candidates
+                    if (ds >= 0) {
+                        u64 inf = w.info[ds];
+                        u64 rr = w.rrem[ds];
+                        int fl = (int)((inf >> 32) & 0xff);
+                        int k = __popcll(rr);
+                        u64 give;
+                        int gflags;
+                        if (k >= 2) {
+                            // give the upper half of the candidates, keep the rest + unmatched branch
+                            give = rr;
+                            for (int j = 0; j < (k + 1) / 2; ++j) give &= give - 1;
+                            gflags = 0;
+                        } else {
+                            give = rr;
+                            gflags = fl & kTaskPending;
+                        }
+                        bool worth = (ds < t.d) || k >= 2;
+                        u64 ticket = 0;
+                        int ok = 0;
+                        if (worth && lane == 0) {
+                            u64 h = vload(&ctl->q_head), tl = vload(&ctl->q_tail);
+                            if (tl - h < (u64)(P.qcap / 2)) {
+                                atomicAdd(&ps.open, 1);
+                                ticket = atomicAdd(&ctl->q_tail, 1ull);
+                                ok = wait_seq(P.qseq + (ticket & (P.qcap - 1)), ticket) ? 1 : -1;
+                            }
+                        }
+                        ok = __shfl_sync(FULL, ok, 0);
+                        if (ok < 0) { if (lane == 0) atomicCAS(&ctl->error, 0, MCS_ERR_DEVICE_STALL); aborted = true; break; }
+                        if (ok > 0) {
+                            ticket = shfl64(ticket, 0);
+                            Task* dst = P.queue + (ticket & (P.qcap - 1));
+                            int C = (int)((inf >> 16) & 0xff);
+                            int bs = (int)(inf & 0xffff);
+                            for (int i = lane; i < C; i += 32) dst->cls[i] = *st.at(bs + i);
+                            for (int i = lane; i < ds; i += 32) { dst->Mg[i] = w.Mg[i]; dst->Mh[i] = w.Mh[i]; }
+                            if (lane == 0) {
+                                dst->h.pair = pair;
+                                dst->h.depth = ds;
+                                dst->h.C = C;
+                                dst->h.v = (int)((inf >> 24) & 0xff);
+                                dst->h.rrem = give;
+                                dst->h.flags = gflags;
+                                dst->h.bound = (int)((inf >> 40) & 0xff);
+                                w.rrem[ds] = rr & ~give;
+                                w.info[ds] = (inf & ~(0xffull << 32)) | ((u64)(fl & ~gflags) << 32);
+                            }
+                            __syncwarp();
+                            __threadfence();
+                            if (lane == 0) {
+                                P.qseq[ticket & (P.qcap - 1)] = ticket + 1;   // publish
+                                atomicAdd(&ctl->donated, 1ull);
+                                atomicMax(&ctl->last_progress, gtimer());
+                            }
+                            __syncwarp();
+                            if (ds == t.d) {
+                                t.rrem = rr & ~give;
+                                t.flags = fl & ~gflags;
+                            }
+                        }
+                    }
+                }
+            }
+            // level prune: every node below this level has bound <= this one
+            if (level_prune && t.bound <= inc) {
+                --t.d;
+                if (t.d >= d0) {
+                    u64 inf = w.info[t.d];
+                    t.rrem = w.rrem[t.d];
+                    t.base = (int)(inf & 0xffff); t.C = (int)((inf >> 16) & 0xff);
+                    t.v = (int)((inf >> 24) & 0xff); t.flags = (int)((inf >> 32) & 0xff);
+                    t.bound = (int)((inf >> 40) & 0xff);
+                }
+                continue;
+            }
+            if (t.rrem) {
+                // ---------------- child (v, u): filterDomain + Eq. 1 ----------------
+                const int u = __ffsll(t.rrem) - 1;
+                t.rrem &= t.rrem - 1;
+                ++nodes;
+                const int v = t.v;
+                const u64 vb = 1ull << v, ub = 1ull << u;
+                const u64 gB = w.gout[v], hB = w.hout[u];
+                const u64 gA = DIR ? w.gin[v] : 0ull, hA = DIR ? w.hin[u] : 0ull;
+                u64 Ls[2], Rs[2];
+                int sum = 0;
+                unsigned best = kKeyNone;
+                u64 bestR = 0;
+                const int nslot = t.C > 32 ? 2 : 1;
+#pragma unroll
+                for (int s = 0; s < 2; ++s) {
+                    Ls[s] = 0; Rs[s] = 0;
+                    if (s < nslot) {
+                        int i = lane + 32 * s;
+                        if (i < t.C) {
+                            ulonglong2 c = *st.at(t.base + i);
+                            Ls[s] = c.x & ~vb;
+                            Rs[s] = c.y & ~ub;
+                        }
+                        const u64 L = Ls[s], R = Rs[s];
+                        if (DIR) {
+                            const u64 la = L & gA, lb = L & gB, ra = R & hA, rb = R & hB;
+                            const u64 lp[4] = {L & ~(la | lb), la & ~lb, lb & ~la, la & lb};
+                            const u64 rp[4] = {R & ~(ra | rb), ra & ~rb, rb & ~ra, ra & rb};
+#pragma unroll
+                            for (int k = 0; k < 4; ++k) {
+                                int a = __popcll(lp[k]), b = __popcll(rp[k]);
+                                int m = min(a, b);
+                                sum += m;
+                                unsigned key = m ? (((unsigned)max(a, b) << 6) | (unsigned)(__ffsll(lp[k]) - 1)) : kKeyNone;
+                                if (key < best) { best = key; bestR = rp[k]; }
+                            }
+                        } else {
+                            const u64 l1 = L & gB, r1 = R & hB, l0 = L ^ l1, r0 = R ^ r1;
+                            int a1 = __popcll(l1), b1 = __popcll(r1), a0 = __popcll(l0), b0 = __popcll(r0);
+                            int m1 = min(a1, b1), m0 = min(a0, b0);
+                            sum += m1 + m0;
+                            unsigned k1 = m1 ? (((unsigned)max(a1, b1) << 6) | (unsigned)(__ffsll(l1) - 1)) : kKeyNone;
+                            unsigned k0 = m0 ? (((unsigned)max(a0, b0) << 6) | (unsigned)(__ffsll(l0) - 1)) : kKeyNone;
+                            if (k1 < best) { best = k1; bestR = r1; }
+                            if (k0 < best) { best = k0; bestR = r0; }
+                        }
+                    }
+                }
+                sum = __reduce_add_sync(FULL, sum);
+                const int dm = t.d + 1;
+                // incumbent (Algorithm 1): |M u {(v,u)}| beats the best so far
+                if (dm > inc) {
+                    int old = 0;
+                    if (lane == 0) old = atomicMax(&ps.inc, dm);
+                    old = __shfl_sync(FULL, old, 0);
+                    if (old < dm) {
+                        write_best<DIR>(P, pair, w, t.d, v, u, lane);
+                        inc = dm;
+                    } else {
+                        inc = old;
+                    }
+                }
+                if (dm + sum <= inc) continue;          // child pruned by Eq. 1
+                // descend: compact the child's classes onto the stack
+                const unsigned kmin = __reduce_min_sync(FULL, best);
+                const unsigned win = __ballot_sync(FULL, best == kmin);
+                const u64 cR = shfl64(bestR, __ffs(win) - 1);
+                const int cbase = t.base + t.C;
+                int pos = cbase;
+#pragma unroll
+                for (int s = 0; s < 2; ++s) {
+                    if (s < nslot) {
+                        const u64 L = Ls[s], R = Rs[s];
+                        if (DIR) {
+                            const u64 la = L & gA, lb = L & gB, ra = R & hA, rb = R & hB;
+                            const u64 lp[4] = {L & ~(la | lb), la & ~lb, lb & ~la, la & lb};
+                            const u64 rp[4] = {R & ~(ra | rb), ra & ~rb, rb & ~ra, ra & rb};
+#pragma unroll
+                            for (int k = 0; k < 4; ++k) {
+                                bool keep = lp[k] && rp[k];
+                                unsigned m = __ballot_sync(FULL, keep);
+                                if (keep) *st.at(pos + __popc(m & lanemask_lt())) = make_ulonglong2(lp[k], rp[k]);
+                                pos += __popc(m);
+                            }
+                        } else {
+                            const u64 l1 = L & gB, r1 = R & hB, l0 = L ^ l1, r0 = R ^ r1;
+                            bool k1 = l1 && r1, k0 = l0 && r0;
+                            unsigned m1 = __ballot_sync(FULL, k1);
+                            if (k1) *st.at(pos + __popc(m1 & lanemask_lt())) = make_ulonglong2(l1, r1);
+                            pos += __popc(m1);
+                            unsigned m0 = __ballot_sync(FULL, k0);
+                            if (k0) *st.at(pos + __popc(m0 & lanemask_lt())) = make_ulonglong2(l0, r0);
+                            pos += __popc(m0);
+                        }
+                    }
+                }
+                if (pos > st.S) spilled += 1;
+                if (lane == 0) {
+                    w.Mg[t.d] = (uint8_t)v;
+                    w.Mh[t.d] = (uint8_t)u;
+                    w.rrem[t.d] = t.rrem;
+                    w.info[t.d] = pack_info(t.base, t.C, t.v, t.flags, t.bound);
+                }
+                __syncwarp();
+                t.d = dm;
+                t.base = cbase;
+                t.C = pos - cbase;
+                t.v = kmin & 63;
+                t.rrem = cR;
+                t.flags = kTaskPending;
+                t.bound = dm + sum;
+            } else if (t.flags & kTaskPending) {
+                // ---------------- "v stays unmatched": same M, v leaves its class ----------------
+                ++nodes;
+                Scan sc = scan_level(st, t.base, t.C, t.v, lane);
+                __syncwarp();
+                t.bound = t.d + sc.sum;
+                if (t.bound <= inc) {
+                    t.flags = 0;            // pruned: the level is exhausted and pops next
+                    t.rrem = 0;
+                } else {
+                    t.v = sc.key & 63;
+                    t.rrem = sc.R;
+                    t.flags = kTaskPending;
+                }
+            } else {
+                --t.d;
+                if (t.d >= d0) {
+                    u64 inf = w.info[t.d];
+                    t.rrem = w.rrem[t.d];
+                    t.base = (int)(inf & 0xffff); t.C = (int)((inf >> 16) & 0xff);
+                    t.v = (int)((inf >> 24) & 0xff); t.flags = (int)((inf >> 32) & 0xff);
+                    t.bound = (int)((inf >> 40) & 0xff);
+                }
+            }
+        }
+        (void)aborted;
+        end_task(P, pair, nodes, lane);
+    }
+    if (lane == 0 && spilled) atomicAdd(&ctl->spilled, spilled);
+}
+
+cudaError_t launch_search(const SearchParams& p, int blocks, int warps_per_block, bool directed,
+                          cudaStream_t s) {
+    size_t smem = (size_t)warps_per_block * p.warp_smem_bytes;
+    if (directed) {
+        cudaFuncSetAttribute(search_kernel<true>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+        search_kernel<true><<<blocks, warps_per_block * 32, smem, s>>>(p);
+    } else {
+        cudaFuncSetAttribute(search_kernel<false>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+        search_kernel<false><<<blocks, warps_per_block * 32, smem, s>>>(p);
+    }
+    return cudaGetLastError();
+}
+
+int search_max_blocks_per_sm(int warps_per_block, int smem_per_block, bool directed) {
+    int nb = 0;
+    if (directed) {
+        cudaFuncSetAttribute(search_kernel<true>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem_per_block);
+        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, search_kernel<true>, warps_per_block * 32, smem_per_block);
+    } else {
+        cudaFuncSetAttribute(search_kernel<false>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem_per_block);
+        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, search_kernel<false>, warps_per_block * 32, smem_per_block);
+    }
+    return nb;
+}
+
+}  // namespace mcsk

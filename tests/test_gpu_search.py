@@ -1,0 +1,223 @@
+"""Parity of the CUDA search (through the C ABI) with the CPU oracle.
+
+Sizes must match bit-exactly; every returned mapping must pass the oracle's
+verifier (several optimal mappings may exist, so mappings are verified rather
+than compared)."""
+import json
+import os
+
+import numpy as np
+import pytest
+
+import oracle
+import synth
+
+pytestmark = pytest.mark.gpu
+HERE = os.path.dirname(os.path.abspath(__file__))
+
+
+@pytest.fixture(scope="module")
+def solver():
+    import torch
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    from paper_1908_06418_b300 import Solver
+    s = Solver(0)
+    yield s
+    s.close()
+
+
+def _rand_pairs(count, nmin, nmax, seed, directed=False, k=0, pmin=0.1, pmax=0.6):
+    rs = np.random.default_rng(seed)
+    out = []
+    for i in range(count):
+        nG, nH = int(rs.integers(nmin, nmax + 1)), int(rs.integers(nmin, nmax + 1))
+        p = float(rs.uniform(pmin, pmax))
+        rg, rh = synth.rng_for(seed, i, 0), synth.rng_for(seed, i, 1)
+        f = synth.er_directed if directed else synth.er_undirected
+        a, b = f(nG, p, rg), f(nH, p, rh)
+        out.append(synth.Pair(synth.Graph(a, synth.uniform_labels(nG, k, rg)),
+                              synth.Graph(b, synth.uniform_labels(nH, k, rh)), directed))
+    return out
+
+
+def _check(pairs, results, expect=None):
+    for i, (p, r) in enumerate(zip(pairs, results)):
+        o = expect[i] if expect is not None else oracle.mcs(
+            p.G.adj, p.H.adj, p.G.labels, p.H.labels, directed=p.directed).size
+        assert r.status == 0, (i, r.status)
+        assert r.size == o, (i, r.size, o)
+        assert len(r.g_idx) == r.size
+        assert oracle.verify(p.G.adj, p.H.adj, r.g_idx, r.h_idx, p.G.labels, p.H.labels) == 1, i
+
+
+@pytest.mark.parametrize("directed,k", [(False, 0), (True, 0), (False, 3), (True, 2)])
+def test_single_warp_traversal_equals_oracle(solver, directed, k):
+    """With one warp and no per-sibling bound re-test, the device walks the
+    same search tree as the sequential recursion: node counts are equal."""
+    from paper_1908_06418_b300 import MCS_NO_LEVEL_PRUNE
+    pairs = _rand_pairs(40, 4, 16, 4242 + k + (100 if directed else 0), directed, k)
+    solver.set_max_warps(1)
+    try:
+        for p in pairs:
+            r = solver.solve(p.G.adj, p.H.adj, p.G.labels, p.H.labels, directed=directed,
+                             flags=MCS_NO_LEVEL_PRUNE, timeout_s=30)
+            o = oracle.mcs(p.G.adj, p.H.adj, p.G.labels, p.H.labels, directed=directed)
+            assert r.status == 0
+            assert r.size == o.size
+            assert r.nodes == o.nodes
+            assert oracle.verify(p.G.adj, p.H.adj, r.g_idx, r.h_idx, p.G.labels, p.H.labels) == 1
+    finally:
+        solver.set_max_warps(0)
+
+
+def test_single_warp_default_prunes_no_more_nodes(solver):
+    pairs = _rand_pairs(20, 8, 16, 777)
+    solver.set_max_warps(1)
+    try:
+        for p in pairs:
+            r = solver.solve(p.G.adj, p.H.adj, timeout_s=30)
+            o = oracle.mcs(p.G.adj, p.H.adj)
+            assert r.size == o.size and r.nodes <= o.nodes
+    finally:
+        solver.set_max_warps(0)
+
+
+def test_config1_pair(solver):
+    p = synth.config1_pair()
+    rows = [json.loads(x) for x in open(os.path.join(HERE, "golden", "c1_oracle.jsonl"))]
+    r = solver.solve(p.G.adj, p.H.adj, timeout_s=60)
+    assert r.status == 0 and r.size == rows[0]["size"] == 13
+    assert oracle.verify(p.G.adj, p.H.adj, r.g_idx, r.h_idx) == 1
+
+
+@pytest.mark.parametrize("directed,k", [(False, 0), (True, 0), (False, 4), (True, 3)])
+def test_random_batch_parity(solver, directed, k):
+    pairs = _rand_pairs(300, 1, 22, 31337 + k + (50 if directed else 0), directed, k)
+    res = solver.solve_batch(pairs, directed=directed, timeout_s=60)
+    _check(pairs, res)
+
+
+def test_ragged_sizes_up_to_64(solver):
+    # spans one and two classes per lane (C > 32) and 64-bit rows at the top end
+    pairs = []
+    rs = np.random.default_rng(5)
+    for i in range(24):
+        nG, nH = int(rs.integers(30, 65)), int(rs.integers(30, 65))
+        rg, rh = synth.rng_for(61, i, 0), synth.rng_for(61, i, 1)
+        # dense labelled graphs: many classes, shallow search
+        pairs.append(synth.Pair(synth.Graph(synth.er_undirected(nG, 0.5, rg), synth.uniform_labels(nG, 12, rg)),
+                                synth.Graph(synth.er_undirected(nH, 0.5, rh), synth.uniform_labels(nH, 12, rh))))
+    res = solver.solve_batch(pairs, timeout_s=60)
+    _check(pairs, res)
+
+
+def test_edge_cases(solver):
+    K = lambda n: (np.ones((n, n), np.uint8) - np.eye(n, dtype=np.uint8))
+    Z = lambda n: np.zeros((n, n), np.uint8)
+    P = lambda n: synth.grid(n, 1)
+    cases = [
+        (Z(0), Z(0), 0), (Z(0), K(5), 0), (Z(1), Z(1), 1), (K(64), K(64), 64),
+        (Z(64), Z(64), 64), (K(64), Z(64), 1), (P(64), P(64), 64), (K(33), K(40), 33),
+        (Z(1), K(64), 1),
+    ]
+    res = solver.solve_batch([(a, b, None, None) for a, b, _ in cases], timeout_s=30)
+    for (a, b, want), r in zip(cases, res):
+        assert r.status == 0 and r.size == want, (a.shape, b.shape, r.size, want)
+        assert oracle.verify(a, b, r.g_idx, r.h_idx) == 1
+    # self-loops must be matched
+    a = K(6); a[0, 0] = 1; a[3, 3] = 1
+    b = K(6); b[2, 2] = 1
+    r = solver.solve(a, b, timeout_s=30)
+    assert r.size == oracle.mcs(a, b).size == 5
+    assert oracle.verify(a, b, r.g_idx, r.h_idx) == 1
+
+
+def test_invalid_inputs_are_reported_per_pair(solver):
+    from paper_1908_06418_b300 import MCS_ERR_ARG
+    good = synth.config1_pair()
+    bad_entry = good.G.adj.copy(); bad_entry[0, 1] = 2; bad_entry[1, 0] = 2
+    asym = good.G.adj.copy(); asym[0, 1] = 1 - asym[1, 0]
+    neg = np.full(20, -1, np.int32)
+    big = np.zeros((65, 65), np.uint8)
+    pairs = [(good.G.adj, good.H.adj, None, None), (bad_entry, good.H.adj, None, None),
+             (asym, good.H.adj, None, None), (good.G.adj, good.H.adj, neg, None),
+             (big, good.H.adj, None, None), (good.G.adj, good.H.adj, None, None)]
+    res = solver.solve_batch(pairs, timeout_s=30)
+    assert [r.status for r in res] == [0, MCS_ERR_ARG, MCS_ERR_ARG, MCS_ERR_ARG, MCS_ERR_ARG, 0]
+    assert res[0].size == res[5].size == 13
+
+
+def test_timeout_returns_verified_lower_bound(solver):
+    from paper_1908_06418_b300 import MCS_TIMEOUT
+    p = synth.config4_pairs(count=1)[0]
+    r = solver.solve(p.G.adj, p.H.adj, timeout_s=0.05)
+    assert r.status == MCS_TIMEOUT
+    assert r.size > 0
+    assert oracle.verify(p.G.adj, p.H.adj, r.g_idx, r.h_idx) == 1
+
+
+def test_batch_equals_single(solver):
+    pairs = synth.config3_pairs(count=64, cid=33)
+    batch = solver.solve_batch(pairs, timeout_s=60)
+    for p, rb in zip(pairs, batch):
+        rs = solver.solve(p.G.adj, p.H.adj, p.G.labels, p.H.labels, timeout_s=60)
+        assert rb.size == rs.size and rb.status == rs.status == 0
+
+
+def test_repeat_runs_same_size(solver):
+    pairs = _rand_pairs(64, 14, 26, 2024)
+    a = solver.solve_batch(pairs, timeout_s=60)
+    b = solver.solve_batch(pairs, timeout_s=60)
+    assert [r.size for r in a] == [r.size for r in b]
+
+
+def _golden(name):
+    path = os.path.join(HERE, "golden", name)
+    if not os.path.exists(path):
+        pytest.skip(f"{name} not generated")
+    return [json.loads(x) for x in open(path)]
+
+
+def test_config2_parity(solver):
+    rows = _golden("c2_oracle.jsonl")
+    pairs = synth.config2_pairs()
+    sys_path = os.path.join(HERE, "golden")
+    import sys
+    sys.path.insert(0, sys_path)
+    from make_oracle_golden import pair_digest
+    idx = [r["idx"] for r in rows]
+    sel = [pairs[i] for i in idx]
+    for r, p in zip(rows, sel):
+        assert r["digest"] == pair_digest(p)
+    res = []
+    for directed in (True, False):
+        sub = [(i, p) for i, p in zip(idx, sel) if p.directed == directed]
+        out = solver.solve_batch([p for _, p in sub], directed=directed, timeout_s=300)
+        res += list(zip([i for i, _ in sub], [p for _, p in sub], out))
+    by = {r["idx"]: r for r in rows}
+    for i, p, r in res:
+        g = by[i]
+        assert r.status == 0, (i, r.status)
+        assert oracle.verify(p.G.adj, p.H.adj, r.g_idx, r.h_idx) == 1
+        if g["complete"]:
+            assert r.size == g["size"], (i, r.size, g["size"])
+        else:
+            assert r.size >= g["size"]
+
+
+def test_config3_full_batch_parity(solver):
+    rows = _golden("c3_oracle.jsonl")
+    pairs = synth.config3_pairs()
+    assert len(rows) == len(pairs) == 4096
+    res = solver.solve_batch(pairs, timeout_s=120)
+    for g, p, r in zip(rows, pairs, res):
+        assert r.status == 0, (g["idx"], r.status)
+        if g["complete"]:
+            assert r.size == g["size"], (g["idx"], r.size, g["size"])
+        else:
+            assert r.size >= g["size"]
+    # mappings verified on a sample (the verifier is O(k^2) per pair in Python overhead)
+    for i in range(0, 4096, 16):
+        p, r = pairs[i], res[i]
+        assert oracle.verify(p.G.adj, p.H.adj, r.g_idx, r.h_idx, p.G.labels, p.H.labels) == 1
