@@ -45,6 +45,10 @@ def workload(name: str):
         return synth.config2_pairs(), dict(
             workload="hard single pairs: 96 directed G(36,p), p in {0.05,0.1,0.3} x 32 seeds "
                      "+ 6x6 grid pair with 10% edges deleted", pairs=97)
+    if name == "c2s":     # small case of the same kernel for profiler captures
+        return synth.config2_pairs()[64:72], dict(
+            workload="8 directed G(36,0.3) pairs (hard single pairs, first 8 seeds of p=0.3)",
+            pairs=8)
     if name == "c3":
         return synth.config3_pairs(), dict(
             workload="batched: 4096 undirected pairs, n U{10..40}, p U[0.05,0.4], 4 labels",
@@ -55,6 +59,9 @@ def workload(name: str):
 
 
 def golden_sizes(name: str):
+    shift = 0
+    if name == "c2s":
+        name, shift = "c2", 64
     path = os.path.join(ROOT, "tests", "golden", f"{name}_oracle.jsonl")
     if not os.path.exists(path):
         return {}
@@ -62,7 +69,8 @@ def golden_sizes(name: str):
     for line in open(path):
         if line.strip():
             d = json.loads(line)
-            out[d["idx"]] = (d["size"], d["complete"])
+            if d["idx"] - shift >= 0:
+                out[d["idx"] - shift] = (d["size"], d["complete"])
     return out
 
 
@@ -158,8 +166,8 @@ def run_reference(a):
     if rank != 0:
         return
     name = a.workload
-    n_sample = 8 if name == "c2" else 64
-    budget = 4.0 if name == "c2" else 2.0
+    n_sample = 8 if name.startswith("c2") else 64
+    budget = 25.0 if name.startswith("c2") else 2.0
     for w in range(a.warmup):
         oracle_sample(name, 2, 0.5, offset=w)
     tot_solved = tot_wall = tot_nodes = 0
@@ -175,7 +183,7 @@ def run_reference(a):
     line = {"impl": "reference", "metric": METRIC, "value": val, "unit": UNIT,
             "n_gpus": a.gpus, "steps": a.steps, "warmup": a.warmup,
             "ms_per_step": 1e3 * tot_wall / max(1, a.steps), "higher_is_better": True,
-            "scaling": "weak", "vs_baseline": None, "dtype": "int64", "data": "synthetic",
+            "scaling": "weak", "vs_baseline": None, "dtype": "u64", "data": "synthetic",
             "nodes_per_s": tot_nodes / tot_wall if tot_wall else 0.0,
             "config": dict(cfg, sample=last["sample"]),
             "cpu_baseline": {"value": val, "unit": UNIT, "cores": last["cores"], "kind": "oracle",
@@ -187,12 +195,6 @@ def run_reference(a):
 # ---------------------------------------------------------------------------
 # our arm
 # ---------------------------------------------------------------------------
-def popc_peak_gops(sm_count: int, mhz: float) -> float:
-    # 16 population counts per SM per clock (32-bit POPC issue rate per SM,
-    # CUDA arithmetic-throughput table for compute capability 9.x / 10.x)
-    return sm_count * 16 * mhz * 1e6 / 1e9
-
-
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -222,7 +224,9 @@ def main():
     gold = golden_sizes(a.workload)
     dev = torch.device("cuda", local)
     solver = Solver(local)
-    stream = torch.cuda.current_stream(dev)
+    # a dedicated stream: the library's device entry point runs on the stream
+    # it is given, and CUDA events recorded on that same stream time it
+    stream = torch.cuda.Stream(dev)
 
     # device-resident inputs, one group per flag set (replicas on every rank)
     groups = []
@@ -246,7 +250,10 @@ def main():
     flush = torch.empty(512 << 20, dtype=torch.uint8, device=dev)
     launches_per_step = 2 * len(groups)      # pack + search per group
 
+    stats = []   # per timed step: [(group, search_us, class_visits, busy, idle, pruned)]
+
     def step(evs=None):
+        rec = []
         for gi, g in enumerate(groups):
             if evs is not None:
                 evs[gi][0].record(stream)
@@ -256,8 +263,14 @@ def main():
                                            timeout_s=a.timeout, stream=stream.cuda_stream)
             if evs is not None:
                 evs[gi][1].record(stream)
+                stream.synchronize()
+                st = solver.last_stats()
+                rec.append((gi, st["kernel_us"], st["class_visits"], st["busy_cycles"],
+                            st["idle_cycles"], st["pruned"]))
             if rc != 0:
                 raise RuntimeError(f"enqueue failed: {solver.strerror(rc)}")
+        if evs is not None:
+            stats.append(rec)
 
     def check():
         solved = 0
@@ -296,7 +309,7 @@ def main():
             step(evs)
             torch.cuda.synchronize()
             step_ms.append(sum(e0.elapsed_time(e1) for e0, e1 in evs))
-            search_ms.append(solver.last_stats()["kernel_us"] / 1e3)
+            search_ms.append(sum(r[1] for r in stats[-1]) / 1e3)
             s, n, l = check()
             solved_tot += s
             nodes_tot += n
@@ -335,25 +348,33 @@ def main():
         e2e_ms.append((time.perf_counter() - t0) * 1e3)
     e2e_value = e2e_solved / (sum(e2e_ms) / 1e3)
 
-    # ---- roofline of the search kernel (integer pipes)
-    sms = torch.cuda.get_device_properties(dev).multi_processor_count
+    # ---- roofline of the dominant kernel (the search kernel of the group
+    # that takes longest).  Algorithmic work per label class read by a node
+    # expansion: 4 hardware popcounts undirected (|L1|, |R1| as two 64-bit
+    # counts), 12 directed (three of the four parts per side); the popcount
+    # unit is the bounding pipe, its sustained device rate is measured live
+    # by mcs_bench_popc.
     csum = clk.summary()
-    mhz = csum["sm_mhz"] or 2032.0
-    # algorithmic integer work per expanded node, from the in-kernel class counts
-    # is not yet exported; use the per-node lower bound of 4 HW POPC per class
-    # with the mean class count measured by the oracle for this workload
-    cbar = float(os.environ.get("MCS_CBAR", "0")) or None
-    roof = None
-    if cbar:
-        popc_per_node = 4 * cbar * (3 if pairs[0].directed else 1)
-        achieved = nodes_per_s * popc_per_node / 1e9
-        peak = popc_peak_gops(sms, 2032.0)
-        roof = {"bound": "alu", "achieved": achieved, "peak": peak, "unit": "Gpopc/s",
-                "frac": achieved / peak, "traffic": None}
+    popc_peak = solver.bench_popc() / 1e9
+    dom = max(range(len(groups)), key=lambda gi: sum(r[gi][1] for r in stats))
+    per_class = 12 if groups[dom]["flags"] & MCS_DIRECTED else 4
+    dom_us = [r[dom][1] for r in stats]
+    dom_cv = [r[dom][2] for r in stats]
+    busy = sum(r[dom][3] for r in stats)
+    idle = sum(r[dom][4] for r in stats)
+    achieved = (sum(dom_cv) * per_class / 1e9) / (sum(dom_us) * 1e-6)
+    roof = {"bound": "alu", "achieved": achieved, "peak": popc_peak, "unit": "Gpopc/s",
+            "frac": achieved / popc_peak, "traffic": None,
+            "kernel": "search_kernel<%s>" % ("directed" if groups[dom]["flags"] & MCS_DIRECTED else "undirected"),
+            "peak_source": "measured: mcs_bench_popc (device-wide sustained 32-bit popc rate)",
+            "class_visits_per_launch": sum(dom_cv) / len(dom_cv), "popc_per_class": per_class,
+            "launch_ms": sum(dom_us) / len(dom_us) / 1e3,
+            "warp_busy_frac": busy / max(1.0, busy + idle),
+            "pruned_per_launch": sum(r[dom][5] for r in stats) / len(stats)}
 
     line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": a.steps,
             "warmup": a.warmup, "ms_per_step": total_ms / a.steps, "higher_is_better": True,
-            "scaling": "weak", "vs_baseline": None, "dtype": "int64", "data": "synthetic",
+            "scaling": "weak", "vs_baseline": None, "dtype": "u64", "data": "synthetic",
             "nodes_per_s": nodes_per_s,
             "p50_latency_ms": float(np.percentile(lats, 50)) if lats else None,
             "p99_latency_ms": float(np.percentile(lats, 99)) if lats else None,
@@ -366,8 +387,8 @@ def main():
                     "d2h_bytes_per_step": int(d2h)},
             "roofline": roof, "clocks": csum}
     if rank == 0 and not a.no_cpu_baseline:
-        cb = oracle_sample(a.workload, 8 if a.workload == "c2" else 64,
-                           4.0 if a.workload == "c2" else 2.0)
+        cb = oracle_sample(a.workload, 8 if a.workload.startswith("c2") else 64,
+                           25.0 if a.workload.startswith("c2") else 2.0)
         line["cpu_baseline"] = {"value": cb["solved"] / cb["wall"], "unit": UNIT, "cores": cb["cores"],
                                 "kind": "oracle", "sample": cb["sample"],
                                 "nodes_per_s": cb["nodes"] / cb["wall"]}

@@ -141,14 +141,29 @@ int mcs_set_max_warps(mcs_ctx* ctx, int warps);
 
 /* Statistics of the last solve on this context: out[0] search-kernel
  * microseconds (for mcs_solve_batch_device: once its stream has passed the
- * launch, else the previous value), out[1] total nodes, out[2] donated tasks,
- * out[3] tasks taken from the ring, out[4] child levels that spilled past the
- * shared-memory class cache, out[5] warps launched, out[6] bytes copied host
- * to device, out[7] bytes copied device to host (out[1..4], out[6..7]: host
- * API calls only).  Returns the number of values written (<= n, <= 8). */
+ * launch, else the previous value), out[1] total nodes (host API calls only),
+ * out[2] donated tasks, out[3] donated tasks taken up, out[4] child levels
+ * that spilled past the shared-memory class cache, out[5] warps launched,
+ * out[6] bytes copied host to device, out[7] bytes copied device to host
+ * (out[6..7]: host API calls only), out[8] label classes read by node
+ * expansions (the unit of algorithmic work), out[9] children cut by the bound
+ * when created, out[10] / out[11] SM cycles summed over warps while working /
+ * waiting for work, out[12..14] index violations recorded by an
+ * MCS_DEBUG_BOUNDS build (count, first code, first source line; 0 in
+ * release builds).  Returns the number of values written (<= n, <= 15). */
 int mcs_last_stats(mcs_ctx* ctx, double* out, int n);
 
+/* Micro-benchmark of the integer pipe the search is bound by: sustained
+ * 32-bit population counts per second over the whole device (8 independent
+ * chains per thread, 8 blocks of 256 threads per SM).  Not part of the
+ * search; used as the measured roofline denominator. */
+int mcs_bench_popc(mcs_ctx* ctx, double* popc_per_s);
+
 const char* mcs_strerror(int code);
+
+/* Detail of the last failing CUDA runtime call made by the library on the
+ * calling host thread (error name, code, call), or "" if none failed. */
+const char* mcs_error_detail(void);
 
 #ifdef __cplusplus
 }

@@ -47,7 +47,7 @@ class _Result(ctypes.Structure):
 
 EXPORTED_SYMBOLS = ["mcs_create", "mcs_destroy", "mcs_solve", "mcs_solve_batch",
                     "mcs_solve_batch_device", "mcs_submit", "mcs_poll", "mcs_set_launch",
-                    "mcs_set_max_warps", "mcs_last_stats", "mcs_strerror"]
+                    "mcs_set_max_warps", "mcs_last_stats", "mcs_bench_popc", "mcs_strerror", "mcs_error_detail"]
 
 _lib = None
 
@@ -59,7 +59,8 @@ def load_library():
     if _lib is not None:
         return _lib
     from . import build as _b
-    path = _b.build()
+    # MCS_DEBUG_BOUNDS=1 selects the index-checking diagnostic build
+    path = _b.build(debug=os.environ.get("MCS_DEBUG_BOUNDS") == "1")
     lib = ctypes.CDLL(path)
     vp, i32, u32, dbl = ctypes.c_void_p, ctypes.c_int32, ctypes.c_uint32, ctypes.c_double
     gp, rp = ctypes.POINTER(_Graph), ctypes.POINTER(_Result)
@@ -84,6 +85,10 @@ def load_library():
     lib.mcs_set_max_warps.restype = ctypes.c_int
     lib.mcs_last_stats.argtypes = [vp, ctypes.POINTER(ctypes.c_double), ctypes.c_int]
     lib.mcs_last_stats.restype = ctypes.c_int
+    lib.mcs_bench_popc.argtypes = [vp, ctypes.POINTER(ctypes.c_double)]
+    lib.mcs_bench_popc.restype = ctypes.c_int
+    lib.mcs_error_detail.argtypes = []
+    lib.mcs_error_detail.restype = ctypes.c_char_p
     lib.mcs_strerror.argtypes = [ctypes.c_int]
     lib.mcs_strerror.restype = ctypes.c_char_p
     _lib = lib
@@ -158,10 +163,21 @@ class Solver:
             raise ValueError(self.strerror(rc))
 
     def last_stats(self) -> dict:
-        buf = (ctypes.c_double * 8)()
-        self.lib.mcs_last_stats(self.ctx, buf, 8)
+        buf = (ctypes.c_double * 15)()
+        self.lib.mcs_last_stats(self.ctx, buf, 15)
         return dict(kernel_us=buf[0], nodes=buf[1], donated=buf[2], stolen=buf[3],
-                    spilled=buf[4], warps=buf[5], h2d_bytes=buf[6], d2h_bytes=buf[7])
+                    spilled=buf[4], warps=buf[5], h2d_bytes=buf[6], d2h_bytes=buf[7],
+                    class_visits=buf[8], pruned=buf[9], busy_cycles=buf[10],
+                    idle_cycles=buf[11], dbg_count=buf[12], dbg_code=buf[13],
+                    dbg_line=buf[14])
+
+    def bench_popc(self) -> float:
+        """Measured device-wide 32-bit popcount rate (per second)."""
+        out = ctypes.c_double(0)
+        rc = self.lib.mcs_bench_popc(self.ctx, ctypes.byref(out))
+        if rc:
+            raise RuntimeError(self.strerror(rc))
+        return out.value
 
     def strerror(self, code: int) -> str:
         return self.lib.mcs_strerror(int(code)).decode()
@@ -196,7 +212,8 @@ class Solver:
             flags |= MCS_DIRECTED
         rc = self.lib.mcs_solve_batch(self.ctx, Gs, Hs, n, flags, float(timeout_s), Rs)
         if rc < 0 and rc not in (MCS_ERR_ARG,):
-            raise RuntimeError(f"mcs_solve_batch: {self.strerror(rc)} ({rc})")
+            raise RuntimeError(f"mcs_solve_batch: {self.strerror(rc)} ({rc}): "
+                               f"{self.lib.mcs_error_detail().decode()}")
         out = []
         for i in range(n):
             r = Rs[i]

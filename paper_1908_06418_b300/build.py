@@ -9,6 +9,7 @@ import sys
 HERE = os.path.dirname(os.path.abspath(__file__))
 CSRC = os.path.join(HERE, "csrc")
 LIB = os.path.join(HERE, "libmcs.so")
+LIB_DEBUG = os.path.join(HERE, "libmcs_debug_bounds.so")
 SOURCES = ["mcs_kernels.cu", "mcs_api.cu"]
 HEADERS = ["mcs_internal.cuh", os.path.join("..", "..", "include", "mcs.h")]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
@@ -21,34 +22,39 @@ def nvcc():
     return "nvcc"
 
 
-def _stale() -> bool:
-    if not os.path.exists(LIB):
+def _stale(lib: str) -> bool:
+    if not os.path.exists(lib):
         return True
-    t = os.path.getmtime(LIB)
+    t = os.path.getmtime(lib)
     deps = [os.path.join(CSRC, s) for s in SOURCES + HEADERS] + [os.path.abspath(__file__)]
     return any(os.path.getmtime(d) > t for d in deps if os.path.exists(d))
 
 
-def build(force: bool = False, verbose: bool = False, extra=None) -> str:
-    if not force and not _stale():
-        return LIB
+def build(force: bool = False, verbose: bool = False, extra=None, debug: bool = False) -> str:
+    """debug=True builds the MCS_DEBUG_BOUNDS variant (index checks that record
+    violations instead of faulting) as libmcs_debug_bounds.so."""
+    lib = LIB_DEBUG if debug else LIB
+    if not force and not _stale(lib):
+        return lib
     objs = []
     flags = ["-O3", "-std=c++17", "-lineinfo", "-Xcompiler", "-fPIC", *ARCH,
              "--expt-relaxed-constexpr"]
     if verbose:
         flags += ["-Xptxas", "-v"]
     flags += list(extra or [])
-    build_dir = os.path.join(HERE, "_build")
+    if debug:
+        flags += ["-DMCS_DEBUG_BOUNDS"]
+    build_dir = os.path.join(HERE, "_build", "debug" if debug else "release")
     os.makedirs(build_dir, exist_ok=True)
     for s in SOURCES:
         o = os.path.join(build_dir, s.replace(".cu", ".o"))
         subprocess.check_call([nvcc(), "-c", os.path.join(CSRC, s), "-o", o, *flags])
         objs.append(o)
-    tmp = LIB + ".tmp"
+    tmp = lib + ".tmp"
     subprocess.check_call([nvcc(), "-shared", *ARCH, *objs, "-o", tmp, "-lcudart"])
-    os.replace(tmp, LIB)
-    return LIB
+    os.replace(tmp, lib)
+    return lib
 
 
 if __name__ == "__main__":
-    print(build(force=True, verbose="-v" in sys.argv))
+    print(build(force=True, verbose="-v" in sys.argv, debug="--debug" in sys.argv))

@@ -46,18 +46,22 @@ struct mcs_ctx {
     uint8_t* d_out = nullptr; size_t d_out_cap = 0;
     uint8_t* h_out = nullptr; size_t h_out_cap = 0;
     cudaEvent_t ev0 = nullptr, ev1 = nullptr;
-    double stats[8] = {0, 0, 0, 0, 0, 0, 0, 0};
+    double stats[15] = {0};
     bool ev_pending = false;       // ev0/ev1 recorded by a device call, not yet read
     Control h_ctl;
 };
 
 namespace {
 
-int cuda_fail(cudaError_t e) {
+thread_local char g_detail[256] = "";
+
+int cuda_fail(cudaError_t e, const char* what, int line) {
+    snprintf(g_detail, sizeof(g_detail), "%s (%d) at mcs_api.cu:%d: %s", cudaGetErrorName(e), (int)e,
+             line, what);
     if (e == cudaErrorMemoryAllocation) return MCS_ERR_NOMEM;
     return MCS_ERR_CUDA;
 }
-#define CK(x) do { cudaError_t _e = (x); if (_e != cudaSuccess) return cuda_fail(_e); } while (0)
+#define CK(x) do { cudaError_t _e = (x); if (_e != cudaSuccess) return cuda_fail(_e, #x, __LINE__); } while (0)
 
 size_t align16(size_t x) { return (x + 15) & ~(size_t)15; }
 
@@ -113,9 +117,10 @@ int ensure_pairs(mcs_ctx* c, int npairs) {
     return 0;
 }
 
-int ensure_warps(mcs_ctx* c, int warps) {
+int ensure_ring(mcs_ctx* c, int warps, int npairs) {
+    // the roots of every pair + at most one outstanding ticket per warp, with slack
     uint32_t q = 1024;
-    while (q < (uint32_t)(4 * warps)) q <<= 1;
+    while (q < (uint32_t)(4 * warps + npairs)) q <<= 1;
     if (q > c->qcap) {
         cudaFree(c->queue); cudaFree(c->qseq);
         c->queue = nullptr; c->qseq = nullptr; c->qcap = 0;
@@ -150,7 +155,7 @@ int run_device(mcs_ctx* c, int npairs, const int32_t* d_n, const int64_t* d_adj_
     int rc = launch_shape(c, directed, &blocks, &warps, &wsmem);
     if (rc) return rc;
     if ((rc = ensure_pairs(c, npairs))) return rc;
-    if ((rc = ensure_warps(c, blocks * c->warps_per_block))) return rc;
+    if ((rc = ensure_ring(c, blocks * c->warps_per_block, npairs))) return rc;
 
     PackParams pp;
     memset(&pp, 0, sizeof(pp));
@@ -170,8 +175,10 @@ int run_device(mcs_ctx* c, int npairs, const int32_t* d_n, const int64_t* d_adj_
     pp.out_map = (flags & MCS_NO_MAPPING) ? nullptr : d_map;
     pp.out_usec = d_usec;
     pp.ctl = c->ctl;
+    pp.queue = c->queue;
     pp.qseq = c->qseq;
     pp.qcap = c->qcap;
+    pp.order = d_order;
     CK(launch_pack(pp, s));
 
     double tmo = timeout_s > 0 ? std::min(timeout_s, 3600.0) : 3600.0;
@@ -282,9 +289,21 @@ int mcs_last_stats(mcs_ctx* c, double* out, int n) {
     if (c->ev_pending && cudaEventQuery(c->ev1) == cudaSuccess) {
         float ms = 0.f;
         if (cudaEventElapsedTime(&ms, c->ev0, c->ev1) == cudaSuccess) c->stats[0] = ms * 1e3;
+        if (cudaMemcpy(&c->h_ctl, c->ctl, sizeof(Control), cudaMemcpyDeviceToHost) == cudaSuccess) {
+            c->stats[2] = (double)c->h_ctl.donated;
+            c->stats[3] = (double)c->h_ctl.stolen;
+            c->stats[4] = (double)c->h_ctl.spilled;
+            c->stats[8] = (double)c->h_ctl.class_visits;
+            c->stats[9] = (double)c->h_ctl.pruned;
+            c->stats[10] = (double)c->h_ctl.busy_cycles;
+            c->stats[11] = (double)c->h_ctl.idle_cycles;
+            c->stats[12] = (double)c->h_ctl.dbg_count;
+            c->stats[13] = (double)c->h_ctl.dbg_code;
+            c->stats[14] = (double)c->h_ctl.dbg_line;
+        }
         c->ev_pending = false;
     }
-    int k = std::min(n, 8);
+    int k = std::min(n, 15);
     for (int i = 0; i < k; ++i) out[i] = c->stats[i];
     return k;
 }
@@ -399,6 +418,13 @@ int mcs_solve_batch(mcs_ctx* c, const mcs_graph* G, const mcs_graph* H, int32_t 
         c->stats[2] = (double)c->h_ctl.donated;
         c->stats[3] = (double)c->h_ctl.stolen;
         c->stats[4] = (double)c->h_ctl.spilled;
+        c->stats[8] = (double)c->h_ctl.class_visits;
+        c->stats[9] = (double)c->h_ctl.pruned;
+        c->stats[10] = (double)c->h_ctl.busy_cycles;
+        c->stats[11] = (double)c->h_ctl.idle_cycles;
+        c->stats[12] = (double)c->h_ctl.dbg_count;
+        c->stats[13] = (double)c->h_ctl.dbg_code;
+        c->stats[14] = (double)c->h_ctl.dbg_line;
         c->stats[6] = (double)L.total;
         c->stats[7] = (double)(copy_bytes + sizeof(Control));
         c->ev_pending = false;
@@ -459,6 +485,30 @@ int mcs_poll(mcs_ctx* c, uint64_t ticket, mcs_result* out) {
     (void)c; (void)ticket; (void)out;
     return MCS_ERR_UNSUPPORTED;
 }
+
+int mcs_bench_popc(mcs_ctx* c, double* popc_per_s) {
+    if (!c || !popc_per_s) return MCS_ERR_ARG;
+    if (cudaSetDevice(c->device) != cudaSuccess) return MCS_ERR_CUDA;
+    unsigned long long* d = nullptr;
+    CK(cudaMalloc((void**)&d, 16));
+    const int blocks = c->sms * 8, iters = 1 << 16;
+    int rc = 0;
+    float ms = 0.f;
+    for (int rep = 0; rep < 2 && rc == 0; ++rep) {      // the first pass warms up
+        if (cudaEventRecord(c->ev0, c->stream) != cudaSuccess ||
+            launch_popc_bench(d, blocks, iters, c->stream) != cudaSuccess ||
+            cudaEventRecord(c->ev1, c->stream) != cudaSuccess ||
+            cudaStreamSynchronize(c->stream) != cudaSuccess ||
+            cudaEventElapsedTime(&ms, c->ev0, c->ev1) != cudaSuccess)
+            rc = MCS_ERR_CUDA;
+    }
+    cudaFree(d);
+    if (rc) return rc;
+    *popc_per_s = (double)blocks * 256.0 * 8.0 * (double)iters / (ms * 1e-3);
+    return 0;
+}
+
+const char* mcs_error_detail(void) { return g_detail; }
 
 const char* mcs_strerror(int code) {
     switch (code) {

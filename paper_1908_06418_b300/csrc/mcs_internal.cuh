@@ -60,18 +60,21 @@ static_assert(sizeof(Task) % 16 == 0, "task slots must stay 16-byte aligned");
 
 // Fields that different warps poll or update sit on separate 128-byte lines.
 struct alignas(128) Control {
-    u64 q_head, q_tail;            // task ring counters (idle warps poll these)
+    u64 q_head, q_tail;            // ticket counters of the task ring
     u64 pad0[14];
-    int32_t hungry;                // warps waiting for work (busy warps poll this)
-    int32_t pad1[31];
-    int32_t next_pair;             // cursor into the pair order
     int32_t remaining;             // pairs not finalised
     int32_t error;                 // MCS_ERR_DEVICE_STALL if a bounded wait expired
-    int32_t pad2;
-    u64 last_progress;             // globaltimer ns of the last pair start/finish/task move
-    u64 pad3[13];
-    u64 donated, stolen, spilled;  // statistics
-    u64 pad4[13];
+    u64 last_progress;             // globaltimer ns of the last pair start/finish/donation
+    u64 pad1[14];
+    u64 donated, stolen, spilled;  // statistics (summed at warp exit)
+    u64 class_visits;              // classes read by node expansions (algorithmic work units)
+    u64 pruned;                    // children cut by the bound at creation
+    u64 busy_cycles, idle_cycles;  // per-warp SM cycles with / waiting for work
+    u64 pad2[9];
+    // MCS_DEBUG_BOUNDS builds only: first index violation (code, value, source
+    // line) and the number of violations; the offending access is skipped
+    u64 dbg_code, dbg_val, dbg_line, dbg_count;
+    u64 pad3[12];
 };
 static_assert(sizeof(Control) == 512, "one 128-byte line per group of fields");
 
@@ -90,7 +93,7 @@ struct SearchParams {
     uint32_t qcap;                 // power of two
     int32_t stack_smem;            // class entries per warp kept in shared memory
     int32_t warp_smem_bytes;
-    int32_t max_warps;             // warps allowed to work (others exit at once)
+    int32_t max_warps;             // warps that take part (others exit at once)
     ulonglong2* gstack;            // per-warp overflow of the class stack
     const uint8_t* rank;           // learned order: [npairs][kMaxN][kMaxN] rank of u for v, or null
     // outputs
@@ -118,8 +121,10 @@ struct PackParams {
     int16_t* out_map;
     float* out_usec;
     Control* ctl;
+    Task* queue;
     u64* qseq;
     uint32_t qcap;
+    const int32_t* order;          // processing order of the pairs (may be null)
 };
 
 // Per-warp shared memory layout (bytes from the warp's base).
@@ -140,4 +145,5 @@ cudaError_t launch_pack(const PackParams& p, cudaStream_t s);
 cudaError_t launch_search(const SearchParams& p, int blocks, int warps_per_block,
                           bool directed, cudaStream_t s);
 int search_max_blocks_per_sm(int warps_per_block, int smem_per_block, bool directed);
+cudaError_t launch_popc_bench(unsigned long long* out, int blocks, int iters, cudaStream_t s);
 }

@@ -37,6 +37,22 @@ __device__ __forceinline__ unsigned lanemask_lt() {
 template <typename T>
 __device__ __forceinline__ T vload(const T* p) { return *(volatile const T*)p; }
 
+// Index checks of the MCS_DEBUG_BOUNDS build: a violation is recorded in the
+// Control block (first code / value / line, plus a count) and the caller
+// skips or clamps the access, so a bad index never becomes a memory fault.
+#ifdef MCS_DEBUG_BOUNDS
+__device__ __noinline__ void dbg_fail(Control* c, int code, long long val, int line) {
+    if (atomicAdd(&c->dbg_count, 1ull) == 0) {
+        c->dbg_code = (u64)code;
+        c->dbg_val = (u64)val;
+        c->dbg_line = (u64)line;
+    }
+}
+#define DBG_OK(ctl, cond, code, val) ((cond) ? true : (dbg_fail((ctl), (code), (long long)(val), __LINE__), false))
+#else
+#define DBG_OK(ctl, cond, code, val) (true)
+#endif
+
 // Loads that bypass L1: task slots are written by other SMs.
 __device__ __forceinline__ ulonglong2 ld_cg(const ulonglong2* p) {
     ulonglong2 r;
@@ -155,18 +171,30 @@ __global__ void pack_kernel(PackParams P) {
     const int lane = threadIdx.x & 31;
     const int wib = threadIdx.x >> 5;
     const int p = blockIdx.x * (blockDim.x >> 5) + wib;
-    // ring sequence numbers: slot i is free for ticket i
-    for (uint32_t i = blockIdx.x * blockDim.x + threadIdx.x; i < P.qcap; i += gridDim.x * blockDim.x)
-        P.qseq[i] = i;
+    // Ring: tickets 0 .. npairs-1 are the pair roots, published up front in
+    // processing order; every other slot i is free for ticket i.
+    for (uint32_t i = blockIdx.x * blockDim.x + threadIdx.x; i < P.qcap; i += gridDim.x * blockDim.x) {
+        if ((int)i < P.npairs) {
+            Task* t = P.queue + i;
+            t->h.pair = P.order ? P.order[i] : (int)i;
+            t->h.flags = kTaskFresh;
+            t->h.depth = 0;
+            t->h.C = 0;
+            P.qseq[i] = (u64)i + 1;
+        } else {
+            P.qseq[i] = i;
+        }
+    }
     if (blockIdx.x == 0 && threadIdx.x == 0) {
         Control* c = P.ctl;
-        c->q_head = c->q_tail = 0;
-        c->hungry = 0;
-        c->next_pair = 0;
+        c->q_head = 0;
+        c->q_tail = (u64)P.npairs;
         c->remaining = P.npairs;
         c->error = 0;
         c->last_progress = gtimer();
-        c->donated = c->stolen = c->spilled = 0;
+        c->donated = c->stolen = c->spilled = c->class_visits = c->pruned = 0;
+        c->busy_cycles = c->idle_cycles = 0;
+        c->dbg_code = c->dbg_val = c->dbg_line = c->dbg_count = 0;
     }
     if (p >= P.npairs) return;
     const bool directed = (P.flags & MCS_DIRECTED) != 0;
@@ -281,7 +309,15 @@ struct Stack {
     ulonglong2* sm;          // shared part
     ulonglong2* gm;          // global overflow part
     int S;
+#ifdef MCS_DEBUG_BOUNDS
+    Control* ctl;
+    __device__ __forceinline__ ulonglong2* at(int p) const {
+        if (!DBG_OK(ctl, p >= 0 && p < kStackMax, 1, p)) p = 0;
+        return p < S ? sm + p : gm + (p - S);
+    }
+#else
     __device__ __forceinline__ ulonglong2* at(int p) const { return p < S ? sm + p : gm + (p - S); }
+#endif
 };
 
 // Result of scanning a level's classes (node entry): Eq. 1 sum and the class
@@ -337,9 +373,28 @@ __device__ __forceinline__ bool wait_seq(const u64* seq, u64 want) {
 template <bool DIR>
 __device__ void write_best(const SearchParams& P, int pair, const WarpSmem& w, int d, int v, int u,
                            int lane) {
+    if (!DBG_OK(P.ctl, d + 1 < kLevels && pair >= 0 && pair < P.npairs, 6, d)) return;
     uint16_t* slot = P.best + ((size_t)pair * kLevels + (d + 1)) * kMaxN;
     for (int i = lane; i < d; i += 32) slot[i] = (uint16_t)((w.Mg[i] << 8) | w.Mh[i]);
     if (lane == 0) slot[d] = (uint16_t)((v << 8) | u);
+}
+
+// Posts `count` exit tokens (pair = -1) at the tail of the ring: every warp
+// waiting on a ticket at or beyond the tail finds one and leaves the kernel.
+__device__ void post_exit_tokens(const SearchParams& P, int count, int lane) {
+    u64 t0 = 0;
+    if (lane == 0) t0 = atomicAdd(&P.ctl->q_tail, (u64)count);
+    t0 = shfl64(t0, 0);
+    bool ok = true;
+    for (int i = lane; i < count; i += 32) {
+        const u64 t = t0 + i;
+        Task* dst = P.queue + (t & (P.qcap - 1));
+        if (!wait_seq(P.qseq + (t & (P.qcap - 1)), t)) { ok = false; continue; }
+        dst->h.pair = -1;
+        __threadfence();
+        P.qseq[t & (P.qcap - 1)] = t + 1;
+    }
+    if (!__all_sync(FULL, ok) && lane == 0) atomicCAS(&P.ctl->error, 0, MCS_ERR_DEVICE_STALL);
 }
 
 // Finish the pair: write size, status, nodes and the mapping (original numbers).
@@ -347,15 +402,24 @@ __device__ void finalize_pair(const SearchParams& P, int pair, int lane) {
     __threadfence();
     PairState& ps = P.state[pair];
     const PairGraph& pg = P.graphs[pair];
-    int status = vload(&ps.status);
-    int k = 0;
-    if (status == MCS_PENDING) {
+    // read by lane 0 and broadcast (see the note at task install)
+    int status = 0, k = 0, ab = 0;
+    if (lane == 0) {
+        status = vload(&ps.status);
         k = vload(&ps.inc);
-        status = vload(&ps.abort) ? MCS_TIMEOUT : MCS_OK;
+        ab = vload(&ps.abort);
+    }
+    status = __shfl_sync(FULL, status, 0);
+    k = __shfl_sync(FULL, k, 0);
+    ab = __shfl_sync(FULL, ab, 0);
+    if (status == MCS_PENDING) {
+        if (!DBG_OK(P.ctl, k >= 0 && k < kLevels, 7, k)) k = 0;
+        status = ab ? MCS_TIMEOUT : MCS_OK;
         if (P.out_map) {
             const uint16_t* slot = P.best + ((size_t)pair * kLevels + k) * kMaxN;
             for (int i = lane; i < k; i += 32) {
                 uint16_t e = vload(slot + i);
+                if (!DBG_OK(P.ctl, (e >> 8) < kMaxN && (e & 0xff) < kMaxN, 8, e)) continue;
                 int g = pg.permG[e >> 8], h = pg.permH[e & 0xff];
                 P.out_map[(size_t)pair * kMaxN + g] = (int16_t)h;
             }
@@ -363,6 +427,7 @@ __device__ void finalize_pair(const SearchParams& P, int pair, int lane) {
     } else {
         k = 0;
     }
+    int last = 0;
     if (lane == 0) {
         u64 now = gtimer();
         if (P.out_size) P.out_size[pair] = k;
@@ -373,9 +438,11 @@ __device__ void finalize_pair(const SearchParams& P, int pair, int lane) {
         if (P.out_status) P.out_status[pair] = status;
         ps.status = status;
         __threadfence();
-        atomicSub(&P.ctl->remaining, 1);
+        last = atomicSub(&P.ctl->remaining, 1) == 1;
         atomicMax(&P.ctl->last_progress, now);
     }
+    last = __shfl_sync(FULL, last, 0);
+    if (last) post_exit_tokens(P, P.max_warps, lane);
     __syncwarp();
 }
 
@@ -393,8 +460,19 @@ __device__ __forceinline__ void end_task(const SearchParams& P, int pair, u64& n
     if (last) finalize_pair(P, pair, lane);
 }
 
+__device__ __forceinline__ void load_level(const WarpSmem& w, int d, Top& t) {
+    if (d < 0 || d >= kLevels) d = 0;   // unreachable: callers test t.d >= d0 >= 0, depth <= 64
+    u64 inf = w.info[d];
+    t.rrem = w.rrem[d];
+    t.base = (int)(inf & 0xffff);
+    t.C = (int)((inf >> 16) & 0xff);
+    t.v = (int)((inf >> 24) & 0xff);
+    t.flags = (int)((inf >> 32) & 0xff);
+    t.bound = (int)((inf >> 40) & 0xff);
+}
+
 template <bool DIR>
-__global__ void __launch_bounds__(256) search_kernel(SearchParams P) {
+__global__ void __launch_bounds__(256, 3) search_kernel(SearchParams P) {
     extern __shared__ __align__(16) unsigned char smem[];
     const int lane = threadIdx.x & 31;
     const int wib = threadIdx.x >> 5;
@@ -415,74 +493,71 @@ __global__ void __launch_bounds__(256) search_kernel(SearchParams P) {
     st.sm = w.cls;
     st.S = P.stack_smem;
     st.gm = P.gstack + (size_t)gw * (size_t)(kStackMax > P.stack_smem ? kStackMax - P.stack_smem : 0);
+#ifdef MCS_DEBUG_BOUNDS
+    st.ctl = P.ctl;
+#endif
 
     Control* ctl = P.ctl;
     const bool level_prune = (P.flags & MCS_NO_LEVEL_PRUNE) == 0;
+    const u64 qmask = P.qcap - 1;
     int cur_pair = -1;
     u64 nodes = 0;
     unsigned tick = 0;
-    u64 spilled = 0;
+    u64 spilled = 0, cvisits = 0, pruned = 0, donated = 0, stolen = 0;
+    long long busy_cyc = 0, idle_cyc = 0;
 
     while (true) {
         // ------------------------------------------------------------------
-        // acquire work: a donated task, else the next pair's root
+        // acquire work: take the next ticket of the ring and sleep on that
+        // slot until it is published (pair roots are published up front in
+        // processing order; donations and exit tokens follow).
         // ------------------------------------------------------------------
-        int pair = -1;
-        Top t;
-        int d0 = 0;
-        bool fresh = false;
-        bool hungry = false;
-        int got = 0;          // 1 task, 2 root, -1 exit
+        long long c_idle = clock64();
+        int got = 0;          // 1 task, -1 exit
         u64 qh = 0;
-        for (int it = 0; got == 0; ++it) {
-            if (lane == 0) {
-                u64 h = vload(&ctl->q_head);
-                u64 tl = vload(&ctl->q_tail);
-                if (h < tl && atomicCAS(&ctl->q_head, h, h + 1) == h) { got = 1; qh = h; }
-                if (!got) {
-                    int np = vload(&ctl->next_pair);
-                    if (np < P.npairs) {
-                        int k = atomicAdd(&ctl->next_pair, 1);
-                        if (k < P.npairs) { got = 2; pair = P.order ? P.order[k] : k; }
+        if (lane == 0) {
+            qh = atomicAdd(&ctl->q_head, 1ull);
+            const u64* seq = P.qseq + (qh & qmask);
+            for (int it = 0; got == 0; ++it) {
+                if (vload(seq) == qh + 1) { got = 1; break; }
+                if ((it & 63) == 63) {
+                    if (vload(&ctl->error) != 0) { got = -1; break; }
+                    u64 now = gtimer(), lp = vload(&ctl->last_progress);
+                    if (now > lp && now - lp > P.stall_ns) {
+                        atomicCAS(&ctl->error, 0, MCS_ERR_DEVICE_STALL);
+                        got = -1;
+                        break;
                     }
                 }
-                if (!got) {
-                    if (vload(&ctl->remaining) <= 0 || vload(&ctl->error) != 0) got = -1;
-                    else {
-                        u64 now = gtimer();
-                        u64 lp = vload(&ctl->last_progress);
-                        if (now > lp && now - lp > P.stall_ns) { atomicCAS(&ctl->error, 0, MCS_ERR_DEVICE_STALL); got = -1; }
-                    }
-                }
-            }
-            got = __shfl_sync(FULL, got, 0);
-            if (got == 0) {
-                if (!hungry) { if (lane == 0) atomicAdd(&ctl->hungry, 1); hungry = true; }
-                // exponential backoff, 0.25 .. 8 us: thousands of idle warps must
-                // not saturate the L2 slice that holds the ring counters
-                __nanosleep(256u << min(it, 5));
+                __nanosleep(128u << min(it >> 2, 6));     // 0.13 .. 8 us
             }
         }
-        if (hungry && lane == 0) atomicSub(&ctl->hungry, 1);
-        if (got < 0) break;
-        pair = __shfl_sync(FULL, pair, 0);
+        got = __shfl_sync(FULL, got, 0);
         qh = shfl64(qh, 0);
-
-        const Task* task = nullptr;
-        if (got == 1) {
-            task = P.queue + (qh & (P.qcap - 1));
-            int okw = 1;
-            if (lane == 0) okw = wait_seq(P.qseq + (qh & (P.qcap - 1)), qh + 1);
-            okw = __shfl_sync(FULL, okw, 0);
-            if (!okw) { if (lane == 0) atomicCAS(&ctl->error, 0, MCS_ERR_DEVICE_STALL); break; }
-            __threadfence();
-            pair = vload(&task->h.pair);
+        if (got < 0) break;
+        __threadfence();
+        const Task* task = P.queue + (qh & qmask);
+        int pair = 0, tflags = 0;
+        if (lane == 0) { pair = vload(&task->h.pair); tflags = vload(&task->h.flags); }
+        pair = __shfl_sync(FULL, pair, 0);
+        tflags = __shfl_sync(FULL, tflags, 0);
+        if (!DBG_OK(ctl, pair < P.npairs, 2, pair)) pair = -1;
+        if (pair < 0) {                                   // exit token
+            __syncwarp();
+            if (lane == 0) P.qseq[qh & qmask] = qh + P.qcap;
+            break;
         }
+        Top t;
+        const bool fresh = (tflags & kTaskFresh) != 0;
         PairState& ps = P.state[pair];
         const PairGraph& pg = P.graphs[pair];
-        if (got == 2) {
-            if (vload(&ps.status) != MCS_PENDING) {       // malformed input: report and skip
-                if (lane == 0) ps.open = 0;
+        int pstat = 0;
+        if (lane == 0) pstat = vload(&ps.status);
+        pstat = __shfl_sync(FULL, pstat, 0);
+        if (fresh) {
+            if (pstat != MCS_PENDING) {                   // malformed input: report and skip
+                __syncwarp();
+                if (lane == 0) { P.qseq[qh & qmask] = qh + P.qcap; ps.open = 0; }
                 finalize_pair(P, pair, lane);
                 continue;
             }
@@ -502,40 +577,63 @@ __global__ void __launch_bounds__(256) search_kernel(SearchParams P) {
             }
             cur_pair = pair;
         }
-        if (got == 1) {
-            t.d = vload(&task->h.depth);
-            t.C = vload(&task->h.C);
-            t.v = vload(&task->h.v);
-            t.rrem = vload(&task->h.rrem);
-            t.flags = vload(&task->h.flags);
-            t.bound = vload(&task->h.bound);
+        if (!fresh) {
+            int hd4[4] = {0, 0, 0, 0};
+            u64 rr = 0;
+            if (lane == 0) {
+                hd4[0] = vload(&task->h.depth);
+                hd4[1] = vload(&task->h.C);
+                hd4[2] = vload(&task->h.v);
+                hd4[3] = vload(&task->h.bound);
+                rr = vload(&task->h.rrem);
+            }
+            t.d = __shfl_sync(FULL, hd4[0], 0);
+            t.C = __shfl_sync(FULL, hd4[1], 0);
+            t.v = __shfl_sync(FULL, hd4[2], 0);
+            t.bound = __shfl_sync(FULL, hd4[3], 0);
+            t.rrem = shfl64(rr, 0);
+            t.flags = tflags;
+            if (!DBG_OK(ctl, t.C >= 0 && t.C <= kMaxN, 3, t.C)) t.C = 0;
+            if (!DBG_OK(ctl, t.d >= 0 && t.d < kMaxN, 4, t.d)) t.d = 0;
             for (int i = lane; i < t.d; i += 32) { w.Mg[i] = ld_cg(&task->Mg[i]); w.Mh[i] = ld_cg(&task->Mh[i]); }
             for (int i = lane; i < t.C; i += 32) *st.at(i) = ld_cg(&task->cls[i]);
-            __syncwarp();
-            if (lane == 0) {
-                __threadfence();
-                P.qseq[qh & (P.qcap - 1)] = qh + P.qcap;      // release the slot
-                atomicAdd(&ctl->stolen, 1ull);
-                atomicMax(&ctl->last_progress, gtimer());
-            }
-            fresh = false;
+            ++stolen;
         } else {
             t.d = 0;
             t.C = pg.C0;
             for (int i = lane; i < t.C; i += 32) *st.at(i) = pg.root[i];
-            fresh = true;
+        }
+        __syncwarp();
+        if (lane == 0) {
+            __threadfence();
+            P.qseq[qh & qmask] = qh + P.qcap;              // release the slot
         }
         t.base = 0;
-        d0 = t.d;
-        __syncwarp();
-        int inc = vload(&ps.inc);
-        if (vload(&ps.abort)) { end_task(P, pair, nodes, lane); continue; }
+        const int d0 = t.d;
+        // Values other warps may be writing are read by lane 0 only and
+        // broadcast: lanes are not guaranteed to execute a load at the same
+        // time, and a lane-dependent copy would split the warp at the next
+        // branch (and make a later full-warp shuffle illegal).
+        int inc = 0, ab0 = 0;
+        u64 deadline = 0;
+        if (lane == 0) {
+            inc = vload(&ps.inc);
+            ab0 = vload(&ps.abort);
+            deadline = vload(&ps.deadline);
+        }
+        inc = __shfl_sync(FULL, inc, 0);
+        ab0 = __shfl_sync(FULL, ab0, 0);
+        deadline = shfl64(deadline, 0);
+        long long c_busy = clock64();
+        idle_cyc += c_busy - c_idle;
+        if (ab0) { end_task(P, pair, nodes, lane); busy_cyc += clock64() - c_busy; continue; }
         if (fresh) {
             // root node entry (Algorithm 1): bound of Eq. 1, then class choice
             ++nodes;
+            cvisits += t.C;
             Scan sc = scan_level(st, 0, t.C, -1, lane);
             t.bound = sc.sum;
-            if (t.bound <= inc) { end_task(P, pair, nodes, lane); continue; }
+            if (t.bound <= inc) { end_task(P, pair, nodes, lane); busy_cyc += clock64() - c_busy; continue; }
             t.v = sc.key & 63;
             t.rrem = sc.R;
             t.flags = kTaskPending;
@@ -544,26 +642,30 @@ __global__ void __launch_bounds__(256) search_kernel(SearchParams P) {
         // ------------------------------------------------------------------
         // depth-first search over this task's subtree
         // ------------------------------------------------------------------
-        bool aborted = false;
+        // polled values, loaded by lane 0 8 ticks before they are used so
+        // that the L2 round trip overlaps node work
+        int p_inc = 0, p_abort = 0;
+        u64 p_head = 0, p_tail = 0;
         while (t.d >= d0) {
-            if ((++tick % kTick) == 0) {
-                int g_inc = 0, ab = 0, hun = 0;
-                if (lane == 0) {
-                    g_inc = vload(&ps.inc);
-                    ab = vload(&ps.abort);
-                    hun = vload(&ctl->hungry);
-                    if (!ab && (tick % kTimeTick) == 0 && gtimer() > vload(&ps.deadline)) {
-                        ps.abort = 1;
-                        ab = 1;
-                    }
+            ++tick;
+            if ((tick & 15) == 0 && lane == 0) {
+                p_inc = vload(&ps.inc);
+                p_abort = vload(&ps.abort);
+                p_head = vload(&ctl->q_head);
+                p_tail = vload(&ctl->q_tail);
+                if (!p_abort && (tick & 255) == 0 && gtimer() > deadline) {
+                    ps.abort = 1;                      // per-pair time limit
+                    p_abort = 1;
                 }
-                g_inc = __shfl_sync(FULL, g_inc, 0);
-                ab = __shfl_sync(FULL, ab, 0);
-                hun = __shfl_sync(FULL, hun, 0);
+            }
+            if ((tick & 15) == 8) {
+                int g_inc = __shfl_sync(FULL, p_inc, 0);
+                const int ab = __shfl_sync(FULL, p_abort, 0);
+                const u64 hd = shfl64(p_head, 0), tl = shfl64(p_tail, 0);
                 inc = max(inc, g_inc);
-                if (ab) { aborted = true; break; }
+                if (ab) break;
                 // ---- donate the shallowest open level to a waiting warp ----
-                if (hun > 0) {
+                if (hd > tl) {
                     // flush the top cursor so that every level is in shared memory
                     if (lane == 0) {
                         w.rrem[t.d] = t.rrem;
@@ -582,8 +684,6 @@ __global__ void __launch_bounds__(256) search_kernel(SearchParams P) {
                         unsigned m = __ballot_sync(FULL, open);
                         if (m) ds = off + __ffs(m) - 1;
                     }
-                    // keep at least one level of work of our own: a level whose
-                    // subtree we are inside (ds < t.d) or the top with >= 2 candidates
                     if (ds >= 0) {
                         u64 inf = w.info[ds];
                         u64 rr = w.rrem[ds];
@@ -600,22 +700,26 @@ __global__ void __launch_bounds__(256) search_kernel(SearchParams P) {
                             give = rr;
                             gflags = fl & kTaskPending;
                         }
+                        // keep work of our own: a level whose subtree we are
+                        // inside (ds < t.d) or the top with >= 2 candidates
                         bool worth = (ds < t.d) || k >= 2;
                         u64 ticket = 0;
                         int ok = 0;
                         if (worth && lane == 0) {
-                            u64 h = vload(&ctl->q_head), tl = vload(&ctl->q_tail);
-                            if (tl - h < (u64)(P.qcap / 2)) {
-                                atomicAdd(&ps.open, 1);
-                                ticket = atomicAdd(&ctl->q_tail, 1ull);
-                                ok = wait_seq(P.qseq + (ticket & (P.qcap - 1)), ticket) ? 1 : -1;
-                            }
+                            // A warp was waiting when we polled.  Donors that saw
+                            // the same waiter may all donate: the surplus (at most
+                            // one task per busy warp per poll window, far below
+                            // the ring capacity) waits in the ring for the next
+                            // idle warp.
+                            ticket = atomicAdd(&ctl->q_tail, 1ull);
+                            atomicAdd(&ps.open, 1);
+                            ok = wait_seq(P.qseq + (ticket & qmask), ticket) ? 1 : -1;
                         }
                         ok = __shfl_sync(FULL, ok, 0);
-                        if (ok < 0) { if (lane == 0) atomicCAS(&ctl->error, 0, MCS_ERR_DEVICE_STALL); aborted = true; break; }
+                        if (ok < 0) { if (lane == 0) atomicCAS(&ctl->error, 0, MCS_ERR_DEVICE_STALL); break; }
                         if (ok > 0) {
                             ticket = shfl64(ticket, 0);
-                            Task* dst = P.queue + (ticket & (P.qcap - 1));
+                            Task* dst = P.queue + (ticket & qmask);
                             int C = (int)((inf >> 16) & 0xff);
                             int bs = (int)(inf & 0xffff);
                             for (int i = lane; i < C; i += 32) dst->cls[i] = *st.at(bs + i);
@@ -634,11 +738,11 @@ __global__ void __launch_bounds__(256) search_kernel(SearchParams P) {
                             __syncwarp();
                             __threadfence();
                             if (lane == 0) {
-                                P.qseq[ticket & (P.qcap - 1)] = ticket + 1;   // publish
-                                atomicAdd(&ctl->donated, 1ull);
+                                P.qseq[ticket & qmask] = ticket + 1;   // publish
                                 atomicMax(&ctl->last_progress, gtimer());
                             }
                             __syncwarp();
+                            ++donated;
                             if (ds == t.d) {
                                 t.rrem = rr & ~give;
                                 t.flags = fl & ~gflags;
@@ -650,13 +754,7 @@ __global__ void __launch_bounds__(256) search_kernel(SearchParams P) {
             // level prune: every node below this level has bound <= this one
             if (level_prune && t.bound <= inc) {
                 --t.d;
-                if (t.d >= d0) {
-                    u64 inf = w.info[t.d];
-                    t.rrem = w.rrem[t.d];
-                    t.base = (int)(inf & 0xffff); t.C = (int)((inf >> 16) & 0xff);
-                    t.v = (int)((inf >> 24) & 0xff); t.flags = (int)((inf >> 32) & 0xff);
-                    t.bound = (int)((inf >> 40) & 0xff);
-                }
+                if (t.d >= d0) load_level(w, t.d, t);
                 continue;
             }
             if (t.rrem) {
@@ -664,6 +762,7 @@ __global__ void __launch_bounds__(256) search_kernel(SearchParams P) {
                 const int u = __ffsll(t.rrem) - 1;
                 t.rrem &= t.rrem - 1;
                 ++nodes;
+                cvisits += t.C;
                 const int v = t.v;
                 const u64 vb = 1ull << v, ub = 1ull << u;
                 const u64 gB = w.gout[v], hB = w.hout[u];
@@ -722,7 +821,7 @@ __global__ void __launch_bounds__(256) search_kernel(SearchParams P) {
                         inc = old;
                     }
                 }
-                if (dm + sum <= inc) continue;          // child pruned by Eq. 1
+                if (dm + sum <= inc) { ++pruned; continue; }    // child pruned by Eq. 1
                 // descend: compact the child's classes onto the stack
                 const unsigned kmin = __reduce_min_sync(FULL, best);
                 const unsigned win = __ballot_sync(FULL, best == kmin);
@@ -757,6 +856,7 @@ __global__ void __launch_bounds__(256) search_kernel(SearchParams P) {
                     }
                 }
                 if (pos > st.S) spilled += 1;
+                if (!DBG_OK(ctl, pos - cbase <= kMaxN && dm <= kMaxN, 5, (pos - cbase) * 1000 + dm)) pos = cbase;
                 if (lane == 0) {
                     w.Mg[t.d] = (uint8_t)v;
                     w.Mh[t.d] = (uint8_t)u;
@@ -774,6 +874,7 @@ __global__ void __launch_bounds__(256) search_kernel(SearchParams P) {
             } else if (t.flags & kTaskPending) {
                 // ---------------- "v stays unmatched": same M, v leaves its class ----------------
                 ++nodes;
+                cvisits += t.C;
                 Scan sc = scan_level(st, t.base, t.C, t.v, lane);
                 __syncwarp();
                 t.bound = t.d + sc.sum;
@@ -787,19 +888,21 @@ __global__ void __launch_bounds__(256) search_kernel(SearchParams P) {
                 }
             } else {
                 --t.d;
-                if (t.d >= d0) {
-                    u64 inf = w.info[t.d];
-                    t.rrem = w.rrem[t.d];
-                    t.base = (int)(inf & 0xffff); t.C = (int)((inf >> 16) & 0xff);
-                    t.v = (int)((inf >> 24) & 0xff); t.flags = (int)((inf >> 32) & 0xff);
-                    t.bound = (int)((inf >> 40) & 0xff);
-                }
+                if (t.d >= d0) load_level(w, t.d, t);
             }
         }
-        (void)aborted;
         end_task(P, pair, nodes, lane);
+        busy_cyc += clock64() - c_busy;
     }
-    if (lane == 0 && spilled) atomicAdd(&ctl->spilled, spilled);
+    if (lane == 0) {
+        if (spilled) atomicAdd(&ctl->spilled, spilled);
+        if (cvisits) atomicAdd(&ctl->class_visits, cvisits);
+        if (pruned) atomicAdd(&ctl->pruned, pruned);
+        if (donated) atomicAdd(&ctl->donated, donated);
+        if (stolen) atomicAdd(&ctl->stolen, stolen);
+        atomicAdd(&ctl->busy_cycles, (u64)busy_cyc);
+        atomicAdd(&ctl->idle_cycles, (u64)idle_cyc);
+    }
 }
 
 cudaError_t launch_search(const SearchParams& p, int blocks, int warps_per_block, bool directed,
@@ -825,6 +928,28 @@ int search_max_blocks_per_sm(int warps_per_block, int smem_per_block, bool direc
         cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, search_kernel<false>, warps_per_block * 32, smem_per_block);
     }
     return nb;
+}
+
+// ---------------------------------------------------------------------------
+// integer-pipe micro-benchmark: sustained 32-bit population counts per second
+// (the denominator of the search kernel's roofline)
+// ---------------------------------------------------------------------------
+__global__ void popc_bench_kernel(unsigned long long* out, int iters) {
+    unsigned x0 = threadIdx.x * 0x9E3779B9u + blockIdx.x, x1 = x0 ^ 0x55555555u, x2 = x0 * 3u,
+             x3 = x0 + 17u, x4 = ~x0, x5 = x0 >> 3, x6 = x0 << 5, x7 = x0 ^ 0xA5A5A5A5u;
+    for (int i = 0; i < iters; ++i) {
+        // 8 independent popc chains per thread; the xor keeps each chain live
+        x0 ^= __popc(x0) + i; x1 ^= __popc(x1) + i; x2 ^= __popc(x2) + i; x3 ^= __popc(x3) + i;
+        x4 ^= __popc(x4) + i; x5 ^= __popc(x5) + i; x6 ^= __popc(x6) + i; x7 ^= __popc(x7) + i;
+    }
+    unsigned acc = x0 ^ x1 ^ x2 ^ x3 ^ x4 ^ x5 ^ x6 ^ x7;
+    if (acc == 0x12345678u) out[1] = acc;   // practically never; keeps the work observable
+    if (threadIdx.x == 0 && blockIdx.x == 0) out[0] = (unsigned long long)iters;
+}
+
+cudaError_t launch_popc_bench(unsigned long long* out, int blocks, int iters, cudaStream_t s) {
+    popc_bench_kernel<<<blocks, 256, 0, s>>>(out, iters);
+    return cudaGetLastError();
 }
 
 }  // namespace mcsk
