@@ -118,6 +118,42 @@ int mcs_solve_batch_device(mcs_ctx* ctx, int32_t npairs,
                            int32_t* d_size, int32_t* d_status, uint64_t* d_nodes,
                            int16_t* d_map, float* d_usec, void* stream);
 
+/* Limits of mcs_solve_batch_noalloc's fixed scratch. */
+#define MCS_NOALLOC_MAX_PAIRS     256
+#define MCS_NOALLOC_MAX_WARPS     592
+#define MCS_NOALLOC_SCRATCH_BYTES (26u << 20)   /* upper bound of the array, per device */
+
+/* Device-resident batch solve that allocates nothing.  The paper has no
+ * counterpart; this entry point exists for callers that cannot call
+ * cudaMalloc -- for example code running while a stream is being captured
+ * into a CUDA graph, a plug-in whose host framework owns all device memory,
+ * or a latency-critical service that must not enter the allocator.
+ *
+ * Arguments, layouts and results are exactly those of
+ * mcs_solve_batch_device, without the context; `stream` is a cudaStream_t
+ * (NULL = the legacy default stream) and the call does not synchronise.  The
+ * caller still owns every input and output buffer.  All scratch lives in one
+ * file-scope device array of at most MCS_NOALLOC_SCRATCH_BYTES that every
+ * GPU which loads the library holds until the process exits; the call makes
+ * no cudaMalloc/cudaFree and uses no allocating library routine.
+ *
+ * Limits: at most MCS_NOALLOC_MAX_PAIRS pairs per call (more returns
+ * MCS_ERR_ARG and enqueues nothing) and at most MCS_NOALLOC_MAX_WARPS search
+ * warps (one block of 4 warps per SM).
+ *
+ * The first call on a device looks up the array's device address
+ * (cudaGetSymbolAddress, with that device current) and caches it; make that
+ * first call before any stream capture begins.  Every call uses the same
+ * array and overwrites what the previous call left there (the kernels
+ * re-initialise all state they read), so calls whose executions overlap on
+ * the GPU -- on different streams, or from different host threads on one
+ * device -- race and must not be issued. */
+int mcs_solve_batch_noalloc(int32_t npairs, const int32_t* d_n, const int64_t* d_adj_off,
+                            const uint8_t* d_adj, const int64_t* d_lab_off,
+                            const int32_t* d_labels, uint32_t flags, double timeout_s,
+                            int32_t* d_size, int32_t* d_status, uint64_t* d_nodes,
+                            int16_t* d_map, float* d_usec, void* stream);
+
 /* Serving: admit one request; returns a ticket.  The search starts on the
  * device as soon as a slot and device memory are free; requests submitted
  * while others run join them (continuous batching). */

@@ -47,7 +47,8 @@ class _Result(ctypes.Structure):
 
 EXPORTED_SYMBOLS = ["mcs_create", "mcs_destroy", "mcs_solve", "mcs_solve_batch",
                     "mcs_solve_batch_device", "mcs_submit", "mcs_poll", "mcs_set_launch",
-                    "mcs_set_max_warps", "mcs_last_stats", "mcs_bench_popc", "mcs_strerror", "mcs_error_detail"]
+                    "mcs_set_max_warps", "mcs_last_stats", "mcs_bench_popc", "mcs_strerror", "mcs_error_detail",
+                    "mcs_solve_batch_noalloc"]
 
 _lib = None
 
@@ -87,6 +88,9 @@ def load_library():
     lib.mcs_last_stats.restype = ctypes.c_int
     lib.mcs_bench_popc.argtypes = [vp, ctypes.POINTER(ctypes.c_double)]
     lib.mcs_bench_popc.restype = ctypes.c_int
+    lib.mcs_solve_batch_noalloc.argtypes = [i32, vp, vp, vp, vp, vp, u32, dbl,
+                                            vp, vp, vp, vp, vp, vp]
+    lib.mcs_solve_batch_noalloc.restype = ctypes.c_int
     lib.mcs_error_detail.argtypes = []
     lib.mcs_error_detail.restype = ctypes.c_char_p
     lib.mcs_strerror.argtypes = [ctypes.c_int]
