@@ -57,8 +57,9 @@ extern "C" {
 /* flags */
 #define MCS_DIRECTED          0x1u  /* arcs are ordered pairs (4-way class split)      */
 #define MCS_ORDER_PLAIN       0x0u  /* degree order (Section IV-A); the default        */
-#define MCS_ORDER_LEARNED     0x2u  /* candidate order from the ordering network;      */
-                                    /* needs mcs_set_order_model(); exact either way   */
+#define MCS_ORDER_LEARNED     0x2u  /* candidate order from the ordering network      */
+                                    /* (mcs_set_order_model); exact either way; falls  */
+                                    /* back to the degree order without a model        */
 #define MCS_NO_MAPPING        0x4u  /* do not return the mapping                       */
 #define MCS_NO_LEVEL_PRUNE    0x8u  /* diagnostic: do not re-test a level's bound      */
                                     /* before each sibling, so that with one warp the  */
@@ -153,6 +154,47 @@ int mcs_solve_batch_noalloc(int32_t npairs, const int32_t* d_n, const int64_t* d
                             const int32_t* d_labels, uint32_t flags, double timeout_s,
                             int32_t* d_size, int32_t* d_status, uint64_t* d_nodes,
                             int16_t* d_map, float* d_usec, void* stream);
+
+/* ---- branching-order network (learned candidate order) ----------------
+ * A small MLP scores candidate pairs (v, u) from vertex features (degree,
+ * label, a 16-bin histogram of the neighbours' degrees) of v in G and u in H:
+ * 36 inputs (zero-padded to 48) -> 128 -> 128 -> 1 logit, fp16 operands on
+ * the tensor cores with fp32 accumulation.  With MCS_ORDER_LEARNED the solver
+ * numbers vertices by their best score (most promising first) and tries the
+ * candidates u of each chosen v in decreasing score.  This reorders McSplit's
+ * choices only: every candidate is still tried and every bound (Eq. 1) is
+ * still exact, so results stay optimal.  Without a loaded model the degree
+ * order (Section IV-A) is used.
+ * Parameter layout (float32): W1[48][128] (row = input), b1[128],
+ * W2[128][128], b2[128], w3[128], b3[1]; inputs 36..47 of W1 must be 0. */
+#define MCS_ORDER_NPARAMS 22913
+
+/* Loads (copies) a model into the context; resets the optimiser state. */
+int mcs_set_order_model(mcs_ctx* ctx, const float* params, int32_t nparams);
+/* Copies the context's current model out (after training, for instance). */
+int mcs_get_order_model(mcs_ctx* ctx, float* params, int32_t nparams);
+
+/* Evaluates the model on a device-resident batch (layout of
+ * mcs_solve_batch_device) and nrows device rows d_rows[r] = (pair, v, u) in
+ * original vertex ids, labels d_y[r] in {0,1}, weights d_w[r] (or NULL = 1).
+ * Host outputs, each optional: h_scores[nrows] logits; h_loss the mean
+ * weighted binary cross-entropy with logits; h_grad[MCS_ORDER_NPARAMS] its
+ * gradient; h_features[npairs][2][64][18] the vertex features.  Synchronous. */
+int mcs_order_eval(mcs_ctx* ctx, int32_t npairs, const int32_t* d_n, const int64_t* d_adj_off,
+                   const uint8_t* d_adj, const int64_t* d_lab_off, const int32_t* d_labels,
+                   uint32_t flags, int32_t nrows, const int32_t* d_rows, const float* d_y,
+                   const float* d_w, float* h_scores, float* h_loss, float* h_grad,
+                   float* h_features);
+
+/* Trains the loaded model on the device: `steps` Adam steps (lr, beta1 0.9,
+ * beta2 0.999) on mini-batches of `batch` rows drawn with replacement by a
+ * counter-based hash of (seed, step, i).  h_loss_per_step[steps] (optional)
+ * receives each step's mean loss.  Synchronous. */
+int mcs_order_train(mcs_ctx* ctx, int32_t npairs, const int32_t* d_n, const int64_t* d_adj_off,
+                    const uint8_t* d_adj, const int64_t* d_lab_off, const int32_t* d_labels,
+                    uint32_t flags, int32_t nrows, const int32_t* d_rows, const float* d_y,
+                    const float* d_w, int32_t steps, int32_t batch, float lr, uint64_t seed,
+                    float* h_loss_per_step);
 
 /* Serving: admit one request; returns a ticket.  The search starts on the
  * device as soon as a slot and device memory are free; requests submitted

@@ -48,7 +48,10 @@ class _Result(ctypes.Structure):
 EXPORTED_SYMBOLS = ["mcs_create", "mcs_destroy", "mcs_solve", "mcs_solve_batch",
                     "mcs_solve_batch_device", "mcs_submit", "mcs_poll", "mcs_set_launch",
                     "mcs_set_max_warps", "mcs_last_stats", "mcs_bench_popc", "mcs_strerror", "mcs_error_detail",
-                    "mcs_solve_batch_noalloc"]
+                    "mcs_solve_batch_noalloc", "mcs_set_order_model", "mcs_get_order_model",
+                    "mcs_order_eval", "mcs_order_train"]
+
+MCS_ORDER_NPARAMS = 22913
 
 _lib = None
 
@@ -91,6 +94,17 @@ def load_library():
     lib.mcs_solve_batch_noalloc.argtypes = [i32, vp, vp, vp, vp, vp, u32, dbl,
                                             vp, vp, vp, vp, vp, vp]
     lib.mcs_solve_batch_noalloc.restype = ctypes.c_int
+    fp = ctypes.POINTER(ctypes.c_float)
+    lib.mcs_set_order_model.argtypes = [vp, fp, i32]
+    lib.mcs_set_order_model.restype = ctypes.c_int
+    lib.mcs_get_order_model.argtypes = [vp, fp, i32]
+    lib.mcs_get_order_model.restype = ctypes.c_int
+    lib.mcs_order_eval.argtypes = [vp, i32, vp, vp, vp, vp, vp, u32, i32, vp, vp, vp,
+                                   fp, fp, fp, fp]
+    lib.mcs_order_eval.restype = ctypes.c_int
+    lib.mcs_order_train.argtypes = [vp, i32, vp, vp, vp, vp, vp, u32, i32, vp, vp, vp,
+                                    i32, i32, ctypes.c_float, ctypes.c_uint64, fp]
+    lib.mcs_order_train.restype = ctypes.c_int
     lib.mcs_error_detail.argtypes = []
     lib.mcs_error_detail.restype = ctypes.c_char_p
     lib.mcs_strerror.argtypes = [ctypes.c_int]
@@ -232,6 +246,70 @@ class Solver:
         return self.solve_batch([(adjG, adjH, labG, labH)],
                                 flags | (MCS_DIRECTED if directed else 0), timeout_s)[0]
 
+    # -- branching-order network -----------------------------------------
+    def set_order_model(self, params: np.ndarray):
+        p = np.ascontiguousarray(params, dtype=np.float32)
+        rc = self.lib.mcs_set_order_model(self.ctx, p.ctypes.data_as(ctypes.POINTER(ctypes.c_float)),
+                                          int(p.size))
+        if rc:
+            raise ValueError(f"mcs_set_order_model: {self.strerror(rc)}")
+
+    def get_order_model(self) -> np.ndarray:
+        p = np.zeros(MCS_ORDER_NPARAMS, np.float32)
+        rc = self.lib.mcs_get_order_model(self.ctx, p.ctypes.data_as(ctypes.POINTER(ctypes.c_float)),
+                                          int(p.size))
+        if rc:
+            raise ValueError(f"mcs_get_order_model: {self.strerror(rc)}")
+        return p
+
+    def order_eval(self, batch: "DeviceBatch", rows=None, y=None, w=None, scores=False,
+                   loss_grad=False, features=False) -> dict:
+        """rows: int32 [R, 3] (pair, v, u) in original ids; y, w: float32 [R]."""
+        import torch
+        fptr = lambda a: a.ctypes.data_as(ctypes.POINTER(ctypes.c_float)) if a is not None else None
+        dev = batch.device
+        d_rows = torch.from_numpy(np.ascontiguousarray(rows, np.int32)).to(dev) if rows is not None else None
+        d_y = torch.from_numpy(np.ascontiguousarray(y, np.float32)).to(dev) if y is not None else None
+        d_w = torch.from_numpy(np.ascontiguousarray(w, np.float32)).to(dev) if w is not None else None
+        R = 0 if rows is None else len(rows)
+        out = {}
+        h_s = np.zeros(max(R, 1), np.float32) if scores else None
+        h_l = np.zeros(1, np.float32) if loss_grad else None
+        h_g = np.zeros(MCS_ORDER_NPARAMS, np.float32) if loss_grad else None
+        h_f = np.zeros((batch.npairs, 2, 64, 18), np.float32) if features else None
+        ptr = _ptr
+        rc = self.lib.mcs_order_eval(self.ctx, batch.npairs, ptr(batch.d_n), ptr(batch.d_adj_off),
+                                     ptr(batch.d_adj), ptr(batch.d_lab_off), ptr(batch.d_labels),
+                                     batch.flags, R, ptr(d_rows), ptr(d_y), ptr(d_w),
+                                     fptr(h_s), fptr(h_l), fptr(h_g), fptr(h_f))
+        if rc:
+            raise RuntimeError(f"mcs_order_eval: {self.strerror(rc)}")
+        if scores:
+            out["scores"] = h_s[:R]
+        if loss_grad:
+            out["loss"] = float(h_l[0])
+            out["grad"] = h_g
+        if features:
+            out["features"] = h_f
+        return out
+
+    def order_train(self, batch: "DeviceBatch", rows, y, w=None, steps=100, batch_size=4096,
+                    lr=1e-3, seed=1) -> np.ndarray:
+        import torch
+        dev = batch.device
+        d_rows = torch.from_numpy(np.ascontiguousarray(rows, np.int32)).to(dev)
+        d_y = torch.from_numpy(np.ascontiguousarray(y, np.float32)).to(dev)
+        d_w = torch.from_numpy(np.ascontiguousarray(w, np.float32)).to(dev) if w is not None else None
+        losses = np.zeros(max(steps, 1), np.float32)
+        rc = self.lib.mcs_order_train(self.ctx, batch.npairs, _ptr(batch.d_n), _ptr(batch.d_adj_off),
+                                      _ptr(batch.d_adj), _ptr(batch.d_lab_off), _ptr(batch.d_labels),
+                                      batch.flags, len(rows), _ptr(d_rows), _ptr(d_y), _ptr(d_w),
+                                      int(steps), int(batch_size), float(lr), int(seed),
+                                      losses.ctypes.data_as(ctypes.POINTER(ctypes.c_float)))
+        if rc:
+            raise RuntimeError(f"mcs_order_train: {self.strerror(rc)}")
+        return losses[:steps]
+
     def solve_batch_device(self, npairs: int, d_n, d_adj_off, d_adj, d_lab_off, d_labels,
                            d_size, d_status, d_nodes, d_map=None, d_usec=None, flags: int = 0,
                            timeout_s: float = 0.0, stream: int = 0) -> int:
@@ -271,3 +349,26 @@ def pack_host(pairs) -> dict:
         adj=np.concatenate(blobs) if blobs else np.zeros(16, np.uint8),
         lab_off=np.asarray(lab_off, np.int64),
         labels=np.concatenate(labs) if labs else None)
+
+
+def _ptr(t):
+    return None if t is None else ctypes.c_void_p(int(t.data_ptr()))
+
+
+class DeviceBatch:
+    """A list of pairs laid out for the device entry points (torch tensors
+    hold the device memory; flags carries MCS_DIRECTED when the pairs are
+    directed)."""
+
+    def __init__(self, pairs, device=0, directed: bool = False):
+        import torch
+        h = pack_host(pairs)
+        self.device = torch.device("cuda", device) if isinstance(device, int) else device
+        self.npairs = len(pairs)
+        self.flags = MCS_DIRECTED if directed else 0
+        self.d_n = torch.from_numpy(h["n"]).to(self.device)
+        self.d_adj_off = torch.from_numpy(h["adj_off"]).to(self.device)
+        self.d_adj = torch.from_numpy(h["adj"]).to(self.device)
+        self.d_lab_off = torch.from_numpy(h["lab_off"]).to(self.device)
+        self.d_labels = (torch.from_numpy(h["labels"]).to(self.device)
+                         if h["labels"] is not None else None)

@@ -20,36 +20,6 @@
 
 using namespace mcsk;
 
-struct mcs_ctx {
-    int device = 0;
-    cudaStream_t stream = nullptr;
-    int sms = 0;
-    int warps_per_block = 4;
-    int blocks_per_sm = 0;        // 0: as many as fit
-    int smem_stack = 256;
-    int max_warps = 0;            // 0: every launched warp
-    // device arenas
-    int pairs_cap = 0;
-    PairGraph* graphs = nullptr;
-    PairState* state = nullptr;
-    uint16_t* best = nullptr;
-    int32_t* order = nullptr;
-    Control* ctl = nullptr;
-    Task* queue = nullptr;
-    u64* qseq = nullptr;
-    uint32_t qcap = 0;
-    ulonglong2* gstack = nullptr;
-    size_t gstack_entries = 0;
-    // host-API staging
-    uint8_t* d_in = nullptr;  size_t d_in_cap = 0;
-    uint8_t* h_in = nullptr;  size_t h_in_cap = 0;
-    uint8_t* d_out = nullptr; size_t d_out_cap = 0;
-    uint8_t* h_out = nullptr; size_t h_out_cap = 0;
-    cudaEvent_t ev0 = nullptr, ev1 = nullptr;
-    double stats[15] = {0};
-    bool ev_pending = false;       // ev0/ev1 recorded by a device call, not yet read
-    Control h_ctl;
-};
 
 namespace {
 
@@ -87,10 +57,10 @@ int grow_host(T*& p, size_t& cap, size_t need) {
     return 0;
 }
 
-int launch_shape(mcs_ctx* c, bool directed, int* blocks, int* warps_total, int* wsmem) {
+int launch_shape(mcs_ctx* c, bool directed, bool learned, int* blocks, int* warps_total, int* wsmem) {
     *wsmem = warp_smem_bytes(c->smem_stack);
     int smem_block = c->warps_per_block * *wsmem;
-    int per_sm = search_max_blocks_per_sm(c->warps_per_block, smem_block, directed);
+    int per_sm = search_max_blocks_per_sm(c->warps_per_block, smem_block, directed, learned);
     if (per_sm <= 0) return MCS_ERR_UNSUPPORTED;
     if (c->blocks_per_sm > 0) per_sm = std::min(per_sm, c->blocks_per_sm);
     *blocks = c->sms * per_sm;
@@ -150,9 +120,20 @@ int run_device(mcs_ctx* c, int npairs, const int32_t* d_n, const int64_t* d_adj_
     if (npairs < 0) return MCS_ERR_ARG;
     if (npairs == 0) return 0;
     const bool directed = (flags & MCS_DIRECTED) != 0;
-    if (flags & MCS_ORDER_LEARNED) return MCS_ERR_UNSUPPORTED;
+    int rc = 0;
+    // learned candidate order: scores of every (v, u), order keys for the
+    // renumbering; without a loaded model the degree order is kept
+    const float* vscore = nullptr;
+    bool learned = false;
+    if (flags & MCS_ORDER_LEARNED) {
+        if ((rc = ensure_pairs(c, npairs))) return rc;
+        rc = mcs_order_prepare(c, npairs, d_n, d_adj_off, d_adj, d_lab_off, d_labels, flags, s, &vscore);
+        if (rc < 0) return rc;
+        learned = (rc == 0);
+        rc = 0;
+    }
     int blocks = 0, warps = 0, wsmem = 0;
-    int rc = launch_shape(c, directed, &blocks, &warps, &wsmem);
+    rc = launch_shape(c, directed, learned, &blocks, &warps, &wsmem);
     if (rc) return rc;
     if ((rc = ensure_pairs(c, npairs))) return rc;
     if ((rc = ensure_ring(c, blocks * c->warps_per_block, npairs))) return rc;
@@ -166,7 +147,7 @@ int run_device(mcs_ctx* c, int npairs, const int32_t* d_n, const int64_t* d_adj_
     pp.adj = d_adj;
     pp.lab_off = d_lab_off;
     pp.labels = d_labels;
-    pp.vscore = nullptr;
+    pp.vscore = vscore;
     pp.graphs = c->graphs;
     pp.state = c->state;
     pp.out_size = d_size;
@@ -180,6 +161,8 @@ int run_device(mcs_ctx* c, int npairs, const int32_t* d_n, const int64_t* d_adj_
     pp.qcap = c->qcap;
     pp.order = d_order;
     CK(launch_pack(pp, s));
+    const uint8_t* rank = nullptr;
+    if (learned && (rc = mcs_order_ranks(c, npairs, s, &rank))) return rc;
 
     double tmo = timeout_s > 0 ? std::min(timeout_s, 3600.0) : 3600.0;
     SearchParams sp;
@@ -200,14 +183,14 @@ int run_device(mcs_ctx* c, int npairs, const int32_t* d_n, const int64_t* d_adj_
     sp.warp_smem_bytes = wsmem;
     sp.max_warps = warps;
     sp.gstack = c->gstack;
-    sp.rank = nullptr;
+    sp.rank = rank;
     sp.out_size = d_size;
     sp.out_status = d_status;
     sp.out_nodes = reinterpret_cast<u64*>(d_nodes);
     sp.out_map = (flags & MCS_NO_MAPPING) ? nullptr : d_map;
     sp.out_usec = d_usec;
     if (timed) CK(cudaEventRecord(c->ev0, s));
-    CK(launch_search(sp, blocks, c->warps_per_block, directed, s));
+    CK(launch_search(sp, blocks, c->warps_per_block, directed, learned, s));
     if (timed) CK(cudaEventRecord(c->ev1, s));
     c->stats[5] = warps;
     return 0;
@@ -256,6 +239,7 @@ void mcs_destroy(mcs_ctx* c) {
     if (!c) return;
     cudaSetDevice(c->device);
     if (c->stream) cudaStreamSynchronize(c->stream);
+    mcs_order_free(c);
     cudaFree(c->graphs); cudaFree(c->state); cudaFree(c->best); cudaFree(c->order);
     cudaFree(c->ctl); cudaFree(c->queue); cudaFree(c->qseq); cudaFree(c->gstack);
     cudaFree(c->d_in); cudaFree(c->d_out);

@@ -139,11 +139,58 @@ inline int warp_smem_bytes(int stack_entries) { return kSmCls + 16 * stack_entri
 
 }  // namespace mcsk
 
+struct MlpState;
+
+// Host-side context behind the opaque mcs_ctx handle of include/mcs.h.
+struct mcs_ctx {
+    typedef mcsk::u64 u64;
+    typedef mcsk::PairGraph PairGraph;
+    typedef mcsk::PairState PairState;
+    typedef mcsk::Control Control;
+    typedef mcsk::Task Task;
+    int device = 0;
+    cudaStream_t stream = nullptr;
+    int sms = 0;
+    int warps_per_block = 4;
+    int blocks_per_sm = 0;        // 0: as many as fit
+    int smem_stack = 256;
+    int max_warps = 0;            // 0: every launched warp
+    // device arenas
+    int pairs_cap = 0;
+    PairGraph* graphs = nullptr;
+    PairState* state = nullptr;
+    uint16_t* best = nullptr;
+    int32_t* order = nullptr;
+    Control* ctl = nullptr;
+    Task* queue = nullptr;
+    u64* qseq = nullptr;
+    uint32_t qcap = 0;
+    ulonglong2* gstack = nullptr;
+    size_t gstack_entries = 0;
+    // host-API staging
+    uint8_t* d_in = nullptr;  size_t d_in_cap = 0;
+    uint8_t* h_in = nullptr;  size_t h_in_cap = 0;
+    uint8_t* d_out = nullptr; size_t d_out_cap = 0;
+    uint8_t* h_out = nullptr; size_t h_out_cap = 0;
+    cudaEvent_t ev0 = nullptr, ev1 = nullptr;
+    double stats[15] = {0};
+    bool ev_pending = false;       // ev0/ev1 recorded by a device call, not yet read
+    Control h_ctl;
+    struct MlpState* mlp = nullptr;   // ordering network (mcs_mlp.cu), created on first use
+};
+
 // kernels.cu entry points used by the host library
 namespace mcsk {
 cudaError_t launch_pack(const PackParams& p, cudaStream_t s);
 cudaError_t launch_search(const SearchParams& p, int blocks, int warps_per_block,
-                          bool directed, cudaStream_t s);
-int search_max_blocks_per_sm(int warps_per_block, int smem_per_block, bool directed);
+                          bool directed, bool learned, cudaStream_t s);
+int search_max_blocks_per_sm(int warps_per_block, int smem_per_block, bool directed, bool learned);
 cudaError_t launch_popc_bench(unsigned long long* out, int blocks, int iters, cudaStream_t s);
 }
+
+// mcs_mlp.cu: learned candidate order
+int mcs_order_prepare(mcs_ctx* c, int npairs, const int32_t* d_n, const int64_t* d_adj_off,
+                      const uint8_t* d_adj, const int64_t* d_lab_off, const int32_t* d_labels,
+                      uint32_t flags, cudaStream_t s, const float** vscore_out);
+int mcs_order_ranks(mcs_ctx* c, int npairs, cudaStream_t s, const uint8_t** rank_out);
+void mcs_order_free(mcs_ctx* c);

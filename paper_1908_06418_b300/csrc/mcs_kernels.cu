@@ -471,7 +471,7 @@ __device__ __forceinline__ void load_level(const WarpSmem& w, int d, Top& t) {
     t.bound = (int)((inf >> 40) & 0xff);
 }
 
-template <bool DIR>
+template <bool DIR, bool LEARNED>
 __global__ void __launch_bounds__(256, 3) search_kernel(SearchParams P) {
     extern __shared__ __align__(16) unsigned char smem[];
     const int lane = threadIdx.x & 31;
@@ -759,8 +759,18 @@ __global__ void __launch_bounds__(256, 3) search_kernel(SearchParams P) {
             }
             if (t.rrem) {
                 // ---------------- child (v, u): filterDomain + Eq. 1 ----------------
-                const int u = __ffsll(t.rrem) - 1;
-                t.rrem &= t.rrem - 1;
+                int u;
+                if (LEARNED) {
+                    // the remaining candidate with the best learned rank for v
+                    const uint8_t* rk = P.rank + ((size_t)pair * kMaxN + t.v) * kMaxN;
+                    const unsigned k0 = ((t.rrem >> lane) & 1ull) ? ((unsigned)__ldg(rk + lane) << 6) | lane : kKeyNone;
+                    const unsigned k1 = ((t.rrem >> (lane + 32)) & 1ull) ? ((unsigned)__ldg(rk + lane + 32) << 6) | (lane + 32) : kKeyNone;
+                    u = (int)(__reduce_min_sync(FULL, min(k0, k1)) & 63u);
+                    t.rrem &= ~(1ull << u);
+                } else {
+                    u = __ffsll(t.rrem) - 1;
+                    t.rrem &= t.rrem - 1;
+                }
                 ++nodes;
                 cvisits += t.C;
                 const int v = t.v;
@@ -905,29 +915,35 @@ __global__ void __launch_bounds__(256, 3) search_kernel(SearchParams P) {
     }
 }
 
-cudaError_t launch_search(const SearchParams& p, int blocks, int warps_per_block, bool directed,
-                          cudaStream_t s) {
-    size_t smem = (size_t)warps_per_block * p.warp_smem_bytes;
-    if (directed) {
-        cudaFuncSetAttribute(search_kernel<true>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-        search_kernel<true><<<blocks, warps_per_block * 32, smem, s>>>(p);
-    } else {
-        cudaFuncSetAttribute(search_kernel<false>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-        search_kernel<false><<<blocks, warps_per_block * 32, smem, s>>>(p);
-    }
+template <bool DIR, bool LEARNED>
+static cudaError_t launch_t(const SearchParams& p, int blocks, int wpb, cudaStream_t s) {
+    size_t smem = (size_t)wpb * p.warp_smem_bytes;
+    cudaFuncSetAttribute(search_kernel<DIR, LEARNED>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    search_kernel<DIR, LEARNED><<<blocks, wpb * 32, smem, s>>>(p);
     return cudaGetLastError();
 }
 
-int search_max_blocks_per_sm(int warps_per_block, int smem_per_block, bool directed) {
+cudaError_t launch_search(const SearchParams& p, int blocks, int warps_per_block, bool directed,
+                          bool learned, cudaStream_t s) {
+    if (directed) return learned ? launch_t<true, true>(p, blocks, warps_per_block, s)
+                                 : launch_t<true, false>(p, blocks, warps_per_block, s);
+    return learned ? launch_t<false, true>(p, blocks, warps_per_block, s)
+                   : launch_t<false, false>(p, blocks, warps_per_block, s);
+}
+
+template <bool DIR, bool LEARNED>
+static int occupancy_t(int wpb, int smem) {
     int nb = 0;
-    if (directed) {
-        cudaFuncSetAttribute(search_kernel<true>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem_per_block);
-        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, search_kernel<true>, warps_per_block * 32, smem_per_block);
-    } else {
-        cudaFuncSetAttribute(search_kernel<false>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem_per_block);
-        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, search_kernel<false>, warps_per_block * 32, smem_per_block);
-    }
+    cudaFuncSetAttribute(search_kernel<DIR, LEARNED>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
+    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, search_kernel<DIR, LEARNED>, wpb * 32, smem);
     return nb;
+}
+
+int search_max_blocks_per_sm(int warps_per_block, int smem_per_block, bool directed, bool learned) {
+    if (directed) return learned ? occupancy_t<true, true>(warps_per_block, smem_per_block)
+                                 : occupancy_t<true, false>(warps_per_block, smem_per_block);
+    return learned ? occupancy_t<false, true>(warps_per_block, smem_per_block)
+                   : occupancy_t<false, false>(warps_per_block, smem_per_block);
 }
 
 // ---------------------------------------------------------------------------

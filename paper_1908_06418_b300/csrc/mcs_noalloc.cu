@@ -150,6 +150,6 @@ extern "C" int mcs_solve_batch_noalloc(int32_t npairs, const int32_t* d_n,
     sp.out_nodes = reinterpret_cast<u64*>(d_nodes);
     sp.out_map = map;
     sp.out_usec = d_usec;
-    if (launch_search(sp, blocks, kNaWarpsPerBlock, directed, s) != cudaSuccess) return MCS_ERR_CUDA;
+    if (launch_search(sp, blocks, kNaWarpsPerBlock, directed, false, s) != cudaSuccess) return MCS_ERR_CUDA;
     return 0;
 }

@@ -1,0 +1,143 @@
+"""The branching-order network on the GPU against its fp64 CPU reference
+(oracle/mlp.py), and exactness of searches that use the learned order."""
+import numpy as np
+import pytest
+
+import oracle
+import synth
+from oracle import mlp
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def solver():
+    import torch
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    from paper_1908_06418_b300 import Solver
+    s = Solver(0)
+    yield s
+    s.close()
+
+
+def _pairs(count, seed, labelled=False, nmin=8, nmax=40):
+    rs = np.random.default_rng(seed)
+    out = []
+    for i in range(count):
+        nG, nH = int(rs.integers(nmin, nmax + 1)), int(rs.integers(nmin, nmax + 1))
+        rg, rh = synth.rng_for(seed, i, 0), synth.rng_for(seed, i, 1)
+        k = 4 if labelled else 0
+        out.append(synth.Pair(synth.Graph(synth.er_undirected(nG, float(rs.uniform(0.1, 0.5)), rg),
+                                          synth.uniform_labels(nG, k, rg)),
+                              synth.Graph(synth.er_undirected(nH, float(rs.uniform(0.1, 0.5)), rh),
+                                          synth.uniform_labels(nH, k, rh))))
+    return out
+
+
+def _rows(pairs, per_pair, seed):
+    rs = np.random.default_rng(seed)
+    rows, y = [], []
+    for p_i, p in enumerate(pairs):
+        for _ in range(per_pair):
+            rows.append((p_i, int(rs.integers(0, p.G.n)), int(rs.integers(0, p.H.n))))
+            y.append(float(rs.random() < 0.3))
+    return np.array(rows, np.int32), np.array(y, np.float32)
+
+
+def _device_view(theta32):
+    """The parameters as the device uses them: W1, W2 rounded to fp16."""
+    th = theta32.astype(np.float64).copy()
+    n1 = mlp.D_PAD * mlp.H
+    th[:n1] = th[:n1].astype(np.float16).astype(np.float64)
+    o2 = n1 + mlp.H
+    th[o2:o2 + mlp.H * mlp.H] = th[o2:o2 + mlp.H * mlp.H].astype(np.float16).astype(np.float64)
+    return th
+
+
+def _inputs(pairs, rows):
+    feats = [(mlp.vertex_features(p.G.adj, p.G.labels), mlp.vertex_features(p.H.adj, p.H.labels))
+             for p in pairs]
+    x = np.zeros((len(rows), mlp.D_PAD))
+    for r, (pi, v, u) in enumerate(rows):
+        x[r, :18] = feats[pi][0][v]
+        x[r, 18:36] = feats[pi][1][u]
+    return x
+
+
+def test_features_equal_reference(solver):
+    from paper_1908_06418_b300 import DeviceBatch
+    pairs = _pairs(12, 11, labelled=True, nmin=1, nmax=64)
+    out = solver.order_eval(DeviceBatch(pairs), features=True)["features"]
+    for i, p in enumerate(pairs):
+        assert np.array_equal(out[i, 0, :p.G.n], mlp.vertex_features(p.G.adj, p.G.labels).astype(np.float32))
+        assert np.array_equal(out[i, 1, :p.H.n], mlp.vertex_features(p.H.adj, p.H.labels).astype(np.float32))
+    # directed
+    dp = [synth.Pair(synth.Graph(synth.er_directed(20, 0.2, synth.rng_for(12, i, 0))),
+                     synth.Graph(synth.er_directed(25, 0.2, synth.rng_for(12, i, 1))), True)
+          for i in range(4)]
+    out = solver.order_eval(DeviceBatch(dp, directed=True), features=True)["features"]
+    for i, p in enumerate(dp):
+        assert np.array_equal(out[i, 0, :20], mlp.vertex_features(p.G.adj, directed=True).astype(np.float32))
+
+
+def test_forward_and_gradient_match_reference(solver):
+    from paper_1908_06418_b300 import DeviceBatch
+    pairs = _pairs(6, 21)
+    rows, y = _rows(pairs, 60, 5)
+    w = np.random.default_rng(3).uniform(0.5, 2.0, len(y)).astype(np.float32)
+    theta = (mlp.init_params(9) + np.random.default_rng(4).normal(0, 0.02, mlp.N_PARAMS))
+    theta[mlp.D_IN * mlp.H:mlp.D_PAD * mlp.H] = 0.0       # padded inputs stay zero
+    theta32 = theta.astype(np.float32)
+    solver.set_order_model(theta32)
+    got = solver.order_eval(DeviceBatch(pairs), rows=rows, y=y, w=w, scores=True, loss_grad=True)
+    th = _device_view(theta32)
+    x = _inputs(pairs, rows)
+    s_ref, _ = mlp.forward(th, x, round_h1_fp16=True)
+    loss_ref, g_ref = mlp.loss_and_grad(th, x, y, w, round_h1_fp16=True)
+    # fp16 operands, fp32 accumulation: the logits agree to ~1e-3 of their scale
+    assert np.max(np.abs(got["scores"] - s_ref)) <= 2e-3 * max(1.0, np.max(np.abs(s_ref)))
+    assert abs(got["loss"] - loss_ref) <= 1e-3 * abs(loss_ref) + 1e-5
+    g = got["grad"].astype(np.float64)
+    # backward keeps dz in fp16: agreement to ~1e-2 relative, blockwise
+    blocks = [(0, mlp.D_PAD * mlp.H), (mlp.D_PAD * mlp.H, mlp.H), (mlp.D_PAD * mlp.H + mlp.H, mlp.H * mlp.H),
+              (mlp.D_PAD * mlp.H + mlp.H + mlp.H * mlp.H, mlp.H),
+              (mlp.N_PARAMS - mlp.H - 1, mlp.H), (mlp.N_PARAMS - 1, 1)]
+    for o, n in blocks:
+        ref = g_ref[o:o + n]
+        err = np.linalg.norm(g[o:o + n] - ref)
+        assert err <= 1e-2 * np.linalg.norm(ref) + 1e-7, (o, n, err, np.linalg.norm(ref))
+
+
+def test_training_lowers_the_loss(solver):
+    from paper_1908_06418_b300 import DeviceBatch
+    pairs = _pairs(16, 31)
+    rows, _ = _rows(pairs, 200, 6)
+    # a learnable target: candidates with equal degree are positives
+    fx = [(mlp.vertex_features(p.G.adj), mlp.vertex_features(p.H.adj)) for p in pairs]
+    y = np.array([float(fx[p][0][v, 0] == fx[p][1][u, 0]) for p, v, u in rows], np.float32)
+    solver.set_order_model(mlp.init_params(1).astype(np.float32))
+    b = DeviceBatch(pairs)
+    before = solver.order_eval(b, rows=rows, y=y, loss_grad=True)["loss"]
+    losses = solver.order_train(b, rows, y, steps=300, batch_size=512, lr=3e-3, seed=7)
+    after = solver.order_eval(b, rows=rows, y=y, loss_grad=True)["loss"]
+    assert np.isfinite(losses).all()
+    assert after < 0.8 * before, (before, after)
+
+
+@pytest.mark.parametrize("directed,labelled", [(False, False), (False, True), (True, False)])
+def test_learned_order_stays_exact(solver, directed, labelled):
+    from paper_1908_06418_b300 import MCS_ORDER_LEARNED
+    if directed:
+        pairs = [synth.Pair(synth.Graph(synth.er_directed(int(12 + i % 10), 0.25, synth.rng_for(41, i, 0))),
+                            synth.Graph(synth.er_directed(int(14 + i % 9), 0.25, synth.rng_for(41, i, 1))), True)
+                 for i in range(60)]
+    else:
+        pairs = _pairs(120, 43 + labelled, labelled=labelled, nmin=6, nmax=26)
+    solver.set_order_model(mlp.init_params(5).astype(np.float32))
+    plain = solver.solve_batch(pairs, directed=directed, timeout_s=60)
+    learned = solver.solve_batch(pairs, flags=MCS_ORDER_LEARNED, directed=directed, timeout_s=60)
+    for p, a, b in zip(pairs, plain, learned):
+        assert a.status == b.status == 0
+        assert a.size == b.size
+        assert oracle.verify(p.G.adj, p.H.adj, b.g_idx, b.h_idx, p.G.labels, p.H.labels) == 1
