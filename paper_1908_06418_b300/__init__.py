@@ -310,6 +310,40 @@ class Solver:
             raise RuntimeError(f"mcs_order_train: {self.strerror(rc)}")
         return losses[:steps]
 
+    # -- serving ---------------------------------------------------------
+    def submit(self, adjG, adjH, labG=None, labH=None, flags: int = 0,
+               timeout_s: float = 1.0) -> int:
+        """Admits one request (undirected); returns its ticket.  The graphs are
+        copied before the call returns."""
+        keep = _Keep()
+        G = keep.graph(adjG, labG)
+        H = keep.graph(adjH, labH)
+        t = ctypes.c_uint64(0)
+        rc = self.lib.mcs_submit(self.ctx, ctypes.byref(G), ctypes.byref(H), int(flags),
+                                 float(timeout_s), ctypes.byref(t))
+        if rc < 0:
+            raise RuntimeError(f"mcs_submit: {self.strerror(rc)} ({rc})")
+        return int(t.value)
+
+    def poll(self, ticket: int) -> Optional[Result]:
+        """None while the request runs; its Result once finished (the ticket is
+        then released)."""
+        gi = np.zeros(MCS_MAX_N, np.int16)
+        hi = np.zeros(MCS_MAX_N, np.int16)
+        r = _Result()
+        r.g_idx = gi.ctypes.data_as(ctypes.POINTER(ctypes.c_int16))
+        r.h_idx = hi.ctypes.data_as(ctypes.POINTER(ctypes.c_int16))
+        rc = self.lib.mcs_poll(self.ctx, ctypes.c_uint64(int(ticket)), ctypes.byref(r))
+        if rc == MCS_PENDING:
+            return None
+        if rc < 0 and rc != MCS_ERR_ARG:
+            raise RuntimeError(f"mcs_poll: {self.strerror(rc)} ({rc})")
+        if rc == MCS_ERR_ARG and r.status == 0 and r.size == 0:
+            raise KeyError(f"unknown ticket {ticket}")
+        k = r.npairs
+        return Result(int(r.size), int(r.status), gi[:k].astype(np.int32), hi[:k].astype(np.int32),
+                      int(r.nodes), float(r.seconds))
+
     def solve_batch_device(self, npairs: int, d_n, d_adj_off, d_adj, d_lab_off, d_labels,
                            d_size, d_status, d_nodes, d_map=None, d_usec=None, flags: int = 0,
                            timeout_s: float = 0.0, stream: int = 0) -> int:

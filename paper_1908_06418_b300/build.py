@@ -10,7 +10,7 @@ HERE = os.path.dirname(os.path.abspath(__file__))
 CSRC = os.path.join(HERE, "csrc")
 LIB = os.path.join(HERE, "libmcs.so")
 LIB_DEBUG = os.path.join(HERE, "libmcs_debug_bounds.so")
-SOURCES = ["mcs_kernels.cu", "mcs_api.cu", "mcs_noalloc.cu", "mcs_mlp.cu"]
+SOURCES = ["mcs_kernels.cu", "mcs_api.cu", "mcs_noalloc.cu", "mcs_mlp.cu", "mcs_serve.cu"]
 HEADERS = ["mcs_internal.cuh", os.path.join("..", "..", "include", "mcs.h")]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 

@@ -239,6 +239,7 @@ void mcs_destroy(mcs_ctx* c) {
     if (!c) return;
     cudaSetDevice(c->device);
     if (c->stream) cudaStreamSynchronize(c->stream);
+    mcs_serve_free(c);
     mcs_order_free(c);
     cudaFree(c->graphs); cudaFree(c->state); cudaFree(c->best); cudaFree(c->order);
     cudaFree(c->ctl); cudaFree(c->queue); cudaFree(c->qseq); cudaFree(c->gstack);
@@ -457,17 +458,6 @@ int mcs_solve(mcs_ctx* c, const mcs_graph* G, const mcs_graph* H, uint32_t flags
     if (!c || !G || !H || !out) return MCS_ERR_ARG;
     int rc = mcs_solve_batch(c, G, H, 1, flags, timeout_s, out);
     return rc < 0 ? rc : out->status;
-}
-
-int mcs_submit(mcs_ctx* c, const mcs_graph* G, const mcs_graph* H, uint32_t flags,
-               double timeout_s, uint64_t* ticket) {
-    (void)c; (void)G; (void)H; (void)flags; (void)timeout_s; (void)ticket;
-    return MCS_ERR_UNSUPPORTED;
-}
-
-int mcs_poll(mcs_ctx* c, uint64_t ticket, mcs_result* out) {
-    (void)c; (void)ticket; (void)out;
-    return MCS_ERR_UNSUPPORTED;
 }
 
 int mcs_bench_popc(mcs_ctx* c, double* popc_per_s) {

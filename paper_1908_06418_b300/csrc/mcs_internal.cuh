@@ -37,7 +37,7 @@ struct PairState {
     int32_t abort;         // 1 once the pair timed out
     u64 nodes;
     u64 t_start, deadline; // globaltimer ns
-    u64 pad;
+    u64 ticket;            // serve mode: the request's ticket
 };
 
 // A unit of work: one level of a pair's search tree (a node, its classes,
@@ -78,7 +78,46 @@ struct alignas(128) Control {
 };
 static_assert(sizeof(Control) == 512, "one 128-byte line per group of fields");
 
+// ---- serving (continuous batching) --------------------------------------
+constexpr int kTaskPack = 4;       // root of a served request: copy + pack it first
+constexpr int kSlotBytes = 2 * kMaxN * kMaxN + 2 * kMaxN * 4;   // adj G, adj H, labels G, H
+
+// Request descriptor, written by the host into mapped pinned memory.
+struct ServeReq {
+    int32_t nG, nH;
+    int32_t labelled;              // bit 0: G has labels, bit 1: H has labels
+    int32_t flags;
+    u64 ticket;
+    u64 timeout_ns;
+};
+// Result record, written by the device into mapped pinned memory; `done`
+// (the request's ticket) is written last, after a system-scope fence.
+struct ServeRes {
+    int32_t size, status;
+    u64 nodes;
+    float usec;
+    int32_t pad;
+    int16_t map[kMaxN];
+    u64 done;
+};
+struct ServeDev {
+    const u64* host_written;       // mapped: ring entries published by the host
+    const int32_t* ring;           // mapped: slot of entry i % ring_cap
+    int32_t ring_cap;
+    int32_t nslots;
+    const ServeReq* req;           // mapped [nslots]
+    const uint8_t* hdata;          // mapped [nslots][kSlotBytes]
+    uint8_t* ddata;                // device [nslots][kSlotBytes]
+    ServeRes* res;                 // mapped [nslots]
+    u64* dev_admitted;             // mapped: ring entries admitted by the device
+    const int32_t* stop;           // mapped: host asks an idle server to exit
+    int32_t* in_flight;            // device: admitted, unfinished requests
+    u64 linger_ns;                 // idle time before the server exits
+};
+
 struct SearchParams {
+    int32_t serving;               // 1: serve mode (requests arrive while the kernel runs)
+    ServeDev sv;
     int32_t npairs;
     uint32_t flags;
     u64 timeout_ns;                // per pair
@@ -140,6 +179,7 @@ inline int warp_smem_bytes(int stack_entries) { return kSmCls + 16 * stack_entri
 }  // namespace mcsk
 
 struct MlpState;
+struct ServeState;
 
 // Host-side context behind the opaque mcs_ctx handle of include/mcs.h.
 struct mcs_ctx {
@@ -177,6 +217,7 @@ struct mcs_ctx {
     bool ev_pending = false;       // ev0/ev1 recorded by a device call, not yet read
     Control h_ctl;
     struct MlpState* mlp = nullptr;   // ordering network (mcs_mlp.cu), created on first use
+    struct ServeState* serve = nullptr; // serving (mcs_serve.cu), created on first mcs_submit
 };
 
 // kernels.cu entry points used by the host library
@@ -186,6 +227,7 @@ cudaError_t launch_search(const SearchParams& p, int blocks, int warps_per_block
                           bool directed, bool learned, cudaStream_t s);
 int search_max_blocks_per_sm(int warps_per_block, int smem_per_block, bool directed, bool learned);
 cudaError_t launch_popc_bench(unsigned long long* out, int blocks, int iters, cudaStream_t s);
+cudaError_t launch_serve_init(Control* ctl, u64* qseq, uint32_t qcap, int32_t* in_flight, cudaStream_t s);
 }
 
 // mcs_mlp.cu: learned candidate order
@@ -194,3 +236,5 @@ int mcs_order_prepare(mcs_ctx* c, int npairs, const int32_t* d_n, const int64_t*
                       uint32_t flags, cudaStream_t s, const float** vscore_out);
 int mcs_order_ranks(mcs_ctx* c, int npairs, cudaStream_t s, const uint8_t** rank_out);
 void mcs_order_free(mcs_ctx* c);
+// mcs_serve.cu
+void mcs_serve_free(mcs_ctx* c);

@@ -166,8 +166,67 @@ __device__ bool pack_graph(const GraphIn& g, bool directed, const float* key,
     return true;
 }
 
+// Packs one pair (one warp): validation, renumbering, row bitsets and the
+// initial label classes into pg.  skey is 2 x 64 long long of shared scratch.
+// Returns false (warp-uniform) when an input graph is malformed.
+__device__ bool pack_pair_warp(const GraphIn (&g)[2], bool directed, const float* key0,
+                               const float* key1, PairGraph& pg, long long* skey, int lane) {
+    bool ok = true;
+    long long vk[2][2];
+    for (int side = 0; side < 2 && ok; ++side) {
+        if (g[side].n < 0 || g[side].n > kMaxN) { ok = false; break; }
+        u64* orows = side ? pg.hout : pg.gout;
+        u64* irows = side ? pg.hin : pg.gin;
+        uint8_t* perm = side ? pg.permH : pg.permG;
+        ok = pack_graph(g[side], directed, side ? key1 : key0, orows, irows, perm, vk[side], lane);
+    }
+    __syncwarp();
+    const int nG = g[0].n, nH = g[1].n;
+    if (ok) {
+        // label keys by new number
+        for (int side = 0; side < 2; ++side) {
+            const uint8_t* perm = side ? pg.permH : pg.permG;
+            const int n = side ? nH : nG;
+            // vk[side][s] belongs to original vertex lane + 32 s; place it at its new number
+            __syncwarp();
+            for (int r = lane; r < kMaxN; r += 32) skey[side * kMaxN + r] = -1;
+            __syncwarp();
+            for (int r = 0; r < n; ++r) {
+                int orig = perm[r];
+                long long k = __shfl_sync(FULL, (unsigned long long)vk[side][orig >> 5], orig & 31);
+                if (lane == 0) skey[side * kMaxN + r] = k;
+            }
+            __syncwarp();
+        }
+        // one class per key present in both graphs; representative = lowest new G number
+        int C = 0;
+        for (int s = 0; s < 2; ++s) {
+            int r = lane + 32 * s;
+            long long k = r < nG ? skey[r] : -2;
+            u64 L = 0, R = 0;
+            bool rep = r < nG;
+            for (int j = 0; j < kMaxN; ++j) {
+                if (j < nG && skey[j] == k) { L |= 1ull << j; if (j < r) rep = false; }
+                if (j < nH && skey[kMaxN + j] == k) R |= 1ull << j;
+            }
+            bool keep = rep && R != 0;
+            unsigned m = __ballot_sync(FULL, keep);
+            int pos = C + __popc(m & lanemask_lt());
+            if (keep) pg.root[pos] = make_ulonglong2(L, R);
+            C += __popc(m);
+        }
+        if (lane == 0) {
+            pg.nG = nG; pg.nH = nH; pg.C0 = C; pg.valid = 1;
+        }
+    } else if (lane == 0) {
+        pg.nG = 0; pg.nH = 0; pg.C0 = 0; pg.valid = 0;
+    }
+    __syncwarp();
+    return ok;
+}
+
 __global__ void pack_kernel(PackParams P) {
-    __shared__ long long s_key[4][2][kMaxN];
+    __shared__ long long s_key[4][2 * kMaxN];
     const int lane = threadIdx.x & 31;
     const int wib = threadIdx.x >> 5;
     const int p = blockIdx.x * (blockDim.x >> 5) + wib;
@@ -199,63 +258,16 @@ __global__ void pack_kernel(PackParams P) {
     if (p >= P.npairs) return;
     const bool directed = (P.flags & MCS_DIRECTED) != 0;
     PairGraph& pg = P.graphs[p];
-    bool ok = true;
-    long long vk[2][2];
-    for (int side = 0; side < 2 && ok; ++side) {
-        int gi = 2 * p + side;
-        GraphIn g;
-        g.n = P.n[gi];
-        if (g.n < 0 || g.n > kMaxN) { ok = false; break; }
-        g.a = P.adj + P.adj_off[gi];
-        g.lab = nullptr;
-        if (P.labels && P.lab_off && P.lab_off[gi] >= 0) g.lab = P.labels + P.lab_off[gi];
-        const float* key = P.vscore ? P.vscore + ((size_t)p * 2 + side) * kMaxN : nullptr;
-        u64* orows = side ? pg.hout : pg.gout;
-        u64* irows = side ? pg.hin : pg.gin;
-        uint8_t* perm = side ? pg.permH : pg.permG;
-        ok = pack_graph(g, directed, key, orows, irows, perm, vk[side], lane);
+    GraphIn g[2];
+    for (int side = 0; side < 2; ++side) {
+        const int gi = 2 * p + side;
+        g[side].n = P.n[gi];
+        g[side].a = P.adj + P.adj_off[gi];
+        g[side].lab = (P.labels && P.lab_off && P.lab_off[gi] >= 0) ? P.labels + P.lab_off[gi] : nullptr;
     }
-    __syncwarp();
-    int nG = P.n[2 * p], nH = P.n[2 * p + 1];
-    if (ok) {
-        // label keys by new number
-        for (int side = 0; side < 2; ++side) {
-            const uint8_t* perm = side ? pg.permH : pg.permG;
-            int n = side ? nH : nG;
-            // vk[side][s] belongs to original vertex lane + 32 s; place it at its new number
-            __syncwarp();
-            for (int r = lane; r < kMaxN; r += 32) s_key[wib][side][r] = -1;
-            __syncwarp();
-            for (int r = 0; r < n; ++r) {
-                int orig = perm[r];
-                long long k = __shfl_sync(FULL, (unsigned long long)vk[side][orig >> 5], orig & 31);
-                if (lane == 0) s_key[wib][side][r] = k;
-            }
-            __syncwarp();
-        }
-        // one class per key present in both graphs; representative = lowest new G number
-        int C = 0;
-        for (int s = 0; s < 2; ++s) {
-            int r = lane + 32 * s;
-            long long k = r < nG ? s_key[wib][0][r] : -2;
-            u64 L = 0, R = 0;
-            bool rep = r < nG;
-            for (int j = 0; j < kMaxN; ++j) {
-                if (j < nG && s_key[wib][0][j] == k) { L |= 1ull << j; if (j < r) rep = false; }
-                if (j < nH && s_key[wib][1][j] == k) R |= 1ull << j;
-            }
-            bool keep = rep && R != 0;
-            unsigned m = __ballot_sync(FULL, keep);
-            int pos = C + __popc(m & lanemask_lt());
-            if (keep) pg.root[pos] = make_ulonglong2(L, R);
-            C += __popc(m);
-        }
-        if (lane == 0) {
-            pg.nG = nG; pg.nH = nH; pg.C0 = C; pg.valid = 1;
-        }
-    } else if (lane == 0) {
-        pg.nG = 0; pg.nH = 0; pg.C0 = 0; pg.valid = 0;
-    }
+    const float* k0 = P.vscore ? P.vscore + ((size_t)p * 2) * kMaxN : nullptr;
+    const float* k1 = P.vscore ? P.vscore + ((size_t)p * 2 + 1) * kMaxN : nullptr;
+    const bool ok = pack_pair_warp(g, directed, k0, k1, pg, s_key[wib], lane);
     if (lane == 0) {
         PairState& st = P.state[p];
         st.inc = 0;
@@ -397,8 +409,48 @@ __device__ void post_exit_tokens(const SearchParams& P, int count, int lane) {
     if (!__all_sync(FULL, ok) && lane == 0) atomicCAS(&P.ctl->error, 0, MCS_ERR_DEVICE_STALL);
 }
 
+// Serve mode: the result record in mapped host memory, map built in shared
+// scratch (64 int16), then a system-scope fence and the done ticket.
+__device__ void finalize_served(const SearchParams& P, int pair, int status, int k, int lane,
+                                int16_t* smap) {
+    PairState& ps = P.state[pair];
+    const PairGraph& pg = P.graphs[pair];
+    for (int i = lane; i < kMaxN; i += 32) smap[i] = -1;
+    __syncwarp();
+    if (status == MCS_OK || status == MCS_TIMEOUT) {
+        const uint16_t* slot = P.best + ((size_t)pair * kLevels + k) * kMaxN;
+        for (int i = lane; i < k; i += 32) {
+            uint16_t e = vload(slot + i);
+            if (!DBG_OK(P.ctl, (e >> 8) < kMaxN && (e & 0xff) < kMaxN, 8, e)) continue;
+            smap[__ldcg(&pg.permG[e >> 8])] = (int16_t)__ldcg(&pg.permH[e & 0xff]);
+        }
+    }
+    __syncwarp();
+    ServeRes* r = P.sv.res + pair;
+    for (int i = lane; i < kMaxN; i += 32) r->map[i] = smap[i];
+    u64 ticket = 0;
+    if (lane == 0) {
+        const u64 now = gtimer(), t0 = vload(&ps.t_start);
+        ticket = vload(&ps.ticket);
+        r->size = k;
+        r->status = status;
+        r->nodes = vload(&ps.nodes);
+        r->usec = t0 ? (float)((now - t0) * 1e-3) : 0.f;
+    }
+    __syncwarp();
+    __threadfence_system();
+    if (lane == 0) {
+        *(volatile u64*)&r->done = ticket;
+        ps.status = status;
+        __threadfence();
+        atomicSub(P.sv.in_flight, 1);
+        atomicMax(&P.ctl->last_progress, gtimer());
+    }
+    __syncwarp();
+}
+
 // Finish the pair: write size, status, nodes and the mapping (original numbers).
-__device__ void finalize_pair(const SearchParams& P, int pair, int lane) {
+__device__ void finalize_pair(const SearchParams& P, int pair, int lane, int16_t* smap) {
     __threadfence();
     PairState& ps = P.state[pair];
     const PairGraph& pg = P.graphs[pair];
@@ -415,17 +467,19 @@ __device__ void finalize_pair(const SearchParams& P, int pair, int lane) {
     if (status == MCS_PENDING) {
         if (!DBG_OK(P.ctl, k >= 0 && k < kLevels, 7, k)) k = 0;
         status = ab ? MCS_TIMEOUT : MCS_OK;
+        if (P.serving) { finalize_served(P, pair, status, k, lane, smap); return; }
         if (P.out_map) {
             const uint16_t* slot = P.best + ((size_t)pair * kLevels + k) * kMaxN;
             for (int i = lane; i < k; i += 32) {
                 uint16_t e = vload(slot + i);
                 if (!DBG_OK(P.ctl, (e >> 8) < kMaxN && (e & 0xff) < kMaxN, 8, e)) continue;
-                int g = pg.permG[e >> 8], h = pg.permH[e & 0xff];
+                int g = __ldcg(&pg.permG[e >> 8]), h = __ldcg(&pg.permH[e & 0xff]);
                 P.out_map[(size_t)pair * kMaxN + g] = (int16_t)h;
             }
         }
     } else {
         k = 0;
+        if (P.serving) { finalize_served(P, pair, status, 0, lane, smap); return; }
     }
     int last = 0;
     if (lane == 0) {
@@ -448,7 +502,8 @@ __device__ void finalize_pair(const SearchParams& P, int pair, int lane) {
 
 // A task of `pair` ended: publish node count, drop the open count and finalise
 // the pair if this was its last task.
-__device__ __forceinline__ void end_task(const SearchParams& P, int pair, u64& nodes, int lane) {
+__device__ __forceinline__ void end_task(const SearchParams& P, int pair, u64& nodes, int lane,
+                                         int16_t* smap) {
     int last = 0;
     if (lane == 0) {
         if (nodes) atomicAdd(&P.state[pair].nodes, nodes);
@@ -457,7 +512,61 @@ __device__ __forceinline__ void end_task(const SearchParams& P, int pair, u64& n
     }
     nodes = 0;
     last = __shfl_sync(FULL, last, 0);
-    if (last) finalize_pair(P, pair, lane);
+    if (last) finalize_pair(P, pair, lane, smap);
+}
+
+// Serve mode, warp 0: admits requests that the host published in the mapped
+// ring, as root tasks of the ticket ring; exits (posting one exit token per
+// other warp) after linger_ns without admitted or unfinished requests.
+__device__ void serve_admit(const SearchParams& P, int lane) {
+    Control* ctl = P.ctl;
+    const ServeDev& S = P.sv;
+    const u64 qmask = P.qcap - 1;
+    if (lane == 0) {
+        u64 admitted = vload(S.dev_admitted);
+        u64 idle0 = gtimer();
+        for (;;) {
+            if (vload(&ctl->error) != 0) break;
+            const u64 hw = vload(S.host_written);
+            if (hw > admitted) {
+                bool ok = true;
+                for (; admitted < hw && ok; ++admitted) {
+                    const int slot = vload(S.ring + (admitted % (u64)S.ring_cap));
+                    if (slot < 0 || slot >= S.nslots) continue;
+                    const u64 t = atomicAdd(&ctl->q_tail, 1ull);
+                    if (!wait_seq(P.qseq + (t & qmask), t)) { ok = false; break; }
+                    Task* dst = P.queue + (t & qmask);
+                    dst->h.pair = slot;
+                    dst->h.flags = kTaskFresh | kTaskPack;
+                    dst->h.depth = 0;
+                    dst->h.C = 0;
+                    atomicAdd(S.in_flight, 1);
+                    __threadfence();
+                    P.qseq[t & qmask] = t + 1;
+                }
+                if (!ok) { atomicCAS(&ctl->error, 0, MCS_ERR_DEVICE_STALL); break; }
+                *(volatile u64*)S.dev_admitted = admitted;
+                __threadfence_system();
+                idle0 = gtimer();
+                atomicMax(&ctl->last_progress, idle0);
+            } else {
+                const u64 now = gtimer();
+                if (vload(S.in_flight) > 0) {
+                    idle0 = now;
+                    const u64 lp = vload(&ctl->last_progress);
+                    if (now > lp && now - lp > P.stall_ns) {      // requests stopped progressing
+                        atomicCAS(&ctl->error, 0, MCS_ERR_DEVICE_STALL);
+                        break;
+                    }
+                } else if (now - idle0 > S.linger_ns || vload(S.stop) != 0) {
+                    break;
+                }
+                __nanosleep(1000);
+            }
+        }
+    }
+    __syncwarp();
+    post_exit_tokens(P, P.max_warps - 1, lane);
 }
 
 __device__ __forceinline__ void load_level(const WarpSmem& w, int d, Top& t) {
@@ -498,6 +607,8 @@ __global__ void __launch_bounds__(256, 3) search_kernel(SearchParams P) {
 #endif
 
     Control* ctl = P.ctl;
+    int16_t* smap = reinterpret_cast<int16_t*>(base + kSmRrem);   // finalize scratch (levels unused then)
+    if (P.serving && gw == 0) { serve_admit(P, lane); return; }
     const bool level_prune = (P.flags & MCS_NO_LEVEL_PRUNE) == 0;
     const u64 qmask = P.qcap - 1;
     int cur_pair = -1;
@@ -551,6 +662,47 @@ __global__ void __launch_bounds__(256, 3) search_kernel(SearchParams P) {
         const bool fresh = (tflags & kTaskFresh) != 0;
         PairState& ps = P.state[pair];
         const PairGraph& pg = P.graphs[pair];
+        u64 req_timeout = P.timeout_ns;
+        if (tflags & kTaskPack) {
+            // a served request: copy it out of mapped host memory, pack it into
+            // its slot and set up its state (this warp is its only user so far)
+            const uint4* src = reinterpret_cast<const uint4*>(P.sv.hdata + (size_t)pair * kSlotBytes);
+            uint4* dst = reinterpret_cast<uint4*>(P.sv.ddata + (size_t)pair * kSlotBytes);
+            for (int i = lane; i < kSlotBytes / 16; i += 32) {
+                uint4 v4;
+                asm volatile("ld.volatile.global.v4.u32 {%0,%1,%2,%3}, [%4];"
+                             : "=r"(v4.x), "=r"(v4.y), "=r"(v4.z), "=r"(v4.w) : "l"(src + i));
+                dst[i] = v4;
+            }
+            int rq[3] = {0, 0, 0};
+            u64 rt = 0, rtk = 0;
+            if (lane == 0) {
+                const ServeReq* q = P.sv.req + pair;
+                rq[0] = vload(&q->nG); rq[1] = vload(&q->nH); rq[2] = vload(&q->labelled);
+                rt = vload(&q->timeout_ns); rtk = vload(&q->ticket);
+            }
+            for (int j = 0; j < 3; ++j) rq[j] = __shfl_sync(FULL, rq[j], 0);
+            rt = shfl64(rt, 0);
+            rtk = shfl64(rtk, 0);
+            req_timeout = rt;
+            __syncwarp();
+            const uint8_t* d = P.sv.ddata + (size_t)pair * kSlotBytes;
+            GraphIn g[2];
+            g[0].n = rq[0]; g[1].n = rq[1];
+            g[0].a = d; g[1].a = d + kMaxN * kMaxN;
+            g[0].lab = (rq[2] & 1) ? reinterpret_cast<const int32_t*>(d + 2 * kMaxN * kMaxN) : nullptr;
+            g[1].lab = (rq[2] & 2) ? reinterpret_cast<const int32_t*>(d + 2 * kMaxN * kMaxN + 4 * kMaxN) : nullptr;
+            const bool ok = pack_pair_warp(g, false, nullptr, nullptr, const_cast<PairGraph&>(pg),
+                                           reinterpret_cast<long long*>(base + kSmRrem), lane);
+            if (lane == 0) {
+                ps.inc = 0; ps.open = 1; ps.abort = 0; ps.nodes = 0;
+                ps.t_start = 0; ps.deadline = 0; ps.ticket = rtk;
+                ps.status = ok ? MCS_PENDING : MCS_ERR_ARG;
+                __threadfence();
+            }
+            __syncwarp();
+            cur_pair = -1;      // a slot is reused by later requests: never trust cached rows
+        }
         int pstat = 0;
         if (lane == 0) pstat = vload(&ps.status);
         pstat = __shfl_sync(FULL, pstat, 0);
@@ -558,24 +710,25 @@ __global__ void __launch_bounds__(256, 3) search_kernel(SearchParams P) {
             if (pstat != MCS_PENDING) {                   // malformed input: report and skip
                 __syncwarp();
                 if (lane == 0) { P.qseq[qh & qmask] = qh + P.qcap; ps.open = 0; }
-                finalize_pair(P, pair, lane);
+                finalize_pair(P, pair, lane, smap);
                 continue;
             }
             if (lane == 0) {
                 u64 now = gtimer();
                 ps.t_start = now;
-                ps.deadline = now + P.timeout_ns;
+                ps.deadline = now + req_timeout;
                 atomicMax(&ctl->last_progress, now);
             }
         }
-        // load the pair's rows into shared memory
-        if (pair != cur_pair) {
+        // load the pair's rows into shared memory (through L2: in serve mode a
+        // slot is repacked while the kernel runs, so L1 may hold old lines)
+        if (pair != cur_pair || P.serving) {
             for (int i = lane; i < kMaxN; i += 32) {
-                w.gout[i] = pg.gout[i];
-                w.hout[i] = pg.hout[i];
-                if (DIR) { w.gin[i] = pg.gin[i]; w.hin[i] = pg.hin[i]; }
+                w.gout[i] = __ldcg(&pg.gout[i]);
+                w.hout[i] = __ldcg(&pg.hout[i]);
+                if (DIR) { w.gin[i] = __ldcg(&pg.gin[i]); w.hin[i] = __ldcg(&pg.hin[i]); }
             }
-            cur_pair = pair;
+            cur_pair = P.serving ? -1 : pair;
         }
         if (!fresh) {
             int hd4[4] = {0, 0, 0, 0};
@@ -600,8 +753,8 @@ __global__ void __launch_bounds__(256, 3) search_kernel(SearchParams P) {
             ++stolen;
         } else {
             t.d = 0;
-            t.C = pg.C0;
-            for (int i = lane; i < t.C; i += 32) *st.at(i) = pg.root[i];
+            t.C = __ldcg(&pg.C0);
+            for (int i = lane; i < t.C; i += 32) *st.at(i) = __ldcg(&pg.root[i]);
         }
         __syncwarp();
         if (lane == 0) {
@@ -626,14 +779,14 @@ __global__ void __launch_bounds__(256, 3) search_kernel(SearchParams P) {
         deadline = shfl64(deadline, 0);
         long long c_busy = clock64();
         idle_cyc += c_busy - c_idle;
-        if (ab0) { end_task(P, pair, nodes, lane); busy_cyc += clock64() - c_busy; continue; }
+        if (ab0) { end_task(P, pair, nodes, lane, smap); busy_cyc += clock64() - c_busy; continue; }
         if (fresh) {
             // root node entry (Algorithm 1): bound of Eq. 1, then class choice
             ++nodes;
             cvisits += t.C;
             Scan sc = scan_level(st, 0, t.C, -1, lane);
             t.bound = sc.sum;
-            if (t.bound <= inc) { end_task(P, pair, nodes, lane); busy_cyc += clock64() - c_busy; continue; }
+            if (t.bound <= inc) { end_task(P, pair, nodes, lane, smap); busy_cyc += clock64() - c_busy; continue; }
             t.v = sc.key & 63;
             t.rrem = sc.R;
             t.flags = kTaskPending;
@@ -901,7 +1054,7 @@ __global__ void __launch_bounds__(256, 3) search_kernel(SearchParams P) {
                 if (t.d >= d0) load_level(w, t.d, t);
             }
         }
-        end_task(P, pair, nodes, lane);
+        end_task(P, pair, nodes, lane, smap);
         busy_cyc += clock64() - c_busy;
     }
     if (lane == 0) {
@@ -944,6 +1097,28 @@ int search_max_blocks_per_sm(int warps_per_block, int smem_per_block, bool direc
                                  : occupancy_t<true, false>(warps_per_block, smem_per_block);
     return learned ? occupancy_t<false, true>(warps_per_block, smem_per_block)
                    : occupancy_t<false, false>(warps_per_block, smem_per_block);
+}
+
+// Serve mode: reset the control block and the ring before a server launch.
+__global__ void serve_init_kernel(Control* c, u64* qseq, uint32_t qcap, int32_t* in_flight) {
+    for (uint32_t i = blockIdx.x * blockDim.x + threadIdx.x; i < qcap; i += gridDim.x * blockDim.x)
+        qseq[i] = i;
+    if (blockIdx.x == 0 && threadIdx.x == 0) {
+        c->q_head = 0;
+        c->q_tail = 0;
+        c->remaining = 0x7fffffff;
+        c->error = 0;
+        c->last_progress = gtimer();
+        c->donated = c->stolen = c->spilled = c->class_visits = c->pruned = 0;
+        c->busy_cycles = c->idle_cycles = 0;
+        c->dbg_code = c->dbg_val = c->dbg_line = c->dbg_count = 0;
+        *in_flight = 0;
+    }
+}
+
+cudaError_t launch_serve_init(Control* ctl, u64* qseq, uint32_t qcap, int32_t* in_flight, cudaStream_t s) {
+    serve_init_kernel<<<64, 256, 0, s>>>(ctl, qseq, qcap, in_flight);
+    return cudaGetLastError();
 }
 
 // ---------------------------------------------------------------------------

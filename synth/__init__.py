@@ -234,16 +234,24 @@ def _c4_graph(r: np.random.Generator, nmin: int, nmax: int, family: int) -> np.n
     return perturbed_mesh(w, h, r)
 
 
+def config4_pair(i: int, nmin: int = 40, nmax: int = 64, cid: int = 4) -> Pair:
+    """Pair i of the bounded-valence family: even i random 3-/4-regular, odd
+    i perturbed 2D meshes (10% edges deleted, as many added)."""
+    fam = i % 2
+    gs = [_c4_graph(rng_for(cid, i, s), nmin, nmax, fam) for s in (0, 1)]
+    return Pair(Graph(gs[0]), Graph(gs[1]), False, f"c4-{cid}-{i}")
+
+
 def config4_pairs(count: int = 2048, nmin: int = 40, nmax: int = 64,
                   cid: int = 4) -> List[Pair]:
     """Bounded-valence pairs: half random 3-/4-regular, half perturbed 2D
     meshes (10% edges deleted, as many added); undirected, unlabelled."""
-    out = []
-    for i in range(count):
-        fam = i % 2
-        gs = [_c4_graph(rng_for(cid, i, s), nmin, nmax, fam) for s in (0, 1)]
-        out.append(Pair(Graph(gs[0]), Graph(gs[1]), False, f"c4-{i}"))
-    return out
+    return [config4_pair(i, nmin, nmax, cid) for i in range(count)]
+
+
+def config4_train_pair(i: int) -> Pair:
+    """Training pair i for the branching network (n <= 30, config id 40)."""
+    return config4_pair(i, 16, 30, cid=40)
 
 
 def config4_train_pairs(count: int = 20000, nmin: int = 16, nmax: int = 30) -> List[Pair]:

@@ -1,0 +1,100 @@
+"""Serving (mcs_submit / mcs_poll): continuous batching on one GPU.
+
+Requests submitted while others run join them on the device; every request's
+result must be the same alone and in the mix (sizes are exact integers, so
+equal), each mapping must be valid, and a sample must match the CPU oracle."""
+import time
+
+import numpy as np
+import pytest
+
+import oracle
+import synth
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def solver():
+    import torch
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    from paper_1908_06418_b300 import Solver
+    s = Solver(0)
+    yield s
+    s.close()
+
+
+def _requests(count, seed=55, nmax=36):
+    reqs = []
+    for r in synth.config5_requests(count=count, rate_per_s=1e9, nmax=nmax, cid=seed):
+        reqs.append(r.pair)
+    return reqs
+
+
+def _wait(solver, tickets, limit_s=120):
+    out = {}
+    t0 = time.time()
+    while len(out) < len(tickets):
+        for t in tickets:
+            if t not in out:
+                r = solver.poll(t)
+                if r is not None:
+                    out[t] = r
+        assert time.time() - t0 < limit_s, "serving did not finish"
+    return [out[t] for t in tickets]
+
+
+def test_alone_equals_mix(solver):
+    pairs = _requests(240)
+    # alone: one request in flight at a time
+    alone = []
+    for p in pairs:
+        t = solver.submit(p.G.adj, p.H.adj, p.G.labels, p.H.labels, timeout_s=20)
+        alone += _wait(solver, [t])
+    # mixed: submitted in waves while earlier ones run
+    tickets = []
+    for i in range(0, len(pairs), 40):
+        for p in pairs[i:i + 40]:
+            tickets.append(solver.submit(p.G.adj, p.H.adj, p.G.labels, p.H.labels, timeout_s=20))
+        time.sleep(0.002)
+    mixed = _wait(solver, tickets)
+    for p, a, b in zip(pairs, alone, mixed):
+        assert a.status == b.status == 0
+        assert a.size == b.size
+        assert oracle.verify(p.G.adj, p.H.adj, b.g_idx, b.h_idx, p.G.labels, p.H.labels) == 1
+    for p, b in list(zip(pairs, mixed))[::6]:
+        assert b.size == oracle.mcs(p.G.adj, p.H.adj, p.G.labels, p.H.labels).size
+
+
+def test_serving_matches_batch_solver(solver):
+    pairs = _requests(150, seed=56)
+    batch = solver.solve_batch(pairs, timeout_s=20)
+    tickets = [solver.submit(p.G.adj, p.H.adj, p.G.labels, p.H.labels, timeout_s=20) for p in pairs]
+    served = _wait(solver, tickets)
+    assert [r.size for r in served] == [r.size for r in batch]
+
+
+def test_more_requests_than_slots_and_bad_input(solver):
+    from paper_1908_06418_b300 import MCS_ERR_ARG
+    pairs = _requests(2600, seed=57, nmax=20)            # > 2048 device slots
+    bad = pairs[0].G.adj.copy()
+    bad[0, 1] = 3
+    tickets = [solver.submit(p.G.adj, p.H.adj, p.G.labels, p.H.labels, timeout_s=20) for p in pairs]
+    tb = solver.submit(bad, pairs[0].H.adj, timeout_s=5)
+    res = _wait(solver, tickets + [tb], limit_s=300)
+    assert all(r.status == 0 for r in res[:-1])
+    assert res[-1].status == MCS_ERR_ARG
+    for p, r in list(zip(pairs, res))[::97]:
+        assert oracle.verify(p.G.adj, p.H.adj, r.g_idx, r.h_idx, p.G.labels, p.H.labels) == 1
+    with pytest.raises(KeyError):
+        solver.poll(tickets[0])                            # already released
+
+
+def test_timeout_in_serving(solver):
+    from paper_1908_06418_b300 import MCS_TIMEOUT
+    p = synth.config4_pairs(count=1)[0]
+    t = solver.submit(p.G.adj, p.H.adj, timeout_s=0.05)
+    r = _wait(solver, [t])[0]
+    assert r.status == MCS_TIMEOUT and r.size > 0
+    assert oracle.verify(p.G.adj, p.H.adj, r.g_idx, r.h_idx) == 1
