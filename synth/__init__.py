@@ -300,3 +300,36 @@ def config5_requests(count: int = 100000, rate_per_s: float = 1000.0,
             p = float(r.uniform(pmin, pmax))
             gs.append(Graph(er_undirected(n, p, r), uniform_labels(n, k, r)))
         yield Request(t, Pair(gs[0], gs[1], False, f"c5-{i}"), timeout_s)
+
+def planted_bvg_pair(i: int, nmin: int = 40, nmax: int = 64, cid: int = 44) -> Pair:
+    """Bounded-valence pair with a planted common induced core, the way the
+    ARG ``mcs10``..``mcs90`` pairs are built: a core of round(f * n) vertices,
+    f in {0.1, 0.3, 0.5, 0.7, 0.9} by i, is a random 3-regular graph (even i)
+    or a 2D mesh (odd i); each graph adds its own n - k vertices, each joined
+    to two or three random vertices; H is then randomly permuted.  The common
+    core makes the MCS at least k."""
+    r = rng_for(cid, i, 0)
+    n = int(r.integers(nmin, nmax + 1))
+    f = (0.1, 0.3, 0.5, 0.7, 0.9)[i % 5]
+    k = max(4, int(round(f * n)))
+    if i % 2 == 0:
+        if (k * 3) % 2:
+            k -= 1
+        core = random_regular(k, 3, r)
+    else:
+        w = max(2, int(round(np.sqrt(k))))
+        h = max(2, k // w)
+        k = w * h
+        core = grid(w, h)
+    gs = []
+    for side in (0, 1):
+        rs = rng_for(cid, i, side + 1)
+        a = np.zeros((n, n), np.uint8)
+        a[:k, :k] = core
+        for x in range(k, n):
+            deg = int(rs.integers(2, 4))
+            for y in rs.choice(x, size=min(deg, x), replace=False):
+                a[x, y] = a[y, x] = 1
+        gs.append(a)
+    perm = rng_for(cid, i, 3).permutation(n)
+    return Pair(Graph(gs[0]), Graph(gs[1][np.ix_(perm, perm)]), False, f"pbvg-{cid}-{i}")

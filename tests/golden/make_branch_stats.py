@@ -32,11 +32,16 @@ NODE_LIMIT = 300000
 NEG = 4
 
 
-def _one(i):
+FAMILY = "bvg"
+
+
+def _one(args):
+    i, family, node_limit = args
     import oracle
-    p = _pair(i)
+    import synth
+    p = _pair(i) if family == "bvg" else synth.planted_bvg_pair(i, 16, 30, cid=46)
     rows, pg, ph, size, complete = oracle.branch_log(p.G.adj, p.H.adj, max_depth=MAX_DEPTH,
-                                                     node_limit=NODE_LIMIT)
+                                                     node_limit=node_limit)
     if not complete or len(rows) == 0:
         return i, None
     v = pg[rows[:, 1]]
@@ -62,13 +67,18 @@ def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--count", type=int, default=20000)
     ap.add_argument("--workers", type=int, default=6)
-    ap.add_argument("--out", default=os.path.join(HERE, "order_train.npz"))
+    ap.add_argument("--family", default="bvg", choices=["bvg", "planted"],
+                    help="bvg: random 3-/4-regular and perturbed meshes; planted: "
+                         "bounded-valence pairs with a planted common core (synth.planted_bvg_pair)")
+    ap.add_argument("--node-limit", type=int, default=NODE_LIMIT)
+    ap.add_argument("--out", default="")
     a = ap.parse_args()
+    out_path = a.out or os.path.join(HERE, "order_train.npz" if a.family == "bvg" else "order_train_planted.npz")
     ctx = mp.get_context("spawn")
     cols = {"pair": [], "v": [], "u": [], "y": []}
     done = 0
     with ctx.Pool(a.workers) as pool:
-        for i, res in pool.imap_unordered(_one, range(a.count), chunksize=16):
+        for i, res in pool.imap_unordered(_one, [(i, a.family, a.node_limit) for i in range(a.count)], chunksize=16):
             done += 1
             if res is not None:
                 v, u, y = res
@@ -81,8 +91,8 @@ def main():
     out = {k: np.concatenate(c) for k, c in cols.items()}
     order = np.lexsort((out["u"], out["v"], out["pair"]))
     out = {k: c[order] for k, c in out.items()}
-    np.savez_compressed(a.out, count=np.int32(a.count), max_depth=np.int32(MAX_DEPTH),
-                        node_limit=np.int64(NODE_LIMIT), **out)
+    np.savez_compressed(out_path, count=np.int32(a.count), max_depth=np.int32(MAX_DEPTH),
+                        node_limit=np.int64(a.node_limit), family=a.family, **out)
     print("rows", len(out["y"]), "positives", int(out["y"].sum()),
           "pairs", len(np.unique(out["pair"])))
 
