@@ -204,6 +204,7 @@ def main():
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--timeout", type=float, default=600.0)
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-tune", action="store_true", help="ignore the autotuner cache")
     a = ap.parse_args()
     if a.impl == "reference":
         run_reference(a)
@@ -247,6 +248,14 @@ def main():
                  usec=torch.zeros(len(idx), dtype=torch.float32, device=dev),
                  map=torch.zeros(len(idx) * 64, dtype=torch.int16, device=dev))
         groups.append(g)
+    # launch shapes recorded by the autotuner for each group's bucket
+    shapes = []
+    for g in groups:
+        e = None if a.no_tune else solver.apply_tuned([pairs[i] for i in g["idx"]],
+                                                      directed=bool(g["flags"] & MCS_DIRECTED))
+        shapes.append(None if e is None else {k: e[k] for k in ("warps_per_block", "smem_stack_entries",
+                                                                 "blocks_per_sm")})
+        g["shape"] = shapes[-1]
     flush = torch.empty(512 << 20, dtype=torch.uint8, device=dev)
     launches_per_step = 2 * len(groups)      # pack + search per group
 
@@ -255,6 +264,9 @@ def main():
     def step(evs=None):
         rec = []
         for gi, g in enumerate(groups):
+            sh = g.get("shape")
+            solver.set_launch(*((sh["warps_per_block"], sh["blocks_per_sm"], sh["smem_stack_entries"])
+                                if sh else (4, 0, 256)))
             if evs is not None:
                 evs[gi][0].record(stream)
             rc = solver.solve_batch_device(g["n"], g["d_n"], g["d_adj_off"], g["d_adj"],
@@ -335,6 +347,9 @@ def main():
         torch.cuda.synchronize()
         t0 = time.perf_counter()
         for g in groups:
+            sh = g.get("shape")
+            solver.set_launch(*((sh["warps_per_block"], sh["blocks_per_sm"], sh["smem_stack_entries"])
+                                if sh else (4, 0, 256)))
             res = solver.solve_batch([pairs[i] for i in g["idx"]], flags=g["flags"],
                                      timeout_s=a.timeout, directed=bool(g["flags"] & MCS_DIRECTED))
             st = solver.last_stats()
@@ -380,7 +395,7 @@ def main():
             "p99_latency_ms": float(np.percentile(lats, 99)) if lats else None,
             "solved_per_step": solved_tot / a.steps / world,
             "config": dict(cfg, parallelism=f"replicas x{world}", l2="flushed between steps (512 MB write)",
-                           timeout_s=a.timeout),
+                           timeout_s=a.timeout, launch_shapes=shapes),
             "gpu_launches": launches_per_step * a.steps,
             "search_ms_per_step": sum(search_ms) / len(search_ms),
             "e2e": {"value": e2e_value, "unit": UNIT, "h2d_bytes_per_step": int(h2d),

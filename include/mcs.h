@@ -61,6 +61,9 @@ extern "C" {
                                     /* (mcs_set_order_model); exact either way; falls  */
                                     /* back to the degree order without a model        */
 #define MCS_NO_MAPPING        0x4u  /* do not return the mapping                       */
+#define MCS_GRAPH_REPLAY      0x10u /* mcs_solve_batch_device only: capture this call's */
+                                    /* launches in a CUDA graph and replay the graph   */
+                                    /* when called again with identical arguments      */
 #define MCS_NO_LEVEL_PRUNE    0x8u  /* diagnostic: do not re-test a level's bound      */
                                     /* before each sibling, so that with one warp the  */
                                     /* node count equals the sequential recursion's    */

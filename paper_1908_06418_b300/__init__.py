@@ -18,12 +18,14 @@ import numpy as np
 __all__ = ["Solver", "Result", "MCS_OK", "MCS_TIMEOUT", "MCS_PENDING", "MCS_ERR_ARG",
            "MCS_ERR_NOMEM", "MCS_ERR_CUDA", "MCS_ERR_DEVICE_STALL", "MCS_ERR_UNSUPPORTED",
            "MCS_DIRECTED", "MCS_ORDER_LEARNED", "MCS_NO_MAPPING", "MCS_NO_LEVEL_PRUNE",
-           "MCS_MAX_N", "lib_path", "load_library", "EXPORTED_SYMBOLS"]
+           "MCS_MAX_N", "MCS_GRAPH_REPLAY", "lib_path", "load_library", "EXPORTED_SYMBOLS",
+           "DeviceBatch", "pack_host"]
 
 MCS_MAX_N = 64
 MCS_OK, MCS_TIMEOUT, MCS_PENDING = 0, 1, 2
 MCS_ERR_ARG, MCS_ERR_NOMEM, MCS_ERR_CUDA, MCS_ERR_DEVICE_STALL, MCS_ERR_UNSUPPORTED = -1, -2, -3, -4, -5
 MCS_DIRECTED, MCS_ORDER_LEARNED, MCS_NO_MAPPING, MCS_NO_LEVEL_PRUNE = 0x1, 0x2, 0x4, 0x8
+MCS_GRAPH_REPLAY = 0x10
 
 _HERE = os.path.dirname(os.path.abspath(__file__))
 
@@ -179,6 +181,16 @@ class Solver:
         rc = self.lib.mcs_set_max_warps(self.ctx, int(warps))
         if rc:
             raise ValueError(self.strerror(rc))
+
+    def apply_tuned(self, pairs, directed: bool = False, cache: Optional[dict] = None) -> Optional[dict]:
+        """Sets the launch shape that the autotuner recorded for the batch's
+        bucket (see autotune.py); returns it, or None when none is cached."""
+        from . import autotune
+        c = autotune.load_cache() if cache is None else cache
+        e = c.get(autotune.bucket(pairs, directed))
+        if e:
+            self.set_launch(e["warps_per_block"], e["blocks_per_sm"], e["smem_stack_entries"])
+        return e
 
     def last_stats(self) -> dict:
         buf = (ctypes.c_double * 15)()

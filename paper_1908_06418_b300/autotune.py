@@ -1,0 +1,113 @@
+"""Autotuner for the search kernel's launch shape.
+
+    python -m paper_1908_06418_b300.autotune --workload c3 --workload c2
+
+For each workload it times device-resident batch solves (inputs already in
+HBM, CUDA events on the launching stream, best of `--reps`) over a grid of
+launch shapes -- warps per block, class-stack entries kept in shared memory
+per warp (which sets shared memory per warp and so the resident warps), and
+blocks per SM -- and records the fastest shape for the workload's bucket
+(directed or not, labelled or not, largest vertex count rounded up to 32 /
+48 / 64) in ``data/tune_cache.json``.  ``Solver.apply_tuned(pairs)`` applies
+the cached shape for a batch's bucket.
+"""
+from __future__ import annotations
+
+import argparse
+import itertools
+import json
+import os
+import time
+
+HERE = os.path.dirname(os.path.abspath(__file__))
+CACHE = os.path.join(HERE, "data", "tune_cache.json")
+
+SHAPES = [dict(warps_per_block=w, smem_stack_entries=s, blocks_per_sm=b)
+          for w, s, b in itertools.product((2, 4, 8), (128, 256, 512), (0,))]
+
+
+def bucket(pairs, directed: bool) -> str:
+    nmax = max(max(p.G.n, p.H.n) for p in pairs)
+    nb = 32 if nmax <= 32 else (48 if nmax <= 48 else 64)
+    lab = any(p.G.labels is not None for p in pairs)
+    return f"{'dir' if directed else 'und'}-{'lab' if lab else 'unl'}-n{nb}"
+
+
+def load_cache(path: str = CACHE) -> dict:
+    if os.path.exists(path):
+        with open(path) as f:
+            return json.load(f)
+    return {}
+
+
+def time_shape(solver, batch, n, shape, reps, timeout_s):
+    import torch
+    from . import MCS_OK
+    dev = batch.device
+    out = dict(size=torch.zeros(n, dtype=torch.int32, device=dev),
+               status=torch.zeros(n, dtype=torch.int32, device=dev),
+               nodes=torch.zeros(n, dtype=torch.int64, device=dev))
+    solver.set_launch(**shape)
+    stream = torch.cuda.Stream(dev)
+    best = None
+    for r in range(reps + 1):
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        rc = solver.solve_batch_device(n, batch.d_n, batch.d_adj_off, batch.d_adj, batch.d_lab_off,
+                                       batch.d_labels, out["size"], out["status"], out["nodes"],
+                                       flags=batch.flags, timeout_s=timeout_s,
+                                       stream=stream.cuda_stream)
+        e1.record(stream)
+        stream.synchronize()
+        if rc != 0 or not bool((out["status"] == MCS_OK).all()):
+            return None
+        if r > 0:
+            ms = e0.elapsed_time(e1)
+            best = ms if best is None else min(best, ms)
+    return best
+
+
+def tune(name: str, pairs, directed: bool, reps: int = 2, timeout_s: float = 120.0,
+         cache_path: str = CACHE) -> dict:
+    from . import Solver, DeviceBatch
+    batch = DeviceBatch(pairs, directed=directed)
+    results = []
+    with Solver(0) as s:
+        for shape in SHAPES:
+            t = time_shape(s, batch, len(pairs), shape, reps, timeout_s)
+            results.append(dict(shape, ms=t))
+            print(name, shape, t, flush=True)
+    ok = [r for r in results if r["ms"] is not None]
+    best = min(ok, key=lambda r: r["ms"])
+    cache = load_cache(cache_path)
+    key = bucket(pairs, directed)
+    cache[key] = dict(best, workload=name, measured=time.strftime("%Y-%m-%d"),
+                      sweep=[{k: r[k] for k in ("warps_per_block", "smem_stack_entries", "blocks_per_sm", "ms")}
+                             for r in results])
+    os.makedirs(os.path.dirname(cache_path), exist_ok=True)
+    with open(cache_path, "w") as f:
+        json.dump(cache, f, indent=1)
+    return cache[key]
+
+
+def main():
+    import synth
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--workload", action="append", default=[])
+    ap.add_argument("--reps", type=int, default=2)
+    ap.add_argument("--cache", default=CACHE)
+    a = ap.parse_args()
+    for w in a.workload or ["c3"]:
+        if w == "c2":
+            ps = [p for p in synth.config2_pairs() if p.directed]
+            tune(w, ps, True, a.reps, cache_path=a.cache)
+        elif w == "c3":
+            tune(w, synth.config3_pairs(), False, a.reps, cache_path=a.cache)
+        elif w == "c1":
+            tune(w, synth.config1_like(64), False, a.reps, cache_path=a.cache)
+        else:
+            raise SystemExit(f"unknown workload {w}")
+
+
+if __name__ == "__main__":
+    main()

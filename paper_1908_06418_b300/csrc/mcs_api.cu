@@ -241,6 +241,8 @@ void mcs_destroy(mcs_ctx* c) {
     if (c->stream) cudaStreamSynchronize(c->stream);
     mcs_serve_free(c);
     mcs_order_free(c);
+    if (c->graph_exec) cudaGraphExecDestroy(c->graph_exec);
+    if (c->graph) cudaGraphDestroy(c->graph);
     cudaFree(c->graphs); cudaFree(c->state); cudaFree(c->best); cudaFree(c->order);
     cudaFree(c->ctl); cudaFree(c->queue); cudaFree(c->qseq); cudaFree(c->gstack);
     cudaFree(c->d_in); cudaFree(c->d_out);
@@ -303,6 +305,43 @@ int mcs_solve_batch_device(mcs_ctx* c, int32_t npairs, const int32_t* d_n,
         return MCS_ERR_ARG;
     if (cudaSetDevice(c->device) != cudaSuccess) return MCS_ERR_CUDA;
     cudaStream_t s = stream ? (cudaStream_t)stream : c->stream;
+    if ((flags & MCS_GRAPH_REPLAY) && npairs > 0) {
+        // the call's identity: every argument that the launches capture
+        double tmo = timeout_s;
+        uint64_t key[16] = {(uint64_t)npairs, (uint64_t)d_n, (uint64_t)d_adj_off, (uint64_t)d_adj,
+                            (uint64_t)d_lab_off, (uint64_t)d_labels, (uint64_t)flags, 0,
+                            (uint64_t)d_size, (uint64_t)d_status, (uint64_t)d_nodes, (uint64_t)d_map,
+                            (uint64_t)d_usec, (uint64_t)c->warps_per_block,
+                            (uint64_t)c->smem_stack | ((uint64_t)c->blocks_per_sm << 32),
+                            (uint64_t)c->max_warps};
+        memcpy(&key[7], &tmo, sizeof(double));
+        if (!c->graph_exec || memcmp(key, c->graph_key, sizeof(key)) != 0) {
+            if (c->graph_exec) { cudaGraphExecDestroy(c->graph_exec); c->graph_exec = nullptr; }
+            if (c->graph) { cudaGraphDestroy(c->graph); c->graph = nullptr; }
+            // size every arena outside the capture: an uncaptured run on the
+            // context's stream (its results are overwritten by the replay)
+            int rc = run_device(c, npairs, d_n, d_adj_off, d_adj, d_lab_off, d_labels, nullptr,
+                                flags & ~MCS_GRAPH_REPLAY, timeout_s, d_size, d_status, d_nodes,
+                                d_map, d_usec, c->stream, false);
+            if (rc) return rc;
+            CK(cudaStreamSynchronize(c->stream));
+            CK(cudaStreamBeginCapture(c->stream, cudaStreamCaptureModeRelaxed));
+            rc = run_device(c, npairs, d_n, d_adj_off, d_adj, d_lab_off, d_labels, nullptr,
+                            flags & ~MCS_GRAPH_REPLAY, timeout_s, d_size, d_status, d_nodes, d_map,
+                            d_usec, c->stream, true);
+            cudaGraph_t g = nullptr;
+            cudaError_t e = cudaStreamEndCapture(c->stream, &g);
+            if (rc) { if (g) cudaGraphDestroy(g); return rc; }
+            CK(e);
+            c->graph = g;
+            CK(cudaGraphInstantiate(&c->graph_exec, g, 0));
+            memcpy(c->graph_key, key, sizeof(key));
+        }
+        CK(cudaGraphLaunch(c->graph_exec, s));
+        c->ev_pending = true;
+        c->stats[6] = c->stats[7] = 0;
+        return 0;
+    }
     int rc = run_device(c, npairs, d_n, d_adj_off, d_adj, d_lab_off, d_labels, nullptr, flags,
                         timeout_s, d_size, d_status, d_nodes, d_map, d_usec, s, true);
     c->ev_pending = (rc == 0 && npairs > 0);

@@ -218,6 +218,10 @@ struct mcs_ctx {
     Control h_ctl;
     struct MlpState* mlp = nullptr;   // ordering network (mcs_mlp.cu), created on first use
     struct ServeState* serve = nullptr; // serving (mcs_serve.cu), created on first mcs_submit
+    // MCS_GRAPH_REPLAY: one captured batch (its arguments and executable graph)
+    cudaGraphExec_t graph_exec = nullptr;
+    cudaGraph_t graph = nullptr;
+    uint64_t graph_key[16] = {0};
 };
 
 // kernels.cu entry points used by the host library
@@ -226,6 +230,7 @@ cudaError_t launch_pack(const PackParams& p, cudaStream_t s);
 cudaError_t launch_search(const SearchParams& p, int blocks, int warps_per_block,
                           bool directed, bool learned, cudaStream_t s);
 int search_max_blocks_per_sm(int warps_per_block, int smem_per_block, bool directed, bool learned);
+int serve_max_blocks_per_sm(int warps_per_block, int smem_per_block);
 cudaError_t launch_popc_bench(unsigned long long* out, int blocks, int iters, cudaStream_t s);
 cudaError_t launch_serve_init(Control* ctl, u64* qseq, uint32_t qcap, int32_t* in_flight, cudaStream_t s);
 }

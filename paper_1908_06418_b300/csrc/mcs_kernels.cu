@@ -450,6 +450,7 @@ __device__ void finalize_served(const SearchParams& P, int pair, int status, int
 }
 
 // Finish the pair: write size, status, nodes and the mapping (original numbers).
+template <bool SERVE>
 __device__ void finalize_pair(const SearchParams& P, int pair, int lane, int16_t* smap) {
     __threadfence();
     PairState& ps = P.state[pair];
@@ -467,7 +468,7 @@ __device__ void finalize_pair(const SearchParams& P, int pair, int lane, int16_t
     if (status == MCS_PENDING) {
         if (!DBG_OK(P.ctl, k >= 0 && k < kLevels, 7, k)) k = 0;
         status = ab ? MCS_TIMEOUT : MCS_OK;
-        if (P.serving) { finalize_served(P, pair, status, k, lane, smap); return; }
+        if (SERVE) { finalize_served(P, pair, status, k, lane, smap); return; }
         if (P.out_map) {
             const uint16_t* slot = P.best + ((size_t)pair * kLevels + k) * kMaxN;
             for (int i = lane; i < k; i += 32) {
@@ -479,7 +480,7 @@ __device__ void finalize_pair(const SearchParams& P, int pair, int lane, int16_t
         }
     } else {
         k = 0;
-        if (P.serving) { finalize_served(P, pair, status, 0, lane, smap); return; }
+        if (SERVE) { finalize_served(P, pair, status, 0, lane, smap); return; }
     }
     int last = 0;
     if (lane == 0) {
@@ -502,6 +503,7 @@ __device__ void finalize_pair(const SearchParams& P, int pair, int lane, int16_t
 
 // A task of `pair` ended: publish node count, drop the open count and finalise
 // the pair if this was its last task.
+template <bool SERVE>
 __device__ __forceinline__ void end_task(const SearchParams& P, int pair, u64& nodes, int lane,
                                          int16_t* smap) {
     int last = 0;
@@ -512,7 +514,7 @@ __device__ __forceinline__ void end_task(const SearchParams& P, int pair, u64& n
     }
     nodes = 0;
     last = __shfl_sync(FULL, last, 0);
-    if (last) finalize_pair(P, pair, lane, smap);
+    if (last) finalize_pair<SERVE>(P, pair, lane, smap);
 }
 
 // Serve mode, warp 0: admits requests that the host published in the mapped
@@ -580,8 +582,14 @@ __device__ __forceinline__ void load_level(const WarpSmem& w, int d, Top& t) {
     t.bound = (int)((inf >> 40) & 0xff);
 }
 
-template <bool DIR, bool LEARNED>
-__global__ void __launch_bounds__(256, 3) search_kernel(SearchParams P) {
+// Minimum resident 256-thread blocks per SM the register allocation must allow
+// (3 caps registers at 80 per thread, 2 at 128).
+#ifndef MCS_SEARCH_MINB
+#define MCS_SEARCH_MINB 3
+#endif
+
+template <bool DIR, bool LEARNED, bool SERVE>
+__global__ void __launch_bounds__(256, MCS_SEARCH_MINB) search_kernel(SearchParams P) {
     extern __shared__ __align__(16) unsigned char smem[];
     const int lane = threadIdx.x & 31;
     const int wib = threadIdx.x >> 5;
@@ -608,7 +616,7 @@ __global__ void __launch_bounds__(256, 3) search_kernel(SearchParams P) {
 
     Control* ctl = P.ctl;
     int16_t* smap = reinterpret_cast<int16_t*>(base + kSmRrem);   // finalize scratch (levels unused then)
-    if (P.serving && gw == 0) { serve_admit(P, lane); return; }
+    if (SERVE && gw == 0) { serve_admit(P, lane); return; }
     const bool level_prune = (P.flags & MCS_NO_LEVEL_PRUNE) == 0;
     const u64 qmask = P.qcap - 1;
     int cur_pair = -1;
@@ -663,7 +671,7 @@ __global__ void __launch_bounds__(256, 3) search_kernel(SearchParams P) {
         PairState& ps = P.state[pair];
         const PairGraph& pg = P.graphs[pair];
         u64 req_timeout = P.timeout_ns;
-        if (tflags & kTaskPack) {
+        if (SERVE && (tflags & kTaskPack)) {
             // a served request: copy it out of mapped host memory, pack it into
             // its slot and set up its state (this warp is its only user so far)
             const uint4* src = reinterpret_cast<const uint4*>(P.sv.hdata + (size_t)pair * kSlotBytes);
@@ -710,7 +718,7 @@ __global__ void __launch_bounds__(256, 3) search_kernel(SearchParams P) {
             if (pstat != MCS_PENDING) {                   // malformed input: report and skip
                 __syncwarp();
                 if (lane == 0) { P.qseq[qh & qmask] = qh + P.qcap; ps.open = 0; }
-                finalize_pair(P, pair, lane, smap);
+                finalize_pair<SERVE>(P, pair, lane, smap);
                 continue;
             }
             if (lane == 0) {
@@ -722,13 +730,13 @@ __global__ void __launch_bounds__(256, 3) search_kernel(SearchParams P) {
         }
         // load the pair's rows into shared memory (through L2: in serve mode a
         // slot is repacked while the kernel runs, so L1 may hold old lines)
-        if (pair != cur_pair || P.serving) {
+        if (pair != cur_pair || SERVE) {
             for (int i = lane; i < kMaxN; i += 32) {
                 w.gout[i] = __ldcg(&pg.gout[i]);
                 w.hout[i] = __ldcg(&pg.hout[i]);
                 if (DIR) { w.gin[i] = __ldcg(&pg.gin[i]); w.hin[i] = __ldcg(&pg.hin[i]); }
             }
-            cur_pair = P.serving ? -1 : pair;
+            cur_pair = SERVE ? -1 : pair;
         }
         if (!fresh) {
             int hd4[4] = {0, 0, 0, 0};
@@ -779,14 +787,14 @@ __global__ void __launch_bounds__(256, 3) search_kernel(SearchParams P) {
         deadline = shfl64(deadline, 0);
         long long c_busy = clock64();
         idle_cyc += c_busy - c_idle;
-        if (ab0) { end_task(P, pair, nodes, lane, smap); busy_cyc += clock64() - c_busy; continue; }
+        if (ab0) { end_task<SERVE>(P, pair, nodes, lane, smap); busy_cyc += clock64() - c_busy; continue; }
         if (fresh) {
             // root node entry (Algorithm 1): bound of Eq. 1, then class choice
             ++nodes;
             cvisits += t.C;
             Scan sc = scan_level(st, 0, t.C, -1, lane);
             t.bound = sc.sum;
-            if (t.bound <= inc) { end_task(P, pair, nodes, lane, smap); busy_cyc += clock64() - c_busy; continue; }
+            if (t.bound <= inc) { end_task<SERVE>(P, pair, nodes, lane, smap); busy_cyc += clock64() - c_busy; continue; }
             t.v = sc.key & 63;
             t.rrem = sc.R;
             t.flags = kTaskPending;
@@ -935,13 +943,16 @@ __global__ void __launch_bounds__(256, 3) search_kernel(SearchParams P) {
                 unsigned best = kKeyNone;
                 u64 bestR = 0;
                 const int nslot = t.C > 32 ? 2 : 1;
+                // parent and child both inside the shared-memory class cache:
+                // shared-memory loads/stores instead of generic ones
+                const bool in_sm = t.base + t.C + kMaxN <= st.S;
 #pragma unroll
                 for (int s = 0; s < 2; ++s) {
                     Ls[s] = 0; Rs[s] = 0;
                     if (s < nslot) {
                         int i = lane + 32 * s;
                         if (i < t.C) {
-                            ulonglong2 c = *st.at(t.base + i);
+                            ulonglong2 c = in_sm ? st.sm[t.base + i] : *st.at(t.base + i);
                             Ls[s] = c.x & ~vb;
                             Rs[s] = c.y & ~ub;
                         }
@@ -1003,17 +1014,29 @@ __global__ void __launch_bounds__(256, 3) search_kernel(SearchParams P) {
                             for (int k = 0; k < 4; ++k) {
                                 bool keep = lp[k] && rp[k];
                                 unsigned m = __ballot_sync(FULL, keep);
-                                if (keep) *st.at(pos + __popc(m & lanemask_lt())) = make_ulonglong2(lp[k], rp[k]);
+                                if (keep) {
+                                    const int q2 = pos + __popc(m & lanemask_lt());
+                                    if (in_sm) st.sm[q2] = make_ulonglong2(lp[k], rp[k]);
+                                    else *st.at(q2) = make_ulonglong2(lp[k], rp[k]);
+                                }
                                 pos += __popc(m);
                             }
                         } else {
                             const u64 l1 = L & gB, r1 = R & hB, l0 = L ^ l1, r0 = R ^ r1;
                             bool k1 = l1 && r1, k0 = l0 && r0;
                             unsigned m1 = __ballot_sync(FULL, k1);
-                            if (k1) *st.at(pos + __popc(m1 & lanemask_lt())) = make_ulonglong2(l1, r1);
+                            if (k1) {
+                                const int q2 = pos + __popc(m1 & lanemask_lt());
+                                if (in_sm) st.sm[q2] = make_ulonglong2(l1, r1);
+                                else *st.at(q2) = make_ulonglong2(l1, r1);
+                            }
                             pos += __popc(m1);
                             unsigned m0 = __ballot_sync(FULL, k0);
-                            if (k0) *st.at(pos + __popc(m0 & lanemask_lt())) = make_ulonglong2(l0, r0);
+                            if (k0) {
+                                const int q2 = pos + __popc(m0 & lanemask_lt());
+                                if (in_sm) st.sm[q2] = make_ulonglong2(l0, r0);
+                                else *st.at(q2) = make_ulonglong2(l0, r0);
+                            }
                             pos += __popc(m0);
                         }
                     }
@@ -1054,7 +1077,7 @@ __global__ void __launch_bounds__(256, 3) search_kernel(SearchParams P) {
                 if (t.d >= d0) load_level(w, t.d, t);
             }
         }
-        end_task(P, pair, nodes, lane, smap);
+        end_task<SERVE>(P, pair, nodes, lane, smap);
         busy_cyc += clock64() - c_busy;
     }
     if (lane == 0) {
@@ -1068,35 +1091,40 @@ __global__ void __launch_bounds__(256, 3) search_kernel(SearchParams P) {
     }
 }
 
-template <bool DIR, bool LEARNED>
+template <bool DIR, bool LEARNED, bool SERVE>
 static cudaError_t launch_t(const SearchParams& p, int blocks, int wpb, cudaStream_t s) {
     size_t smem = (size_t)wpb * p.warp_smem_bytes;
-    cudaFuncSetAttribute(search_kernel<DIR, LEARNED>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-    search_kernel<DIR, LEARNED><<<blocks, wpb * 32, smem, s>>>(p);
+    cudaFuncSetAttribute(search_kernel<DIR, LEARNED, SERVE>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    search_kernel<DIR, LEARNED, SERVE><<<blocks, wpb * 32, smem, s>>>(p);
     return cudaGetLastError();
 }
 
 cudaError_t launch_search(const SearchParams& p, int blocks, int warps_per_block, bool directed,
                           bool learned, cudaStream_t s) {
-    if (directed) return learned ? launch_t<true, true>(p, blocks, warps_per_block, s)
-                                 : launch_t<true, false>(p, blocks, warps_per_block, s);
-    return learned ? launch_t<false, true>(p, blocks, warps_per_block, s)
-                   : launch_t<false, false>(p, blocks, warps_per_block, s);
+    if (p.serving) return launch_t<false, false, true>(p, blocks, warps_per_block, s);
+    if (directed) return learned ? launch_t<true, true, false>(p, blocks, warps_per_block, s)
+                                 : launch_t<true, false, false>(p, blocks, warps_per_block, s);
+    return learned ? launch_t<false, true, false>(p, blocks, warps_per_block, s)
+                   : launch_t<false, false, false>(p, blocks, warps_per_block, s);
 }
 
-template <bool DIR, bool LEARNED>
+template <bool DIR, bool LEARNED, bool SERVE>
 static int occupancy_t(int wpb, int smem) {
     int nb = 0;
-    cudaFuncSetAttribute(search_kernel<DIR, LEARNED>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
-    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, search_kernel<DIR, LEARNED>, wpb * 32, smem);
+    cudaFuncSetAttribute(search_kernel<DIR, LEARNED, SERVE>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
+    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, search_kernel<DIR, LEARNED, SERVE>, wpb * 32, smem);
     return nb;
 }
 
 int search_max_blocks_per_sm(int warps_per_block, int smem_per_block, bool directed, bool learned) {
-    if (directed) return learned ? occupancy_t<true, true>(warps_per_block, smem_per_block)
-                                 : occupancy_t<true, false>(warps_per_block, smem_per_block);
-    return learned ? occupancy_t<false, true>(warps_per_block, smem_per_block)
-                   : occupancy_t<false, false>(warps_per_block, smem_per_block);
+    if (directed) return learned ? occupancy_t<true, true, false>(warps_per_block, smem_per_block)
+                                 : occupancy_t<true, false, false>(warps_per_block, smem_per_block);
+    return learned ? occupancy_t<false, true, false>(warps_per_block, smem_per_block)
+                   : occupancy_t<false, false, false>(warps_per_block, smem_per_block);
+}
+
+int serve_max_blocks_per_sm(int warps_per_block, int smem_per_block) {
+    return occupancy_t<false, false, true>(warps_per_block, smem_per_block);
 }
 
 // Serve mode: reset the control block and the ring before a server launch.

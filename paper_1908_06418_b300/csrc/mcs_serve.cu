@@ -118,7 +118,7 @@ int serve_state(mcs_ctx* c, ServeState** out) {
     CKS(cudaMalloc((void**)&S->in_flight, sizeof(int32_t)));
     // launch shape: the context's, undirected, plain order
     S->wsmem = warp_smem_bytes(c->smem_stack);
-    int per_sm = search_max_blocks_per_sm(c->warps_per_block, c->warps_per_block * S->wsmem, false, false);
+    int per_sm = serve_max_blocks_per_sm(c->warps_per_block, c->warps_per_block * S->wsmem);
     if (per_sm <= 0) return MCS_ERR_UNSUPPORTED;
     if (c->blocks_per_sm > 0 && c->blocks_per_sm < per_sm) per_sm = c->blocks_per_sm;
     S->blocks = c->sms * per_sm;

@@ -221,3 +221,56 @@ def test_config3_full_batch_parity(solver):
     for i in range(0, 4096, 16):
         p, r = pairs[i], res[i]
         assert oracle.verify(p.G.adj, p.H.adj, r.g_idx, r.h_idx, p.G.labels, p.H.labels) == 1
+
+
+def test_graph_replay_matches_direct_launch(solver):
+    import torch
+    from paper_1908_06418_b300 import DeviceBatch, MCS_GRAPH_REPLAY
+    pairs = _rand_pairs(64, 8, 24, 99)
+    b = DeviceBatch(pairs)
+    n = len(pairs)
+    stream = torch.cuda.Stream(b.device)
+
+    def run(flags):
+        o = [torch.full((n,), -9, dtype=torch.int32, device=b.device) for _ in range(2)]
+        nodes = torch.zeros(n, dtype=torch.int64, device=b.device)
+        mp = torch.zeros(n * 64, dtype=torch.int16, device=b.device)
+        rc = solver.solve_batch_device(n, b.d_n, b.d_adj_off, b.d_adj, b.d_lab_off, b.d_labels,
+                                       o[0], o[1], nodes, mp, flags=flags, timeout_s=60,
+                                       stream=stream.cuda_stream)
+        stream.synchronize()
+        assert rc == 0
+        return o[0].cpu().numpy(), o[1].cpu().numpy(), mp.cpu().numpy().reshape(n, 64)
+
+    s0, st0, _ = run(0)
+    for rep in range(3):
+        s1, st1, mp = run(MCS_GRAPH_REPLAY)
+        assert (st1 == 0).all() and (s1 == s0).all()
+        for i, p in enumerate(pairs):
+            g = np.nonzero(mp[i] >= 0)[0]
+            assert oracle.verify(p.G.adj, p.H.adj, g, mp[i][g]) == 1
+
+
+@pytest.mark.parametrize("shape", [(2, 0, 128), (8, 0, 512), (4, 1, 64), (2, 2, 2080)])
+def test_launch_shapes_give_same_sizes(solver, shape):
+    pairs = _rand_pairs(80, 6, 24, 123, k=2)
+    ref = [oracle.mcs(p.G.adj, p.H.adj, p.G.labels, p.H.labels).size for p in pairs]
+    solver.set_launch(*shape)
+    try:
+        res = solver.solve_batch(pairs, timeout_s=60)
+    finally:
+        solver.set_launch(4, 0, 256)
+    assert [r.size for r in res] == ref
+    assert all(r.status == 0 for r in res)
+
+
+def test_launch_shape_that_does_not_fit_is_rejected(solver):
+    from paper_1908_06418_b300 import MCS_ERR_UNSUPPORTED
+    p = synth.config1_pair()
+    solver.set_launch(8, 0, 2080)          # 8 x 36.5 KB of shared memory per block
+    try:
+        with pytest.raises(RuntimeError, match="unsupported"):
+            solver.solve(p.G.adj, p.H.adj, timeout_s=10)
+    finally:
+        solver.set_launch(4, 0, 256)
+    assert solver.solve(p.G.adj, p.H.adj, timeout_s=10).size == 13
