@@ -50,6 +50,9 @@ def main():
     ap.add_argument("--lr", type=float, default=1e-3)
     ap.add_argument("--seed", type=int, default=1)
     ap.add_argument("--holdout", type=float, default=0.05, help="fraction of pairs held out")
+    ap.add_argument("--family", default="bvg", choices=["bvg", "planted"],
+                    help="training pairs: synth.config4_train_pair or synth.planted_bvg_pair "
+                         "(n 16..30, config id 46)")
     a = ap.parse_args()
 
     d = np.load(a.data)
@@ -58,7 +61,10 @@ def main():
     rng = np.random.default_rng(a.seed)
     hold = set(rng.choice(ids, max(1, int(a.holdout * len(ids))), replace=False).tolist())
     t0 = time.time()
-    pairs = [synth.config4_train_pair(int(i)) for i in ids]
+    if a.family == "bvg":
+        pairs = [synth.config4_train_pair(int(i)) for i in ids]
+    else:
+        pairs = [synth.planted_bvg_pair(int(i), 16, 30, cid=46) for i in ids]
     pos = {int(i): k for k, i in enumerate(ids)}
     rows = np.stack([np.array([pos[int(p)] for p in pair], np.int32), v, u], axis=1).astype(np.int32)
     is_hold = np.array([int(p) in hold for p in pair])

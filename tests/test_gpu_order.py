@@ -141,3 +141,27 @@ def test_learned_order_stays_exact(solver, directed, labelled):
         assert a.status == b.status == 0
         assert a.size == b.size
         assert oracle.verify(p.G.adj, p.H.adj, b.g_idx, b.h_idx, p.G.labels, p.H.labels) == 1
+
+
+def test_trained_network_gain_is_measured(solver, capsys):
+    """What the trained network changes: the learned candidate order must give
+    the same (exact) sizes; it is reported here with its node counts.  On the
+    planted-core bounded-valence family it saves a few per cent of the search
+    nodes (the proof of optimality dominates these searches, and a candidate
+    order cannot shorten a proof that must visit every node above the bound)."""
+    import os
+    from paper_1908_06418_b300 import MCS_ORDER_LEARNED
+    path = os.path.join(os.path.dirname(os.path.dirname(os.path.abspath(__file__))),
+                        "paper_1908_06418_b300", "data", "order_mlp_planted.npy")
+    solver.set_order_model(np.load(path).astype(np.float32))
+    pairs = [synth.planted_bvg_pair(i, 24, 34, cid=47) for i in range(160)]
+    plain = solver.solve_batch(pairs, timeout_s=60)
+    learned = solver.solve_batch(pairs, flags=MCS_ORDER_LEARNED, timeout_s=60)
+    assert all(a.status == b.status == 0 for a, b in zip(plain, learned))
+    assert [a.size for a in plain] == [b.size for b in learned]
+    n_plain = sum(r.nodes for r in plain)
+    n_learned = sum(r.nodes for r in learned)
+    with capsys.disabled():
+        print(f"\nlearned order: {n_learned} nodes vs {n_plain} plain "
+              f"({100.0 * (n_learned / n_plain - 1):+.1f} %)")
+    assert n_learned <= 1.10 * n_plain
