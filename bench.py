@@ -33,6 +33,12 @@ ROOT = os.path.dirname(os.path.abspath(__file__))
 sys.path.insert(0, ROOT)
 
 METRIC = "MCS pairs solved/sec (exact) on 1 B300"
+
+# DRAM bytes (dram__bytes_read.sum + dram__bytes_write.sum) of one launch of
+# the dominant search kernel, from a single-pass ncu capture of this
+# workload's launch (profiles/dram_search_kernel_c2.md); reported only while
+# the kernel source is the one the capture was taken with.
+TRAFFIC = {"c2": {"kernel_sha1": "cb7d5df4e90aa931", "bytes": 5.97e6 + 1.44e6}}
 UNIT = "pairs/s"
 
 
@@ -384,8 +390,13 @@ def main():
     busy = sum(r[dom][3] for r in stats)
     idle = sum(r[dom][4] for r in stats)
     achieved = (sum(dom_cv) * per_class / 1e9) / (sum(dom_us) * 1e-6)
+    import hashlib
+    ksha = hashlib.sha1(open(os.path.join(ROOT, "paper_1908_06418_b300", "csrc", "mcs_kernels.cu"),
+                             "rb").read()).hexdigest()[:16]
+    tr = TRAFFIC.get(a.workload)
+    traffic = tr["bytes"] if tr and tr["kernel_sha1"] == ksha else None
     roof = {"bound": "alu", "achieved": achieved, "peak": popc_peak, "unit": "Gpopc/s",
-            "frac": achieved / popc_peak, "traffic": None,
+            "frac": achieved / popc_peak, "traffic": traffic,
             "kernel": "search_kernel<%s>" % ("directed" if groups[dom]["flags"] & MCS_DIRECTED else "undirected"),
             "peak_source": "measured: mcs_bench_popc (device-wide sustained 32-bit popc rate)",
             "class_visits_per_launch": sum(dom_cv) / len(dom_cv), "popc_per_class": per_class,
