@@ -167,6 +167,15 @@ def oracle_sample(name: str, n_pairs: int, budget: float, offset: int = 0):
                        f"{min(cores, len(idx))} worker processes")
 
 
+def apply_shape(solver, sh):
+    """The autotuned launch shape of a group, else the library's defaults."""
+    if sh:
+        solver.set_launch(sh["warps_per_block"], sh["blocks_per_sm"] or -1, sh["smem_stack_entries"],
+                          search_group=sh["search_group"])
+    else:
+        solver.reset_launch()
+
+
 def run_reference(a):
     rank = int(os.environ.get("RANK", "0"))
     if rank != 0:
@@ -265,8 +274,9 @@ def main():
     for g in groups:
         e = None if a.no_tune else solver.apply_tuned([pairs[i] for i in g["idx"]],
                                                       directed=bool(g["flags"] & MCS_DIRECTED))
-        shapes.append(None if e is None else {k: e[k] for k in ("warps_per_block", "smem_stack_entries",
-                                                                 "blocks_per_sm")})
+        shapes.append(None if e is None else dict({k: e[k] for k in ("warps_per_block", "smem_stack_entries",
+                                                                      "blocks_per_sm")},
+                                                  search_group=e.get("search_group", 32)))
         g["shape"] = shapes[-1]
     flush = torch.empty(512 << 20, dtype=torch.uint8, device=dev)
     launches_per_step = 2 * len(groups)      # pack + search per group
@@ -277,8 +287,7 @@ def main():
         rec = []
         for gi, g in enumerate(groups):
             sh = g.get("shape")
-            solver.set_launch(*((sh["warps_per_block"], sh["blocks_per_sm"], sh["smem_stack_entries"])
-                                if sh else (4, 0, 256)))
+            apply_shape(solver, sh)
             if evs is not None:
                 evs[gi][0].record(stream)
             rc = solver.solve_batch_device(g["n"], g["d_n"], g["d_adj_off"], g["d_adj"],
@@ -360,8 +369,7 @@ def main():
         t0 = time.perf_counter()
         for g in groups:
             sh = g.get("shape")
-            solver.set_launch(*((sh["warps_per_block"], sh["blocks_per_sm"], sh["smem_stack_entries"])
-                                if sh else (4, 0, 256)))
+            apply_shape(solver, sh)
             res = solver.solve_batch([pairs[i] for i in g["idx"]], flags=g["flags"],
                                      timeout_s=a.timeout, directed=bool(g["flags"] & MCS_DIRECTED))
             st = solver.last_stats()

@@ -210,21 +210,34 @@ int mcs_submit(mcs_ctx* ctx, const mcs_graph* G, const mcs_graph* H,
  * the first poll that reports it. */
 int mcs_poll(mcs_ctx* ctx, uint64_t ticket, mcs_result* out);
 
-/* Launch shape used by every solve on this context (0 keeps the current or
- * the tuned value): warps per block, blocks per SM, class-stack entries kept
- * in shared memory per warp. */
+/* Launch shape used by every solve on this context: warps per block (1..8,
+ * default 4), blocks per SM (default: as many as fit), class-stack entries
+ * kept in shared memory per searcher (default 256 for whole-warp searchers,
+ * 32 for narrower ones).  0 keeps the current value, -1 restores the default;
+ * anything else out of range is MCS_ERR_ARG.  A shape whose shared memory
+ * does not fit an SM makes the next solve return MCS_ERR_UNSUPPORTED. */
 int mcs_set_launch(mcs_ctx* ctx, int warps_per_block, int blocks_per_sm,
                    int smem_stack_entries);
 
-/* Restricts a solve to `warps` resident warps in total (0 = the full grid).
+/* Restricts a solve to `warps` resident searchers in total (0 = the full
+ * grid; a searcher is one warp unless mcs_set_search_group splits warps).
  * With warps == 1 the search order is deterministic. */
 int mcs_set_max_warps(mcs_ctx* ctx, int warps);
+
+/* Lanes per depth-first searcher of mcs_solve_batch[_device] (Section III's
+ * data-parallel node step, Algorithm 1): 32 runs one search per warp with the
+ * label classes of a node spread over the lanes; 16 or 8 runs two or four
+ * independent searches per warp, each over its own lane group, for instances
+ * whose nodes hold few classes.  Results are the same for every value (the
+ * node counts of a multi-searcher solve vary as with any work stealing).
+ * Any other value: MCS_ERR_ARG.  Serving (mcs_submit) always uses 32. */
+int mcs_set_search_group(mcs_ctx* ctx, int lanes);
 
 /* Statistics of the last solve on this context: out[0] search-kernel
  * microseconds (for mcs_solve_batch_device: once its stream has passed the
  * launch, else the previous value), out[1] total nodes (host API calls only),
  * out[2] donated tasks, out[3] donated tasks taken up, out[4] child levels
- * that spilled past the shared-memory class cache, out[5] warps launched,
+ * that spilled past the shared-memory class cache, out[5] searchers launched,
  * out[6] bytes copied host to device, out[7] bytes copied device to host
  * (out[6..7]: host API calls only), out[8] label classes read by node
  * expansions (the unit of algorithmic work), out[9] children cut by the bound

@@ -49,7 +49,7 @@ class _Result(ctypes.Structure):
 
 EXPORTED_SYMBOLS = ["mcs_create", "mcs_destroy", "mcs_solve", "mcs_solve_batch",
                     "mcs_solve_batch_device", "mcs_submit", "mcs_poll", "mcs_set_launch",
-                    "mcs_set_max_warps", "mcs_last_stats", "mcs_bench_popc", "mcs_strerror", "mcs_error_detail",
+                    "mcs_set_max_warps", "mcs_set_search_group", "mcs_last_stats", "mcs_bench_popc", "mcs_strerror", "mcs_error_detail",
                     "mcs_solve_batch_noalloc", "mcs_set_order_model", "mcs_get_order_model",
                     "mcs_order_eval", "mcs_order_train"]
 
@@ -89,6 +89,8 @@ def load_library():
     lib.mcs_set_launch.restype = ctypes.c_int
     lib.mcs_set_max_warps.argtypes = [vp, ctypes.c_int]
     lib.mcs_set_max_warps.restype = ctypes.c_int
+    lib.mcs_set_search_group.argtypes = [vp, ctypes.c_int]
+    lib.mcs_set_search_group.restype = ctypes.c_int
     lib.mcs_last_stats.argtypes = [vp, ctypes.POINTER(ctypes.c_double), ctypes.c_int]
     lib.mcs_last_stats.restype = ctypes.c_int
     lib.mcs_bench_popc.argtypes = [vp, ctypes.POINTER(ctypes.c_double)]
@@ -172,13 +174,27 @@ class Solver:
         self.close()
 
     # -- configuration ----------------------------------------------------
-    def set_launch(self, warps_per_block=0, blocks_per_sm=0, smem_stack_entries=0):
+    def set_launch(self, warps_per_block=0, blocks_per_sm=0, smem_stack_entries=0, search_group=None):
+        """0 keeps a value, -1 restores its default; search_group (lanes per
+        searcher: 32, 16, 8 or 4) is left alone when None."""
         rc = self.lib.mcs_set_launch(self.ctx, warps_per_block, blocks_per_sm, smem_stack_entries)
         if rc:
             raise ValueError(self.strerror(rc))
+        if search_group is not None:
+            self.set_search_group(search_group)
+
+    def reset_launch(self):
+        """Back to the default launch shape and search group (8 lanes)."""
+        self.set_launch(-1, -1, -1, search_group=8)
 
     def set_max_warps(self, warps: int):
         rc = self.lib.mcs_set_max_warps(self.ctx, int(warps))
+        if rc:
+            raise ValueError(self.strerror(rc))
+
+    def set_search_group(self, lanes: int):
+        """Lanes per searcher: 32 (one search per warp), 16 or 8."""
+        rc = self.lib.mcs_set_search_group(self.ctx, int(lanes))
         if rc:
             raise ValueError(self.strerror(rc))
 
@@ -189,7 +205,8 @@ class Solver:
         c = autotune.load_cache() if cache is None else cache
         e = c.get(autotune.bucket(pairs, directed))
         if e:
-            self.set_launch(e["warps_per_block"], e["blocks_per_sm"], e["smem_stack_entries"])
+            self.set_launch(e["warps_per_block"], e["blocks_per_sm"] or -1, e["smem_stack_entries"],
+                            search_group=e.get("search_group", 32))
         return e
 
     def last_stats(self) -> dict:

@@ -4,9 +4,11 @@
 
 For each workload it times device-resident batch solves (inputs already in
 HBM, CUDA events on the launching stream, best of `--reps`) over a grid of
-launch shapes -- warps per block, class-stack entries kept in shared memory
-per warp (which sets shared memory per warp and so the resident warps), and
-blocks per SM -- and records the fastest shape for the workload's bucket
+launch shapes -- lanes per searcher (32: one search per warp; 16, 8, 4: two,
+four or eight per warp), warps per block, class-stack entries kept in shared
+memory per searcher (which sets shared memory per searcher and so the
+resident searchers), and blocks per SM -- and records the fastest shape for
+the workload's bucket
 (directed or not, labelled or not, largest vertex count rounded up to 32 /
 48 / 64) in ``data/tune_cache.json``.  ``Solver.apply_tuned(pairs)`` applies
 the cached shape for a batch's bucket.
@@ -22,8 +24,15 @@ import time
 HERE = os.path.dirname(os.path.abspath(__file__))
 CACHE = os.path.join(HERE, "data", "tune_cache.json")
 
-SHAPES = [dict(warps_per_block=w, smem_stack_entries=s, blocks_per_sm=b)
-          for w, s, b in itertools.product((2, 4, 8), (128, 256, 512), (0,))]
+SHAPES = ([dict(search_group=32, warps_per_block=w, smem_stack_entries=s, blocks_per_sm=0)
+           for w, s in itertools.product((4,), (128, 256))]
+          + [dict(search_group=16, warps_per_block=w, smem_stack_entries=s, blocks_per_sm=0)
+             for w, s in itertools.product((4,), (64, 128))]
+          + [dict(search_group=8, warps_per_block=w, smem_stack_entries=s, blocks_per_sm=0)
+             for w, s in itertools.product((2, 4, 8), (16, 32, 64))]
+          + [dict(search_group=4, warps_per_block=w, smem_stack_entries=s, blocks_per_sm=0)
+             for w, s in itertools.product((2, 4), (8, 16))])
+KEYS = ("search_group", "warps_per_block", "smem_stack_entries", "blocks_per_sm")
 
 
 def bucket(pairs, directed: bool) -> str:
@@ -47,7 +56,8 @@ def time_shape(solver, batch, n, shape, reps, timeout_s):
     out = dict(size=torch.zeros(n, dtype=torch.int32, device=dev),
                status=torch.zeros(n, dtype=torch.int32, device=dev),
                nodes=torch.zeros(n, dtype=torch.int64, device=dev))
-    solver.set_launch(**shape)
+    solver.set_launch(shape["warps_per_block"], shape["blocks_per_sm"] or -1, shape["smem_stack_entries"],
+                      search_group=shape["search_group"])
     stream = torch.cuda.Stream(dev)
     best = None
     for r in range(reps + 1):
@@ -82,8 +92,7 @@ def tune(name: str, pairs, directed: bool, reps: int = 2, timeout_s: float = 120
     cache = load_cache(cache_path)
     key = bucket(pairs, directed)
     cache[key] = dict(best, workload=name, measured=time.strftime("%Y-%m-%d"),
-                      sweep=[{k: r[k] for k in ("warps_per_block", "smem_stack_entries", "blocks_per_sm", "ms")}
-                             for r in results])
+                      sweep=[{k: r[k] for k in KEYS + ("ms",)} for r in results])
     os.makedirs(os.path.dirname(cache_path), exist_ok=True)
     with open(cache_path, "w") as f:
         json.dump(cache, f, indent=1)
@@ -101,6 +110,9 @@ def main():
         if w == "c2":
             ps = [p for p in synth.config2_pairs() if p.directed]
             tune(w, ps, True, a.reps, cache_path=a.cache)
+        elif w == "c2u":
+            ps = [p for p in synth.config2_pairs() if not p.directed]
+            tune(w, ps, False, a.reps, cache_path=a.cache)
         elif w == "c3":
             tune(w, synth.config3_pairs(), False, a.reps, cache_path=a.cache)
         elif w == "c1":

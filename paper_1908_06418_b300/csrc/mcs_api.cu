@@ -58,15 +58,17 @@ int grow_host(T*& p, size_t& cap, size_t need) {
 }
 
 int launch_shape(mcs_ctx* c, bool directed, bool learned, int* blocks, int* warps_total, int* wsmem) {
-    *wsmem = warp_smem_bytes(c->smem_stack);
-    int smem_block = c->warps_per_block * *wsmem;
-    int per_sm = search_max_blocks_per_sm(c->warps_per_block, smem_block, directed, learned);
+    // warps_total counts searchers: 32 / group_lanes of them share a warp
+    const int spb = c->warps_per_block * (32 / c->group_lanes);
+    *wsmem = warp_smem_bytes(stack_entries(c, c->group_lanes), c->group_lanes);
+    int smem_block = spb * *wsmem;
+    int per_sm = search_max_blocks_per_sm(c->warps_per_block, smem_block, directed, learned, c->group_lanes);
     if (per_sm <= 0) return MCS_ERR_UNSUPPORTED;
     if (c->blocks_per_sm > 0) per_sm = std::min(per_sm, c->blocks_per_sm);
     *blocks = c->sms * per_sm;
-    *warps_total = *blocks * c->warps_per_block;
+    *warps_total = *blocks * spb;
     if (c->max_warps > 0) {
-        int need_blocks = (c->max_warps + c->warps_per_block - 1) / c->warps_per_block;
+        int need_blocks = (c->max_warps + spb - 1) / spb;
         *blocks = std::min(*blocks, need_blocks);
         *warps_total = std::min(*warps_total, c->max_warps);
     }
@@ -98,7 +100,8 @@ int ensure_ring(mcs_ctx* c, int warps, int npairs) {
         CK(cudaMalloc((void**)&c->qseq, sizeof(u64) * (size_t)q));
         c->qcap = q;
     }
-    size_t per = kStackMax > c->smem_stack ? (size_t)(kStackMax - c->smem_stack) : 0;
+    const int S = stack_entries(c, c->group_lanes);
+    size_t per = kStackMax > S ? (size_t)(kStackMax - S) : 0;
     size_t need = per * (size_t)warps;
     if (need > c->gstack_entries || !c->gstack) {
         cudaFree(c->gstack);
@@ -136,7 +139,7 @@ int run_device(mcs_ctx* c, int npairs, const int32_t* d_n, const int64_t* d_adj_
     rc = launch_shape(c, directed, learned, &blocks, &warps, &wsmem);
     if (rc) return rc;
     if ((rc = ensure_pairs(c, npairs))) return rc;
-    if ((rc = ensure_ring(c, blocks * c->warps_per_block, npairs))) return rc;
+    if ((rc = ensure_ring(c, warps, npairs))) return rc;
 
     PackParams pp;
     memset(&pp, 0, sizeof(pp));
@@ -179,7 +182,7 @@ int run_device(mcs_ctx* c, int npairs, const int32_t* d_n, const int64_t* d_adj_
     sp.queue = c->queue;
     sp.qseq = c->qseq;
     sp.qcap = c->qcap;
-    sp.stack_smem = c->smem_stack;
+    sp.stack_smem = stack_entries(c, c->group_lanes);
     sp.warp_smem_bytes = wsmem;
     sp.max_warps = warps;
     sp.gstack = c->gstack;
@@ -190,7 +193,7 @@ int run_device(mcs_ctx* c, int npairs, const int32_t* d_n, const int64_t* d_adj_
     sp.out_map = (flags & MCS_NO_MAPPING) ? nullptr : d_map;
     sp.out_usec = d_usec;
     if (timed) CK(cudaEventRecord(c->ev0, s));
-    CK(launch_search(sp, blocks, c->warps_per_block, directed, learned, s));
+    CK(launch_search(sp, blocks, c->warps_per_block, directed, learned, s, c->group_lanes));
     if (timed) CK(cudaEventRecord(c->ev1, s));
     c->stats[5] = warps;
     return 0;
@@ -256,12 +259,19 @@ void mcs_destroy(mcs_ctx* c) {
 
 int mcs_set_launch(mcs_ctx* c, int warps_per_block, int blocks_per_sm, int smem_stack_entries) {
     if (!c) return MCS_ERR_ARG;
-    if (warps_per_block < 0 || warps_per_block > 8 || blocks_per_sm < 0 || smem_stack_entries < 0 ||
+    if (warps_per_block < -1 || warps_per_block > 8 || blocks_per_sm < -1 || smem_stack_entries < -1 ||
         smem_stack_entries > kStackMax)
         return MCS_ERR_ARG;
-    if (warps_per_block) c->warps_per_block = warps_per_block;
-    if (blocks_per_sm) c->blocks_per_sm = blocks_per_sm;
-    if (smem_stack_entries) c->smem_stack = smem_stack_entries;
+    // 0 keeps the current value, -1 restores the default
+    if (warps_per_block) c->warps_per_block = warps_per_block > 0 ? warps_per_block : 4;
+    if (blocks_per_sm) c->blocks_per_sm = blocks_per_sm > 0 ? blocks_per_sm : 0;
+    if (smem_stack_entries) c->smem_stack = smem_stack_entries > 0 ? smem_stack_entries : 0;
+    return 0;
+}
+
+int mcs_set_search_group(mcs_ctx* c, int lanes) {
+    if (!c || (lanes != 4 && lanes != 8 && lanes != 16 && lanes != 32)) return MCS_ERR_ARG;
+    c->group_lanes = lanes;
     return 0;
 }
 
@@ -311,7 +321,7 @@ int mcs_solve_batch_device(mcs_ctx* c, int32_t npairs, const int32_t* d_n,
         uint64_t key[16] = {(uint64_t)npairs, (uint64_t)d_n, (uint64_t)d_adj_off, (uint64_t)d_adj,
                             (uint64_t)d_lab_off, (uint64_t)d_labels, (uint64_t)flags, 0,
                             (uint64_t)d_size, (uint64_t)d_status, (uint64_t)d_nodes, (uint64_t)d_map,
-                            (uint64_t)d_usec, (uint64_t)c->warps_per_block,
+                            (uint64_t)d_usec, (uint64_t)c->warps_per_block | ((uint64_t)c->group_lanes << 32),
                             (uint64_t)c->smem_stack | ((uint64_t)c->blocks_per_sm << 32),
                             (uint64_t)c->max_warps};
         memcpy(&key[7], &tmo, sizeof(double));

@@ -132,7 +132,7 @@ struct SearchParams {
     uint32_t qcap;                 // power of two
     int32_t stack_smem;            // class entries per warp kept in shared memory
     int32_t warp_smem_bytes;
-    int32_t max_warps;             // warps that take part (others exit at once)
+    int32_t max_warps;             // searchers that take part (others exit at once)
     ulonglong2* gstack;            // per-warp overflow of the class stack
     const uint8_t* rank;           // learned order: [npairs][kMaxN][kMaxN] rank of u for v, or null
     // outputs
@@ -166,15 +166,23 @@ struct PackParams {
     const int32_t* order;          // processing order of the pairs (may be null)
 };
 
-// Per-warp shared memory layout (bytes from the warp's base).
-constexpr int kSmAdj = 0;                        // 4 * 64 * 8 = 2048
-constexpr int kSmRrem = 2048;                    // 65 * 8 -> 528
-constexpr int kSmInfo = kSmRrem + 528;           // 65 * 8 -> 528
-constexpr int kSmM = kSmInfo + 528;              // 64 + 64
-constexpr int kSmCls = kSmM + 128;               // 16-byte aligned
-static_assert(kSmCls % 16 == 0, "class cache must be 16-byte aligned");
+// Per-searcher shared memory layout (bytes from the searcher's base).  The
+// pair's adjacency rows are copied into shared memory for whole-warp
+// searchers; narrower searchers (several per warp) read them from global
+// memory through the read-only cache, which leaves room for more of them.
+constexpr int kSmAdjBytes = 4 * 64 * 8;          // gout, gin, hout, hin
+__host__ __device__ constexpr bool adj_in_smem(int gs) { return gs == 32; }
+__host__ __device__ constexpr int sm_adj_bytes(int gs) { return adj_in_smem(gs) ? kSmAdjBytes : 0; }
+constexpr int kSmRremOff = 0;                    // 65 * 8 -> 528   (offsets after the adjacency)
+constexpr int kSmInfoOff = 528;                  // 65 * 8 -> 528
+constexpr int kSmMOff = 1056;                    // 64 + 64
+constexpr int kSmCycOff = 1184;                  // busy, idle cycle counters, clock mark (3 x 8)
+constexpr int kSmClsOff = 1216;                  // 16-byte aligned
+static_assert(kSmClsOff % 16 == 0 && kSmAdjBytes % 16 == 0, "class cache must be 16-byte aligned");
 
-inline int warp_smem_bytes(int stack_entries) { return kSmCls + 16 * stack_entries; }
+inline int warp_smem_bytes(int stack_entries, int gs = 32) {
+    return sm_adj_bytes(gs) + kSmClsOff + 16 * stack_entries;
+}
 
 }  // namespace mcsk
 
@@ -193,8 +201,9 @@ struct mcs_ctx {
     int sms = 0;
     int warps_per_block = 4;
     int blocks_per_sm = 0;        // 0: as many as fit
-    int smem_stack = 256;
-    int max_warps = 0;            // 0: every launched warp
+    int smem_stack = 0;           // class entries per searcher in shared memory (0: default)
+    int max_warps = 0;            // 0: every launched searcher
+    int group_lanes = 8;          // lanes per searcher of batch solves: 32, 16, 8 or 4
     // device arenas
     int pairs_cap = 0;
     PairGraph* graphs = nullptr;
@@ -224,12 +233,21 @@ struct mcs_ctx {
     uint64_t graph_key[16] = {0};
 };
 
+// Class-stack entries per searcher kept in shared memory: the value set by
+// mcs_set_launch, else 256 for whole-warp searchers and 32 for narrower ones
+// (many more of them share an SM; deeper levels go to the global overflow).
+inline int stack_entries(const mcs_ctx* c, int gs) {
+    return c->smem_stack > 0 ? c->smem_stack : (gs == 32 ? 256 : 32);
+}
+
 // kernels.cu entry points used by the host library
 namespace mcsk {
 cudaError_t launch_pack(const PackParams& p, cudaStream_t s);
+// gs: lanes per searcher (32: one search per warp; 16, 8 or 4: two, four or eight)
 cudaError_t launch_search(const SearchParams& p, int blocks, int warps_per_block,
-                          bool directed, bool learned, cudaStream_t s);
-int search_max_blocks_per_sm(int warps_per_block, int smem_per_block, bool directed, bool learned);
+                          bool directed, bool learned, cudaStream_t s, int gs = 32);
+int search_max_blocks_per_sm(int warps_per_block, int smem_per_block, bool directed, bool learned,
+                             int gs = 32);
 int serve_max_blocks_per_sm(int warps_per_block, int smem_per_block);
 cudaError_t launch_popc_bench(unsigned long long* out, int blocks, int iters, cudaStream_t s);
 cudaError_t launch_serve_init(Control* ctl, u64* qseq, uint32_t qcap, int32_t* in_flight, cudaStream_t s);

@@ -296,17 +296,58 @@ cudaError_t launch_pack(const PackParams& p, cudaStream_t s) {
 // search kernel
 // ---------------------------------------------------------------------------
 constexpr unsigned kKeyNone = 0xFFFFu;
-constexpr int kTick = 32;             // nodes between incumbent/hunger refreshes
-constexpr int kTimeTick = 512;        // nodes between deadline checks
 constexpr int kSpinLimit = 1 << 22;   // iterations of a ring-slot wait
 
+// A searcher is a group of GS lanes (GS = 32: one warp; 16 or 8: two or four
+// independent depth-first searches per warp).  Every warp-level primitive of
+// the search goes through this group: shuffles, votes and reductions carry
+// the group's lane mask, so groups of one warp may take different branches.
+template <int GS>
+struct Grp {
+    unsigned mask;      // the group's lanes
+    int q;              // lane within the group
+    int lane0;          // first lane of the group
+    __device__ __forceinline__ explicit Grp(int lane) {
+        q = lane & (GS - 1);
+        lane0 = lane - q;
+        mask = GS == 32 ? FULL : (((1u << GS) - 1u) << lane0);
+    }
+    __device__ __forceinline__ int shfl(int x, int src) const { return __shfl_sync(mask, x, src, GS); }
+    __device__ __forceinline__ unsigned shflu(unsigned x, int src) const { return __shfl_sync(mask, x, src, GS); }
+    __device__ __forceinline__ u64 shfl64(u64 x, int src) const {
+        unsigned lo = (unsigned)x, hi = (unsigned)(x >> 32);
+        lo = __shfl_sync(mask, lo, src, GS);
+        hi = __shfl_sync(mask, hi, src, GS);
+        return ((u64)hi << 32) | lo;
+    }
+    // group-relative vote: bit i = lane q == i
+    __device__ __forceinline__ unsigned ballot(bool p) const {
+        const unsigned b = __ballot_sync(mask, p);
+        return GS == 32 ? b : (b >> lane0) & ((1u << GS) - 1u);
+    }
+    __device__ __forceinline__ bool all(bool p) const { return __all_sync(mask, p); }
+    // redux.sync reduces over the lanes of its member mask only
+    __device__ __forceinline__ int add(int x) const { return __reduce_add_sync(mask, x); }
+    __device__ __forceinline__ unsigned umin(unsigned x) const { return __reduce_min_sync(mask, x); }
+    __device__ __forceinline__ void sync() const { __syncwarp(mask); }
+    __device__ __forceinline__ unsigned lt() const { return (1u << q) - 1u; }
+};
+
 struct WarpSmem {
-    u64* gout; u64* gin; u64* hout; u64* hin;
+    const u64* adj; // rows gout | gin | hout | hin (64 each), shared or global
     u64* rrem;      // per level: candidates still to try
     u64* info;      // per level: base | C << 16 | v << 24 | flags << 32 | bound << 40
     uint8_t* Mg; uint8_t* Mh;
     ulonglong2* cls;
 };
+
+// An adjacency row: shared-memory copy, or the packed pair in global memory
+// (read-only for the kernel's lifetime, so through the non-coherent cache).
+template <bool SM>
+__device__ __forceinline__ u64 adj_row(const u64* rows, int i) {
+    if constexpr (SM) return rows[i];
+    else return __ldg(rows + i);
+}
 
 __device__ __forceinline__ u64 pack_info(int base, int C, int v, int flags, int bound) {
     return (u64)base | ((u64)C << 16) | ((u64)v << 24) | ((u64)flags << 32) | ((u64)bound << 40);
@@ -342,14 +383,15 @@ struct Scan {
 
 // Scan the classes of a level (optionally removing v from its class first,
 // which is the "v stays unmatched" step) and choose the next branching class.
-__device__ __forceinline__ Scan scan_level(const Stack& st, int base, int C, int remove_v, int lane) {
+template <int GS>
+__device__ __forceinline__ Scan scan_level(const Grp<GS>& g, const Stack& st, int base, int C,
+                                           int remove_v) {
     int sum = 0;
     unsigned best = kKeyNone;
     u64 bestR = 0;
     const u64 vb = remove_v >= 0 ? (1ull << remove_v) : 0ull;
-    for (int s = 0; s < 2; ++s) {
-        if (s == 1 && C <= 32) break;
-        int i = lane + 32 * s;
+    for (int i0 = 0; i0 < C; i0 += GS) {
+        const int i = i0 + g.q;
         if (i < C) {
             ulonglong2* ptr = st.at(base + i);
             ulonglong2 c = *ptr;
@@ -366,10 +408,10 @@ __device__ __forceinline__ Scan scan_level(const Stack& st, int base, int C, int
         }
     }
     Scan r;
-    r.sum = __reduce_add_sync(FULL, sum);
-    r.key = __reduce_min_sync(FULL, best);
-    unsigned win = __ballot_sync(FULL, best == r.key && r.key != kKeyNone);
-    r.R = win ? shfl64(bestR, __ffs(win) - 1) : 0ull;
+    r.sum = g.add(sum);
+    r.key = g.umin(best);
+    unsigned win = g.ballot(best == r.key && r.key != kKeyNone);
+    r.R = win ? g.shfl64(bestR, __ffs(win) - 1) : 0ull;
     return r;
 }
 
@@ -382,23 +424,24 @@ __device__ __forceinline__ bool wait_seq(const u64* seq, u64 want) {
     return false;
 }
 
-template <bool DIR>
+template <int GS>
 __device__ void write_best(const SearchParams& P, int pair, const WarpSmem& w, int d, int v, int u,
-                           int lane) {
+                           const Grp<GS>& g) {
     if (!DBG_OK(P.ctl, d + 1 < kLevels && pair >= 0 && pair < P.npairs, 6, d)) return;
     uint16_t* slot = P.best + ((size_t)pair * kLevels + (d + 1)) * kMaxN;
-    for (int i = lane; i < d; i += 32) slot[i] = (uint16_t)((w.Mg[i] << 8) | w.Mh[i]);
-    if (lane == 0) slot[d] = (uint16_t)((v << 8) | u);
+    for (int i = g.q; i < d; i += GS) slot[i] = (uint16_t)((w.Mg[i] << 8) | w.Mh[i]);
+    if (g.q == 0) slot[d] = (uint16_t)((v << 8) | u);
 }
 
-// Posts `count` exit tokens (pair = -1) at the tail of the ring: every warp
-// waiting on a ticket at or beyond the tail finds one and leaves the kernel.
-__device__ void post_exit_tokens(const SearchParams& P, int count, int lane) {
+// Posts `count` exit tokens (pair = -1) at the tail of the ring: every
+// searcher waiting on a ticket at or beyond the tail finds one and leaves.
+template <int GS>
+__device__ void post_exit_tokens(const SearchParams& P, int count, const Grp<GS>& g) {
     u64 t0 = 0;
-    if (lane == 0) t0 = atomicAdd(&P.ctl->q_tail, (u64)count);
-    t0 = shfl64(t0, 0);
+    if (g.q == 0) t0 = atomicAdd(&P.ctl->q_tail, (u64)count);
+    t0 = g.shfl64(t0, 0);
     bool ok = true;
-    for (int i = lane; i < count; i += 32) {
+    for (int i = g.q; i < count; i += GS) {
         const u64 t = t0 + i;
         Task* dst = P.queue + (t & (P.qcap - 1));
         if (!wait_seq(P.qseq + (t & (P.qcap - 1)), t)) { ok = false; continue; }
@@ -406,11 +449,12 @@ __device__ void post_exit_tokens(const SearchParams& P, int count, int lane) {
         __threadfence();
         P.qseq[t & (P.qcap - 1)] = t + 1;
     }
-    if (!__all_sync(FULL, ok) && lane == 0) atomicCAS(&P.ctl->error, 0, MCS_ERR_DEVICE_STALL);
+    if (!g.all(ok) && g.q == 0) atomicCAS(&P.ctl->error, 0, MCS_ERR_DEVICE_STALL);
 }
 
-// Serve mode: the result record in mapped host memory, map built in shared
-// scratch (64 int16), then a system-scope fence and the done ticket.
+// Serve mode (whole-warp searchers only): the result record in mapped host
+// memory, map built in shared scratch (64 int16), then a system-scope fence
+// and the done ticket.
 __device__ void finalize_served(const SearchParams& P, int pair, int status, int k, int lane,
                                 int16_t* smap) {
     PairState& ps = P.state[pair];
@@ -450,40 +494,40 @@ __device__ void finalize_served(const SearchParams& P, int pair, int status, int
 }
 
 // Finish the pair: write size, status, nodes and the mapping (original numbers).
-template <bool SERVE>
-__device__ void finalize_pair(const SearchParams& P, int pair, int lane, int16_t* smap) {
+template <bool SERVE, int GS>
+__device__ void finalize_pair(const SearchParams& P, int pair, const Grp<GS>& g, int16_t* smap) {
     __threadfence();
     PairState& ps = P.state[pair];
     const PairGraph& pg = P.graphs[pair];
     // read by lane 0 and broadcast (see the note at task install)
     int status = 0, k = 0, ab = 0;
-    if (lane == 0) {
+    if (g.q == 0) {
         status = vload(&ps.status);
         k = vload(&ps.inc);
         ab = vload(&ps.abort);
     }
-    status = __shfl_sync(FULL, status, 0);
-    k = __shfl_sync(FULL, k, 0);
-    ab = __shfl_sync(FULL, ab, 0);
+    status = g.shfl(status, 0);
+    k = g.shfl(k, 0);
+    ab = g.shfl(ab, 0);
     if (status == MCS_PENDING) {
         if (!DBG_OK(P.ctl, k >= 0 && k < kLevels, 7, k)) k = 0;
         status = ab ? MCS_TIMEOUT : MCS_OK;
-        if (SERVE) { finalize_served(P, pair, status, k, lane, smap); return; }
+        if (SERVE) { finalize_served(P, pair, status, k, g.q, smap); return; }
         if (P.out_map) {
             const uint16_t* slot = P.best + ((size_t)pair * kLevels + k) * kMaxN;
-            for (int i = lane; i < k; i += 32) {
+            for (int i = g.q; i < k; i += GS) {
                 uint16_t e = vload(slot + i);
                 if (!DBG_OK(P.ctl, (e >> 8) < kMaxN && (e & 0xff) < kMaxN, 8, e)) continue;
-                int g = __ldcg(&pg.permG[e >> 8]), h = __ldcg(&pg.permH[e & 0xff]);
-                P.out_map[(size_t)pair * kMaxN + g] = (int16_t)h;
+                int gg = __ldcg(&pg.permG[e >> 8]), h = __ldcg(&pg.permH[e & 0xff]);
+                P.out_map[(size_t)pair * kMaxN + gg] = (int16_t)h;
             }
         }
     } else {
         k = 0;
-        if (SERVE) { finalize_served(P, pair, status, 0, lane, smap); return; }
+        if (SERVE) { finalize_served(P, pair, status, 0, g.q, smap); return; }
     }
     int last = 0;
-    if (lane == 0) {
+    if (g.q == 0) {
         u64 now = gtimer();
         if (P.out_size) P.out_size[pair] = k;
         if (P.out_nodes) P.out_nodes[pair] = vload(&ps.nodes);
@@ -496,35 +540,35 @@ __device__ void finalize_pair(const SearchParams& P, int pair, int lane, int16_t
         last = atomicSub(&P.ctl->remaining, 1) == 1;
         atomicMax(&P.ctl->last_progress, now);
     }
-    last = __shfl_sync(FULL, last, 0);
-    if (last) post_exit_tokens(P, P.max_warps, lane);
-    __syncwarp();
+    last = g.shfl(last, 0);
+    if (last) post_exit_tokens<GS>(P, P.max_warps, g);
+    g.sync();
 }
 
 // A task of `pair` ended: publish node count, drop the open count and finalise
 // the pair if this was its last task.
-template <bool SERVE>
-__device__ __forceinline__ void end_task(const SearchParams& P, int pair, u64& nodes, int lane,
+template <bool SERVE, int GS>
+__device__ __forceinline__ void end_task(const SearchParams& P, int pair, u64& nodes, const Grp<GS>& g,
                                          int16_t* smap) {
     int last = 0;
-    if (lane == 0) {
+    if (g.q == 0) {
         if (nodes) atomicAdd(&P.state[pair].nodes, nodes);
         __threadfence();
         last = atomicSub(&P.state[pair].open, 1) == 1;
     }
     nodes = 0;
-    last = __shfl_sync(FULL, last, 0);
-    if (last) finalize_pair<SERVE>(P, pair, lane, smap);
+    last = g.shfl(last, 0);
+    if (last) finalize_pair<SERVE, GS>(P, pair, g, smap);
 }
 
 // Serve mode, warp 0: admits requests that the host published in the mapped
 // ring, as root tasks of the ticket ring; exits (posting one exit token per
-// other warp) after linger_ns without admitted or unfinished requests.
-__device__ void serve_admit(const SearchParams& P, int lane) {
+// other searcher) after linger_ns without admitted or unfinished requests.
+__device__ void serve_admit(const SearchParams& P, const Grp<32>& g) {
     Control* ctl = P.ctl;
     const ServeDev& S = P.sv;
     const u64 qmask = P.qcap - 1;
-    if (lane == 0) {
+    if (g.q == 0) {
         u64 admitted = vload(S.dev_admitted);
         u64 idle0 = gtimer();
         for (;;) {
@@ -567,8 +611,8 @@ __device__ void serve_admit(const SearchParams& P, int lane) {
             }
         }
     }
-    __syncwarp();
-    post_exit_tokens(P, P.max_warps - 1, lane);
+    g.sync();
+    post_exit_tokens<32>(P, P.max_warps - 1, g);
 }
 
 __device__ __forceinline__ void load_level(const WarpSmem& w, int d, Top& t) {
@@ -582,48 +626,160 @@ __device__ __forceinline__ void load_level(const WarpSmem& w, int d, Top& t) {
     t.bound = (int)((inf >> 40) & 0xff);
 }
 
+// Work sharing: hands part of the shallowest open level of this searcher's
+// subtree to a waiting searcher through the ring -- the upper half of its
+// remaining candidates u, or, with one candidate left, the rest of the level
+// including its "v unmatched" branch.  The level's classes and the mapping
+// prefix M travel with the task.  Returns false if the bounded wait for the
+// ring slot expired (the error is recorded in the control block).
+template <int GS>
+__device__ __forceinline__ bool donate(const SearchParams& P, int pair, int d0, Top& t, int inc,
+                                       const WarpSmem& w, const Stack& st, const Grp<GS>& g,
+                                       unsigned& donated) {
+    Control* ctl = P.ctl;
+    const uint32_t qmask = P.qcap - 1;
+    // flush the top cursor so that every level is in shared memory
+    if (g.q == 0) {
+        w.rrem[t.d] = t.rrem;
+        w.info[t.d] = pack_info(t.base, t.C, t.v, t.flags, t.bound);
+    }
+    g.sync();
+    int ds = -1;
+    for (int off = d0; off <= t.d && ds < 0; off += GS) {
+        const int d = off + g.q;
+        bool open = false;
+        if (d <= t.d) {
+            const u64 inf = w.info[d];
+            const int fl = (int)((inf >> 32) & 0xff), bd = (int)((inf >> 40) & 0xff);
+            open = (w.rrem[d] != 0 || (fl & kTaskPending)) && bd > inc;
+        }
+        const unsigned m = g.ballot(open);
+        if (m) ds = off + __ffs(m) - 1;
+    }
+    if (ds < 0) return true;
+    const u64 inf = w.info[ds];
+    const u64 rr = w.rrem[ds];
+    const int fl = (int)((inf >> 32) & 0xff);
+    const int k = __popcll(rr);
+    u64 give;
+    int gflags;
+    if (k >= 2) {
+        // the upper half of the candidates; the rest and the unmatched branch stay
+        give = rr;
+        for (int j = 0; j < (k + 1) / 2; ++j) give &= give - 1;
+        gflags = 0;
+    } else {
+        give = rr;
+        gflags = fl & kTaskPending;
+    }
+    // keep work of our own: a level whose subtree we are inside (ds < t.d)
+    // or the top with >= 2 candidates
+    const bool worth = (ds < t.d) || k >= 2;
+    u64 ticket = 0;
+    int ok = 0;
+    if (worth && g.q == 0) {
+        // A searcher was waiting when we polled.  Donors that saw the same
+        // waiter may all donate: the surplus (at most one task per busy
+        // searcher per poll window, far below the ring capacity) waits in
+        // the ring for the next idle searcher.
+        ticket = atomicAdd(&ctl->q_tail, 1ull);
+        atomicAdd(&P.state[pair].open, 1);
+        ok = wait_seq(P.qseq + (ticket & qmask), ticket) ? 1 : -1;
+    }
+    ok = g.shfl(ok, 0);
+    if (ok < 0) {
+        if (g.q == 0) atomicCAS(&ctl->error, 0, MCS_ERR_DEVICE_STALL);
+        return false;
+    }
+    if (ok == 0) return true;
+    ticket = g.shfl64(ticket, 0);
+    Task* dst = P.queue + (ticket & qmask);
+    const int C = (int)((inf >> 16) & 0xff);
+    const int bs = (int)(inf & 0xffff);
+    for (int i = g.q; i < C; i += GS) dst->cls[i] = *st.at(bs + i);
+    for (int i = g.q; i < ds; i += GS) { dst->Mg[i] = w.Mg[i]; dst->Mh[i] = w.Mh[i]; }
+    if (g.q == 0) {
+        dst->h.pair = pair;
+        dst->h.depth = ds;
+        dst->h.C = C;
+        dst->h.v = (int)((inf >> 24) & 0xff);
+        dst->h.rrem = give;
+        dst->h.flags = gflags;
+        dst->h.bound = (int)((inf >> 40) & 0xff);
+        w.rrem[ds] = rr & ~give;
+        w.info[ds] = (inf & ~(0xffull << 32)) | ((u64)(fl & ~gflags) << 32);
+    }
+    g.sync();
+    __threadfence();
+    if (g.q == 0) {
+        P.qseq[ticket & qmask] = ticket + 1;   // publish
+        atomicMax(&ctl->last_progress, gtimer());
+    }
+    g.sync();
+    ++donated;
+    if (ds == t.d) {
+        t.rrem = rr & ~give;
+        t.flags = fl & ~gflags;
+    }
+    return true;
+}
+
 // Minimum resident 256-thread blocks per SM the register allocation must allow
-// (3 caps registers at 80 per thread, 2 at 128).
+// (3 caps registers at 80 per thread, 4 at 64).  Narrow searchers take the
+// tighter cap: more resident warps outweigh the few spilled registers.
 #ifndef MCS_SEARCH_MINB
 #define MCS_SEARCH_MINB 3
 #endif
+#ifndef MCS_GROUP_MINB
+#define MCS_GROUP_MINB 4
+#endif
 
-template <bool DIR, bool LEARNED, bool SERVE>
-__global__ void __launch_bounds__(256, MCS_SEARCH_MINB) search_kernel(SearchParams P) {
+template <bool DIR, bool LEARNED, bool SERVE, int GS>
+__global__ void __launch_bounds__(256, (GS == 32 ? MCS_SEARCH_MINB : MCS_GROUP_MINB)) search_kernel(SearchParams P) {
+    static_assert(GS == 4 || GS == 8 || GS == 16 || GS == 32, "searcher group size");
+    static_assert(!SERVE || GS == 32, "serve mode packs requests with whole warps");
     extern __shared__ __align__(16) unsigned char smem[];
+    constexpr int GPW = 32 / GS;                       // searchers per warp
     const int lane = threadIdx.x & 31;
     const int wib = threadIdx.x >> 5;
-    const int gw = blockIdx.x * (blockDim.x >> 5) + wib;
-    if (gw >= P.max_warps) return;
-    unsigned char* base = smem + (size_t)wib * P.warp_smem_bytes;
+    const Grp<GS> g(lane);
+    const int sid = (blockIdx.x * (blockDim.x >> 5) + wib) * GPW + (lane / GS);
+    if (sid >= P.max_warps) return;
+    constexpr bool ADJ_SM = adj_in_smem(GS);
+    static_assert(!SERVE || ADJ_SM, "serve mode repacks slots while it runs: rows go through shared memory");
+    unsigned char* base = smem + (size_t)(wib * GPW + lane / GS) * P.warp_smem_bytes;
+    unsigned char* lv = base + sm_adj_bytes(GS);       // level arrays and class cache
     WarpSmem w;
-    w.gout = (u64*)(base + kSmAdj);
-    w.gin = w.gout + kMaxN;
-    w.hout = w.gout + 2 * kMaxN;
-    w.hin = w.gout + 3 * kMaxN;
-    w.rrem = (u64*)(base + kSmRrem);
-    w.info = (u64*)(base + kSmInfo);
-    w.Mg = base + kSmM;
-    w.Mh = base + kSmM + kMaxN;
-    w.cls = (ulonglong2*)(base + kSmCls);
+    u64* adj_sm = (u64*)base;                          // rows copied here when ADJ_SM
+    w.adj = adj_sm;
+    w.rrem = (u64*)(lv + kSmRremOff);
+    w.info = (u64*)(lv + kSmInfoOff);
+    w.Mg = lv + kSmMOff;
+    w.Mh = lv + kSmMOff + kMaxN;
+    w.cls = (ulonglong2*)(lv + kSmClsOff);
     Stack st;
     st.sm = w.cls;
     st.S = P.stack_smem;
-    st.gm = P.gstack + (size_t)gw * (size_t)(kStackMax > P.stack_smem ? kStackMax - P.stack_smem : 0);
+    st.gm = P.gstack + (size_t)sid * (size_t)(kStackMax > P.stack_smem ? kStackMax - P.stack_smem : 0);
 #ifdef MCS_DEBUG_BOUNDS
     st.ctl = P.ctl;
 #endif
 
     Control* ctl = P.ctl;
-    int16_t* smap = reinterpret_cast<int16_t*>(base + kSmRrem);   // finalize scratch (levels unused then)
-    if (SERVE && gw == 0) { serve_admit(P, lane); return; }
+    int16_t* smap = reinterpret_cast<int16_t*>(lv + kSmRremOff);   // finalize scratch (levels unused then)
+    if constexpr (SERVE) {
+        if (sid == 0) { serve_admit(P, g); return; }
+    }
     const bool level_prune = (P.flags & MCS_NO_LEVEL_PRUNE) == 0;
-    const u64 qmask = P.qcap - 1;
+    const uint32_t qmask = P.qcap - 1;
     int cur_pair = -1;
     u64 nodes = 0;
     unsigned tick = 0;
-    u64 spilled = 0, cvisits = 0, pruned = 0, donated = 0, stolen = 0;
-    long long busy_cyc = 0, idle_cyc = 0;
+    // statistics, meaningful in lane 0 of the group (32-bit: flushed to the
+    // control block before they can wrap, and when the searcher leaves)
+    unsigned spilled = 0, cvisits = 0, pruned = 0, donated = 0, stolen = 0;
+    u64* cyc = (u64*)(lv + kSmCycOff);                  // busy, idle clock cycles
+    if (g.q == 0) { cyc[0] = 0; cyc[1] = 0; }
 
     while (true) {
         // ------------------------------------------------------------------
@@ -631,10 +787,10 @@ __global__ void __launch_bounds__(256, MCS_SEARCH_MINB) search_kernel(SearchPara
         // slot until it is published (pair roots are published up front in
         // processing order; donations and exit tokens follow).
         // ------------------------------------------------------------------
-        long long c_idle = clock64();
+        const long long c_idle = clock64();
         int got = 0;          // 1 task, -1 exit
         u64 qh = 0;
-        if (lane == 0) {
+        if (g.q == 0) {
             qh = atomicAdd(&ctl->q_head, 1ull);
             const u64* seq = P.qseq + (qh & qmask);
             for (int it = 0; got == 0; ++it) {
@@ -651,19 +807,19 @@ __global__ void __launch_bounds__(256, MCS_SEARCH_MINB) search_kernel(SearchPara
                 __nanosleep(128u << min(it >> 2, 6));     // 0.13 .. 8 us
             }
         }
-        got = __shfl_sync(FULL, got, 0);
-        qh = shfl64(qh, 0);
+        got = g.shfl(got, 0);
+        qh = g.shfl64(qh, 0);
         if (got < 0) break;
         __threadfence();
         const Task* task = P.queue + (qh & qmask);
         int pair = 0, tflags = 0;
-        if (lane == 0) { pair = vload(&task->h.pair); tflags = vload(&task->h.flags); }
-        pair = __shfl_sync(FULL, pair, 0);
-        tflags = __shfl_sync(FULL, tflags, 0);
+        if (g.q == 0) { pair = vload(&task->h.pair); tflags = vload(&task->h.flags); }
+        pair = g.shfl(pair, 0);
+        tflags = g.shfl(tflags, 0);
         if (!DBG_OK(ctl, pair < P.npairs, 2, pair)) pair = -1;
         if (pair < 0) {                                   // exit token
-            __syncwarp();
-            if (lane == 0) P.qseq[qh & qmask] = qh + P.qcap;
+            g.sync();
+            if (g.q == 0) P.qseq[qh & qmask] = qh + P.qcap;
             break;
         }
         Top t;
@@ -671,57 +827,59 @@ __global__ void __launch_bounds__(256, MCS_SEARCH_MINB) search_kernel(SearchPara
         PairState& ps = P.state[pair];
         const PairGraph& pg = P.graphs[pair];
         u64 req_timeout = P.timeout_ns;
-        if (SERVE && (tflags & kTaskPack)) {
-            // a served request: copy it out of mapped host memory, pack it into
-            // its slot and set up its state (this warp is its only user so far)
-            const uint4* src = reinterpret_cast<const uint4*>(P.sv.hdata + (size_t)pair * kSlotBytes);
-            uint4* dst = reinterpret_cast<uint4*>(P.sv.ddata + (size_t)pair * kSlotBytes);
-            for (int i = lane; i < kSlotBytes / 16; i += 32) {
-                uint4 v4;
-                asm volatile("ld.volatile.global.v4.u32 {%0,%1,%2,%3}, [%4];"
-                             : "=r"(v4.x), "=r"(v4.y), "=r"(v4.z), "=r"(v4.w) : "l"(src + i));
-                dst[i] = v4;
+        if constexpr (SERVE) {
+            if (tflags & kTaskPack) {
+                // a served request: copy it out of mapped host memory, pack it into
+                // its slot and set up its state (this warp is its only user so far)
+                const uint4* src = reinterpret_cast<const uint4*>(P.sv.hdata + (size_t)pair * kSlotBytes);
+                uint4* dst = reinterpret_cast<uint4*>(P.sv.ddata + (size_t)pair * kSlotBytes);
+                for (int i = lane; i < kSlotBytes / 16; i += 32) {
+                    uint4 v4;
+                    asm volatile("ld.volatile.global.v4.u32 {%0,%1,%2,%3}, [%4];"
+                                 : "=r"(v4.x), "=r"(v4.y), "=r"(v4.z), "=r"(v4.w) : "l"(src + i));
+                    dst[i] = v4;
+                }
+                int rq[3] = {0, 0, 0};
+                u64 rt = 0, rtk = 0;
+                if (lane == 0) {
+                    const ServeReq* q = P.sv.req + pair;
+                    rq[0] = vload(&q->nG); rq[1] = vload(&q->nH); rq[2] = vload(&q->labelled);
+                    rt = vload(&q->timeout_ns); rtk = vload(&q->ticket);
+                }
+                for (int j = 0; j < 3; ++j) rq[j] = __shfl_sync(FULL, rq[j], 0);
+                rt = shfl64(rt, 0);
+                rtk = shfl64(rtk, 0);
+                req_timeout = rt;
+                __syncwarp();
+                const uint8_t* d = P.sv.ddata + (size_t)pair * kSlotBytes;
+                GraphIn gi[2];
+                gi[0].n = rq[0]; gi[1].n = rq[1];
+                gi[0].a = d; gi[1].a = d + kMaxN * kMaxN;
+                gi[0].lab = (rq[2] & 1) ? reinterpret_cast<const int32_t*>(d + 2 * kMaxN * kMaxN) : nullptr;
+                gi[1].lab = (rq[2] & 2) ? reinterpret_cast<const int32_t*>(d + 2 * kMaxN * kMaxN + 4 * kMaxN) : nullptr;
+                const bool ok = pack_pair_warp(gi, false, nullptr, nullptr, const_cast<PairGraph&>(pg),
+                                               reinterpret_cast<long long*>(lv + kSmRremOff), lane);
+                if (lane == 0) {
+                    ps.inc = 0; ps.open = 1; ps.abort = 0; ps.nodes = 0;
+                    ps.t_start = 0; ps.deadline = 0; ps.ticket = rtk;
+                    ps.status = ok ? MCS_PENDING : MCS_ERR_ARG;
+                    __threadfence();
+                }
+                __syncwarp();
+                cur_pair = -1;      // a slot is reused by later requests: never trust cached rows
             }
-            int rq[3] = {0, 0, 0};
-            u64 rt = 0, rtk = 0;
-            if (lane == 0) {
-                const ServeReq* q = P.sv.req + pair;
-                rq[0] = vload(&q->nG); rq[1] = vload(&q->nH); rq[2] = vload(&q->labelled);
-                rt = vload(&q->timeout_ns); rtk = vload(&q->ticket);
-            }
-            for (int j = 0; j < 3; ++j) rq[j] = __shfl_sync(FULL, rq[j], 0);
-            rt = shfl64(rt, 0);
-            rtk = shfl64(rtk, 0);
-            req_timeout = rt;
-            __syncwarp();
-            const uint8_t* d = P.sv.ddata + (size_t)pair * kSlotBytes;
-            GraphIn g[2];
-            g[0].n = rq[0]; g[1].n = rq[1];
-            g[0].a = d; g[1].a = d + kMaxN * kMaxN;
-            g[0].lab = (rq[2] & 1) ? reinterpret_cast<const int32_t*>(d + 2 * kMaxN * kMaxN) : nullptr;
-            g[1].lab = (rq[2] & 2) ? reinterpret_cast<const int32_t*>(d + 2 * kMaxN * kMaxN + 4 * kMaxN) : nullptr;
-            const bool ok = pack_pair_warp(g, false, nullptr, nullptr, const_cast<PairGraph&>(pg),
-                                           reinterpret_cast<long long*>(base + kSmRrem), lane);
-            if (lane == 0) {
-                ps.inc = 0; ps.open = 1; ps.abort = 0; ps.nodes = 0;
-                ps.t_start = 0; ps.deadline = 0; ps.ticket = rtk;
-                ps.status = ok ? MCS_PENDING : MCS_ERR_ARG;
-                __threadfence();
-            }
-            __syncwarp();
-            cur_pair = -1;      // a slot is reused by later requests: never trust cached rows
         }
         int pstat = 0;
-        if (lane == 0) pstat = vload(&ps.status);
-        pstat = __shfl_sync(FULL, pstat, 0);
+        if (g.q == 0) pstat = vload(&ps.status);
+        pstat = g.shfl(pstat, 0);
         if (fresh) {
             if (pstat != MCS_PENDING) {                   // malformed input: report and skip
-                __syncwarp();
-                if (lane == 0) { P.qseq[qh & qmask] = qh + P.qcap; ps.open = 0; }
-                finalize_pair<SERVE>(P, pair, lane, smap);
+                g.sync();
+                if (g.q == 0) { P.qseq[qh & qmask] = qh + P.qcap; ps.open = 0; }
+                finalize_pair<SERVE, GS>(P, pair, g, smap);
                 continue;
             }
-            if (lane == 0) {
+            if (g.q == 0) {
                 u64 now = gtimer();
                 ps.t_start = now;
                 ps.deadline = now + req_timeout;
@@ -730,71 +888,79 @@ __global__ void __launch_bounds__(256, MCS_SEARCH_MINB) search_kernel(SearchPara
         }
         // load the pair's rows into shared memory (through L2: in serve mode a
         // slot is repacked while the kernel runs, so L1 may hold old lines)
-        if (pair != cur_pair || SERVE) {
-            for (int i = lane; i < kMaxN; i += 32) {
-                w.gout[i] = __ldcg(&pg.gout[i]);
-                w.hout[i] = __ldcg(&pg.hout[i]);
-                if (DIR) { w.gin[i] = __ldcg(&pg.gin[i]); w.hin[i] = __ldcg(&pg.hin[i]); }
+        if (!ADJ_SM) {
+            // rows read in place: written by the pack kernel before this launch
+            w.adj = pg.gout;                  // gout, gin, hout, hin are consecutive
+        } else if (pair != cur_pair || SERVE) {
+            for (int i = g.q; i < kMaxN; i += GS) {
+                adj_sm[i] = __ldcg(&pg.gout[i]);
+                adj_sm[2 * kMaxN + i] = __ldcg(&pg.hout[i]);
+                if (DIR) { adj_sm[kMaxN + i] = __ldcg(&pg.gin[i]); adj_sm[3 * kMaxN + i] = __ldcg(&pg.hin[i]); }
             }
             cur_pair = SERVE ? -1 : pair;
         }
         if (!fresh) {
             int hd4[4] = {0, 0, 0, 0};
             u64 rr = 0;
-            if (lane == 0) {
+            if (g.q == 0) {
                 hd4[0] = vload(&task->h.depth);
                 hd4[1] = vload(&task->h.C);
                 hd4[2] = vload(&task->h.v);
                 hd4[3] = vload(&task->h.bound);
                 rr = vload(&task->h.rrem);
             }
-            t.d = __shfl_sync(FULL, hd4[0], 0);
-            t.C = __shfl_sync(FULL, hd4[1], 0);
-            t.v = __shfl_sync(FULL, hd4[2], 0);
-            t.bound = __shfl_sync(FULL, hd4[3], 0);
-            t.rrem = shfl64(rr, 0);
+            t.d = g.shfl(hd4[0], 0);
+            t.C = g.shfl(hd4[1], 0);
+            t.v = g.shfl(hd4[2], 0);
+            t.bound = g.shfl(hd4[3], 0);
+            t.rrem = g.shfl64(rr, 0);
             t.flags = tflags;
             if (!DBG_OK(ctl, t.C >= 0 && t.C <= kMaxN, 3, t.C)) t.C = 0;
             if (!DBG_OK(ctl, t.d >= 0 && t.d < kMaxN, 4, t.d)) t.d = 0;
-            for (int i = lane; i < t.d; i += 32) { w.Mg[i] = ld_cg(&task->Mg[i]); w.Mh[i] = ld_cg(&task->Mh[i]); }
-            for (int i = lane; i < t.C; i += 32) *st.at(i) = ld_cg(&task->cls[i]);
+            for (int i = g.q; i < t.d; i += GS) { w.Mg[i] = ld_cg(&task->Mg[i]); w.Mh[i] = ld_cg(&task->Mh[i]); }
+            for (int i = g.q; i < t.C; i += GS) *st.at(i) = ld_cg(&task->cls[i]);
             ++stolen;
         } else {
             t.d = 0;
             t.C = __ldcg(&pg.C0);
-            for (int i = lane; i < t.C; i += 32) *st.at(i) = __ldcg(&pg.root[i]);
+            for (int i = g.q; i < t.C; i += GS) *st.at(i) = __ldcg(&pg.root[i]);
         }
-        __syncwarp();
-        if (lane == 0) {
+        g.sync();
+        if (g.q == 0) {
             __threadfence();
             P.qseq[qh & qmask] = qh + P.qcap;              // release the slot
         }
         t.base = 0;
         const int d0 = t.d;
-        // Values other warps may be writing are read by lane 0 only and
+        // Values other searchers may be writing are read by lane 0 only and
         // broadcast: lanes are not guaranteed to execute a load at the same
-        // time, and a lane-dependent copy would split the warp at the next
-        // branch (and make a later full-warp shuffle illegal).
+        // time, and a lane-dependent copy would split the group at the next
+        // branch (and make a later group-wide shuffle illegal).
         int inc = 0, ab0 = 0;
-        u64 deadline = 0;
-        if (lane == 0) {
+        if (g.q == 0) {
             inc = vload(&ps.inc);
             ab0 = vload(&ps.abort);
-            deadline = vload(&ps.deadline);
         }
-        inc = __shfl_sync(FULL, inc, 0);
-        ab0 = __shfl_sync(FULL, ab0, 0);
-        deadline = shfl64(deadline, 0);
-        long long c_busy = clock64();
-        idle_cyc += c_busy - c_idle;
-        if (ab0) { end_task<SERVE>(P, pair, nodes, lane, smap); busy_cyc += clock64() - c_busy; continue; }
+        inc = g.shfl(inc, 0);
+        ab0 = g.shfl(ab0, 0);
+        const long long c_busy = clock64();
+        if (g.q == 0) cyc[1] += (u64)(c_busy - c_idle);
+        if (ab0) {
+            end_task<SERVE, GS>(P, pair, nodes, g, smap);
+            if (g.q == 0) cyc[0] += (u64)(clock64() - c_busy);
+            continue;
+        }
         if (fresh) {
             // root node entry (Algorithm 1): bound of Eq. 1, then class choice
             ++nodes;
             cvisits += t.C;
-            Scan sc = scan_level(st, 0, t.C, -1, lane);
+            Scan sc = scan_level<GS>(g, st, 0, t.C, -1);
             t.bound = sc.sum;
-            if (t.bound <= inc) { end_task<SERVE>(P, pair, nodes, lane, smap); busy_cyc += clock64() - c_busy; continue; }
+            if (t.bound <= inc) {
+                end_task<SERVE, GS>(P, pair, nodes, g, smap);
+                if (g.q == 0) cyc[0] += (u64)(clock64() - c_busy);
+                continue;
+            }
             t.v = sc.key & 63;
             t.rrem = sc.R;
             t.flags = kTaskPending;
@@ -805,326 +971,257 @@ __global__ void __launch_bounds__(256, MCS_SEARCH_MINB) search_kernel(SearchPara
         // ------------------------------------------------------------------
         // polled values, loaded by lane 0 8 ticks before they are used so
         // that the L2 round trip overlaps node work
-        int p_inc = 0, p_abort = 0;
-        u64 p_head = 0, p_tail = 0;
+        int p_inc = 0, p_abort = 0, p_hungry = 0;
         while (t.d >= d0) {
             ++tick;
-            if ((tick & 15) == 0 && lane == 0) {
+            if ((tick & 15) == 0 && g.q == 0) {
                 p_inc = vload(&ps.inc);
                 p_abort = vload(&ps.abort);
-                p_head = vload(&ctl->q_head);
-                p_tail = vload(&ctl->q_tail);
-                if (!p_abort && (tick & 255) == 0 && gtimer() > deadline) {
+                p_hungry = vload(&ctl->q_head) > vload(&ctl->q_tail);   // a searcher waits
+                if (!p_abort && (tick & 255) == 0 && gtimer() > vload(&ps.deadline)) {
                     ps.abort = 1;                      // per-pair time limit
                     p_abort = 1;
                 }
+                if (cvisits >= (1u << 31)) { atomicAdd(&ctl->class_visits, (u64)cvisits); cvisits = 0; }
+                if (pruned >= (1u << 31)) { atomicAdd(&ctl->pruned, (u64)pruned); pruned = 0; }
             }
             if ((tick & 15) == 8) {
-                int g_inc = __shfl_sync(FULL, p_inc, 0);
-                const int ab = __shfl_sync(FULL, p_abort, 0);
-                const u64 hd = shfl64(p_head, 0), tl = shfl64(p_tail, 0);
+                const int g_inc = g.shfl(p_inc, 0);
+                const int ab = g.shfl(p_abort, 0);
+                const int hungry = g.shfl(p_hungry, 0);
                 inc = max(inc, g_inc);
                 if (ab) break;
-                // ---- donate the shallowest open level to a waiting warp ----
-                if (hd > tl) {
-                    // flush the top cursor so that every level is in shared memory
-                    if (lane == 0) {
-                        w.rrem[t.d] = t.rrem;
-                        w.info[t.d] = pack_info(t.base, t.C, t.v, t.flags, t.bound);
-                    }
-                    __syncwarp();
-                    int ds = -1;
-                    for (int off = d0; off <= t.d && ds < 0; off += 32) {
-                        int d = off + lane;
-                        bool open = false;
-                        if (d <= t.d) {
-                            u64 inf = w.info[d];
-                            int fl = (int)((inf >> 32) & 0xff), bd = (int)((inf >> 40) & 0xff);
-                            open = (w.rrem[d] != 0 || (fl & kTaskPending)) && bd > inc;
-                        }
-                        unsigned m = __ballot_sync(FULL, open);
-                        if (m) ds = off + __ffs(m) - 1;
-                    }
-                    if (ds >= 0) {
-                        u64 inf = w.info[ds];
-                        u64 rr = w.rrem[ds];
-                        int fl = (int)((inf >> 32) & 0xff);
-                        int k = __popcll(rr);
-                        u64 give;
-                        int gflags;
-                        if (k >= 2) {
-                            // give the upper half of the candidates, keep the rest + unmatched branch
-                            give = rr;
-                            for (int j = 0; j < (k + 1) / 2; ++j) give &= give - 1;
-                            gflags = 0;
-                        } else {
-                            give = rr;
-                            gflags = fl & kTaskPending;
-                        }
-                        // keep work of our own: a level whose subtree we are
-                        // inside (ds < t.d) or the top with >= 2 candidates
-                        bool worth = (ds < t.d) || k >= 2;
-                        u64 ticket = 0;
-                        int ok = 0;
-                        if (worth && lane == 0) {
-                            // A warp was waiting when we polled.  Donors that saw
-                            // the same waiter may all donate: the surplus (at most
-                            // one task per busy warp per poll window, far below
-                            // the ring capacity) waits in the ring for the next
-                            // idle warp.
-                            ticket = atomicAdd(&ctl->q_tail, 1ull);
-                            atomicAdd(&ps.open, 1);
-                            ok = wait_seq(P.qseq + (ticket & qmask), ticket) ? 1 : -1;
-                        }
-                        ok = __shfl_sync(FULL, ok, 0);
-                        if (ok < 0) { if (lane == 0) atomicCAS(&ctl->error, 0, MCS_ERR_DEVICE_STALL); break; }
-                        if (ok > 0) {
-                            ticket = shfl64(ticket, 0);
-                            Task* dst = P.queue + (ticket & qmask);
-                            int C = (int)((inf >> 16) & 0xff);
-                            int bs = (int)(inf & 0xffff);
-                            for (int i = lane; i < C; i += 32) dst->cls[i] = *st.at(bs + i);
-                            for (int i = lane; i < ds; i += 32) { dst->Mg[i] = w.Mg[i]; dst->Mh[i] = w.Mh[i]; }
-                            if (lane == 0) {
-                                dst->h.pair = pair;
-                                dst->h.depth = ds;
-                                dst->h.C = C;
-                                dst->h.v = (int)((inf >> 24) & 0xff);
-                                dst->h.rrem = give;
-                                dst->h.flags = gflags;
-                                dst->h.bound = (int)((inf >> 40) & 0xff);
-                                w.rrem[ds] = rr & ~give;
-                                w.info[ds] = (inf & ~(0xffull << 32)) | ((u64)(fl & ~gflags) << 32);
-                            }
-                            __syncwarp();
-                            __threadfence();
-                            if (lane == 0) {
-                                P.qseq[ticket & qmask] = ticket + 1;   // publish
-                                atomicMax(&ctl->last_progress, gtimer());
-                            }
-                            __syncwarp();
-                            ++donated;
-                            if (ds == t.d) {
-                                t.rrem = rr & ~give;
-                                t.flags = fl & ~gflags;
-                            }
-                        }
-                    }
-                }
+                // ---- donate the shallowest open level to a waiting searcher ----
+                if (hungry && !donate<GS>(P, pair, d0, t, inc, w, st, g, donated)) break;
             }
             // level prune: every node below this level has bound <= this one
-            if (level_prune && t.bound <= inc) {
+            if ((level_prune && t.bound <= inc) || (t.rrem == 0 && !(t.flags & kTaskPending))) {
                 --t.d;
                 if (t.d >= d0) load_level(w, t.d, t);
                 continue;
             }
-            if (t.rrem) {
-                // ---------------- child (v, u): filterDomain + Eq. 1 ----------------
-                int u;
-                if (LEARNED) {
-                    // the remaining candidate with the best learned rank for v
-                    const uint8_t* rk = P.rank + ((size_t)pair * kMaxN + t.v) * kMaxN;
-                    const unsigned k0 = ((t.rrem >> lane) & 1ull) ? ((unsigned)__ldg(rk + lane) << 6) | lane : kKeyNone;
-                    const unsigned k1 = ((t.rrem >> (lane + 32)) & 1ull) ? ((unsigned)__ldg(rk + lane + 32) << 6) | (lane + 32) : kKeyNone;
-                    u = (int)(__reduce_min_sync(FULL, min(k0, k1)) & 63u);
-                    t.rrem &= ~(1ull << u);
-                } else {
-                    u = __ffsll(t.rrem) - 1;
-                    t.rrem &= t.rrem - 1;
-                }
-                ++nodes;
-                cvisits += t.C;
-                const int v = t.v;
-                const u64 vb = 1ull << v, ub = 1ull << u;
-                const u64 gB = w.gout[v], hB = w.hout[u];
-                const u64 gA = DIR ? w.gin[v] : 0ull, hA = DIR ? w.hin[u] : 0ull;
-                u64 Ls[2], Rs[2];
-                int sum = 0;
-                unsigned best = kKeyNone;
-                u64 bestR = 0;
-                const int nslot = t.C > 32 ? 2 : 1;
-                // parent and child both inside the shared-memory class cache:
-                // shared-memory loads/stores instead of generic ones
-                const bool in_sm = t.base + t.C + kMaxN <= st.S;
-#pragma unroll
-                for (int s = 0; s < 2; ++s) {
-                    Ls[s] = 0; Rs[s] = 0;
-                    if (s < nslot) {
-                        int i = lane + 32 * s;
-                        if (i < t.C) {
-                            ulonglong2 c = in_sm ? st.sm[t.base + i] : *st.at(t.base + i);
-                            Ls[s] = c.x & ~vb;
-                            Rs[s] = c.y & ~ub;
-                        }
-                        const u64 L = Ls[s], R = Rs[s];
-                        if (DIR) {
-                            const u64 la = L & gA, lb = L & gB, ra = R & hA, rb = R & hB;
-                            const u64 lp[4] = {L & ~(la | lb), la & ~lb, lb & ~la, la & lb};
-                            const u64 rp[4] = {R & ~(ra | rb), ra & ~rb, rb & ~ra, ra & rb};
-#pragma unroll
-                            for (int k = 0; k < 4; ++k) {
-                                int a = __popcll(lp[k]), b = __popcll(rp[k]);
-                                int m = min(a, b);
-                                sum += m;
-                                unsigned key = m ? (((unsigned)max(a, b) << 6) | (unsigned)(__ffsll(lp[k]) - 1)) : kKeyNone;
-                                if (key < best) { best = key; bestR = rp[k]; }
-                            }
-                        } else {
-                            const u64 l1 = L & gB, r1 = R & hB, l0 = L ^ l1, r0 = R ^ r1;
-                            int a1 = __popcll(l1), b1 = __popcll(r1), a0 = __popcll(l0), b0 = __popcll(r0);
-                            int m1 = min(a1, b1), m0 = min(a0, b0);
-                            sum += m1 + m0;
-                            unsigned k1 = m1 ? (((unsigned)max(a1, b1) << 6) | (unsigned)(__ffsll(l1) - 1)) : kKeyNone;
-                            unsigned k0 = m0 ? (((unsigned)max(a0, b0) << 6) | (unsigned)(__ffsll(l0) - 1)) : kKeyNone;
-                            if (k1 < best) { best = k1; bestR = r1; }
-                            if (k0 < best) { best = k0; bestR = r0; }
-                        }
-                    }
-                }
-                sum = __reduce_add_sync(FULL, sum);
-                const int dm = t.d + 1;
-                // incumbent (Algorithm 1): |M u {(v,u)}| beats the best so far
-                if (dm > inc) {
-                    int old = 0;
-                    if (lane == 0) old = atomicMax(&ps.inc, dm);
-                    old = __shfl_sync(FULL, old, 0);
-                    if (old < dm) {
-                        write_best<DIR>(P, pair, w, t.d, v, u, lane);
-                        inc = dm;
-                    } else {
-                        inc = old;
-                    }
-                }
-                if (dm + sum <= inc) { ++pruned; continue; }    // child pruned by Eq. 1
-                // descend: compact the child's classes onto the stack
-                const unsigned kmin = __reduce_min_sync(FULL, best);
-                const unsigned win = __ballot_sync(FULL, best == kmin);
-                const u64 cR = shfl64(bestR, __ffs(win) - 1);
-                const int cbase = t.base + t.C;
-                int pos = cbase;
-#pragma unroll
-                for (int s = 0; s < 2; ++s) {
-                    if (s < nslot) {
-                        const u64 L = Ls[s], R = Rs[s];
-                        if (DIR) {
-                            const u64 la = L & gA, lb = L & gB, ra = R & hA, rb = R & hB;
-                            const u64 lp[4] = {L & ~(la | lb), la & ~lb, lb & ~la, la & lb};
-                            const u64 rp[4] = {R & ~(ra | rb), ra & ~rb, rb & ~ra, ra & rb};
-#pragma unroll
-                            for (int k = 0; k < 4; ++k) {
-                                bool keep = lp[k] && rp[k];
-                                unsigned m = __ballot_sync(FULL, keep);
-                                if (keep) {
-                                    const int q2 = pos + __popc(m & lanemask_lt());
-                                    if (in_sm) st.sm[q2] = make_ulonglong2(lp[k], rp[k]);
-                                    else *st.at(q2) = make_ulonglong2(lp[k], rp[k]);
-                                }
-                                pos += __popc(m);
-                            }
-                        } else {
-                            const u64 l1 = L & gB, r1 = R & hB, l0 = L ^ l1, r0 = R ^ r1;
-                            bool k1 = l1 && r1, k0 = l0 && r0;
-                            unsigned m1 = __ballot_sync(FULL, k1);
-                            if (k1) {
-                                const int q2 = pos + __popc(m1 & lanemask_lt());
-                                if (in_sm) st.sm[q2] = make_ulonglong2(l1, r1);
-                                else *st.at(q2) = make_ulonglong2(l1, r1);
-                            }
-                            pos += __popc(m1);
-                            unsigned m0 = __ballot_sync(FULL, k0);
-                            if (k0) {
-                                const int q2 = pos + __popc(m0 & lanemask_lt());
-                                if (in_sm) st.sm[q2] = make_ulonglong2(l0, r0);
-                                else *st.at(q2) = make_ulonglong2(l0, r0);
-                            }
-                            pos += __popc(m0);
-                        }
-                    }
-                }
-                if (pos > st.S) spilled += 1;
-                if (!DBG_OK(ctl, pos - cbase <= kMaxN && dm <= kMaxN, 5, (pos - cbase) * 1000 + dm)) pos = cbase;
-                if (lane == 0) {
-                    w.Mg[t.d] = (uint8_t)v;
-                    w.Mh[t.d] = (uint8_t)u;
-                    w.rrem[t.d] = t.rrem;
-                    w.info[t.d] = pack_info(t.base, t.C, t.v, t.flags, t.bound);
-                }
-                __syncwarp();
-                t.d = dm;
-                t.base = cbase;
-                t.C = pos - cbase;
-                t.v = kmin & 63;
-                t.rrem = cR;
-                t.flags = kTaskPending;
-                t.bound = dm + sum;
-            } else if (t.flags & kTaskPending) {
+            if (t.rrem == 0) {
                 // ---------------- "v stays unmatched": same M, v leaves its class ----------------
                 ++nodes;
                 cvisits += t.C;
-                Scan sc = scan_level(st, t.base, t.C, t.v, lane);
-                __syncwarp();
+                const Scan sc = scan_level<GS>(g, st, t.base, t.C, t.v);
+                g.sync();
                 t.bound = t.d + sc.sum;
                 if (t.bound <= inc) {
                     t.flags = 0;            // pruned: the level is exhausted and pops next
-                    t.rrem = 0;
                 } else {
                     t.v = sc.key & 63;
                     t.rrem = sc.R;
                     t.flags = kTaskPending;
                 }
-            } else {
-                --t.d;
-                if (t.d >= d0) load_level(w, t.d, t);
+                continue;
             }
+            // ---------------- child (v, u): filterDomain + Eq. 1 ----------------
+            int u;
+            if (LEARNED) {
+                // the remaining candidate with the best learned rank for v
+                const uint8_t* rk = P.rank + ((size_t)pair * kMaxN + t.v) * kMaxN;
+                unsigned kk = kKeyNone;
+                for (int j = g.q; j < kMaxN; j += GS)
+                    if ((t.rrem >> j) & 1ull) kk = min(kk, ((unsigned)__ldg(rk + j) << 6) | (unsigned)j);
+                u = (int)(g.umin(kk) & 63u);
+            } else {
+                u = __ffsll(t.rrem) - 1;
+            }
+            t.rrem &= ~(1ull << u);
+            ++nodes;
+            cvisits += t.C;
+            const int v = t.v;
+            const u64 vb = 1ull << v, ub = 1ull << u;
+            const u64 gB = adj_row<ADJ_SM>(w.adj, v), hB = adj_row<ADJ_SM>(w.adj, 2 * kMaxN + u);
+            const u64 gA = DIR ? adj_row<ADJ_SM>(w.adj, kMaxN + v) : 0ull;
+            const u64 hA = DIR ? adj_row<ADJ_SM>(w.adj, 3 * kMaxN + u) : 0ull;
+            const int dm = t.d + 1;
+            const int cbase = t.base + t.C;
+            // parent and child both inside the shared-memory class cache:
+            // shared-memory loads/stores instead of generic ones
+            const bool in_sm = cbase + kMaxN <= st.S;
+            int sum = 0;
+            unsigned best = kKeyNone;
+            u64 bestR = 0;
+            int pos = cbase;
+            // Appends the part (l, r) to the child level when both sides are
+            // non-empty (group-wide ballot compaction, order kept).
+            auto emit = [&](u64 l, u64 r, bool keep) {
+                const unsigned mk = g.ballot(keep);
+                if (keep) {
+                    const int q2 = pos + __popc(mk & g.lt());
+                    if (in_sm) st.sm[q2] = make_ulonglong2(l, r);
+                    else *st.at(q2) = make_ulonglong2(l, r);
+                }
+                pos += __popc(mk);
+            };
+            // Whole-warp searchers write the child's classes only once it
+            // survives Eq. 1, in a second pass over the classes kept in
+            // registers.  Narrow searchers write them in the same pass, before
+            // Eq. 1 decides (a pruned child's writes land in free stack space
+            // above the level): one pass is shorter, and the searchers that
+            // share a warp are more often on the same instruction.
+            constexpr bool SPEC = GS < 32;
+            u64 Ls[2], Rs[2];                                  // GS == 32: the two slots
+#pragma unroll (GS == 32 ? 2 : 1)
+            for (int sl = 0; sl < kMaxN / GS; ++sl) {
+                const int i0 = sl * GS;
+                if (i0 >= t.C) break;
+                const int i = i0 + g.q;
+                u64 L = 0, R = 0;
+                if (i < t.C) {
+                    const ulonglong2 c = in_sm ? st.sm[t.base + i] : *st.at(t.base + i);
+                    L = c.x & ~vb;
+                    R = c.y & ~ub;
+                }
+                if constexpr (GS == 32) { Ls[sl] = L; Rs[sl] = R; }
+                if (DIR) {
+                    const u64 la = L & gA, lb = L & gB, ra = R & hA, rb = R & hB;
+                    const u64 lp[4] = {L & ~(la | lb), la & ~lb, lb & ~la, la & lb};
+                    const u64 rp[4] = {R & ~(ra | rb), ra & ~rb, rb & ~ra, ra & rb};
+#pragma unroll
+                    for (int k = 0; k < 4; ++k) {
+                        const int a = __popcll(lp[k]), b = __popcll(rp[k]);
+                        const int m = min(a, b);
+                        sum += m;
+                        const unsigned key = m ? (((unsigned)max(a, b) << 6) | (unsigned)(__ffsll(lp[k]) - 1)) : kKeyNone;
+                        if (key < best) { best = key; bestR = rp[k]; }
+                        if (SPEC) emit(lp[k], rp[k], m != 0);
+                    }
+                } else {
+                    const u64 l1 = L & gB, r1 = R & hB, l0 = L ^ l1, r0 = R ^ r1;
+                    const int a1 = __popcll(l1), b1 = __popcll(r1), a0 = __popcll(l0), b0 = __popcll(r0);
+                    const int m1 = min(a1, b1), m0 = min(a0, b0);
+                    sum += m1 + m0;
+                    const unsigned k1 = m1 ? (((unsigned)max(a1, b1) << 6) | (unsigned)(__ffsll(l1) - 1)) : kKeyNone;
+                    const unsigned k0 = m0 ? (((unsigned)max(a0, b0) << 6) | (unsigned)(__ffsll(l0) - 1)) : kKeyNone;
+                    if (k1 < best) { best = k1; bestR = r1; }
+                    if (k0 < best) { best = k0; bestR = r0; }
+                    if (SPEC) {
+                        emit(l1, r1, m1 != 0);
+                        emit(l0, r0, m0 != 0);
+                    }
+                }
+            }
+            if (SPEC) g.sync();     // the child's writes land before a sibling rewrites the space
+            sum = g.add(sum);
+            // incumbent (Algorithm 1): |M u {(v,u)}| beats the best so far
+            if (dm > inc) {
+                int old = 0;
+                if (g.q == 0) old = atomicMax(&ps.inc, dm);
+                old = g.shfl(old, 0);
+                if (old < dm) {
+                    write_best<GS>(P, pair, w, t.d, v, u, g);
+                    inc = dm;
+                } else {
+                    inc = old;
+                }
+            }
+            if (dm + sum <= inc) { ++pruned; continue; }    // child pruned by Eq. 1
+            const unsigned kmin = g.umin(best);
+            const unsigned win = g.ballot(best == kmin);
+            const u64 cR = g.shfl64(bestR, __ffs(win) - 1);
+            if constexpr (GS == 32) {
+                // descend: compact the child's classes onto the stack
+#pragma unroll
+                for (int sl = 0; sl < 2; ++sl) {
+                    if (sl * 32 >= t.C) break;
+                    const u64 L = Ls[sl], R = Rs[sl];
+                    if (DIR) {
+                        const u64 la = L & gA, lb = L & gB, ra = R & hA, rb = R & hB;
+                        const u64 lp[4] = {L & ~(la | lb), la & ~lb, lb & ~la, la & lb};
+                        const u64 rp[4] = {R & ~(ra | rb), ra & ~rb, rb & ~ra, ra & rb};
+#pragma unroll
+                        for (int k = 0; k < 4; ++k) emit(lp[k], rp[k], lp[k] && rp[k]);
+                    } else {
+                        const u64 l1 = L & gB, r1 = R & hB, l0 = L ^ l1, r0 = R ^ r1;
+                        emit(l1, r1, l1 && r1);
+                        emit(l0, r0, l0 && r0);
+                    }
+                }
+            }
+            if (pos > st.S) spilled += 1;
+            if (!DBG_OK(ctl, pos - cbase <= kMaxN && dm <= kMaxN, 5, (pos - cbase) * 1000 + dm)) pos = cbase;
+            if (g.q == 0) {
+                w.Mg[t.d] = (uint8_t)v;
+                w.Mh[t.d] = (uint8_t)u;
+                w.rrem[t.d] = t.rrem;
+                w.info[t.d] = pack_info(t.base, t.C, t.v, t.flags, t.bound);
+            }
+            g.sync();
+            t.d = dm;
+            t.base = cbase;
+            t.C = pos - cbase;
+            t.v = kmin & 63;
+            t.rrem = cR;
+            t.flags = kTaskPending;
+            t.bound = dm + sum;
         }
-        end_task<SERVE>(P, pair, nodes, lane, smap);
-        busy_cyc += clock64() - c_busy;
+        end_task<SERVE, GS>(P, pair, nodes, g, smap);
+        if (g.q == 0) cyc[0] += (u64)(clock64() - c_busy);
     }
-    if (lane == 0) {
-        if (spilled) atomicAdd(&ctl->spilled, spilled);
-        if (cvisits) atomicAdd(&ctl->class_visits, cvisits);
-        if (pruned) atomicAdd(&ctl->pruned, pruned);
-        if (donated) atomicAdd(&ctl->donated, donated);
-        if (stolen) atomicAdd(&ctl->stolen, stolen);
-        atomicAdd(&ctl->busy_cycles, (u64)busy_cyc);
-        atomicAdd(&ctl->idle_cycles, (u64)idle_cyc);
+    if (g.q == 0) {
+        if (spilled) atomicAdd(&ctl->spilled, (u64)spilled);
+        if (cvisits) atomicAdd(&ctl->class_visits, (u64)cvisits);
+        if (pruned) atomicAdd(&ctl->pruned, (u64)pruned);
+        if (donated) atomicAdd(&ctl->donated, (u64)donated);
+        if (stolen) atomicAdd(&ctl->stolen, (u64)stolen);
+        atomicAdd(&ctl->busy_cycles, cyc[0]);
+        atomicAdd(&ctl->idle_cycles, cyc[1]);
     }
 }
 
-template <bool DIR, bool LEARNED, bool SERVE>
+template <bool DIR, bool LEARNED, bool SERVE, int GS>
 static cudaError_t launch_t(const SearchParams& p, int blocks, int wpb, cudaStream_t s) {
-    size_t smem = (size_t)wpb * p.warp_smem_bytes;
-    cudaFuncSetAttribute(search_kernel<DIR, LEARNED, SERVE>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-    search_kernel<DIR, LEARNED, SERVE><<<blocks, wpb * 32, smem, s>>>(p);
+    size_t smem = (size_t)wpb * (32 / GS) * p.warp_smem_bytes;
+    cudaFuncSetAttribute(search_kernel<DIR, LEARNED, SERVE, GS>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    search_kernel<DIR, LEARNED, SERVE, GS><<<blocks, wpb * 32, smem, s>>>(p);
     return cudaGetLastError();
 }
 
-cudaError_t launch_search(const SearchParams& p, int blocks, int warps_per_block, bool directed,
-                          bool learned, cudaStream_t s) {
-    if (p.serving) return launch_t<false, false, true>(p, blocks, warps_per_block, s);
-    if (directed) return learned ? launch_t<true, true, false>(p, blocks, warps_per_block, s)
-                                 : launch_t<true, false, false>(p, blocks, warps_per_block, s);
-    return learned ? launch_t<false, true, false>(p, blocks, warps_per_block, s)
-                   : launch_t<false, false, false>(p, blocks, warps_per_block, s);
+template <bool DIR, bool LEARNED>
+static cudaError_t launch_g(const SearchParams& p, int blocks, int wpb, int gs, cudaStream_t s) {
+    if (gs == 4) return launch_t<DIR, LEARNED, false, 4>(p, blocks, wpb, s);
+    if (gs == 8) return launch_t<DIR, LEARNED, false, 8>(p, blocks, wpb, s);
+    if (gs == 16) return launch_t<DIR, LEARNED, false, 16>(p, blocks, wpb, s);
+    return launch_t<DIR, LEARNED, false, 32>(p, blocks, wpb, s);
 }
 
-template <bool DIR, bool LEARNED, bool SERVE>
+cudaError_t launch_search(const SearchParams& p, int blocks, int warps_per_block, bool directed,
+                          bool learned, cudaStream_t s, int gs) {
+    if (p.serving) return launch_t<false, false, true, 32>(p, blocks, warps_per_block, s);
+    if (directed) return learned ? launch_g<true, true>(p, blocks, warps_per_block, gs, s)
+                                 : launch_g<true, false>(p, blocks, warps_per_block, gs, s);
+    return learned ? launch_g<false, true>(p, blocks, warps_per_block, gs, s)
+                   : launch_g<false, false>(p, blocks, warps_per_block, gs, s);
+}
+
+template <bool DIR, bool LEARNED, bool SERVE, int GS>
 static int occupancy_t(int wpb, int smem) {
     int nb = 0;
-    cudaFuncSetAttribute(search_kernel<DIR, LEARNED, SERVE>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
-    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, search_kernel<DIR, LEARNED, SERVE>, wpb * 32, smem);
+    cudaFuncSetAttribute(search_kernel<DIR, LEARNED, SERVE, GS>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
+    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, search_kernel<DIR, LEARNED, SERVE, GS>, wpb * 32, smem);
     return nb;
 }
 
-int search_max_blocks_per_sm(int warps_per_block, int smem_per_block, bool directed, bool learned) {
-    if (directed) return learned ? occupancy_t<true, true, false>(warps_per_block, smem_per_block)
-                                 : occupancy_t<true, false, false>(warps_per_block, smem_per_block);
-    return learned ? occupancy_t<false, true, false>(warps_per_block, smem_per_block)
-                   : occupancy_t<false, false, false>(warps_per_block, smem_per_block);
+template <bool DIR, bool LEARNED>
+static int occupancy_g(int wpb, int smem, int gs) {
+    if (gs == 4) return occupancy_t<DIR, LEARNED, false, 4>(wpb, smem);
+    if (gs == 8) return occupancy_t<DIR, LEARNED, false, 8>(wpb, smem);
+    if (gs == 16) return occupancy_t<DIR, LEARNED, false, 16>(wpb, smem);
+    return occupancy_t<DIR, LEARNED, false, 32>(wpb, smem);
+}
+
+int search_max_blocks_per_sm(int warps_per_block, int smem_per_block, bool directed, bool learned, int gs) {
+    if (directed) return learned ? occupancy_g<true, true>(warps_per_block, smem_per_block, gs)
+                                 : occupancy_g<true, false>(warps_per_block, smem_per_block, gs);
+    return learned ? occupancy_g<false, true>(warps_per_block, smem_per_block, gs)
+                   : occupancy_g<false, false>(warps_per_block, smem_per_block, gs);
 }
 
 int serve_max_blocks_per_sm(int warps_per_block, int smem_per_block) {
-    return occupancy_t<false, false, true>(warps_per_block, smem_per_block);
+    return occupancy_t<false, false, true, 32>(warps_per_block, smem_per_block);
 }
 
 // Serve mode: reset the control block and the ring before a server launch.

@@ -117,7 +117,7 @@ int serve_state(mcs_ctx* c, ServeState** out) {
     CKS(cudaMalloc((void**)&S->ctl, sizeof(Control)));
     CKS(cudaMalloc((void**)&S->in_flight, sizeof(int32_t)));
     // launch shape: the context's, undirected, plain order
-    S->wsmem = warp_smem_bytes(c->smem_stack);
+    S->wsmem = warp_smem_bytes(stack_entries(c, 32));
     int per_sm = serve_max_blocks_per_sm(c->warps_per_block, c->warps_per_block * S->wsmem);
     if (per_sm <= 0) return MCS_ERR_UNSUPPORTED;
     if (c->blocks_per_sm > 0 && c->blocks_per_sm < per_sm) per_sm = c->blocks_per_sm;
@@ -128,7 +128,7 @@ int serve_state(mcs_ctx* c, ServeState** out) {
     S->qcap = q;
     CKS(cudaMalloc((void**)&S->queue, sizeof(Task) * q));
     CKS(cudaMalloc((void**)&S->qseq, sizeof(u64) * q));
-    const size_t per = (size_t)(kStackMax - c->smem_stack > 0 ? kStackMax - c->smem_stack : 0);
+    const size_t per = (size_t)(kStackMax - stack_entries(c, 32) > 0 ? kStackMax - stack_entries(c, 32) : 0);
     CKS(cudaMalloc((void**)&S->gstack, sizeof(ulonglong2) * std::max<size_t>(per * S->warps, 1)));
     CKS(cudaStreamCreateWithFlags(&S->stream, cudaStreamNonBlocking));
     CKS(cudaEventCreateWithFlags(&S->done_ev, cudaEventDisableTiming));
@@ -177,7 +177,7 @@ int launch_server(mcs_ctx* c, ServeState* S) {
     sp.queue = S->queue;
     sp.qseq = S->qseq;
     sp.qcap = S->qcap;
-    sp.stack_smem = c->smem_stack;
+    sp.stack_smem = stack_entries(c, 32);
     sp.warp_smem_bytes = S->wsmem;
     sp.max_warps = S->warps;
     sp.gstack = S->gstack;

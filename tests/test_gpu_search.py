@@ -251,26 +251,35 @@ def test_graph_replay_matches_direct_launch(solver):
             assert oracle.verify(p.G.adj, p.H.adj, g, mp[i][g]) == 1
 
 
-@pytest.mark.parametrize("shape", [(2, 0, 128), (8, 0, 512), (4, 1, 64), (2, 2, 2080)])
+@pytest.mark.parametrize("shape", [(2, 0, 128, 32), (8, 0, 512, 32), (4, 1, 64, 32), (2, 2, 2080, 32),
+                                   (4, 0, 32, 8), (8, 0, 16, 8), (2, 3, 64, 16), (2, 0, 8, 4)])
 def test_launch_shapes_give_same_sizes(solver, shape):
     pairs = _rand_pairs(80, 6, 24, 123, k=2)
     ref = [oracle.mcs(p.G.adj, p.H.adj, p.G.labels, p.H.labels).size for p in pairs]
-    solver.set_launch(*shape)
+    solver.set_launch(*shape[:3], search_group=shape[3])
     try:
         res = solver.solve_batch(pairs, timeout_s=60)
     finally:
-        solver.set_launch(4, 0, 256)
+        solver.reset_launch()
     assert [r.size for r in res] == ref
     assert all(r.status == 0 for r in res)
 
 
-def test_launch_shape_that_does_not_fit_is_rejected(solver):
+@pytest.mark.parametrize("group", [32, 8])
+def test_launch_shape_that_does_not_fit_is_rejected(solver, group):
     from paper_1908_06418_b300 import MCS_ERR_UNSUPPORTED
     p = synth.config1_pair()
-    solver.set_launch(8, 0, 2080)          # 8 x 36.5 KB of shared memory per block
+    solver.set_launch(8, 0, 2080, search_group=group)   # >= 8 x 34.5 KB of shared memory per block
     try:
         with pytest.raises(RuntimeError, match="unsupported"):
             solver.solve(p.G.adj, p.H.adj, timeout_s=10)
     finally:
-        solver.set_launch(4, 0, 256)
+        solver.reset_launch()
     assert solver.solve(p.G.adj, p.H.adj, timeout_s=10).size == 13
+
+
+def test_launch_values_out_of_range_are_rejected(solver):
+    for bad in [(9, 0, 0), (-2, 0, 0), (0, -2, 0), (0, 0, -2), (0, 0, 5000)]:
+        with pytest.raises(ValueError):
+            solver.set_launch(*bad)
+    solver.reset_launch()
