@@ -240,7 +240,7 @@ def main():
     if world > 1:
         import torch.distributed as dist
         dist.init_process_group("nccl")
-    from paper_1908_06418_b300 import Solver, pack_host, MCS_DIRECTED, MCS_OK
+    from paper_1908_06418_b300 import Solver, pack_host, MCS_DIRECTED, MCS_OK, MCS_WORD32
 
     pairs, cfg = workload(a.workload)
     gold = golden_sizes(a.workload)
@@ -250,14 +250,16 @@ def main():
     # it is given, and CUDA events recorded on that same stream time it
     stream = torch.cuda.Stream(dev)
 
-    # device-resident inputs, one group per flag set (replicas on every rank)
+    # device-resident inputs, one group per flag set (replicas on every rank);
+    # a group whose graphs all have at most 32 vertices takes the 32-bit node step
     groups = []
     for directed in (True, False):
         idx = [i for i, p in enumerate(pairs) if p.directed == directed]
         if not idx:
             continue
+        narrow = all(max(pairs[i].G.n, pairs[i].H.n) <= 32 for i in idx)
         h = pack_host([pairs[i] for i in idx])
-        g = dict(idx=idx, flags=MCS_DIRECTED if directed else 0, n=len(idx),
+        g = dict(idx=idx, flags=(MCS_DIRECTED if directed else 0) | (MCS_WORD32 if narrow else 0), n=len(idx),
                  d_n=torch.from_numpy(h["n"]).to(dev),
                  d_adj_off=torch.from_numpy(h["adj_off"]).to(dev),
                  d_adj=torch.from_numpy(h["adj"]).to(dev),
@@ -392,7 +394,9 @@ def main():
     csum = clk.summary()
     popc_peak = solver.bench_popc() / 1e9
     dom = max(range(len(groups)), key=lambda gi: sum(r[gi][1] for r in stats))
-    per_class = 12 if groups[dom]["flags"] & MCS_DIRECTED else 4
+    # hardware popcounts per class read: undirected |L1|, |R1|, directed three
+    # parts per side; a 64-bit count is two 32-bit ones
+    per_class = (12 if groups[dom]["flags"] & MCS_DIRECTED else 4) // (2 if groups[dom]["flags"] & MCS_WORD32 else 1)
     dom_us = [r[dom][1] for r in stats]
     dom_cv = [r[dom][2] for r in stats]
     busy = sum(r[dom][3] for r in stats)

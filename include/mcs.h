@@ -67,6 +67,10 @@ extern "C" {
 #define MCS_NO_LEVEL_PRUNE    0x8u  /* diagnostic: do not re-test a level's bound      */
                                     /* before each sibling, so that with one warp the  */
                                     /* node count equals the sequential recursion's    */
+#define MCS_WORD32            0x20u /* 32-bit node step: every graph of the call has at */
+                                    /* most 32 vertices (others: MCS_ERR_ARG for that  */
+                                    /* pair).  mcs_solve and mcs_solve_batch set it    */
+                                    /* themselves when all graphs fit                  */
 
 typedef struct mcs_ctx mcs_ctx;
 

@@ -18,13 +18,14 @@ import numpy as np
 __all__ = ["Solver", "Result", "MCS_OK", "MCS_TIMEOUT", "MCS_PENDING", "MCS_ERR_ARG",
            "MCS_ERR_NOMEM", "MCS_ERR_CUDA", "MCS_ERR_DEVICE_STALL", "MCS_ERR_UNSUPPORTED",
            "MCS_DIRECTED", "MCS_ORDER_LEARNED", "MCS_NO_MAPPING", "MCS_NO_LEVEL_PRUNE",
-           "MCS_MAX_N", "MCS_GRAPH_REPLAY", "lib_path", "load_library", "EXPORTED_SYMBOLS",
+           "MCS_MAX_N", "MCS_GRAPH_REPLAY", "MCS_WORD32", "lib_path", "load_library", "EXPORTED_SYMBOLS",
            "DeviceBatch", "pack_host"]
 
 MCS_MAX_N = 64
 MCS_OK, MCS_TIMEOUT, MCS_PENDING = 0, 1, 2
 MCS_ERR_ARG, MCS_ERR_NOMEM, MCS_ERR_CUDA, MCS_ERR_DEVICE_STALL, MCS_ERR_UNSUPPORTED = -1, -2, -3, -4, -5
 MCS_DIRECTED, MCS_ORDER_LEARNED, MCS_NO_MAPPING, MCS_NO_LEVEL_PRUNE = 0x1, 0x2, 0x4, 0x8
+MCS_WORD32 = 0x20
 MCS_GRAPH_REPLAY = 0x10
 
 _HERE = os.path.dirname(os.path.abspath(__file__))
@@ -421,14 +422,20 @@ def _ptr(t):
 class DeviceBatch:
     """A list of pairs laid out for the device entry points (torch tensors
     hold the device memory; flags carries MCS_DIRECTED when the pairs are
-    directed)."""
+    directed, and MCS_WORD32 when every graph has at most 32 vertices unless
+    word32=False)."""
 
-    def __init__(self, pairs, device=0, directed: bool = False):
+    def __init__(self, pairs, device=0, directed: bool = False, word32: Optional[bool] = None):
         import torch
         h = pack_host(pairs)
         self.device = torch.device("cuda", device) if isinstance(device, int) else device
         self.npairs = len(pairs)
         self.flags = MCS_DIRECTED if directed else 0
+        fits = len(pairs) > 0 and all(p.G.n <= 32 and p.H.n <= 32 for p in pairs)
+        if word32 is None:
+            word32 = fits
+        if word32:
+            self.flags |= MCS_WORD32
         self.d_n = torch.from_numpy(h["n"]).to(self.device)
         self.d_adj_off = torch.from_numpy(h["adj_off"]).to(self.device)
         self.d_adj = torch.from_numpy(h["adj"]).to(self.device)

@@ -57,12 +57,14 @@ int grow_host(T*& p, size_t& cap, size_t need) {
     return 0;
 }
 
-int launch_shape(mcs_ctx* c, bool directed, bool learned, int* blocks, int* warps_total, int* wsmem) {
+int launch_shape(mcs_ctx* c, bool directed, bool learned, bool narrow, int* blocks, int* warps_total,
+                 int* wsmem) {
     // warps_total counts searchers: 32 / group_lanes of them share a warp
     const int spb = c->warps_per_block * (32 / c->group_lanes);
     *wsmem = warp_smem_bytes(stack_entries(c, c->group_lanes), c->group_lanes);
     int smem_block = spb * *wsmem;
-    int per_sm = search_max_blocks_per_sm(c->warps_per_block, smem_block, directed, learned, c->group_lanes);
+    int per_sm = search_max_blocks_per_sm(c->warps_per_block, smem_block, directed, learned, c->group_lanes,
+                                          narrow);
     if (per_sm <= 0) return MCS_ERR_UNSUPPORTED;
     if (c->blocks_per_sm > 0) per_sm = std::min(per_sm, c->blocks_per_sm);
     *blocks = c->sms * per_sm;
@@ -136,7 +138,7 @@ int run_device(mcs_ctx* c, int npairs, const int32_t* d_n, const int64_t* d_adj_
         rc = 0;
     }
     int blocks = 0, warps = 0, wsmem = 0;
-    rc = launch_shape(c, directed, learned, &blocks, &warps, &wsmem);
+    rc = launch_shape(c, directed, learned, (flags & MCS_WORD32) != 0, &blocks, &warps, &wsmem);
     if (rc) return rc;
     if ((rc = ensure_pairs(c, npairs))) return rc;
     if ((rc = ensure_ring(c, warps, npairs))) return rc;
@@ -409,6 +411,13 @@ int mcs_solve_batch(mcs_ctx* c, const mcs_graph* G, const mcs_graph* H, int32_t 
                 hlo[gi] = -1;
             }
         }
+    }
+    // 32-bit node step when every graph of the call has at most 32 vertices
+    {
+        bool fit = true;
+        for (int p = 0; p < npairs && fit; ++p)
+            if (!bad[p] && (G[p].n > 32 || H[p].n > 32)) fit = false;
+        if (fit) flags |= MCS_WORD32;
     }
     // longest-processing-time-first: larger and denser pairs start first
     {

@@ -247,7 +247,7 @@ cudaError_t launch_pack(const PackParams& p, cudaStream_t s);
 cudaError_t launch_search(const SearchParams& p, int blocks, int warps_per_block,
                           bool directed, bool learned, cudaStream_t s, int gs = 32);
 int search_max_blocks_per_sm(int warps_per_block, int smem_per_block, bool directed, bool learned,
-                             int gs = 32);
+                             int gs = 32, bool narrow = false);
 int serve_max_blocks_per_sm(int warps_per_block, int smem_per_block);
 cudaError_t launch_popc_bench(unsigned long long* out, int blocks, int iters, cudaStream_t s);
 cudaError_t launch_serve_init(Control* ctl, u64* qseq, uint32_t qcap, int32_t* in_flight, cudaStream_t s);

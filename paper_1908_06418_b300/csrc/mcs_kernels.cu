@@ -17,6 +17,7 @@
 //
 // Every device-side wait is bounded (iteration count and globaltimer) and
 // reports MCS_ERR_DEVICE_STALL through Control::error instead of trapping.
+#include <type_traits>
 #include "mcs_internal.cuh"
 #include "../../include/mcs.h"
 
@@ -267,7 +268,9 @@ __global__ void pack_kernel(PackParams P) {
     }
     const float* k0 = P.vscore ? P.vscore + ((size_t)p * 2) * kMaxN : nullptr;
     const float* k1 = P.vscore ? P.vscore + ((size_t)p * 2 + 1) * kMaxN : nullptr;
-    const bool ok = pack_pair_warp(g, directed, k0, k1, pg, s_key[wib], lane);
+    // the 32-bit node step holds graphs of at most 32 vertices
+    const bool fits = !(P.flags & MCS_WORD32) || (g[0].n <= 32 && g[1].n <= 32);
+    const bool ok = pack_pair_warp(g, directed, k0, k1, pg, s_key[wib], lane) && fits;
     if (lane == 0) {
         PairState& st = P.state[p];
         st.inc = 0;
@@ -381,37 +384,52 @@ struct Scan {
     u64 R;
 };
 
+// Bit-set words of the node step.  Pairs whose graphs both have at most 32
+// vertices run it on 32-bit words (one hardware popcount per set instead of
+// two); the stored rows and classes stay 64-bit (their upper halves are 0).
+template <typename W> struct Word;
+template <> struct Word<u64> {
+    static __device__ __forceinline__ int popc(u64 x) { return __popcll(x); }
+    static __device__ __forceinline__ int low(u64 x) { return __ffsll(x) - 1; }   // lowest set bit
+};
+template <> struct Word<uint32_t> {
+    static __device__ __forceinline__ int popc(uint32_t x) { return __popc(x); }
+    static __device__ __forceinline__ int low(uint32_t x) { return __ffs(x) - 1; }
+};
+
 // Scan the classes of a level (optionally removing v from its class first,
 // which is the "v stays unmatched" step) and choose the next branching class.
-template <int GS>
+template <typename W, int GS>
 __device__ __forceinline__ Scan scan_level(const Grp<GS>& g, const Stack& st, int base, int C,
                                            int remove_v) {
     int sum = 0;
     unsigned best = kKeyNone;
-    u64 bestR = 0;
-    const u64 vb = remove_v >= 0 ? (1ull << remove_v) : 0ull;
+    W bestR = 0;
+    const W vb = remove_v >= 0 ? ((W)1 << remove_v) : (W)0;
     for (int i0 = 0; i0 < C; i0 += GS) {
         const int i = i0 + g.q;
         if (i < C) {
             ulonglong2* ptr = st.at(base + i);
-            ulonglong2 c = *ptr;
-            if (c.x & vb) {
-                c.x &= ~vb;
-                ptr->x = c.x;
+            const ulonglong2 c = *ptr;
+            W L = (W)c.x;
+            const W R = (W)c.y;
+            if (L & vb) {
+                L &= ~vb;
+                ptr->x = L;
             }
-            if (c.x) {
-                int a = __popcll(c.x), b = __popcll(c.y);
+            if (L) {
+                const int a = Word<W>::popc(L), b = Word<W>::popc(R);
                 sum += min(a, b);
-                unsigned key = ((unsigned)max(a, b) << 6) | (unsigned)(__ffsll(c.x) - 1);
-                if (key < best) { best = key; bestR = c.y; }
+                const unsigned key = ((unsigned)max(a, b) << 6) | (unsigned)Word<W>::low(L);
+                if (key < best) { best = key; bestR = R; }
             }
         }
     }
     Scan r;
     r.sum = g.add(sum);
     r.key = g.umin(best);
-    unsigned win = g.ballot(best == r.key && r.key != kKeyNone);
-    r.R = win ? g.shfl64(bestR, __ffs(win) - 1) : 0ull;
+    const unsigned win = g.ballot(best == r.key && r.key != kKeyNone);
+    r.R = win ? g.shfl64((u64)bestR, __ffs(win) - 1) : 0ull;
     return r;
 }
 
@@ -734,7 +752,7 @@ __device__ __forceinline__ bool donate(const SearchParams& P, int pair, int d0, 
 #define MCS_GROUP_MINB 4
 #endif
 
-template <bool DIR, bool LEARNED, bool SERVE, int GS>
+template <bool DIR, bool LEARNED, bool SERVE, int GS, bool NARROW>
 __global__ void __launch_bounds__(256, (GS == 32 ? MCS_SEARCH_MINB : MCS_GROUP_MINB)) search_kernel(SearchParams P) {
     static_assert(GS == 4 || GS == 8 || GS == 16 || GS == 32, "searcher group size");
     static_assert(!SERVE || GS == 32, "serve mode packs requests with whole warps");
@@ -899,6 +917,7 @@ __global__ void __launch_bounds__(256, (GS == 32 ? MCS_SEARCH_MINB : MCS_GROUP_M
             }
             cur_pair = SERVE ? -1 : pair;
         }
+        // NARROW: every pair has at most 32 vertices per graph (checked by the pack kernel)
         if (!fresh) {
             int hd4[4] = {0, 0, 0, 0};
             u64 rr = 0;
@@ -954,7 +973,7 @@ __global__ void __launch_bounds__(256, (GS == 32 ? MCS_SEARCH_MINB : MCS_GROUP_M
             // root node entry (Algorithm 1): bound of Eq. 1, then class choice
             ++nodes;
             cvisits += t.C;
-            Scan sc = scan_level<GS>(g, st, 0, t.C, -1);
+            const Scan sc = scan_level<typename std::conditional<NARROW, uint32_t, u64>::type, GS>(g, st, 0, t.C, -1);
             t.bound = sc.sum;
             if (t.bound <= inc) {
                 end_task<SERVE, GS>(P, pair, nodes, g, smap);
@@ -971,6 +990,169 @@ __global__ void __launch_bounds__(256, (GS == 32 ? MCS_SEARCH_MINB : MCS_GROUP_M
         // ------------------------------------------------------------------
         // polled values, loaded by lane 0 8 ticks before they are used so
         // that the L2 round trip overlaps node work
+        // One search node at the top of the stack: "v unmatched" when no
+        // candidate u is left, else the child (v, u).  W is the bit-set word.
+        auto node_step = [&](auto wtag) {
+            using W = decltype(wtag);
+                if (t.rrem == 0) {
+                    // ---------------- "v stays unmatched": same M, v leaves its class ----------------
+                    ++nodes;
+                    cvisits += t.C;
+                    const Scan sc = scan_level<W, GS>(g, st, t.base, t.C, t.v);
+                    g.sync();
+                    t.bound = t.d + sc.sum;
+                    if (t.bound <= inc) {
+                        t.flags = 0;            // pruned: the level is exhausted and pops next
+                    } else {
+                        t.v = sc.key & 63;
+                        t.rrem = sc.R;
+                        t.flags = kTaskPending;
+                    }
+                    return;
+                }
+                // ---------------- child (v, u): filterDomain + Eq. 1 ----------------
+                int u;
+                if (LEARNED) {
+                    // the remaining candidate with the best learned rank for v
+                    const uint8_t* rk = P.rank + ((size_t)pair * kMaxN + t.v) * kMaxN;
+                    unsigned kk = kKeyNone;
+                    for (int j = g.q; j < kMaxN; j += GS)
+                        if ((t.rrem >> j) & 1ull) kk = min(kk, ((unsigned)__ldg(rk + j) << 6) | (unsigned)j);
+                    u = (int)(g.umin(kk) & 63u);
+                } else {
+                    u = __ffsll(t.rrem) - 1;
+                }
+                t.rrem &= ~(1ull << u);
+                ++nodes;
+                cvisits += t.C;
+                const int v = t.v;
+                const W vb = (W)1 << v, ub = (W)1 << u;
+                const W gB = (W)adj_row<ADJ_SM>(w.adj, v), hB = (W)adj_row<ADJ_SM>(w.adj, 2 * kMaxN + u);
+                const W gA = DIR ? (W)adj_row<ADJ_SM>(w.adj, kMaxN + v) : (W)0;
+                const W hA = DIR ? (W)adj_row<ADJ_SM>(w.adj, 3 * kMaxN + u) : (W)0;
+                const int dm = t.d + 1;
+                const int cbase = t.base + t.C;
+                // parent and child both inside the shared-memory class cache:
+                // shared-memory loads/stores instead of generic ones
+                const bool in_sm = cbase + kMaxN <= st.S;
+                int sum = 0;
+                unsigned best = kKeyNone;
+                W bestR = 0;
+                int pos = cbase;
+                // Appends the part (l, r) to the child level when both sides are
+                // non-empty (group-wide ballot compaction, order kept).
+                auto emit = [&](W l, W r, bool keep) {
+                    const unsigned mk = g.ballot(keep);
+                    if (keep) {
+                        const int q2 = pos + __popc(mk & g.lt());
+                        if (in_sm) st.sm[q2] = make_ulonglong2((u64)l, (u64)r);
+                        else *st.at(q2) = make_ulonglong2((u64)l, (u64)r);
+                    }
+                    pos += __popc(mk);
+                };
+                // Whole-warp searchers write the child's classes only once it
+                // survives Eq. 1, in a second pass over the classes kept in
+                // registers.  Narrow searchers write them in the same pass, before
+                // Eq. 1 decides (a pruned child's writes land in free stack space
+                // above the level): one pass is shorter, and the searchers that
+                // share a warp are more often on the same instruction.
+                constexpr bool SPEC = GS < 32;
+                W Ls[2], Rs[2];                                    // GS == 32: the two slots
+    #pragma unroll (GS == 32 ? 2 : 1)
+                for (int sl = 0; sl < kMaxN / GS; ++sl) {
+                    const int i0 = sl * GS;
+                    if (i0 >= t.C) break;
+                    const int i = i0 + g.q;
+                    W L = 0, R = 0;
+                    if (i < t.C) {
+                        const ulonglong2 c = in_sm ? st.sm[t.base + i] : *st.at(t.base + i);
+                        L = (W)c.x & ~vb;
+                        R = (W)c.y & ~ub;
+                    }
+                    if constexpr (GS == 32) { Ls[sl] = L; Rs[sl] = R; }
+                    if (DIR) {
+                        const W la = L & gA, lb = L & gB, ra = R & hA, rb = R & hB;
+                        const W lp[4] = {(W)(L & ~(la | lb)), (W)(la & ~lb), (W)(lb & ~la), (W)(la & lb)};
+                        const W rp[4] = {(W)(R & ~(ra | rb)), (W)(ra & ~rb), (W)(rb & ~ra), (W)(ra & rb)};
+    #pragma unroll
+                        for (int k = 0; k < 4; ++k) {
+                            const int a = Word<W>::popc(lp[k]), b = Word<W>::popc(rp[k]);
+                            const int m = min(a, b);
+                            sum += m;
+                            const unsigned key = m ? (((unsigned)max(a, b) << 6) | (unsigned)Word<W>::low(lp[k])) : kKeyNone;
+                            if (key < best) { best = key; bestR = rp[k]; }
+                            if (SPEC) emit(lp[k], rp[k], m != 0);
+                        }
+                    } else {
+                        const W l1 = L & gB, r1 = R & hB, l0 = L ^ l1, r0 = R ^ r1;
+                        const int a1 = Word<W>::popc(l1), b1 = Word<W>::popc(r1), a0 = Word<W>::popc(l0), b0 = Word<W>::popc(r0);
+                        const int m1 = min(a1, b1), m0 = min(a0, b0);
+                        sum += m1 + m0;
+                        const unsigned k1 = m1 ? (((unsigned)max(a1, b1) << 6) | (unsigned)Word<W>::low(l1)) : kKeyNone;
+                        const unsigned k0 = m0 ? (((unsigned)max(a0, b0) << 6) | (unsigned)Word<W>::low(l0)) : kKeyNone;
+                        if (k1 < best) { best = k1; bestR = r1; }
+                        if (k0 < best) { best = k0; bestR = r0; }
+                        if (SPEC) {
+                            emit(l1, r1, m1 != 0);
+                            emit(l0, r0, m0 != 0);
+                        }
+                    }
+                }
+                if (SPEC) g.sync();     // the child's writes land before a sibling rewrites the space
+                sum = g.add(sum);
+                // incumbent (Algorithm 1): |M u {(v,u)}| beats the best so far
+                if (dm > inc) {
+                    int old = 0;
+                    if (g.q == 0) old = atomicMax(&ps.inc, dm);
+                    old = g.shfl(old, 0);
+                    if (old < dm) {
+                        write_best<GS>(P, pair, w, t.d, v, u, g);
+                        inc = dm;
+                    } else {
+                        inc = old;
+                    }
+                }
+                if (dm + sum <= inc) { ++pruned; return; }    // child pruned by Eq. 1
+                const unsigned kmin = g.umin(best);
+                const unsigned win = g.ballot(best == kmin);
+                const u64 cR = g.shfl64((u64)bestR, __ffs(win) - 1);
+                if constexpr (GS == 32) {
+                    // descend: compact the child's classes onto the stack
+    #pragma unroll
+                    for (int sl = 0; sl < 2; ++sl) {
+                        if (sl * 32 >= t.C) break;
+                        const W L = Ls[sl], R = Rs[sl];
+                        if (DIR) {
+                            const W la = L & gA, lb = L & gB, ra = R & hA, rb = R & hB;
+                            const W lp[4] = {(W)(L & ~(la | lb)), (W)(la & ~lb), (W)(lb & ~la), (W)(la & lb)};
+                            const W rp[4] = {(W)(R & ~(ra | rb)), (W)(ra & ~rb), (W)(rb & ~ra), (W)(ra & rb)};
+    #pragma unroll
+                            for (int k = 0; k < 4; ++k) emit(lp[k], rp[k], lp[k] && rp[k]);
+                        } else {
+                            const W l1 = L & gB, r1 = R & hB, l0 = L ^ l1, r0 = R ^ r1;
+                            emit(l1, r1, l1 && r1);
+                            emit(l0, r0, l0 && r0);
+                        }
+                    }
+                }
+                if (pos > st.S) spilled += 1;
+                if (!DBG_OK(ctl, pos - cbase <= kMaxN && dm <= kMaxN, 5, (pos - cbase) * 1000 + dm)) pos = cbase;
+                if (g.q == 0) {
+                    w.Mg[t.d] = (uint8_t)v;
+                    w.Mh[t.d] = (uint8_t)u;
+                    w.rrem[t.d] = t.rrem;
+                    w.info[t.d] = pack_info(t.base, t.C, t.v, t.flags, t.bound);
+                }
+                g.sync();
+                t.d = dm;
+                t.base = cbase;
+                t.C = pos - cbase;
+                t.v = kmin & 63;
+                t.rrem = cR;
+                t.flags = kTaskPending;
+                t.bound = dm + sum;
+        };
+
         int p_inc = 0, p_abort = 0, p_hungry = 0;
         while (t.d >= d0) {
             ++tick;
@@ -1000,163 +1182,8 @@ __global__ void __launch_bounds__(256, (GS == 32 ? MCS_SEARCH_MINB : MCS_GROUP_M
                 if (t.d >= d0) load_level(w, t.d, t);
                 continue;
             }
-            if (t.rrem == 0) {
-                // ---------------- "v stays unmatched": same M, v leaves its class ----------------
-                ++nodes;
-                cvisits += t.C;
-                const Scan sc = scan_level<GS>(g, st, t.base, t.C, t.v);
-                g.sync();
-                t.bound = t.d + sc.sum;
-                if (t.bound <= inc) {
-                    t.flags = 0;            // pruned: the level is exhausted and pops next
-                } else {
-                    t.v = sc.key & 63;
-                    t.rrem = sc.R;
-                    t.flags = kTaskPending;
-                }
-                continue;
-            }
-            // ---------------- child (v, u): filterDomain + Eq. 1 ----------------
-            int u;
-            if (LEARNED) {
-                // the remaining candidate with the best learned rank for v
-                const uint8_t* rk = P.rank + ((size_t)pair * kMaxN + t.v) * kMaxN;
-                unsigned kk = kKeyNone;
-                for (int j = g.q; j < kMaxN; j += GS)
-                    if ((t.rrem >> j) & 1ull) kk = min(kk, ((unsigned)__ldg(rk + j) << 6) | (unsigned)j);
-                u = (int)(g.umin(kk) & 63u);
-            } else {
-                u = __ffsll(t.rrem) - 1;
-            }
-            t.rrem &= ~(1ull << u);
-            ++nodes;
-            cvisits += t.C;
-            const int v = t.v;
-            const u64 vb = 1ull << v, ub = 1ull << u;
-            const u64 gB = adj_row<ADJ_SM>(w.adj, v), hB = adj_row<ADJ_SM>(w.adj, 2 * kMaxN + u);
-            const u64 gA = DIR ? adj_row<ADJ_SM>(w.adj, kMaxN + v) : 0ull;
-            const u64 hA = DIR ? adj_row<ADJ_SM>(w.adj, 3 * kMaxN + u) : 0ull;
-            const int dm = t.d + 1;
-            const int cbase = t.base + t.C;
-            // parent and child both inside the shared-memory class cache:
-            // shared-memory loads/stores instead of generic ones
-            const bool in_sm = cbase + kMaxN <= st.S;
-            int sum = 0;
-            unsigned best = kKeyNone;
-            u64 bestR = 0;
-            int pos = cbase;
-            // Appends the part (l, r) to the child level when both sides are
-            // non-empty (group-wide ballot compaction, order kept).
-            auto emit = [&](u64 l, u64 r, bool keep) {
-                const unsigned mk = g.ballot(keep);
-                if (keep) {
-                    const int q2 = pos + __popc(mk & g.lt());
-                    if (in_sm) st.sm[q2] = make_ulonglong2(l, r);
-                    else *st.at(q2) = make_ulonglong2(l, r);
-                }
-                pos += __popc(mk);
-            };
-            // Whole-warp searchers write the child's classes only once it
-            // survives Eq. 1, in a second pass over the classes kept in
-            // registers.  Narrow searchers write them in the same pass, before
-            // Eq. 1 decides (a pruned child's writes land in free stack space
-            // above the level): one pass is shorter, and the searchers that
-            // share a warp are more often on the same instruction.
-            constexpr bool SPEC = GS < 32;
-            u64 Ls[2], Rs[2];                                  // GS == 32: the two slots
-#pragma unroll (GS == 32 ? 2 : 1)
-            for (int sl = 0; sl < kMaxN / GS; ++sl) {
-                const int i0 = sl * GS;
-                if (i0 >= t.C) break;
-                const int i = i0 + g.q;
-                u64 L = 0, R = 0;
-                if (i < t.C) {
-                    const ulonglong2 c = in_sm ? st.sm[t.base + i] : *st.at(t.base + i);
-                    L = c.x & ~vb;
-                    R = c.y & ~ub;
-                }
-                if constexpr (GS == 32) { Ls[sl] = L; Rs[sl] = R; }
-                if (DIR) {
-                    const u64 la = L & gA, lb = L & gB, ra = R & hA, rb = R & hB;
-                    const u64 lp[4] = {L & ~(la | lb), la & ~lb, lb & ~la, la & lb};
-                    const u64 rp[4] = {R & ~(ra | rb), ra & ~rb, rb & ~ra, ra & rb};
-#pragma unroll
-                    for (int k = 0; k < 4; ++k) {
-                        const int a = __popcll(lp[k]), b = __popcll(rp[k]);
-                        const int m = min(a, b);
-                        sum += m;
-                        const unsigned key = m ? (((unsigned)max(a, b) << 6) | (unsigned)(__ffsll(lp[k]) - 1)) : kKeyNone;
-                        if (key < best) { best = key; bestR = rp[k]; }
-                        if (SPEC) emit(lp[k], rp[k], m != 0);
-                    }
-                } else {
-                    const u64 l1 = L & gB, r1 = R & hB, l0 = L ^ l1, r0 = R ^ r1;
-                    const int a1 = __popcll(l1), b1 = __popcll(r1), a0 = __popcll(l0), b0 = __popcll(r0);
-                    const int m1 = min(a1, b1), m0 = min(a0, b0);
-                    sum += m1 + m0;
-                    const unsigned k1 = m1 ? (((unsigned)max(a1, b1) << 6) | (unsigned)(__ffsll(l1) - 1)) : kKeyNone;
-                    const unsigned k0 = m0 ? (((unsigned)max(a0, b0) << 6) | (unsigned)(__ffsll(l0) - 1)) : kKeyNone;
-                    if (k1 < best) { best = k1; bestR = r1; }
-                    if (k0 < best) { best = k0; bestR = r0; }
-                    if (SPEC) {
-                        emit(l1, r1, m1 != 0);
-                        emit(l0, r0, m0 != 0);
-                    }
-                }
-            }
-            if (SPEC) g.sync();     // the child's writes land before a sibling rewrites the space
-            sum = g.add(sum);
-            // incumbent (Algorithm 1): |M u {(v,u)}| beats the best so far
-            if (dm > inc) {
-                int old = 0;
-                if (g.q == 0) old = atomicMax(&ps.inc, dm);
-                old = g.shfl(old, 0);
-                if (old < dm) {
-                    write_best<GS>(P, pair, w, t.d, v, u, g);
-                    inc = dm;
-                } else {
-                    inc = old;
-                }
-            }
-            if (dm + sum <= inc) { ++pruned; continue; }    // child pruned by Eq. 1
-            const unsigned kmin = g.umin(best);
-            const unsigned win = g.ballot(best == kmin);
-            const u64 cR = g.shfl64(bestR, __ffs(win) - 1);
-            if constexpr (GS == 32) {
-                // descend: compact the child's classes onto the stack
-#pragma unroll
-                for (int sl = 0; sl < 2; ++sl) {
-                    if (sl * 32 >= t.C) break;
-                    const u64 L = Ls[sl], R = Rs[sl];
-                    if (DIR) {
-                        const u64 la = L & gA, lb = L & gB, ra = R & hA, rb = R & hB;
-                        const u64 lp[4] = {L & ~(la | lb), la & ~lb, lb & ~la, la & lb};
-                        const u64 rp[4] = {R & ~(ra | rb), ra & ~rb, rb & ~ra, ra & rb};
-#pragma unroll
-                        for (int k = 0; k < 4; ++k) emit(lp[k], rp[k], lp[k] && rp[k]);
-                    } else {
-                        const u64 l1 = L & gB, r1 = R & hB, l0 = L ^ l1, r0 = R ^ r1;
-                        emit(l1, r1, l1 && r1);
-                        emit(l0, r0, l0 && r0);
-                    }
-                }
-            }
-            if (pos > st.S) spilled += 1;
-            if (!DBG_OK(ctl, pos - cbase <= kMaxN && dm <= kMaxN, 5, (pos - cbase) * 1000 + dm)) pos = cbase;
-            if (g.q == 0) {
-                w.Mg[t.d] = (uint8_t)v;
-                w.Mh[t.d] = (uint8_t)u;
-                w.rrem[t.d] = t.rrem;
-                w.info[t.d] = pack_info(t.base, t.C, t.v, t.flags, t.bound);
-            }
-            g.sync();
-            t.d = dm;
-            t.base = cbase;
-            t.C = pos - cbase;
-            t.v = kmin & 63;
-            t.rrem = cR;
-            t.flags = kTaskPending;
-            t.bound = dm + sum;
+            if constexpr (NARROW) node_step(uint32_t{});
+            else node_step(u64{});
         }
         end_task<SERVE, GS>(P, pair, nodes, g, smap);
         if (g.q == 0) cyc[0] += (u64)(clock64() - c_busy);
@@ -1172,56 +1199,71 @@ __global__ void __launch_bounds__(256, (GS == 32 ? MCS_SEARCH_MINB : MCS_GROUP_M
     }
 }
 
-template <bool DIR, bool LEARNED, bool SERVE, int GS>
+template <bool DIR, bool LEARNED, bool SERVE, int GS, bool NARROW>
 static cudaError_t launch_t(const SearchParams& p, int blocks, int wpb, cudaStream_t s) {
     size_t smem = (size_t)wpb * (32 / GS) * p.warp_smem_bytes;
-    cudaFuncSetAttribute(search_kernel<DIR, LEARNED, SERVE, GS>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-    search_kernel<DIR, LEARNED, SERVE, GS><<<blocks, wpb * 32, smem, s>>>(p);
+    auto* k = search_kernel<DIR, LEARNED, SERVE, GS, NARROW>;
+    cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    k<<<blocks, wpb * 32, smem, s>>>(p);
     return cudaGetLastError();
 }
 
-template <bool DIR, bool LEARNED>
+template <bool DIR, bool LEARNED, bool NARROW>
 static cudaError_t launch_g(const SearchParams& p, int blocks, int wpb, int gs, cudaStream_t s) {
-    if (gs == 4) return launch_t<DIR, LEARNED, false, 4>(p, blocks, wpb, s);
-    if (gs == 8) return launch_t<DIR, LEARNED, false, 8>(p, blocks, wpb, s);
-    if (gs == 16) return launch_t<DIR, LEARNED, false, 16>(p, blocks, wpb, s);
-    return launch_t<DIR, LEARNED, false, 32>(p, blocks, wpb, s);
+    if (gs == 4) return launch_t<DIR, LEARNED, false, 4, NARROW>(p, blocks, wpb, s);
+    if (gs == 8) return launch_t<DIR, LEARNED, false, 8, NARROW>(p, blocks, wpb, s);
+    if (gs == 16) return launch_t<DIR, LEARNED, false, 16, NARROW>(p, blocks, wpb, s);
+    return launch_t<DIR, LEARNED, false, 32, NARROW>(p, blocks, wpb, s);
+}
+
+template <bool DIR, bool LEARNED>
+static cudaError_t launch_w(const SearchParams& p, int blocks, int wpb, int gs, bool narrow, cudaStream_t s) {
+    return narrow ? launch_g<DIR, LEARNED, true>(p, blocks, wpb, gs, s)
+                  : launch_g<DIR, LEARNED, false>(p, blocks, wpb, gs, s);
 }
 
 cudaError_t launch_search(const SearchParams& p, int blocks, int warps_per_block, bool directed,
                           bool learned, cudaStream_t s, int gs) {
-    if (p.serving) return launch_t<false, false, true, 32>(p, blocks, warps_per_block, s);
-    if (directed) return learned ? launch_g<true, true>(p, blocks, warps_per_block, gs, s)
-                                 : launch_g<true, false>(p, blocks, warps_per_block, gs, s);
-    return learned ? launch_g<false, true>(p, blocks, warps_per_block, gs, s)
-                   : launch_g<false, false>(p, blocks, warps_per_block, gs, s);
+    if (p.serving) return launch_t<false, false, true, 32, false>(p, blocks, warps_per_block, s);
+    const bool narrow = (p.flags & MCS_WORD32) != 0;
+    if (directed) return learned ? launch_w<true, true>(p, blocks, warps_per_block, gs, narrow, s)
+                                 : launch_w<true, false>(p, blocks, warps_per_block, gs, narrow, s);
+    return learned ? launch_w<false, true>(p, blocks, warps_per_block, gs, narrow, s)
+                   : launch_w<false, false>(p, blocks, warps_per_block, gs, narrow, s);
 }
 
-template <bool DIR, bool LEARNED, bool SERVE, int GS>
+template <bool DIR, bool LEARNED, bool SERVE, int GS, bool NARROW>
 static int occupancy_t(int wpb, int smem) {
     int nb = 0;
-    cudaFuncSetAttribute(search_kernel<DIR, LEARNED, SERVE, GS>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
-    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, search_kernel<DIR, LEARNED, SERVE, GS>, wpb * 32, smem);
+    auto* k = search_kernel<DIR, LEARNED, SERVE, GS, NARROW>;
+    cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
+    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, k, wpb * 32, smem);
     return nb;
 }
 
-template <bool DIR, bool LEARNED>
+template <bool DIR, bool LEARNED, bool NARROW>
 static int occupancy_g(int wpb, int smem, int gs) {
-    if (gs == 4) return occupancy_t<DIR, LEARNED, false, 4>(wpb, smem);
-    if (gs == 8) return occupancy_t<DIR, LEARNED, false, 8>(wpb, smem);
-    if (gs == 16) return occupancy_t<DIR, LEARNED, false, 16>(wpb, smem);
-    return occupancy_t<DIR, LEARNED, false, 32>(wpb, smem);
+    if (gs == 4) return occupancy_t<DIR, LEARNED, false, 4, NARROW>(wpb, smem);
+    if (gs == 8) return occupancy_t<DIR, LEARNED, false, 8, NARROW>(wpb, smem);
+    if (gs == 16) return occupancy_t<DIR, LEARNED, false, 16, NARROW>(wpb, smem);
+    return occupancy_t<DIR, LEARNED, false, 32, NARROW>(wpb, smem);
 }
 
-int search_max_blocks_per_sm(int warps_per_block, int smem_per_block, bool directed, bool learned, int gs) {
-    if (directed) return learned ? occupancy_g<true, true>(warps_per_block, smem_per_block, gs)
-                                 : occupancy_g<true, false>(warps_per_block, smem_per_block, gs);
-    return learned ? occupancy_g<false, true>(warps_per_block, smem_per_block, gs)
-                   : occupancy_g<false, false>(warps_per_block, smem_per_block, gs);
+template <bool DIR, bool LEARNED>
+static int occupancy_w(int wpb, int smem, int gs, bool narrow) {
+    return narrow ? occupancy_g<DIR, LEARNED, true>(wpb, smem, gs) : occupancy_g<DIR, LEARNED, false>(wpb, smem, gs);
+}
+
+int search_max_blocks_per_sm(int warps_per_block, int smem_per_block, bool directed, bool learned, int gs,
+                             bool narrow) {
+    if (directed) return learned ? occupancy_w<true, true>(warps_per_block, smem_per_block, gs, narrow)
+                                 : occupancy_w<true, false>(warps_per_block, smem_per_block, gs, narrow);
+    return learned ? occupancy_w<false, true>(warps_per_block, smem_per_block, gs, narrow)
+                   : occupancy_w<false, false>(warps_per_block, smem_per_block, gs, narrow);
 }
 
 int serve_max_blocks_per_sm(int warps_per_block, int smem_per_block) {
-    return occupancy_t<false, false, true, 32>(warps_per_block, smem_per_block);
+    return occupancy_t<false, false, true, 32, false>(warps_per_block, smem_per_block);
 }
 
 // Serve mode: reset the control block and the ring before a server launch.

@@ -51,13 +51,15 @@ def _check(pairs, results, expect=None):
         assert oracle.verify(p.G.adj, p.H.adj, r.g_idx, r.h_idx, p.G.labels, p.H.labels) == 1, i
 
 
+@pytest.mark.parametrize("group", [32, 8])
 @pytest.mark.parametrize("directed,k", [(False, 0), (True, 0), (False, 3), (True, 2)])
-def test_single_warp_traversal_equals_oracle(solver, directed, k):
-    """With one warp and no per-sibling bound re-test, the device walks the
-    same search tree as the sequential recursion: node counts are equal."""
+def test_single_warp_traversal_equals_oracle(solver, group, directed, k):
+    """With one searcher and no per-sibling bound re-test, the device walks
+    the same search tree as the sequential recursion: node counts are equal."""
     from paper_1908_06418_b300 import MCS_NO_LEVEL_PRUNE
     pairs = _rand_pairs(40, 4, 16, 4242 + k + (100 if directed else 0), directed, k)
     solver.set_max_warps(1)
+    solver.set_search_group(group)
     try:
         for p in pairs:
             r = solver.solve(p.G.adj, p.H.adj, p.G.labels, p.H.labels, directed=directed,
@@ -69,6 +71,28 @@ def test_single_warp_traversal_equals_oracle(solver, directed, k):
             assert oracle.verify(p.G.adj, p.H.adj, r.g_idx, r.h_idx, p.G.labels, p.H.labels) == 1
     finally:
         solver.set_max_warps(0)
+        solver.set_search_group(8)
+
+
+@pytest.mark.parametrize("group", [32, 8])
+@pytest.mark.parametrize("directed,k", [(False, 12), (True, 8), (True, 12)])
+def test_single_searcher_wide_words_equals_oracle(solver, group, directed, k):
+    """Graphs of 33..40 vertices take the 64-bit node step (the pairs above
+    take the 32-bit one): a lone searcher walks the oracle's tree there too."""
+    from paper_1908_06418_b300 import MCS_NO_LEVEL_PRUNE
+    pairs = _rand_pairs(10, 33, 40, 919 + k, directed, k, pmin=0.1, pmax=0.3)
+    solver.set_max_warps(1)
+    solver.set_search_group(group)
+    try:
+        for p in pairs:
+            r = solver.solve(p.G.adj, p.H.adj, p.G.labels, p.H.labels, directed=directed,
+                             flags=MCS_NO_LEVEL_PRUNE, timeout_s=60)
+            o = oracle.mcs(p.G.adj, p.H.adj, p.G.labels, p.H.labels, directed=directed)
+            assert r.status == 0 and r.size == o.size and r.nodes == o.nodes
+            assert oracle.verify(p.G.adj, p.H.adj, r.g_idx, r.h_idx, p.G.labels, p.H.labels) == 1
+    finally:
+        solver.set_max_warps(0)
+        solver.set_search_group(8)
 
 
 def test_single_warp_default_prunes_no_more_nodes(solver):
@@ -283,3 +307,39 @@ def test_launch_values_out_of_range_are_rejected(solver):
         with pytest.raises(ValueError):
             solver.set_launch(*bad)
     solver.reset_launch()
+
+
+def test_word32_flag_rejects_graphs_over_32_vertices(solver):
+    """MCS_WORD32 promises graphs of at most 32 vertices: a pair that breaks
+    it is reported as MCS_ERR_ARG; the others are solved (32-bit node step)."""
+    import torch
+    from paper_1908_06418_b300 import DeviceBatch, MCS_ERR_ARG, MCS_WORD32
+    pairs = _rand_pairs(12, 10, 30, 515, k=2)
+    big = _rand_pairs(1, 33, 33, 516, k=2)[0]
+    pairs = pairs[:5] + [big] + pairs[5:]
+    b = DeviceBatch(pairs, word32=True)
+    assert b.flags & MCS_WORD32
+    n = len(pairs)
+    size = torch.zeros(n, dtype=torch.int32, device=b.device)
+    status = torch.zeros(n, dtype=torch.int32, device=b.device)
+    nodes = torch.zeros(n, dtype=torch.int64, device=b.device)
+    rc = solver.solve_batch_device(n, b.d_n, b.d_adj_off, b.d_adj, b.d_lab_off, b.d_labels,
+                                   size, status, nodes, flags=b.flags, timeout_s=60)
+    torch.cuda.synchronize()
+    assert rc == 0
+    st, sz = status.cpu().numpy(), size.cpu().numpy()
+    for i, p in enumerate(pairs):
+        if i == 5:
+            assert st[i] == MCS_ERR_ARG and sz[i] == 0
+        else:
+            assert st[i] == 0
+            assert sz[i] == oracle.mcs(p.G.adj, p.H.adj, p.G.labels, p.H.labels).size
+    # without the flag the same batch runs on 64-bit words and solves every pair
+    b2 = DeviceBatch(pairs)
+    assert not (b2.flags & MCS_WORD32)
+    rc = solver.solve_batch_device(n, b2.d_n, b2.d_adj_off, b2.d_adj, b2.d_lab_off, b2.d_labels,
+                                   size, status, nodes, flags=b2.flags, timeout_s=60)
+    torch.cuda.synchronize()
+    assert rc == 0 and (status.cpu().numpy() == 0).all()
+    assert size.cpu().numpy()[5] == oracle.mcs(big.G.adj, big.H.adj, big.G.labels, big.H.labels).size
+
