@@ -216,8 +216,9 @@ int mcs_poll(mcs_ctx* ctx, uint64_t ticket, mcs_result* out);
 
 /* Launch shape used by every solve on this context: warps per block (1..8,
  * default 4), blocks per SM (default: as many as fit), class-stack entries
- * kept in shared memory per searcher (default 256 for whole-warp searchers,
- * 32 for narrower ones).  0 keeps the current value, -1 restores the default;
+ * kept in shared memory per whole-warp searcher (default 256; narrower
+ * searchers keep their class stacks in global memory and ignore it).  0
+ * keeps the current value, -1 restores the default;
  * anything else out of range is MCS_ERR_ARG.  A shape whose shared memory
  * does not fit an SM makes the next solve return MCS_ERR_UNSUPPORTED. */
 int mcs_set_launch(mcs_ctx* ctx, int warps_per_block, int blocks_per_sm,

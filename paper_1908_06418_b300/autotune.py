@@ -6,9 +6,9 @@ For each workload it times device-resident batch solves (inputs already in
 HBM, CUDA events on the launching stream, best of `--reps`) over a grid of
 launch shapes -- lanes per searcher (32: one search per warp; 16, 8, 4: two,
 four or eight per warp), warps per block, class-stack entries kept in shared
-memory per searcher (which sets shared memory per searcher and so the
-resident searchers), and blocks per SM -- and records the fastest shape for
-the workload's bucket
+memory per whole-warp searcher (which sets shared memory per warp and so the
+resident warps), and blocks per SM -- and records the fastest shape for the
+workload's bucket
 (directed or not, labelled or not, largest vertex count rounded up to 32 /
 48 / 64) in ``data/tune_cache.json``.  ``Solver.apply_tuned(pairs)`` applies
 the cached shape for a batch's bucket.
@@ -26,12 +26,9 @@ CACHE = os.path.join(HERE, "data", "tune_cache.json")
 
 SHAPES = ([dict(search_group=32, warps_per_block=w, smem_stack_entries=s, blocks_per_sm=0)
            for w, s in itertools.product((4,), (128, 256))]
-          + [dict(search_group=16, warps_per_block=w, smem_stack_entries=s, blocks_per_sm=0)
-             for w, s in itertools.product((4,), (64, 128))]
-          + [dict(search_group=8, warps_per_block=w, smem_stack_entries=s, blocks_per_sm=0)
-             for w, s in itertools.product((2, 4, 8), (16, 32, 64))]
-          + [dict(search_group=4, warps_per_block=w, smem_stack_entries=s, blocks_per_sm=0)
-             for w, s in itertools.product((2, 4), (8, 16))])
+          # narrow searchers keep class stacks in global memory: no shared-memory size to sweep
+          + [dict(search_group=g, warps_per_block=w, smem_stack_entries=-1, blocks_per_sm=0)
+             for g, w in ((16, 4), (8, 2), (8, 4), (8, 8), (4, 4))])
 KEYS = ("search_group", "warps_per_block", "smem_stack_entries", "blocks_per_sm")
 
 

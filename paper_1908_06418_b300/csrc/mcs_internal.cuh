@@ -233,11 +233,12 @@ struct mcs_ctx {
     uint64_t graph_key[16] = {0};
 };
 
-// Class-stack entries per searcher kept in shared memory: the value set by
-// mcs_set_launch, else 256 for whole-warp searchers and 32 for narrower ones
-// (many more of them share an SM; deeper levels go to the global overflow).
+// Class-stack entries per searcher kept in shared memory: for whole-warp
+// searchers the value set by mcs_set_launch, else 256; narrower searchers
+// keep their class stacks in global memory (0).
 inline int stack_entries(const mcs_ctx* c, int gs) {
-    return c->smem_stack > 0 ? c->smem_stack : (gs == 32 ? 256 : 32);
+    if (gs != 32) return 0;
+    return c->smem_stack > 0 ? c->smem_stack : 256;
 }
 
 // kernels.cu entry points used by the host library

@@ -361,18 +361,27 @@ struct Top {                // the cursor of the deepest level, kept in register
     u64 rrem;
 };
 
-struct Stack {
-    ulonglong2* sm;          // shared part
-    ulonglong2* gm;          // global overflow part
-    int S;
+// A searcher's class stack.  Whole-warp searchers keep its first S entries
+// in shared memory and the rest in their global overflow; narrow searchers
+// (many per SM, so little shared memory each) keep it all in global memory,
+// where the L1 cache holds the top levels that are in use.
+template <bool HAS_SM>
+struct StackT {
+    ulonglong2* sm;          // shared part (HAS_SM)
+    ulonglong2* gm;          // global part
+    int S;                   // entries in the shared part (0 without one)
 #ifdef MCS_DEBUG_BOUNDS
     Control* ctl;
     __device__ __forceinline__ ulonglong2* at(int p) const {
         if (!DBG_OK(ctl, p >= 0 && p < kStackMax, 1, p)) p = 0;
-        return p < S ? sm + p : gm + (p - S);
+        if constexpr (HAS_SM) return p < S ? sm + p : gm + (p - S);
+        else return gm + p;
     }
 #else
-    __device__ __forceinline__ ulonglong2* at(int p) const { return p < S ? sm + p : gm + (p - S); }
+    __device__ __forceinline__ ulonglong2* at(int p) const {
+        if constexpr (HAS_SM) return p < S ? sm + p : gm + (p - S);
+        else return gm + p;
+    }
 #endif
 };
 
@@ -399,7 +408,7 @@ template <> struct Word<uint32_t> {
 
 // Scan the classes of a level (optionally removing v from its class first,
 // which is the "v stays unmatched" step) and choose the next branching class.
-template <typename W, int GS>
+template <typename W, int GS, typename Stack>
 __device__ __forceinline__ Scan scan_level(const Grp<GS>& g, const Stack& st, int base, int C,
                                            int remove_v) {
     int sum = 0;
@@ -650,7 +659,7 @@ __device__ __forceinline__ void load_level(const WarpSmem& w, int d, Top& t) {
 // including its "v unmatched" branch.  The level's classes and the mapping
 // prefix M travel with the task.  Returns false if the bounded wait for the
 // ring slot expired (the error is recorded in the control block).
-template <int GS>
+template <int GS, typename Stack>
 __device__ __forceinline__ bool donate(const SearchParams& P, int pair, int d0, Top& t, int inc,
                                        const WarpSmem& w, const Stack& st, const Grp<GS>& g,
                                        unsigned& donated) {
@@ -775,10 +784,11 @@ __global__ void __launch_bounds__(256, (GS == 32 ? MCS_SEARCH_MINB : MCS_GROUP_M
     w.Mg = lv + kSmMOff;
     w.Mh = lv + kSmMOff + kMaxN;
     w.cls = (ulonglong2*)(lv + kSmClsOff);
-    Stack st;
+    constexpr bool STACK_SM = GS == 32;
+    StackT<STACK_SM> st;
     st.sm = w.cls;
-    st.S = P.stack_smem;
-    st.gm = P.gstack + (size_t)sid * (size_t)(kStackMax > P.stack_smem ? kStackMax - P.stack_smem : 0);
+    st.S = STACK_SM ? P.stack_smem : 0;
+    st.gm = P.gstack + (size_t)sid * (size_t)(kStackMax > st.S ? kStackMax - st.S : 0);
 #ifdef MCS_DEBUG_BOUNDS
     st.ctl = P.ctl;
 #endif
@@ -1034,7 +1044,7 @@ __global__ void __launch_bounds__(256, (GS == 32 ? MCS_SEARCH_MINB : MCS_GROUP_M
                 const int cbase = t.base + t.C;
                 // parent and child both inside the shared-memory class cache:
                 // shared-memory loads/stores instead of generic ones
-                const bool in_sm = cbase + kMaxN <= st.S;
+                const bool in_sm = STACK_SM && cbase + kMaxN <= st.S;
                 int sum = 0;
                 unsigned best = kKeyNone;
                 W bestR = 0;
