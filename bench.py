@@ -38,7 +38,7 @@ METRIC = "MCS pairs solved/sec (exact) on 1 B300"
 # the dominant search kernel, from a single-pass ncu capture of this
 # workload's launch (profiles/dram_search_kernel_c2.md); reported only while
 # the kernel source is the one the capture was taken with.
-TRAFFIC = {"c2": {"kernel_sha1": "cb7d5df4e90aa931", "bytes": 5.97e6 + 1.44e6}}
+TRAFFIC = {"c2": {"kernel_sha1": "e0ac6dd293de26f2", "bytes": 86.74e6 + 255.29e6}}
 UNIT = "pairs/s"
 
 
@@ -172,6 +172,7 @@ def apply_shape(solver, sh):
     if sh:
         solver.set_launch(sh["warps_per_block"], sh["blocks_per_sm"] or -1, sh["smem_stack_entries"],
                           search_group=sh["search_group"])
+        solver.set_steal(sh["poll_nodes"], sh["steal_keep_quarters"])
     else:
         solver.reset_launch()
 
@@ -278,7 +279,9 @@ def main():
                                                       directed=bool(g["flags"] & MCS_DIRECTED))
         shapes.append(None if e is None else dict({k: e[k] for k in ("warps_per_block", "smem_stack_entries",
                                                                       "blocks_per_sm")},
-                                                  search_group=e.get("search_group", 32)))
+                                                  search_group=e.get("search_group", 32),
+                                                  poll_nodes=e.get("poll_nodes", -1),
+                                                  steal_keep_quarters=e.get("steal_keep_quarters", -1)))
         g["shape"] = shapes[-1]
     flush = torch.empty(512 << 20, dtype=torch.uint8, device=dev)
     launches_per_step = 2 * len(groups)      # pack + search per group

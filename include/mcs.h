@@ -229,6 +229,14 @@ int mcs_set_launch(mcs_ctx* ctx, int warps_per_block, int blocks_per_sm,
  * With warps == 1 the search order is deterministic. */
 int mcs_set_max_warps(mcs_ctx* ctx, int warps);
 
+/* Work-sharing granularity of batch solves: a busy searcher checks every
+ * poll_nodes search nodes (a power of two, 4..1024; default 16) whether a
+ * searcher waits for work, and then hands over the upper part of the
+ * candidates of its shallowest open level, keeping keep_quarters / 4 of them
+ * (1..3; default 2, i.e. half; at least one).  0 keeps a value, -1 restores
+ * its default; anything else is MCS_ERR_ARG.  Results do not depend on it. */
+int mcs_set_steal(mcs_ctx* ctx, int poll_nodes, int keep_quarters);
+
 /* Lanes per depth-first searcher of mcs_solve_batch[_device] (Section III's
  * data-parallel node step, Algorithm 1): 32 runs one search per warp with the
  * label classes of a node spread over the lanes; 16 or 8 runs two or four

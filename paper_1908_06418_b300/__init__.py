@@ -50,7 +50,7 @@ class _Result(ctypes.Structure):
 
 EXPORTED_SYMBOLS = ["mcs_create", "mcs_destroy", "mcs_solve", "mcs_solve_batch",
                     "mcs_solve_batch_device", "mcs_submit", "mcs_poll", "mcs_set_launch",
-                    "mcs_set_max_warps", "mcs_set_search_group", "mcs_last_stats", "mcs_bench_popc", "mcs_strerror", "mcs_error_detail",
+                    "mcs_set_max_warps", "mcs_set_search_group", "mcs_set_steal", "mcs_last_stats", "mcs_bench_popc", "mcs_strerror", "mcs_error_detail",
                     "mcs_solve_batch_noalloc", "mcs_set_order_model", "mcs_get_order_model",
                     "mcs_order_eval", "mcs_order_train"]
 
@@ -92,6 +92,8 @@ def load_library():
     lib.mcs_set_max_warps.restype = ctypes.c_int
     lib.mcs_set_search_group.argtypes = [vp, ctypes.c_int]
     lib.mcs_set_search_group.restype = ctypes.c_int
+    lib.mcs_set_steal.argtypes = [vp, ctypes.c_int, ctypes.c_int]
+    lib.mcs_set_steal.restype = ctypes.c_int
     lib.mcs_last_stats.argtypes = [vp, ctypes.POINTER(ctypes.c_double), ctypes.c_int]
     lib.mcs_last_stats.restype = ctypes.c_int
     lib.mcs_bench_popc.argtypes = [vp, ctypes.POINTER(ctypes.c_double)]
@@ -185,8 +187,17 @@ class Solver:
             self.set_search_group(search_group)
 
     def reset_launch(self):
-        """Back to the default launch shape and search group (8 lanes)."""
+        """Back to the default launch shape, search group (8 lanes) and work
+        sharing."""
         self.set_launch(-1, -1, -1, search_group=8)
+        self.set_steal(-1, -1)
+
+    def set_steal(self, poll_nodes: int = 0, keep_quarters: int = 0):
+        """Work-sharing poll interval (nodes) and the donor's kept share in
+        quarters; 0 keeps a value, -1 restores its default."""
+        rc = self.lib.mcs_set_steal(self.ctx, int(poll_nodes), int(keep_quarters))
+        if rc:
+            raise ValueError(self.strerror(rc))
 
     def set_max_warps(self, warps: int):
         rc = self.lib.mcs_set_max_warps(self.ctx, int(warps))
@@ -208,6 +219,7 @@ class Solver:
         if e:
             self.set_launch(e["warps_per_block"], e["blocks_per_sm"] or -1, e["smem_stack_entries"],
                             search_group=e.get("search_group", 32))
+            self.set_steal(e.get("poll_nodes", -1), e.get("steal_keep_quarters", -1))
         return e
 
     def last_stats(self) -> dict:

@@ -7,8 +7,9 @@ HBM, CUDA events on the launching stream, best of `--reps`) over a grid of
 launch shapes -- lanes per searcher (32: one search per warp; 16, 8, 4: two,
 four or eight per warp), warps per block, class-stack entries kept in shared
 memory per whole-warp searcher (which sets shared memory per warp and so the
-resident warps), and blocks per SM -- and records the fastest shape for the
-workload's bucket
+resident warps), and blocks per SM -- then, on the fastest shape, the
+work-sharing poll interval and the share a donor keeps, and records the
+fastest setting for the workload's bucket
 (directed or not, labelled or not, largest vertex count rounded up to 32 /
 48 / 64) in ``data/tune_cache.json``.  ``Solver.apply_tuned(pairs)`` applies
 the cached shape for a batch's bucket.
@@ -30,6 +31,8 @@ SHAPES = ([dict(search_group=32, warps_per_block=w, smem_stack_entries=s, blocks
           + [dict(search_group=g, warps_per_block=w, smem_stack_entries=-1, blocks_per_sm=0)
              for g, w in ((16, 4), (8, 2), (8, 4), (8, 8), (4, 4))])
 KEYS = ("search_group", "warps_per_block", "smem_stack_entries", "blocks_per_sm")
+# second stage, on the fastest shape: work-sharing poll interval x the donor's kept share
+STEAL = [dict(poll_nodes=pn, steal_keep_quarters=kq) for pn, kq in itertools.product((8, 16, 32), (1, 2, 3))]
 
 
 def bucket(pairs, directed: bool) -> str:
@@ -55,6 +58,7 @@ def time_shape(solver, batch, n, shape, reps, timeout_s):
                nodes=torch.zeros(n, dtype=torch.int64, device=dev))
     solver.set_launch(shape["warps_per_block"], shape["blocks_per_sm"] or -1, shape["smem_stack_entries"],
                       search_group=shape["search_group"])
+    solver.set_steal(shape.get("poll_nodes", -1), shape.get("steal_keep_quarters", -1))
     stream = torch.cuda.Stream(dev)
     best = None
     for r in range(reps + 1):
@@ -84,12 +88,21 @@ def tune(name: str, pairs, directed: bool, reps: int = 2, timeout_s: float = 120
             t = time_shape(s, batch, len(pairs), shape, reps, timeout_s)
             results.append(dict(shape, ms=t))
             print(name, shape, t, flush=True)
-    ok = [r for r in results if r["ms"] is not None]
+        ok = [r for r in results if r["ms"] is not None]
+        best = {k: min(ok, key=lambda r: r["ms"])[k] for k in KEYS}
+        steal = []
+        for st in STEAL:
+            shape = dict(best, **st)
+            t = time_shape(s, batch, len(pairs), shape, reps, timeout_s)
+            steal.append(dict(shape, ms=t))
+            print(name, shape, t, flush=True)
+    ok = [r for r in steal if r["ms"] is not None]
     best = min(ok, key=lambda r: r["ms"])
     cache = load_cache(cache_path)
     key = bucket(pairs, directed)
     cache[key] = dict(best, workload=name, measured=time.strftime("%Y-%m-%d"),
-                      sweep=[{k: r[k] for k in KEYS + ("ms",)} for r in results])
+                      sweep=[{k: r[k] for k in KEYS + ("ms",)} for r in results],
+                      steal_sweep=[{k: r[k] for k in ("poll_nodes", "steal_keep_quarters", "ms")} for r in steal])
     os.makedirs(os.path.dirname(cache_path), exist_ok=True)
     with open(cache_path, "w") as f:
         json.dump(cache, f, indent=1)

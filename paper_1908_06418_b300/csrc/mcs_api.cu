@@ -189,6 +189,8 @@ int run_device(mcs_ctx* c, int npairs, const int32_t* d_n, const int64_t* d_adj_
     sp.max_warps = warps;
     sp.gstack = c->gstack;
     sp.rank = rank;
+    sp.poll_mask = (uint32_t)c->poll_nodes - 1;
+    sp.steal_keep_q4 = c->steal_keep_q4;
     sp.out_size = d_size;
     sp.out_status = d_status;
     sp.out_nodes = reinterpret_cast<u64*>(d_nodes);
@@ -271,6 +273,17 @@ int mcs_set_launch(mcs_ctx* c, int warps_per_block, int blocks_per_sm, int smem_
     return 0;
 }
 
+int mcs_set_steal(mcs_ctx* c, int poll_nodes, int keep_quarters) {
+    if (!c) return MCS_ERR_ARG;
+    const bool pow2 = poll_nodes > 0 && (poll_nodes & (poll_nodes - 1)) == 0;
+    if (!(poll_nodes == 0 || poll_nodes == -1 || (pow2 && poll_nodes >= 4 && poll_nodes <= 1024)))
+        return MCS_ERR_ARG;
+    if (keep_quarters < -1 || keep_quarters > 3) return MCS_ERR_ARG;
+    if (poll_nodes) c->poll_nodes = poll_nodes > 0 ? poll_nodes : (int)kPollMaskDefault + 1;
+    if (keep_quarters) c->steal_keep_q4 = keep_quarters > 0 ? keep_quarters : kStealKeepDefault;
+    return 0;
+}
+
 int mcs_set_search_group(mcs_ctx* c, int lanes) {
     if (!c || (lanes != 4 && lanes != 8 && lanes != 16 && lanes != 32)) return MCS_ERR_ARG;
     c->group_lanes = lanes;
@@ -325,7 +338,8 @@ int mcs_solve_batch_device(mcs_ctx* c, int32_t npairs, const int32_t* d_n,
                             (uint64_t)d_size, (uint64_t)d_status, (uint64_t)d_nodes, (uint64_t)d_map,
                             (uint64_t)d_usec, (uint64_t)c->warps_per_block | ((uint64_t)c->group_lanes << 32),
                             (uint64_t)c->smem_stack | ((uint64_t)c->blocks_per_sm << 32),
-                            (uint64_t)c->max_warps};
+                            (uint64_t)c->max_warps | ((uint64_t)c->poll_nodes << 32) |
+                                ((uint64_t)c->steal_keep_q4 << 48)};
         memcpy(&key[7], &tmo, sizeof(double));
         if (!c->graph_exec || memcmp(key, c->graph_key, sizeof(key)) != 0) {
             if (c->graph_exec) { cudaGraphExecDestroy(c->graph_exec); c->graph_exec = nullptr; }

@@ -135,6 +135,8 @@ struct SearchParams {
     int32_t max_warps;             // searchers that take part (others exit at once)
     ulonglong2* gstack;            // per-warp overflow of the class stack
     const uint8_t* rank;           // learned order: [npairs][kMaxN][kMaxN] rank of u for v, or null
+    uint32_t poll_mask;            // work sharing: poll every poll_mask + 1 nodes (power of two)
+    int32_t steal_keep_q4;         // a donor keeps ceil(k * q / 4) of k candidates (1..3)
     // outputs
     int32_t* out_size;
     int32_t* out_status;
@@ -204,6 +206,8 @@ struct mcs_ctx {
     int smem_stack = 0;           // class entries per searcher in shared memory (0: default)
     int max_warps = 0;            // 0: every launched searcher
     int group_lanes = 8;          // lanes per searcher of batch solves: 32, 16, 8 or 4
+    int poll_nodes = 16;          // work-sharing poll interval (nodes, power of two)
+    int steal_keep_q4 = 2;        // quarters of a donated level's candidates the donor keeps
     // device arenas
     int pairs_cap = 0;
     PairGraph* graphs = nullptr;
@@ -232,6 +236,10 @@ struct mcs_ctx {
     cudaGraph_t graph = nullptr;
     uint64_t graph_key[16] = {0};
 };
+
+// Work-sharing defaults for launches that do not take them from a context.
+constexpr uint32_t kPollMaskDefault = 15;
+constexpr int32_t kStealKeepDefault = 2;
 
 // Class-stack entries per searcher kept in shared memory: for whole-warp
 // searchers the value set by mcs_set_launch, else 256; narrower searchers

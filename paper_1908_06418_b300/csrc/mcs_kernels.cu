@@ -654,8 +654,9 @@ __device__ __forceinline__ void load_level(const WarpSmem& w, int d, Top& t) {
 }
 
 // Work sharing: hands part of the shallowest open level of this searcher's
-// subtree to a waiting searcher through the ring -- the upper half of its
-// remaining candidates u, or, with one candidate left, the rest of the level
+// subtree to a waiting searcher through the ring -- the upper part of its
+// remaining candidates u (the donor keeps the share P.steal_keep_q4 / 4, by
+// default half), or, with one candidate left, the rest of the level
 // including its "v unmatched" branch.  The level's classes and the mapping
 // prefix M travel with the task.  Returns false if the bounded wait for the
 // ring slot expired (the error is recorded in the control block).
@@ -691,9 +692,11 @@ __device__ __forceinline__ bool donate(const SearchParams& P, int pair, int d0, 
     u64 give;
     int gflags;
     if (k >= 2) {
-        // the upper half of the candidates; the rest and the unmatched branch stay
+        // the upper candidates; the rest and the unmatched branch stay
         give = rr;
-        for (int j = 0; j < (k + 1) / 2; ++j) give &= give - 1;
+        // the donor keeps the lowest ceil(k q / 4) (at least 1, at most k - 1)
+        const int keep = min(k - 1, max(1, (k * P.steal_keep_q4 + 3) / 4));
+        for (int j = 0; j < keep; ++j) give &= give - 1;
         gflags = 0;
     } else {
         give = rr;
@@ -998,8 +1001,8 @@ __global__ void __launch_bounds__(256, (GS == 32 ? MCS_SEARCH_MINB : MCS_GROUP_M
         // ------------------------------------------------------------------
         // depth-first search over this task's subtree
         // ------------------------------------------------------------------
-        // polled values, loaded by lane 0 8 ticks before they are used so
-        // that the L2 round trip overlaps node work
+        // polled values, loaded by lane 0 half a poll interval before they
+        // are used so that the L2 round trip overlaps node work
         // One search node at the top of the stack: "v unmatched" when no
         // candidate u is left, else the child (v, u).  W is the bit-set word.
         auto node_step = [&](auto wtag) {
@@ -1166,7 +1169,7 @@ __global__ void __launch_bounds__(256, (GS == 32 ? MCS_SEARCH_MINB : MCS_GROUP_M
         int p_inc = 0, p_abort = 0, p_hungry = 0;
         while (t.d >= d0) {
             ++tick;
-            if ((tick & 15) == 0 && g.q == 0) {
+            if ((tick & P.poll_mask) == 0 && g.q == 0) {
                 p_inc = vload(&ps.inc);
                 p_abort = vload(&ps.abort);
                 p_hungry = vload(&ctl->q_head) > vload(&ctl->q_tail);   // a searcher waits
@@ -1177,7 +1180,7 @@ __global__ void __launch_bounds__(256, (GS == 32 ? MCS_SEARCH_MINB : MCS_GROUP_M
                 if (cvisits >= (1u << 31)) { atomicAdd(&ctl->class_visits, (u64)cvisits); cvisits = 0; }
                 if (pruned >= (1u << 31)) { atomicAdd(&ctl->pruned, (u64)pruned); pruned = 0; }
             }
-            if ((tick & 15) == 8) {
+            if ((tick & P.poll_mask) == (P.poll_mask + 1) / 2) {
                 const int g_inc = g.shfl(p_inc, 0);
                 const int ab = g.shfl(p_abort, 0);
                 const int hungry = g.shfl(p_hungry, 0);

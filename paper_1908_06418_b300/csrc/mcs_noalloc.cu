@@ -130,6 +130,8 @@ extern "C" int mcs_solve_batch_noalloc(int32_t npairs, const int32_t* d_n,
     double tmo = timeout_s > 0 ? (timeout_s < 3600.0 ? timeout_s : 3600.0) : 3600.0;
     SearchParams sp;
     memset(&sp, 0, sizeof(sp));
+    sp.poll_mask = kPollMaskDefault;
+    sp.steal_keep_q4 = kStealKeepDefault;
     sp.npairs = npairs;
     sp.flags = flags;
     sp.timeout_ns = (u64)(tmo * 1e9);

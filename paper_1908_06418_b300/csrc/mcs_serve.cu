@@ -150,6 +150,8 @@ int launch_server(mcs_ctx* c, ServeState* S) {
     CKS(launch_serve_init(S->ctl, S->qseq, S->qcap, S->in_flight, S->stream));
     SearchParams sp;
     memset(&sp, 0, sizeof(sp));
+    sp.poll_mask = kPollMaskDefault;
+    sp.steal_keep_q4 = kStealKeepDefault;
     sp.serving = 1;
     sp.sv.host_written = dev_view(S->h_written);
     sp.sv.ring = dev_view(S->h_ring);

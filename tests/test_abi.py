@@ -44,6 +44,8 @@ def test_strerror_and_argument_checks_without_gpu():
     # NULL context is rejected before any CUDA call
     assert lib.mcs_solve(None, None, None, 0, 0.0, None) == m.MCS_ERR_ARG
     assert lib.mcs_set_launch(None, 4, 0, 0) == m.MCS_ERR_ARG
+    assert lib.mcs_set_search_group(None, 8) == m.MCS_ERR_ARG
+    assert lib.mcs_set_steal(None, 16, 2) == m.MCS_ERR_ARG
 
 
 def test_create_without_device_returns_null():

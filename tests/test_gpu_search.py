@@ -342,3 +342,24 @@ def test_word32_flag_rejects_graphs_over_32_vertices(solver):
     assert rc == 0 and (status.cpu().numpy() == 0).all()
     assert size.cpu().numpy()[5] == oracle.mcs(big.G.adj, big.H.adj, big.G.labels, big.H.labels).size
 
+
+@pytest.mark.parametrize("steal", [(4, 1), (64, 3), (1024, 2)])
+def test_work_sharing_settings_give_same_sizes(solver, steal):
+    pairs = _rand_pairs(60, 10, 26, 321, k=1)
+    ref = [oracle.mcs(p.G.adj, p.H.adj, p.G.labels, p.H.labels).size for p in pairs]
+    solver.set_steal(*steal)
+    try:
+        res = solver.solve_batch(pairs, timeout_s=60)
+        st = solver.last_stats()
+    finally:
+        solver.reset_launch()
+    assert [r.size for r in res] == ref and all(r.status == 0 for r in res)
+    assert st["donated"] > 0
+
+
+def test_work_sharing_values_out_of_range_are_rejected(solver):
+    for bad in [(3, 0), (12, 0), (2048, 0), (-2, 0), (0, 4), (0, -2)]:
+        with pytest.raises(ValueError):
+            solver.set_steal(*bad)
+    solver.reset_launch()
+
