@@ -19,7 +19,7 @@ __all__ = ["Solver", "Result", "MCS_OK", "MCS_TIMEOUT", "MCS_PENDING", "MCS_ERR_
            "MCS_ERR_NOMEM", "MCS_ERR_CUDA", "MCS_ERR_DEVICE_STALL", "MCS_ERR_UNSUPPORTED",
            "MCS_DIRECTED", "MCS_ORDER_LEARNED", "MCS_NO_MAPPING", "MCS_NO_LEVEL_PRUNE",
            "MCS_MAX_N", "MCS_GRAPH_REPLAY", "MCS_WORD32", "lib_path", "load_library", "EXPORTED_SYMBOLS",
-           "DeviceBatch", "pack_host"]
+           "DeviceBatch", "HostBatch", "pack_host"]
 
 MCS_MAX_N = 64
 MCS_OK, MCS_TIMEOUT, MCS_PENDING = 0, 1, 2
@@ -283,6 +283,25 @@ class Solver:
                               hi[:k].astype(np.int32), int(r.nodes), float(r.seconds)))
         return out
 
+    def solve_host(self, batch: "HostBatch", flags: int = 0, timeout_s: float = 0.0) -> dict:
+        """mcs_solve_batch on a HostBatch: the same C call as solve_batch
+        (host buffers; one host-to-device and one device-to-host copy inside)
+        without per-pair Python objects.  Returns numpy arrays: size, status,
+        nodes, seconds, and the mapping as g_idx/h_idx rows (the first size[i]
+        entries of row i)."""
+        gp, rp = ctypes.POINTER(_Graph), ctypes.POINTER(_Result)
+        rc = self.lib.mcs_solve_batch(self.ctx, ctypes.cast(batch.G.ctypes.data, gp),
+                                      ctypes.cast(batch.H.ctypes.data, gp), batch.npairs,
+                                      int(flags | batch.flags), float(timeout_s),
+                                      ctypes.cast(batch.res.ctypes.data, rp))
+        if rc < 0 and rc not in (MCS_ERR_ARG,):
+            raise RuntimeError(f"mcs_solve_batch: {self.strerror(rc)} ({rc}): "
+                               f"{self.lib.mcs_error_detail().decode()}")
+        k = batch.npairs
+        r = batch.res[:k]
+        return dict(size=r["size"].copy(), status=r["status"].copy(), nodes=r["nodes"].copy(),
+                    seconds=r["seconds"].copy(), g_idx=batch.map_g[:k], h_idx=batch.map_h[:k])
+
     def solve(self, adjG, adjH, labG=None, labH=None, directed: bool = False,
               flags: int = 0, timeout_s: float = 0.0) -> Result:
         return self.solve_batch([(adjG, adjH, labG, labH)],
@@ -429,6 +448,40 @@ def pack_host(pairs) -> dict:
 
 def _ptr(t):
     return None if t is None else ctypes.c_void_p(int(t.data_ptr()))
+
+
+# numpy images of mcs_graph / mcs_result (include/mcs.h), for whole-batch marshalling
+_GRAPH_DTYPE = np.dtype([("n", "<i4"), ("_pad", "<i4"), ("adj", "<u8"), ("labels", "<u8")])
+_RESULT_DTYPE = np.dtype([("size", "<i4"), ("status", "<i4"), ("npairs", "<i4"), ("_pad", "<i4"),
+                          ("g_idx", "<u8"), ("h_idx", "<u8"), ("nodes", "<u8"), ("seconds", "<f8")])
+assert _GRAPH_DTYPE.itemsize == ctypes.sizeof(_Graph) and _RESULT_DTYPE.itemsize == ctypes.sizeof(_Result)
+
+
+class HostBatch:
+    """A list of pairs in host memory, laid out once for mcs_solve_batch
+    (Solver.solve_host): the mcs_graph arrays point into one adjacency buffer
+    and one label buffer, and the mcs_result array into one mapping buffer of
+    64 entries per pair.  Marshalling only."""
+
+    def __init__(self, pairs, directed: bool = False):
+        h = pack_host(pairs)
+        self.npairs = len(pairs)
+        self.flags = MCS_DIRECTED if directed else 0
+        self.adj = h["adj"]
+        self.labels = h["labels"] if h["labels"] is not None else np.zeros(1, np.int32)
+        n = h["n"]
+        g = np.zeros(2 * max(self.npairs, 1), _GRAPH_DTYPE)
+        g["n"][:n.size] = n
+        g["adj"][:n.size] = self.adj.ctypes.data + h["adj_off"]
+        lo = h["lab_off"]
+        g["labels"][:n.size] = np.where(lo >= 0, self.labels.ctypes.data + 4 * np.maximum(lo, 0), 0)
+        self.G = np.ascontiguousarray(g[0::2])
+        self.H = np.ascontiguousarray(g[1::2])
+        self.map_g = np.zeros((max(self.npairs, 1), MCS_MAX_N), np.int16)
+        self.map_h = np.zeros((max(self.npairs, 1), MCS_MAX_N), np.int16)
+        self.res = np.zeros(max(self.npairs, 1), _RESULT_DTYPE)
+        self.res["g_idx"] = self.map_g.ctypes.data + 2 * MCS_MAX_N * np.arange(self.res.size)
+        self.res["h_idx"] = self.map_h.ctypes.data + 2 * MCS_MAX_N * np.arange(self.res.size)
 
 
 class DeviceBatch:

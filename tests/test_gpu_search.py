@@ -363,3 +363,20 @@ def test_work_sharing_values_out_of_range_are_rejected(solver):
             solver.set_steal(*bad)
     solver.reset_launch()
 
+
+
+@pytest.mark.parametrize("directed,k", [(False, 2), (True, 0)])
+def test_host_batch_call_matches_per_pair_objects(solver, directed, k):
+    """Solver.solve_host (whole-batch marshalling of the same mcs_solve_batch
+    call) returns what solve_batch returns, mappings included."""
+    from paper_1908_06418_b300 import HostBatch
+    pairs = _rand_pairs(150, 1, 28, 808 + k, directed, k, pmin=0.1, pmax=0.4)
+    ref = solver.solve_batch(pairs, directed=directed, timeout_s=60)
+    hb = HostBatch(pairs, directed=directed)
+    out = solver.solve_host(hb, timeout_s=60)
+    assert list(out["size"]) == [r.size for r in ref]
+    assert (out["status"] == 0).all()
+    for i, p in enumerate(pairs):
+        s = int(out["size"][i])
+        g, h = out["g_idx"][i, :s], out["h_idx"][i, :s]
+        assert oracle.verify(p.G.adj, p.H.adj, g, h, p.G.labels, p.H.labels) == 1
