@@ -1063,14 +1063,11 @@ __global__ void __launch_bounds__(256, (GS == 32 ? MCS_SEARCH_MINB : MCS_GROUP_M
                     }
                     pos += __popc(mk);
                 };
-                // Whole-warp searchers write the child's classes only once it
-                // survives Eq. 1, in a second pass over the classes kept in
-                // registers.  Narrow searchers write them in the same pass, before
-                // Eq. 1 decides (a pruned child's writes land in free stack space
-                // above the level): one pass is shorter, and the searchers that
-                // share a warp are more often on the same instruction.
-                constexpr bool SPEC = GS < 32;
-                W Ls[2], Rs[2];                                    // GS == 32: the two slots
+                // The child's classes are written only once it survives Eq. 1, in
+                // a second pass over the classes kept in registers (both slots of
+                // a whole warp, slot 0 of a narrow searcher; further slots of a
+                // narrow searcher are re-read).
+                W Ls[2], Rs[2];
     #pragma unroll (GS == 32 ? 2 : 1)
                 for (int sl = 0; sl < kMaxN / GS; ++sl) {
                     const int i0 = sl * GS;
@@ -1083,6 +1080,7 @@ __global__ void __launch_bounds__(256, (GS == 32 ? MCS_SEARCH_MINB : MCS_GROUP_M
                         R = (W)c.y & ~ub;
                     }
                     if constexpr (GS == 32) { Ls[sl] = L; Rs[sl] = R; }
+                    else if (sl == 0) { Ls[0] = L; Rs[0] = R; }
                     if (DIR) {
                         const W la = L & gA, lb = L & gB, ra = R & hA, rb = R & hB;
                         const W lp[4] = {(W)(L & ~(la | lb)), (W)(la & ~lb), (W)(lb & ~la), (W)(la & lb)};
@@ -1094,7 +1092,6 @@ __global__ void __launch_bounds__(256, (GS == 32 ? MCS_SEARCH_MINB : MCS_GROUP_M
                             sum += m;
                             const unsigned key = m ? (((unsigned)max(a, b) << 6) | (unsigned)Word<W>::low(lp[k])) : kKeyNone;
                             if (key < best) { best = key; bestR = rp[k]; }
-                            if (SPEC) emit(lp[k], rp[k], m != 0);
                         }
                     } else {
                         const W l1 = L & gB, r1 = R & hB, l0 = L ^ l1, r0 = R ^ r1;
@@ -1105,13 +1102,8 @@ __global__ void __launch_bounds__(256, (GS == 32 ? MCS_SEARCH_MINB : MCS_GROUP_M
                         const unsigned k0 = m0 ? (((unsigned)max(a0, b0) << 6) | (unsigned)Word<W>::low(l0)) : kKeyNone;
                         if (k1 < best) { best = k1; bestR = r1; }
                         if (k0 < best) { best = k0; bestR = r0; }
-                        if (SPEC) {
-                            emit(l1, r1, m1 != 0);
-                            emit(l0, r0, m0 != 0);
-                        }
                     }
                 }
-                if (SPEC) g.sync();     // the child's writes land before a sibling rewrites the space
                 sum = g.add(sum);
                 // incumbent (Algorithm 1): |M u {(v,u)}| beats the best so far
                 if (dm > inc) {
@@ -1129,23 +1121,32 @@ __global__ void __launch_bounds__(256, (GS == 32 ? MCS_SEARCH_MINB : MCS_GROUP_M
                 const unsigned kmin = g.umin(best);
                 const unsigned win = g.ballot(best == kmin);
                 const u64 cR = g.shfl64((u64)bestR, __ffs(win) - 1);
-                if constexpr (GS == 32) {
-                    // descend: compact the child's classes onto the stack
-    #pragma unroll
-                    for (int sl = 0; sl < 2; ++sl) {
-                        if (sl * 32 >= t.C) break;
-                        const W L = Ls[sl], R = Rs[sl];
-                        if (DIR) {
-                            const W la = L & gA, lb = L & gB, ra = R & hA, rb = R & hB;
-                            const W lp[4] = {(W)(L & ~(la | lb)), (W)(la & ~lb), (W)(lb & ~la), (W)(la & lb)};
-                            const W rp[4] = {(W)(R & ~(ra | rb)), (W)(ra & ~rb), (W)(rb & ~ra), (W)(ra & rb)};
-    #pragma unroll
-                            for (int k = 0; k < 4; ++k) emit(lp[k], rp[k], lp[k] && rp[k]);
-                        } else {
-                            const W l1 = L & gB, r1 = R & hB, l0 = L ^ l1, r0 = R ^ r1;
-                            emit(l1, r1, l1 && r1);
-                            emit(l0, r0, l0 && r0);
+                // descend: compact the child's classes onto the stack
+#pragma unroll (GS == 32 ? 2 : 1)
+                for (int sl = 0; sl < kMaxN / GS; ++sl) {
+                    if (sl * GS >= t.C) break;
+                    W L = 0, R = 0;
+                    if (GS == 32 || sl == 0) {
+                        L = Ls[GS == 32 ? sl : 0];
+                        R = Rs[GS == 32 ? sl : 0];
+                    } else {
+                        const int i = sl * GS + g.q;
+                        if (i < t.C) {
+                            const ulonglong2 c = *st.at(t.base + i);
+                            L = (W)c.x & ~vb;
+                            R = (W)c.y & ~ub;
                         }
+                    }
+                    if (DIR) {
+                        const W la = L & gA, lb = L & gB, ra = R & hA, rb = R & hB;
+                        const W lp[4] = {(W)(L & ~(la | lb)), (W)(la & ~lb), (W)(lb & ~la), (W)(la & lb)};
+                        const W rp[4] = {(W)(R & ~(ra | rb)), (W)(ra & ~rb), (W)(rb & ~ra), (W)(ra & rb)};
+#pragma unroll
+                        for (int k = 0; k < 4; ++k) emit(lp[k], rp[k], lp[k] && rp[k]);
+                    } else {
+                        const W l1 = L & gB, r1 = R & hB, l0 = L ^ l1, r0 = R ^ r1;
+                        emit(l1, r1, l1 && r1);
+                        emit(l0, r0, l0 && r0);
                     }
                 }
                 if (pos > st.S) spilled += 1;
