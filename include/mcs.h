@@ -239,11 +239,12 @@ int mcs_set_steal(mcs_ctx* ctx, int poll_nodes, int keep_quarters);
 
 /* Lanes per depth-first searcher of mcs_solve_batch[_device] (Section III's
  * data-parallel node step, Algorithm 1): 32 runs one search per warp with the
- * label classes of a node spread over the lanes; 16 or 8 runs two or four
- * independent searches per warp, each over its own lane group, for instances
- * whose nodes hold few classes.  Results are the same for every value (the
- * node counts of a multi-searcher solve vary as with any work stealing).
- * Any other value: MCS_ERR_ARG.  Serving (mcs_submit) always uses 32. */
+ * label classes of a node spread over the lanes; 16, 8, 4 or 2 run two to
+ * sixteen independent searches per warp, each over its own lane group, for
+ * instances whose nodes hold few classes (default 8).  Results are the same
+ * for every value (the node counts of a multi-searcher solve vary as with any
+ * work stealing).  Any other value: MCS_ERR_ARG.  Serving (mcs_submit) always
+ * uses 32. */
 int mcs_set_search_group(mcs_ctx* ctx, int lanes);
 
 /* Statistics of the last solve on this context: out[0] search-kernel

@@ -179,7 +179,7 @@ class Solver:
     # -- configuration ----------------------------------------------------
     def set_launch(self, warps_per_block=0, blocks_per_sm=0, smem_stack_entries=0, search_group=None):
         """0 keeps a value, -1 restores its default; search_group (lanes per
-        searcher: 32, 16, 8 or 4) is left alone when None."""
+        searcher: 32, 16, 8, 4 or 2) is left alone when None."""
         rc = self.lib.mcs_set_launch(self.ctx, warps_per_block, blocks_per_sm, smem_stack_entries)
         if rc:
             raise ValueError(self.strerror(rc))
@@ -205,7 +205,7 @@ class Solver:
             raise ValueError(self.strerror(rc))
 
     def set_search_group(self, lanes: int):
-        """Lanes per searcher: 32 (one search per warp), 16 or 8."""
+        """Lanes per searcher: 32 (one search per warp), 16, 8, 4 or 2."""
         rc = self.lib.mcs_set_search_group(self.ctx, int(lanes))
         if rc:
             raise ValueError(self.strerror(rc))

@@ -4,8 +4,8 @@
 
 For each workload it times device-resident batch solves (inputs already in
 HBM, CUDA events on the launching stream, best of `--reps`) over a grid of
-launch shapes -- lanes per searcher (32: one search per warp; 16, 8, 4: two,
-four or eight per warp), warps per block, class-stack entries kept in shared
+launch shapes -- lanes per searcher (32: one search per warp; 16, 8, 4, 2:
+two to sixteen per warp), warps per block, class-stack entries kept in shared
 memory per whole-warp searcher (which sets shared memory per warp and so the
 resident warps), and blocks per SM -- then, on the fastest shape, the
 work-sharing poll interval and the share a donor keeps, and records the
@@ -29,7 +29,7 @@ SHAPES = ([dict(search_group=32, warps_per_block=w, smem_stack_entries=s, blocks
            for w, s in itertools.product((4,), (128, 256))]
           # narrow searchers keep class stacks in global memory: no shared-memory size to sweep
           + [dict(search_group=g, warps_per_block=w, smem_stack_entries=-1, blocks_per_sm=0)
-             for g, w in ((16, 4), (8, 2), (8, 4), (8, 8), (4, 4))])
+             for g, w in ((16, 4), (8, 2), (8, 4), (8, 8), (4, 2), (4, 4), (4, 8), (2, 4))])
 KEYS = ("search_group", "warps_per_block", "smem_stack_entries", "blocks_per_sm")
 # second stage, on the fastest shape: work-sharing poll interval x the donor's kept share
 STEAL = [dict(poll_nodes=pn, steal_keep_quarters=kq) for pn, kq in itertools.product((8, 16, 32), (1, 2, 3))]

@@ -102,8 +102,7 @@ int ensure_ring(mcs_ctx* c, int warps, int npairs) {
         CK(cudaMalloc((void**)&c->qseq, sizeof(u64) * (size_t)q));
         c->qcap = q;
     }
-    const int S = stack_entries(c, c->group_lanes);
-    size_t per = kStackMax > S ? (size_t)(kStackMax - S) : 0;
+    const size_t per = gstack_entries(stack_entries(c, c->group_lanes), c->group_lanes);
     size_t need = per * (size_t)warps;
     if (need > c->gstack_entries || !c->gstack) {
         cudaFree(c->gstack);
@@ -285,7 +284,7 @@ int mcs_set_steal(mcs_ctx* c, int poll_nodes, int keep_quarters) {
 }
 
 int mcs_set_search_group(mcs_ctx* c, int lanes) {
-    if (!c || (lanes != 4 && lanes != 8 && lanes != 16 && lanes != 32)) return MCS_ERR_ARG;
+    if (!c || (lanes != 2 && lanes != 4 && lanes != 8 && lanes != 16 && lanes != 32)) return MCS_ERR_ARG;
     c->group_lanes = lanes;
     return 0;
 }

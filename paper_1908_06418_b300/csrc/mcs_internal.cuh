@@ -182,8 +182,19 @@ constexpr int kSmCycOff = 1184;                  // busy, idle cycle counters, c
 constexpr int kSmClsOff = 1216;                  // 16-byte aligned
 static_assert(kSmClsOff % 16 == 0 && kSmAdjBytes % 16 == 0, "class cache must be 16-byte aligned");
 
+// Searchers of at most 4 lanes (8 or more per warp, up to 256 per SM) keep
+// their level arrays in their global region as well, after the class stack.
+__host__ __device__ constexpr bool levels_in_smem(int gs) { return gs >= 8; }
+constexpr int kLvEntries = 80;                   // 1,280 B >= kSmClsOff: level arrays in global
+
 inline int warp_smem_bytes(int stack_entries, int gs = 32) {
-    return sm_adj_bytes(gs) + kSmClsOff + 16 * stack_entries;
+    return sm_adj_bytes(gs) + (levels_in_smem(gs) ? kSmClsOff : 0) + 16 * stack_entries;
+}
+// 16-byte entries of a searcher's global region: class-stack overflow, plus
+// the level arrays of searchers that keep none in shared memory.
+inline size_t gstack_entries(int stack_entries, int gs) {
+    return (size_t)(kStackMax > stack_entries ? kStackMax - stack_entries : 0) +
+           (levels_in_smem(gs) ? 0 : (size_t)kLvEntries);
 }
 
 }  // namespace mcsk
@@ -205,7 +216,7 @@ struct mcs_ctx {
     int blocks_per_sm = 0;        // 0: as many as fit
     int smem_stack = 0;           // class entries per searcher in shared memory (0: default)
     int max_warps = 0;            // 0: every launched searcher
-    int group_lanes = 8;          // lanes per searcher of batch solves: 32, 16, 8 or 4
+    int group_lanes = 8;          // lanes per searcher of batch solves: 32, 16, 8, 4 or 2
     int poll_nodes = 16;          // work-sharing poll interval (nodes, power of two)
     int steal_keep_q4 = 2;        // quarters of a donated level's candidates the donor keeps
     // device arenas
@@ -252,7 +263,7 @@ inline int stack_entries(const mcs_ctx* c, int gs) {
 // kernels.cu entry points used by the host library
 namespace mcsk {
 cudaError_t launch_pack(const PackParams& p, cudaStream_t s);
-// gs: lanes per searcher (32: one search per warp; 16, 8 or 4: two, four or eight)
+// gs: lanes per searcher (32: one search per warp; 16, 8, 4 or 2: two to sixteen)
 cudaError_t launch_search(const SearchParams& p, int blocks, int warps_per_block,
                           bool directed, bool learned, cudaStream_t s, int gs = 32);
 int search_max_blocks_per_sm(int warps_per_block, int smem_per_block, bool directed, bool learned,

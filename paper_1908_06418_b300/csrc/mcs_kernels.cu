@@ -766,7 +766,7 @@ __device__ __forceinline__ bool donate(const SearchParams& P, int pair, int d0, 
 
 template <bool DIR, bool LEARNED, bool SERVE, int GS, bool NARROW>
 __global__ void __launch_bounds__(256, (GS == 32 ? MCS_SEARCH_MINB : MCS_GROUP_MINB)) search_kernel(SearchParams P) {
-    static_assert(GS == 4 || GS == 8 || GS == 16 || GS == 32, "searcher group size");
+    static_assert(GS == 2 || GS == 4 || GS == 8 || GS == 16 || GS == 32, "searcher group size");
     static_assert(!SERVE || GS == 32, "serve mode packs requests with whole warps");
     extern __shared__ __align__(16) unsigned char smem[];
     constexpr int GPW = 32 / GS;                       // searchers per warp
@@ -791,7 +791,16 @@ __global__ void __launch_bounds__(256, (GS == 32 ? MCS_SEARCH_MINB : MCS_GROUP_M
     StackT<STACK_SM> st;
     st.sm = w.cls;
     st.S = STACK_SM ? P.stack_smem : 0;
-    st.gm = P.gstack + (size_t)sid * (size_t)(kStackMax > st.S ? kStackMax - st.S : 0);
+    const size_t gper = (size_t)(kStackMax > st.S ? kStackMax - st.S : 0) + (levels_in_smem(GS) ? 0 : kLvEntries);
+    st.gm = P.gstack + (size_t)sid * gper;
+    if constexpr (!levels_in_smem(GS)) {
+        // level arrays (and cycle counters) after the class stack, in global memory
+        lv = reinterpret_cast<unsigned char*>(st.gm + kStackMax);
+        w.rrem = (u64*)(lv + kSmRremOff);
+        w.info = (u64*)(lv + kSmInfoOff);
+        w.Mg = lv + kSmMOff;
+        w.Mh = lv + kSmMOff + kMaxN;
+    }
 #ifdef MCS_DEBUG_BOUNDS
     st.ctl = P.ctl;
 #endif
@@ -1224,6 +1233,7 @@ static cudaError_t launch_t(const SearchParams& p, int blocks, int wpb, cudaStre
 
 template <bool DIR, bool LEARNED, bool NARROW>
 static cudaError_t launch_g(const SearchParams& p, int blocks, int wpb, int gs, cudaStream_t s) {
+    if (gs == 2) return launch_t<DIR, LEARNED, false, 2, NARROW>(p, blocks, wpb, s);
     if (gs == 4) return launch_t<DIR, LEARNED, false, 4, NARROW>(p, blocks, wpb, s);
     if (gs == 8) return launch_t<DIR, LEARNED, false, 8, NARROW>(p, blocks, wpb, s);
     if (gs == 16) return launch_t<DIR, LEARNED, false, 16, NARROW>(p, blocks, wpb, s);
@@ -1257,6 +1267,7 @@ static int occupancy_t(int wpb, int smem) {
 
 template <bool DIR, bool LEARNED, bool NARROW>
 static int occupancy_g(int wpb, int smem, int gs) {
+    if (gs == 2) return occupancy_t<DIR, LEARNED, false, 2, NARROW>(wpb, smem);
     if (gs == 4) return occupancy_t<DIR, LEARNED, false, 4, NARROW>(wpb, smem);
     if (gs == 8) return occupancy_t<DIR, LEARNED, false, 8, NARROW>(wpb, smem);
     if (gs == 16) return occupancy_t<DIR, LEARNED, false, 16, NARROW>(wpb, smem);

@@ -74,7 +74,7 @@ def test_single_warp_traversal_equals_oracle(solver, group, directed, k):
         solver.set_search_group(8)
 
 
-@pytest.mark.parametrize("group", [32, 8])
+@pytest.mark.parametrize("group", [32, 8, 2])
 @pytest.mark.parametrize("directed,k", [(False, 12), (True, 8), (True, 12)])
 def test_single_searcher_wide_words_equals_oracle(solver, group, directed, k):
     """Graphs of 33..40 vertices take the 64-bit node step (the pairs above

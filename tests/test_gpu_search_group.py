@@ -1,4 +1,4 @@
-"""Searchers narrower than a warp (16, 8 or 4 lanes: two, four or eight independent
+"""Searchers narrower than a warp (16, 8, 4 or 2 lanes: two to sixteen independent
 depth-first searches per warp) against the CPU oracle: sizes bit-exact,
 mappings verified, and a lone searcher walks the oracle's search tree."""
 import numpy as np
@@ -41,7 +41,7 @@ def group(solver, request):
     solver.set_search_group(32)
 
 
-@pytest.mark.parametrize("group", [16, 8, 4], indirect=True)
+@pytest.mark.parametrize("group", [16, 8, 4, 2], indirect=True)
 @pytest.mark.parametrize("directed,k", [(False, 0), (True, 0), (False, 3)])
 def test_lone_group_traversal_equals_oracle(solver, group, directed, k):
     from paper_1908_06418_b300 import MCS_NO_LEVEL_PRUNE
@@ -58,7 +58,7 @@ def test_lone_group_traversal_equals_oracle(solver, group, directed, k):
         solver.set_max_warps(0)
 
 
-@pytest.mark.parametrize("group", [16, 8, 4], indirect=True)
+@pytest.mark.parametrize("group", [16, 8, 4, 2], indirect=True)
 @pytest.mark.parametrize("directed,k", [(False, 0), (True, 0), (False, 4), (True, 3)])
 def test_group_batch_parity(solver, group, directed, k):
     pairs = _rand_pairs(300, 1, 24, 2718 + k + (50 if directed else 0), directed, k)
@@ -69,7 +69,7 @@ def test_group_batch_parity(solver, group, directed, k):
         assert oracle.verify(p.G.adj, p.H.adj, r.g_idx, r.h_idx, p.G.labels, p.H.labels) == 1, i
 
 
-@pytest.mark.parametrize("group", [8, 4], indirect=True)
+@pytest.mark.parametrize("group", [8, 4, 2], indirect=True)
 def test_group_ragged_sizes_up_to_64(solver, group):
     """Up to 64 classes per node: several slots of an 8-lane group, a ragged last slot."""
     pairs = [synth.Pair(synth.Graph(synth.er_undirected(n, 0.5, synth.rng_for(77, n, 0)),
@@ -84,7 +84,7 @@ def test_group_ragged_sizes_up_to_64(solver, group):
         assert oracle.verify(p.G.adj, p.H.adj, r.g_idx, r.h_idx, p.G.labels, p.H.labels) == 1
 
 
-@pytest.mark.parametrize("group", [16, 8, 4], indirect=True)
+@pytest.mark.parametrize("group", [16, 8, 4, 2], indirect=True)
 def test_group_learned_order_stays_exact(solver, group):
     from oracle import mlp
     from paper_1908_06418_b300 import MCS_ORDER_LEARNED
@@ -95,7 +95,7 @@ def test_group_learned_order_stays_exact(solver, group):
     assert [r.size for r in res] == ref and all(r.status == 0 for r in res)
 
 
-@pytest.mark.parametrize("group", [8, 4], indirect=True)
+@pytest.mark.parametrize("group", [8, 4, 2], indirect=True)
 def test_group_graph_replay(solver, group):
     import torch
     from paper_1908_06418_b300 import DeviceBatch, MCS_GRAPH_REPLAY
@@ -117,7 +117,7 @@ def test_group_graph_replay(solver, group):
 
 
 def test_invalid_group_is_rejected(solver):
-    for bad in (0, 2, 12, 64, -8):
+    for bad in (0, 1, 3, 12, 64, -8):
         with pytest.raises(ValueError):
             solver.set_search_group(bad)
     p = synth.config1_pair()
