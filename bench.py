@@ -52,9 +52,8 @@ def workload(name: str):
             workload="hard single pairs: 96 directed G(36,p), p in {0.05,0.1,0.3} x 32 seeds "
                      "+ 6x6 grid pair with 10% edges deleted", pairs=97)
     if name == "c2s":     # small case of the same kernel for profiler captures
-        return synth.config2_pairs()[64:72], dict(
-            workload="8 directed G(36,0.3) pairs (hard single pairs, first 8 seeds of p=0.3)",
-            pairs=8)
+        return synth.config2_pairs()[0:96:4], dict(
+            workload="24 directed G(36,p) pairs (every 4th of the hard single pairs)", pairs=24)
     if name == "c3":
         return synth.config3_pairs(), dict(
             workload="batched: 4096 undirected pairs, n U{10..40}, p U[0.05,0.4], 4 labels",
@@ -65,9 +64,10 @@ def workload(name: str):
 
 
 def golden_sizes(name: str):
-    shift = 0
+    """Stored oracle sizes by position in the workload (c2s: every 4th c2 pair)."""
+    stride = 1
     if name == "c2s":
-        name, shift = "c2", 64
+        name, stride = "c2", 4
     path = os.path.join(ROOT, "tests", "golden", f"{name}_oracle.jsonl")
     if not os.path.exists(path):
         return {}
@@ -75,8 +75,10 @@ def golden_sizes(name: str):
     for line in open(path):
         if line.strip():
             d = json.loads(line)
-            if d["idx"] - shift >= 0:
-                out[d["idx"] - shift] = (d["size"], d["complete"])
+            if stride == 1:
+                out[d["idx"]] = (d["size"], d["complete"])
+            elif d["idx"] % stride == 0 and d["idx"] < 96:        # the directed pairs
+                out[d["idx"] // stride] = (d["size"], d["complete"])
     return out
 
 
@@ -177,6 +179,50 @@ def apply_shape(solver, sh):
         solver.reset_launch()
 
 
+def single_instance_vs_batch(solver, pairs, a):
+    """The plain single-instance form on the same GPU: a bounded sample of the
+    workload solved one pair per mcs_solve call (whole-warp searchers, the
+    tuned shape for single pairs), in FIFO order from t = 0, against the same
+    sample as one mcs_solve_batch call with the workload's tuned shape.
+    Both go through the host C ABI (copies included).  Latency of a pair =
+    time from t = 0 to its result."""
+    import torch
+    from paper_1908_06418_b300 import MCS_OK, MCS_DIRECTED, HostBatch
+    n = len(pairs)
+    k = {"c2": 24, "c2s": 8, "c3": 256, "c1": 1}.get(a.workload, min(n, 64))
+    idx = list(range(0, n, max(1, n // k)))[:k]
+    sample = [pairs[i] for i in idx]
+    # one pair per call
+    solver.set_launch(4, -1, 256, search_group=32)
+    solver.set_steal(-1, -1)
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    done, ok1 = [], 0
+    for p in sample:
+        r = solver.solve(p.G.adj, p.H.adj, p.G.labels, p.H.labels, directed=bool(p.directed),
+                         timeout_s=a.timeout)
+        done.append((time.perf_counter() - t0) * 1e3)
+        ok1 += int(r.status == MCS_OK)
+    t_single = done[-1] / 1e3
+    # the same sample as one batch per flag group
+    t0 = time.perf_counter()
+    ok2 = 0
+    for directed in (True, False):
+        sub = [p for p in sample if bool(p.directed) == directed]
+        if not sub:
+            continue
+        solver.apply_tuned(sub, directed=directed) or solver.reset_launch()
+        out = solver.solve_host(HostBatch(sub, directed=directed), timeout_s=a.timeout)
+        ok2 += int((out["status"] == MCS_OK).sum())
+    t_batch = time.perf_counter() - t0
+    solver.reset_launch()
+    return {"sample": f"{len(sample)} of {n} pairs (every {max(1, n // k)}th)",
+            "single_pairs_s": ok1 / t_single, "single_p50_ms": float(np.percentile(done, 50)),
+            "single_p99_ms": float(np.percentile(done, 99)),
+            "batch_pairs_s": ok2 / t_batch, "batch_p99_ms": t_batch * 1e3,
+            "note": "latency from t = 0: FIFO one pair per call vs all pairs in one batch call"}
+
+
 def run_reference(a):
     rank = int(os.environ.get("RANK", "0"))
     if rank != 0:
@@ -221,6 +267,8 @@ def main():
     ap.add_argument("--timeout", type=float, default=600.0)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-tune", action="store_true", help="ignore the autotuner cache")
+    ap.add_argument("--no-single", action="store_true",
+                    help="skip the single-instance (one pair per call) comparison")
     ap.add_argument("--requests", type=int, default=100000, help="c5: requests in the stream")
     ap.add_argument("--rate-frac", type=float, default=0.5, help="c5: arrival rate / saturated rate")
     ap.add_argument("--single-sample", type=int, default=2000, help="c5: single-instance baseline sample")
@@ -438,6 +486,8 @@ def main():
             "e2e": {"value": e2e_value, "unit": UNIT, "h2d_bytes_per_step": int(h2d),
                     "d2h_bytes_per_step": int(d2h)},
             "roofline": roof, "clocks": csum}
+    if rank == 0 and not a.no_single:
+        line["single_instance"] = single_instance_vs_batch(solver, pairs, a)
     if rank == 0 and not a.no_cpu_baseline:
         cb = oracle_sample(a.workload, 8 if a.workload.startswith("c2") else 64,
                            25.0 if a.workload.startswith("c2") else 2.0)
