@@ -60,6 +60,11 @@ def workload(name: str):
             pairs=4096)
     if name == "c1":
         return [synth.config1_pair()], dict(workload="single pair G(20,0.3) x G(20,0.3)", pairs=1)
+    if name == "c4":
+        return synth.config4_pairs(2048), dict(
+            workload="learned ordering: 2048 bounded-valence pairs (random 3-/4-regular and perturbed "
+                     "2D meshes, n U{40..64}), 1 s per pair, order network data/order_mlp_bvg.npy",
+            pairs=2048)
     raise SystemExit(f"unknown workload {name}")
 
 
@@ -179,17 +184,18 @@ def apply_shape(solver, sh):
         solver.reset_launch()
 
 
-def single_instance_vs_batch(solver, pairs, a):
+def single_instance_vs_batch(solver, pairs, a, batch_flags=0):
     """The plain single-instance form on the same GPU: a bounded sample of the
     workload solved one pair per mcs_solve call (whole-warp searchers, the
-    tuned shape for single pairs), in FIFO order from t = 0, against the same
-    sample as one mcs_solve_batch call with the workload's tuned shape.
+    tuned shape for single pairs, degree order), in FIFO order from t = 0,
+    against the same sample as one mcs_solve_batch call with the workload's
+    tuned shape (and batch_flags, e.g. the learned order).
     Both go through the host C ABI (copies included).  Latency of a pair =
     time from t = 0 to its result."""
     import torch
     from paper_1908_06418_b300 import MCS_OK, MCS_DIRECTED, HostBatch
     n = len(pairs)
-    k = {"c2": 24, "c2s": 8, "c3": 256, "c1": 1}.get(a.workload, min(n, 64))
+    k = {"c2": 24, "c2s": 8, "c3": 256, "c1": 1, "c4": 8}.get(a.workload, min(n, 64))
     idx = list(range(0, n, max(1, n // k)))[:k]
     sample = [pairs[i] for i in idx]
     # one pair per call
@@ -212,7 +218,7 @@ def single_instance_vs_batch(solver, pairs, a):
         if not sub:
             continue
         solver.apply_tuned(sub, directed=directed) or solver.reset_launch()
-        out = solver.solve_host(HostBatch(sub, directed=directed), timeout_s=a.timeout)
+        out = solver.solve_host(HostBatch(sub, directed=directed), flags=batch_flags, timeout_s=a.timeout)
         ok2 += int((out["status"] == MCS_OK).sum())
     t_batch = time.perf_counter() - t0
     solver.reset_launch()
@@ -229,7 +235,7 @@ def run_reference(a):
         return
     name = a.workload
     n_sample = 8 if name.startswith("c2") else 64
-    budget = 25.0 if name.startswith("c2") else 2.0
+    budget = a.timeout if name == "c4" else (25.0 if name.startswith("c2") else 2.0)
     for w in range(a.warmup):
         oracle_sample(name, 2, 0.5, offset=w)
     tot_solved = tot_wall = tot_nodes = 0
@@ -264,7 +270,8 @@ def main():
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--workload", default="c2")
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
-    ap.add_argument("--timeout", type=float, default=600.0)
+    ap.add_argument("--timeout", type=float, default=None,
+                    help="per-pair limit in seconds (default 600; c4: 1)")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-tune", action="store_true", help="ignore the autotuner cache")
     ap.add_argument("--no-single", action="store_true",
@@ -273,6 +280,8 @@ def main():
     ap.add_argument("--rate-frac", type=float, default=0.5, help="c5: arrival rate / saturated rate")
     ap.add_argument("--single-sample", type=int, default=2000, help="c5: single-instance baseline sample")
     a = ap.parse_args()
+    if a.timeout is None:
+        a.timeout = 1.0 if a.workload == "c4" else 600.0
     if a.impl == "reference":
         run_reference(a)
         return
@@ -289,12 +298,16 @@ def main():
     if world > 1:
         import torch.distributed as dist
         dist.init_process_group("nccl")
-    from paper_1908_06418_b300 import Solver, pack_host, MCS_DIRECTED, MCS_OK, MCS_WORD32
+    from paper_1908_06418_b300 import Solver, pack_host, MCS_DIRECTED, MCS_OK, MCS_WORD32, MCS_ORDER_LEARNED
 
     pairs, cfg = workload(a.workload)
     gold = golden_sizes(a.workload)
     dev = torch.device("cuda", local)
     solver = Solver(local)
+    learned = a.workload == "c4"
+    if learned:       # the candidate order of the trained network (exactness unchanged)
+        solver.set_order_model(np.load(os.path.join(ROOT, "paper_1908_06418_b300", "data",
+                                                    "order_mlp_bvg.npy")).astype(np.float32))
     # a dedicated stream: the library's device entry point runs on the stream
     # it is given, and CUDA events recorded on that same stream time it
     stream = torch.cuda.Stream(dev)
@@ -308,7 +321,8 @@ def main():
             continue
         narrow = all(max(pairs[i].G.n, pairs[i].H.n) <= 32 for i in idx)
         h = pack_host([pairs[i] for i in idx])
-        g = dict(idx=idx, flags=(MCS_DIRECTED if directed else 0) | (MCS_WORD32 if narrow else 0), n=len(idx),
+        g = dict(idx=idx, flags=(MCS_DIRECTED if directed else 0) | (MCS_WORD32 if narrow else 0)
+                 | (MCS_ORDER_LEARNED if learned else 0), n=len(idx),
                  d_n=torch.from_numpy(h["n"]).to(dev),
                  d_adj_off=torch.from_numpy(h["adj_off"]).to(dev),
                  d_adj=torch.from_numpy(h["adj"]).to(dev),
@@ -486,11 +500,34 @@ def main():
             "e2e": {"value": e2e_value, "unit": UNIT, "h2d_bytes_per_step": int(h2d),
                     "d2h_bytes_per_step": int(d2h)},
             "roofline": roof, "clocks": csum}
+    if rank == 0 and learned:
+        # the same batch with the learned order and with the plain degree order
+        def one_pass(flag_clear):
+            torch.cuda.synchronize()
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record(stream)
+            for g in groups:
+                apply_shape(solver, g.get("shape"))
+                solver.solve_batch_device(g["n"], g["d_n"], g["d_adj_off"], g["d_adj"], g["d_lab_off"],
+                                          g["d_labels"], g["size"], g["status"], g["nodes"], g["map"],
+                                          g["usec"], flags=g["flags"] & ~flag_clear, timeout_s=a.timeout,
+                                          stream=stream.cuda_stream)
+            e1.record(stream)
+            torch.cuda.synchronize()
+            st = np.concatenate([g["status"].cpu().numpy() for g in groups])
+            sz = np.concatenate([g["size"].cpu().numpy() for g in groups])
+            nd = sum(int(g["nodes"].sum().item()) for g in groups)
+            return {"ms": e0.elapsed_time(e1), "solved": int((st == MCS_OK).sum()),
+                    "mean_size": float(sz.mean()), "nodes": nd}
+        line["order_comparison"] = {"learned": one_pass(0), "plain": one_pass(MCS_ORDER_LEARNED),
+                                    "note": "one pass each over the whole batch; exact either way, "
+                                            "solved = proven within the per-pair limit"}
     if rank == 0 and not a.no_single:
-        line["single_instance"] = single_instance_vs_batch(solver, pairs, a)
+        line["single_instance"] = single_instance_vs_batch(
+            solver, pairs, a, batch_flags=MCS_ORDER_LEARNED if learned else 0)
     if rank == 0 and not a.no_cpu_baseline:
         cb = oracle_sample(a.workload, 8 if a.workload.startswith("c2") else 64,
-                           25.0 if a.workload.startswith("c2") else 2.0)
+                           a.timeout if a.workload == "c4" else (25.0 if a.workload.startswith("c2") else 2.0))
         line["cpu_baseline"] = {"value": cb["solved"] / cb["wall"], "unit": UNIT, "cores": cb["cores"],
                                 "kind": "oracle", "sample": cb["sample"],
                                 "nodes_per_s": cb["nodes"] / cb["wall"]}
