@@ -278,7 +278,11 @@ def main():
                     help="skip the single-instance (one pair per call) comparison")
     ap.add_argument("--requests", type=int, default=100000, help="c5: requests in the stream")
     ap.add_argument("--rate-frac", type=float, default=0.5, help="c5: arrival rate / saturated rate")
+    ap.add_argument("--rate", type=float, default=0.0, help="c5: absolute arrival rate (requests/s), "
+                                                             "instead of --rate-frac")
     ap.add_argument("--single-sample", type=int, default=2000, help="c5: single-instance baseline sample")
+    ap.add_argument("--serve-lanes", type=int, default=0,
+                    help="c5: lanes per searcher of the server (8, 16 or 32; default: the library's, 32)")
     a = ap.parse_args()
     if a.timeout is None:
         a.timeout = 1.0 if a.workload == "c4" else 600.0
@@ -555,7 +559,9 @@ def run_serving(a):
     t = time.perf_counter()
     res = solver.solve_batch(sat_pairs, timeout_s=1.0)
     sat = len(sat_pairs) / (time.perf_counter() - t)
-    rate = a.rate_frac * sat
+    rate = a.rate if a.rate > 0 else a.rate_frac * sat
+    if a.serve_lanes:
+        solver.set_serve_group(a.serve_lanes)    # before the first submit creates the server
     reqs = list(synth.config5_requests(count=n_req, rate_per_s=rate))
     lat, status = [], []
     out = {}
@@ -584,8 +590,10 @@ def run_serving(a):
         wall = time.perf_counter() - t0
     lat_ms = np.array(lat) * 1e3
     solved = sum(1 for st in status if st == MCS_OK)
-    # plain single-instance baseline: one pair per launch, in arrival order
+    # plain single-instance baseline: one pair per launch, in arrival order,
+    # with the shape that suits single pairs (whole-warp searchers)
     m = min(a.single_sample, n_req)
+    solver.set_launch(4, -1, 256, search_group=32)
     serv = []
     for q in reqs[:m]:
         t = time.perf_counter()
@@ -603,7 +611,8 @@ def run_serving(a):
             "data": "synthetic",
             "config": {"workload": f"Poisson stream of {n_req} requests, n log-uniform [16,56], p U[0.05,0.4], "
                                    f"0-8 labels, 1 s timeout", "rate_per_s": rate,
-                       "rate_frac_of_saturated": a.rate_frac, "saturated_batch_pairs_per_s": sat},
+                       "rate_frac_of_saturated": a.rate_frac, "saturated_batch_pairs_per_s": sat,
+                       "serve_lanes_per_searcher": a.serve_lanes or 32},
             "p50_latency_ms": float(np.percentile(lat_ms, 50)), "p99_latency_ms": float(np.percentile(lat_ms, 99)),
             "timeouts": sum(1 for st in status if st == MCS_TIMEOUT), "requests": len(status),
             "single_instance": {"pairs_per_s": m / sum(serv), "p50_latency_ms": float(np.percentile(lat1, 50)),

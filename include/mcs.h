@@ -243,9 +243,17 @@ int mcs_set_steal(mcs_ctx* ctx, int poll_nodes, int keep_quarters);
  * sixteen independent searches per warp, each over its own lane group, for
  * instances whose nodes hold few classes (default 8).  Results are the same
  * for every value (the node counts of a multi-searcher solve vary as with any
- * work stealing).  Any other value: MCS_ERR_ARG.  Serving (mcs_submit) always
- * uses 32. */
+ * work stealing).  Any other value: MCS_ERR_ARG.  Serving has its own
+ * setting (mcs_set_serve_group). */
 int mcs_set_search_group(mcs_ctx* ctx, int lanes);
+
+/* Lanes per searcher of the server launch behind mcs_submit / mcs_poll:
+ * 32 (default; the best throughput and p50 latency measured on the
+ * config-5 stream), 16 or 8.  The first warp of the server always admits
+ * requests (it copies and packs each one).  Call before the first
+ * mcs_submit on the context: MCS_ERR_UNSUPPORTED afterwards (unless the
+ * value is unchanged); other values: MCS_ERR_ARG. */
+int mcs_set_serve_group(mcs_ctx* ctx, int lanes);
 
 /* Statistics of the last solve on this context: out[0] search-kernel
  * microseconds (for mcs_solve_batch_device: once its stream has passed the

@@ -50,7 +50,8 @@ class _Result(ctypes.Structure):
 
 EXPORTED_SYMBOLS = ["mcs_create", "mcs_destroy", "mcs_solve", "mcs_solve_batch",
                     "mcs_solve_batch_device", "mcs_submit", "mcs_poll", "mcs_set_launch",
-                    "mcs_set_max_warps", "mcs_set_search_group", "mcs_set_steal", "mcs_last_stats", "mcs_bench_popc", "mcs_strerror", "mcs_error_detail",
+                    "mcs_set_max_warps", "mcs_set_search_group", "mcs_set_serve_group", "mcs_set_steal",
+                    "mcs_last_stats", "mcs_bench_popc", "mcs_strerror", "mcs_error_detail",
                     "mcs_solve_batch_noalloc", "mcs_set_order_model", "mcs_get_order_model",
                     "mcs_order_eval", "mcs_order_train"]
 
@@ -92,6 +93,8 @@ def load_library():
     lib.mcs_set_max_warps.restype = ctypes.c_int
     lib.mcs_set_search_group.argtypes = [vp, ctypes.c_int]
     lib.mcs_set_search_group.restype = ctypes.c_int
+    lib.mcs_set_serve_group.argtypes = [vp, ctypes.c_int]
+    lib.mcs_set_serve_group.restype = ctypes.c_int
     lib.mcs_set_steal.argtypes = [vp, ctypes.c_int, ctypes.c_int]
     lib.mcs_set_steal.restype = ctypes.c_int
     lib.mcs_last_stats.argtypes = [vp, ctypes.POINTER(ctypes.c_double), ctypes.c_int]
@@ -191,6 +194,12 @@ class Solver:
         sharing."""
         self.set_launch(-1, -1, -1, search_group=8)
         self.set_steal(-1, -1)
+
+    def set_serve_group(self, lanes: int):
+        """Lanes per searcher of the server (32, 16 or 8); before the first submit."""
+        rc = self.lib.mcs_set_serve_group(self.ctx, int(lanes))
+        if rc:
+            raise ValueError(self.strerror(rc))
 
     def set_steal(self, poll_nodes: int = 0, keep_quarters: int = 0):
         """Work-sharing poll interval (nodes) and the donor's kept share in

@@ -283,6 +283,13 @@ int mcs_set_steal(mcs_ctx* c, int poll_nodes, int keep_quarters) {
     return 0;
 }
 
+int mcs_set_serve_group(mcs_ctx* c, int lanes) {
+    if (!c || (lanes != 8 && lanes != 16 && lanes != 32)) return MCS_ERR_ARG;
+    if (c->serve) return lanes == c->serve_lanes ? 0 : MCS_ERR_UNSUPPORTED;   // the server exists
+    c->serve_lanes = lanes;
+    return 0;
+}
+
 int mcs_set_search_group(mcs_ctx* c, int lanes) {
     if (!c || (lanes != 2 && lanes != 4 && lanes != 8 && lanes != 16 && lanes != 32)) return MCS_ERR_ARG;
     c->group_lanes = lanes;

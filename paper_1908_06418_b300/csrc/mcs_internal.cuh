@@ -38,6 +38,7 @@ struct PairState {
     u64 nodes;
     u64 t_start, deadline; // globaltimer ns
     u64 ticket;            // serve mode: the request's ticket
+    u64 timeout_ns;        // serve mode: the request's limit (from its root's start)
 };
 
 // A unit of work: one level of a pair's search tree (a node, its classes,
@@ -217,6 +218,7 @@ struct mcs_ctx {
     int smem_stack = 0;           // class entries per searcher in shared memory (0: default)
     int max_warps = 0;            // 0: every launched searcher
     int group_lanes = 8;          // lanes per searcher of batch solves: 32, 16, 8, 4 or 2
+    int serve_lanes = 32;         // lanes per searcher of the server launch: 32, 16 or 8
     int poll_nodes = 16;          // work-sharing poll interval (nodes, power of two)
     int steal_keep_q4 = 2;        // quarters of a donated level's candidates the donor keeps
     // device arenas
@@ -268,7 +270,7 @@ cudaError_t launch_search(const SearchParams& p, int blocks, int warps_per_block
                           bool directed, bool learned, cudaStream_t s, int gs = 32);
 int search_max_blocks_per_sm(int warps_per_block, int smem_per_block, bool directed, bool learned,
                              int gs = 32, bool narrow = false);
-int serve_max_blocks_per_sm(int warps_per_block, int smem_per_block);
+int serve_max_blocks_per_sm(int warps_per_block, int smem_per_block, int gs);
 cudaError_t launch_popc_bench(unsigned long long* out, int blocks, int iters, cudaStream_t s);
 cudaError_t launch_serve_init(Control* ctl, u64* qseq, uint32_t qcap, int32_t* in_flight, cudaStream_t s);
 }

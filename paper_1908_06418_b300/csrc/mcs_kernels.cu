@@ -346,9 +346,12 @@ struct WarpSmem {
 
 // An adjacency row: shared-memory copy, or the packed pair in global memory
 // (read-only for the kernel's lifetime, so through the non-coherent cache).
-template <bool SM>
+// In serve mode (COHERENT) slots are repacked while the kernel runs, so rows
+// read in place go through L2.
+template <bool SM, bool COHERENT = false>
 __device__ __forceinline__ u64 adj_row(const u64* rows, int i) {
     if constexpr (SM) return rows[i];
+    else if constexpr (COHERENT) return __ldcg(rows + i);
     else return __ldg(rows + i);
 }
 
@@ -479,28 +482,29 @@ __device__ void post_exit_tokens(const SearchParams& P, int count, const Grp<GS>
     if (!g.all(ok) && g.q == 0) atomicCAS(&P.ctl->error, 0, MCS_ERR_DEVICE_STALL);
 }
 
-// Serve mode (whole-warp searchers only): the result record in mapped host
-// memory, map built in shared scratch (64 int16), then a system-scope fence
-// and the done ticket.
-__device__ void finalize_served(const SearchParams& P, int pair, int status, int k, int lane,
+// Serve mode: the result record in mapped host memory, map built in the
+// searcher's shared scratch (64 int16), then a system-scope fence and the
+// done ticket.
+template <int GS>
+__device__ void finalize_served(const SearchParams& P, int pair, int status, int k, const Grp<GS>& g,
                                 int16_t* smap) {
     PairState& ps = P.state[pair];
     const PairGraph& pg = P.graphs[pair];
-    for (int i = lane; i < kMaxN; i += 32) smap[i] = -1;
-    __syncwarp();
+    for (int i = g.q; i < kMaxN; i += GS) smap[i] = -1;
+    g.sync();
     if (status == MCS_OK || status == MCS_TIMEOUT) {
         const uint16_t* slot = P.best + ((size_t)pair * kLevels + k) * kMaxN;
-        for (int i = lane; i < k; i += 32) {
+        for (int i = g.q; i < k; i += GS) {
             uint16_t e = vload(slot + i);
             if (!DBG_OK(P.ctl, (e >> 8) < kMaxN && (e & 0xff) < kMaxN, 8, e)) continue;
             smap[__ldcg(&pg.permG[e >> 8])] = (int16_t)__ldcg(&pg.permH[e & 0xff]);
         }
     }
-    __syncwarp();
+    g.sync();
     ServeRes* r = P.sv.res + pair;
-    for (int i = lane; i < kMaxN; i += 32) r->map[i] = smap[i];
+    for (int i = g.q; i < kMaxN; i += GS) r->map[i] = smap[i];
     u64 ticket = 0;
-    if (lane == 0) {
+    if (g.q == 0) {
         const u64 now = gtimer(), t0 = vload(&ps.t_start);
         ticket = vload(&ps.ticket);
         r->size = k;
@@ -508,16 +512,16 @@ __device__ void finalize_served(const SearchParams& P, int pair, int status, int
         r->nodes = vload(&ps.nodes);
         r->usec = t0 ? (float)((now - t0) * 1e-3) : 0.f;
     }
-    __syncwarp();
+    g.sync();
     __threadfence_system();
-    if (lane == 0) {
+    if (g.q == 0) {
         *(volatile u64*)&r->done = ticket;
         ps.status = status;
         __threadfence();
         atomicSub(P.sv.in_flight, 1);
         atomicMax(&P.ctl->last_progress, gtimer());
     }
-    __syncwarp();
+    g.sync();
 }
 
 // Finish the pair: write size, status, nodes and the mapping (original numbers).
@@ -539,7 +543,7 @@ __device__ void finalize_pair(const SearchParams& P, int pair, const Grp<GS>& g,
     if (status == MCS_PENDING) {
         if (!DBG_OK(P.ctl, k >= 0 && k < kLevels, 7, k)) k = 0;
         status = ab ? MCS_TIMEOUT : MCS_OK;
-        if (SERVE) { finalize_served(P, pair, status, k, g.q, smap); return; }
+        if constexpr (SERVE) { finalize_served<GS>(P, pair, status, k, g, smap); return; }
         if (P.out_map) {
             const uint16_t* slot = P.best + ((size_t)pair * kLevels + k) * kMaxN;
             for (int i = g.q; i < k; i += GS) {
@@ -551,7 +555,7 @@ __device__ void finalize_pair(const SearchParams& P, int pair, const Grp<GS>& g,
         }
     } else {
         k = 0;
-        if (SERVE) { finalize_served(P, pair, status, 0, g.q, smap); return; }
+        if constexpr (SERVE) { finalize_served<GS>(P, pair, status, 0, g, smap); return; }
     }
     int last = 0;
     if (g.q == 0) {
@@ -588,58 +592,144 @@ __device__ __forceinline__ void end_task(const SearchParams& P, int pair, u64& n
     if (last) finalize_pair<SERVE, GS>(P, pair, g, smap);
 }
 
-// Serve mode, warp 0: admits requests that the host published in the mapped
-// ring, as root tasks of the ticket ring; exits (posting one exit token per
-// other searcher) after linger_ns without admitted or unfinished requests.
-__device__ void serve_admit(const SearchParams& P, const Grp<32>& g) {
+// Serve mode: copies request `slot` out of mapped host memory into its device
+// slot, packs it (validation, renumbering, rows, root classes; the whole
+// warp) and sets up its search state.  skey: 2 x 64 long long of scratch.
+__device__ void serve_pack(const SearchParams& P, int slot, int lane, long long* skey) {
+    int rq[3] = {0, 0, 0};
+    u64 rt = 0, rtk = 0;
+    if (lane == 0) {
+        const ServeReq* q = P.sv.req + slot;
+        rq[0] = vload(&q->nG); rq[1] = vload(&q->nH); rq[2] = vload(&q->labelled);
+        rt = vload(&q->timeout_ns); rtk = vload(&q->ticket);
+    }
+    for (int j = 0; j < 3; ++j) rq[j] = __shfl_sync(FULL, rq[j], 0);
+    rt = shfl64(rt, 0);
+    rtk = shfl64(rtk, 0);
+    // copy the bytes the request uses (n*n per graph, labels when present) out
+    // of mapped host memory: four 16-byte loads in flight per lane
+    const uint4* src = reinterpret_cast<const uint4*>(P.sv.hdata + (size_t)slot * kSlotBytes);
+    uint4* dst = reinterpret_cast<uint4*>(P.sv.ddata + (size_t)slot * kSlotBytes);
+    const int nG = min(max(rq[0], 0), kMaxN), nH = min(max(rq[1], 0), kMaxN);
+    const int seg_lo[4] = {0, kMaxN * kMaxN / 16, 2 * kMaxN * kMaxN / 16, (2 * kMaxN * kMaxN + 4 * kMaxN) / 16};
+    const int seg_n[4] = {(nG * nG + 15) / 16, (nH * nH + 15) / 16, (rq[2] & 1) ? 4 * kMaxN / 16 : 0,
+                          (rq[2] & 2) ? 4 * kMaxN / 16 : 0};
+#pragma unroll
+    for (int sg = 0; sg < 4; ++sg) {
+        for (int i0 = lane; i0 < seg_n[sg]; i0 += 128) {
+            uint4 v[4];
+#pragma unroll
+            for (int u = 0; u < 4; ++u) {
+                const int i = i0 + 32 * u;
+                if (i < seg_n[sg])
+                    asm volatile("ld.volatile.global.v4.u32 {%0,%1,%2,%3}, [%4];"
+                                 : "=r"(v[u].x), "=r"(v[u].y), "=r"(v[u].z), "=r"(v[u].w)
+                                 : "l"(src + seg_lo[sg] + i));
+            }
+#pragma unroll
+            for (int u = 0; u < 4; ++u)
+                if (i0 + 32 * u < seg_n[sg]) dst[seg_lo[sg] + i0 + 32 * u] = v[u];
+        }
+    }
+    __syncwarp();
+    const uint8_t* d = P.sv.ddata + (size_t)slot * kSlotBytes;
+    GraphIn gi[2];
+    gi[0].n = rq[0]; gi[1].n = rq[1];
+    gi[0].a = d; gi[1].a = d + kMaxN * kMaxN;
+    gi[0].lab = (rq[2] & 1) ? reinterpret_cast<const int32_t*>(d + 2 * kMaxN * kMaxN) : nullptr;
+    gi[1].lab = (rq[2] & 2) ? reinterpret_cast<const int32_t*>(d + 2 * kMaxN * kMaxN + 4 * kMaxN) : nullptr;
+    const bool ok = pack_pair_warp(gi, false, nullptr, nullptr, const_cast<PairGraph&>(P.graphs[slot]), skey, lane);
+    if (lane == 0) {
+        PairState& ps = P.state[slot];
+        ps.inc = 0; ps.open = 1; ps.abort = 0; ps.nodes = 0;
+        ps.t_start = 0; ps.deadline = 0; ps.ticket = rtk; ps.timeout_ns = rt;
+        ps.status = ok ? MCS_PENDING : MCS_ERR_ARG;
+    }
+    // every lane's packed rows and classes are visible before the root is published
+    __threadfence();
+    __syncwarp();
+}
+
+// Serve mode, warp 0 of the grid: admits requests that the host published in
+// the mapped ring.  Each is packed here (serve_pack) and published as a fresh
+// root of the ticket ring, which searchers of any width take like a batch
+// root.  Exits, posting one exit token per searcher (ntok), after linger_ns
+// without admitted or unfinished requests.
+__device__ void serve_admit(const SearchParams& P, int lane, long long* skey, int ntok) {
     Control* ctl = P.ctl;
     const ServeDev& S = P.sv;
-    const u64 qmask = P.qcap - 1;
-    if (g.q == 0) {
-        u64 admitted = vload(S.dev_admitted);
-        u64 idle0 = gtimer();
-        for (;;) {
-            if (vload(&ctl->error) != 0) break;
-            const u64 hw = vload(S.host_written);
-            if (hw > admitted) {
-                bool ok = true;
-                for (; admitted < hw && ok; ++admitted) {
-                    const int slot = vload(S.ring + (admitted % (u64)S.ring_cap));
-                    if (slot < 0 || slot >= S.nslots) continue;
-                    const u64 t = atomicAdd(&ctl->q_tail, 1ull);
-                    if (!wait_seq(P.qseq + (t & qmask), t)) { ok = false; break; }
+    const uint32_t qmask = P.qcap - 1;
+    u64 admitted = 0, idle0 = 0;
+    if (lane == 0) { admitted = vload(S.dev_admitted); idle0 = gtimer(); }
+    admitted = shfl64(admitted, 0);
+    for (;;) {
+        int act = 0;                   // 1: admit up to hw, -1: leave, 0: wait
+        u64 hw = 0;
+        if (lane == 0) {
+            if (vload(&ctl->error) != 0) {
+                act = -1;
+            } else {
+                hw = vload(S.host_written);
+                if (hw > admitted) {
+                    act = 1;
+                } else {
+                    const u64 now = gtimer();
+                    if (vload(S.in_flight) > 0) {
+                        idle0 = now;
+                        const u64 lp = vload(&ctl->last_progress);
+                        if (now > lp && now - lp > P.stall_ns) {      // requests stopped progressing
+                            atomicCAS(&ctl->error, 0, MCS_ERR_DEVICE_STALL);
+                            act = -1;
+                        }
+                    } else if (now - idle0 > S.linger_ns || vload(S.stop) != 0) {
+                        act = -1;
+                    }
+                }
+            }
+        }
+        act = __shfl_sync(FULL, act, 0);
+        hw = shfl64(hw, 0);
+        if (act < 0) break;
+        if (act == 0) { __nanosleep(1000); continue; }
+        int ok = 1;
+        for (; admitted < hw; ++admitted) {
+            int slot = 0;
+            if (lane == 0) slot = vload(S.ring + (admitted % (u64)S.ring_cap));
+            slot = __shfl_sync(FULL, slot, 0);
+            if (slot < 0 || slot >= S.nslots) continue;
+            serve_pack(P, slot, lane, skey);
+            if (lane == 0) {
+                const u64 t = atomicAdd(&ctl->q_tail, 1ull);
+                if (wait_seq(P.qseq + (t & qmask), t)) {
                     Task* dst = P.queue + (t & qmask);
                     dst->h.pair = slot;
-                    dst->h.flags = kTaskFresh | kTaskPack;
+                    dst->h.flags = kTaskFresh;
                     dst->h.depth = 0;
                     dst->h.C = 0;
                     atomicAdd(S.in_flight, 1);
                     __threadfence();
                     P.qseq[t & qmask] = t + 1;
+                } else {
+                    ok = 0;
                 }
-                if (!ok) { atomicCAS(&ctl->error, 0, MCS_ERR_DEVICE_STALL); break; }
-                *(volatile u64*)S.dev_admitted = admitted;
-                __threadfence_system();
-                idle0 = gtimer();
-                atomicMax(&ctl->last_progress, idle0);
-            } else {
-                const u64 now = gtimer();
-                if (vload(S.in_flight) > 0) {
-                    idle0 = now;
-                    const u64 lp = vload(&ctl->last_progress);
-                    if (now > lp && now - lp > P.stall_ns) {      // requests stopped progressing
-                        atomicCAS(&ctl->error, 0, MCS_ERR_DEVICE_STALL);
-                        break;
-                    }
-                } else if (now - idle0 > S.linger_ns || vload(S.stop) != 0) {
-                    break;
-                }
-                __nanosleep(1000);
             }
+            ok = __shfl_sync(FULL, ok, 0);
+            if (!ok) break;
         }
+        if (!ok) {
+            if (lane == 0) atomicCAS(&ctl->error, 0, MCS_ERR_DEVICE_STALL);
+            break;
+        }
+        if (lane == 0) {
+            *(volatile u64*)S.dev_admitted = admitted;
+            __threadfence_system();
+            idle0 = gtimer();
+            atomicMax(&ctl->last_progress, idle0);
+        }
+        __syncwarp();
     }
-    g.sync();
-    post_exit_tokens<32>(P, P.max_warps - 1, g);
+    __syncwarp();
+    post_exit_tokens<32>(P, ntok, Grp<32>(lane));
 }
 
 __device__ __forceinline__ void load_level(const WarpSmem& w, int d, Top& t) {
@@ -767,7 +857,7 @@ __device__ __forceinline__ bool donate(const SearchParams& P, int pair, int d0, 
 template <bool DIR, bool LEARNED, bool SERVE, int GS, bool NARROW>
 __global__ void __launch_bounds__(256, (GS == 32 ? MCS_SEARCH_MINB : MCS_GROUP_MINB)) search_kernel(SearchParams P) {
     static_assert(GS == 2 || GS == 4 || GS == 8 || GS == 16 || GS == 32, "searcher group size");
-    static_assert(!SERVE || GS == 32, "serve mode packs requests with whole warps");
+    static_assert(!SERVE || GS >= 8, "serve mode keeps the level arrays and result scratch in shared memory");
     extern __shared__ __align__(16) unsigned char smem[];
     constexpr int GPW = 32 / GS;                       // searchers per warp
     const int lane = threadIdx.x & 31;
@@ -776,7 +866,6 @@ __global__ void __launch_bounds__(256, (GS == 32 ? MCS_SEARCH_MINB : MCS_GROUP_M
     const int sid = (blockIdx.x * (blockDim.x >> 5) + wib) * GPW + (lane / GS);
     if (sid >= P.max_warps) return;
     constexpr bool ADJ_SM = adj_in_smem(GS);
-    static_assert(!SERVE || ADJ_SM, "serve mode repacks slots while it runs: rows go through shared memory");
     unsigned char* base = smem + (size_t)(wib * GPW + lane / GS) * P.warp_smem_bytes;
     unsigned char* lv = base + sm_adj_bytes(GS);       // level arrays and class cache
     WarpSmem w;
@@ -808,7 +897,11 @@ __global__ void __launch_bounds__(256, (GS == 32 ? MCS_SEARCH_MINB : MCS_GROUP_M
     Control* ctl = P.ctl;
     int16_t* smap = reinterpret_cast<int16_t*>(lv + kSmRremOff);   // finalize scratch (levels unused then)
     if constexpr (SERVE) {
-        if (sid == 0) { serve_admit(P, g); return; }
+        // warp 0 of the grid admits requests; its groups do not search
+        if (blockIdx.x == 0 && wib == 0) {
+            serve_admit(P, lane, reinterpret_cast<long long*>(smem), P.max_warps - GPW);
+            return;
+        }
     }
     const bool level_prune = (P.flags & MCS_NO_LEVEL_PRUNE) == 0;
     const uint32_t qmask = P.qcap - 1;
@@ -866,49 +959,6 @@ __global__ void __launch_bounds__(256, (GS == 32 ? MCS_SEARCH_MINB : MCS_GROUP_M
         const bool fresh = (tflags & kTaskFresh) != 0;
         PairState& ps = P.state[pair];
         const PairGraph& pg = P.graphs[pair];
-        u64 req_timeout = P.timeout_ns;
-        if constexpr (SERVE) {
-            if (tflags & kTaskPack) {
-                // a served request: copy it out of mapped host memory, pack it into
-                // its slot and set up its state (this warp is its only user so far)
-                const uint4* src = reinterpret_cast<const uint4*>(P.sv.hdata + (size_t)pair * kSlotBytes);
-                uint4* dst = reinterpret_cast<uint4*>(P.sv.ddata + (size_t)pair * kSlotBytes);
-                for (int i = lane; i < kSlotBytes / 16; i += 32) {
-                    uint4 v4;
-                    asm volatile("ld.volatile.global.v4.u32 {%0,%1,%2,%3}, [%4];"
-                                 : "=r"(v4.x), "=r"(v4.y), "=r"(v4.z), "=r"(v4.w) : "l"(src + i));
-                    dst[i] = v4;
-                }
-                int rq[3] = {0, 0, 0};
-                u64 rt = 0, rtk = 0;
-                if (lane == 0) {
-                    const ServeReq* q = P.sv.req + pair;
-                    rq[0] = vload(&q->nG); rq[1] = vload(&q->nH); rq[2] = vload(&q->labelled);
-                    rt = vload(&q->timeout_ns); rtk = vload(&q->ticket);
-                }
-                for (int j = 0; j < 3; ++j) rq[j] = __shfl_sync(FULL, rq[j], 0);
-                rt = shfl64(rt, 0);
-                rtk = shfl64(rtk, 0);
-                req_timeout = rt;
-                __syncwarp();
-                const uint8_t* d = P.sv.ddata + (size_t)pair * kSlotBytes;
-                GraphIn gi[2];
-                gi[0].n = rq[0]; gi[1].n = rq[1];
-                gi[0].a = d; gi[1].a = d + kMaxN * kMaxN;
-                gi[0].lab = (rq[2] & 1) ? reinterpret_cast<const int32_t*>(d + 2 * kMaxN * kMaxN) : nullptr;
-                gi[1].lab = (rq[2] & 2) ? reinterpret_cast<const int32_t*>(d + 2 * kMaxN * kMaxN + 4 * kMaxN) : nullptr;
-                const bool ok = pack_pair_warp(gi, false, nullptr, nullptr, const_cast<PairGraph&>(pg),
-                                               reinterpret_cast<long long*>(lv + kSmRremOff), lane);
-                if (lane == 0) {
-                    ps.inc = 0; ps.open = 1; ps.abort = 0; ps.nodes = 0;
-                    ps.t_start = 0; ps.deadline = 0; ps.ticket = rtk;
-                    ps.status = ok ? MCS_PENDING : MCS_ERR_ARG;
-                    __threadfence();
-                }
-                __syncwarp();
-                cur_pair = -1;      // a slot is reused by later requests: never trust cached rows
-            }
-        }
         int pstat = 0;
         if (g.q == 0) pstat = vload(&ps.status);
         pstat = g.shfl(pstat, 0);
@@ -922,7 +972,7 @@ __global__ void __launch_bounds__(256, (GS == 32 ? MCS_SEARCH_MINB : MCS_GROUP_M
             if (g.q == 0) {
                 u64 now = gtimer();
                 ps.t_start = now;
-                ps.deadline = now + req_timeout;
+                ps.deadline = now + (SERVE ? vload(&ps.timeout_ns) : P.timeout_ns);
                 atomicMax(&ctl->last_progress, now);
             }
         }
@@ -1049,9 +1099,9 @@ __global__ void __launch_bounds__(256, (GS == 32 ? MCS_SEARCH_MINB : MCS_GROUP_M
                 cvisits += t.C;
                 const int v = t.v;
                 const W vb = (W)1 << v, ub = (W)1 << u;
-                const W gB = (W)adj_row<ADJ_SM>(w.adj, v), hB = (W)adj_row<ADJ_SM>(w.adj, 2 * kMaxN + u);
-                const W gA = DIR ? (W)adj_row<ADJ_SM>(w.adj, kMaxN + v) : (W)0;
-                const W hA = DIR ? (W)adj_row<ADJ_SM>(w.adj, 3 * kMaxN + u) : (W)0;
+                const W gB = (W)adj_row<ADJ_SM, SERVE>(w.adj, v), hB = (W)adj_row<ADJ_SM, SERVE>(w.adj, 2 * kMaxN + u);
+                const W gA = DIR ? (W)adj_row<ADJ_SM, SERVE>(w.adj, kMaxN + v) : (W)0;
+                const W hA = DIR ? (W)adj_row<ADJ_SM, SERVE>(w.adj, 3 * kMaxN + u) : (W)0;
                 const int dm = t.d + 1;
                 const int cbase = t.base + t.C;
                 // parent and child both inside the shared-memory class cache:
@@ -1248,7 +1298,11 @@ static cudaError_t launch_w(const SearchParams& p, int blocks, int wpb, int gs, 
 
 cudaError_t launch_search(const SearchParams& p, int blocks, int warps_per_block, bool directed,
                           bool learned, cudaStream_t s, int gs) {
-    if (p.serving) return launch_t<false, false, true, 32, false>(p, blocks, warps_per_block, s);
+    if (p.serving) {
+        if (gs == 8) return launch_t<false, false, true, 8, false>(p, blocks, warps_per_block, s);
+        if (gs == 16) return launch_t<false, false, true, 16, false>(p, blocks, warps_per_block, s);
+        return launch_t<false, false, true, 32, false>(p, blocks, warps_per_block, s);
+    }
     const bool narrow = (p.flags & MCS_WORD32) != 0;
     if (directed) return learned ? launch_w<true, true>(p, blocks, warps_per_block, gs, narrow, s)
                                  : launch_w<true, false>(p, blocks, warps_per_block, gs, narrow, s);
@@ -1287,7 +1341,9 @@ int search_max_blocks_per_sm(int warps_per_block, int smem_per_block, bool direc
                    : occupancy_w<false, false>(warps_per_block, smem_per_block, gs, narrow);
 }
 
-int serve_max_blocks_per_sm(int warps_per_block, int smem_per_block) {
+int serve_max_blocks_per_sm(int warps_per_block, int smem_per_block, int gs) {
+    if (gs == 8) return occupancy_t<false, false, true, 8, false>(warps_per_block, smem_per_block);
+    if (gs == 16) return occupancy_t<false, false, true, 16, false>(warps_per_block, smem_per_block);
     return occupancy_t<false, false, true, 32, false>(warps_per_block, smem_per_block);
 }
 

@@ -3,10 +3,11 @@
 // Requests are written into mapped pinned host memory (a ring of slot
 // numbers, per-slot descriptors and raw graphs).  A resident launch of the
 // search kernel in serve mode admits them while it runs: its first warp polls
-// the ring and turns each request into a root task of the ticket ring, the
-// warp that takes the root copies and packs the request into its device slot,
-// and the request's search then shares the GPU with every other in-flight
-// request through the same work donation as a batch.  Results come back into
+// the ring, copies and packs each request into its device slot and publishes
+// it as a root task of the ticket ring; searchers of the context's width (8
+// lanes by default) take it like a batch root, and the request's search then
+// shares the GPU with every other in-flight request through the same work
+// donation as a batch.  Results come back into
 // mapped memory, marked done by the request's ticket after a system fence.
 //
 // Admission is bounded by device memory: a fixed pool of slots (packed
@@ -68,7 +69,8 @@ struct ServeState {
     uint32_t qcap = 0;
     ulonglong2* gstack = nullptr;
     int32_t* in_flight = nullptr;
-    int blocks = 0, warps = 0, wsmem = 0;
+    int blocks = 0, warps = 0, wsmem = 0;   // warps: searchers of the server launch
+    int gs = 32;                            // lanes per searcher of the server launch
     cudaStream_t stream = nullptr;
     cudaEvent_t done_ev = nullptr;
     bool running = false;
@@ -116,19 +118,24 @@ int serve_state(mcs_ctx* c, ServeState** out) {
     CKS(cudaMalloc((void**)&S->best, sizeof(uint16_t) * (size_t)kSlots * kLevels * kMaxN));
     CKS(cudaMalloc((void**)&S->ctl, sizeof(Control)));
     CKS(cudaMalloc((void**)&S->in_flight, sizeof(int32_t)));
-    // launch shape: the context's, undirected, plain order
-    S->wsmem = warp_smem_bytes(stack_entries(c, 32));
-    int per_sm = serve_max_blocks_per_sm(c->warps_per_block, c->warps_per_block * S->wsmem);
+    // launch shape: the context's warps per block and serving searcher width
+    // (mcs_set_serve_group; at least 8 lanes: the level arrays and result
+    // scratch stay in shared memory), undirected, plain order; warp 0 of the
+    // grid admits requests
+    S->gs = c->serve_lanes;
+    S->wsmem = warp_smem_bytes(stack_entries(c, S->gs), S->gs);
+    const int spw = 32 / S->gs;                     // searchers per warp
+    int per_sm = serve_max_blocks_per_sm(c->warps_per_block, c->warps_per_block * spw * S->wsmem, S->gs);
     if (per_sm <= 0) return MCS_ERR_UNSUPPORTED;
     if (c->blocks_per_sm > 0 && c->blocks_per_sm < per_sm) per_sm = c->blocks_per_sm;
     S->blocks = c->sms * per_sm;
-    S->warps = S->blocks * c->warps_per_block;
+    S->warps = S->blocks * c->warps_per_block * spw;     // searchers (warp 0's are the admitter)
     uint32_t q = 1024;
     while (q < (uint32_t)(4 * S->warps + kSlots)) q <<= 1;
     S->qcap = q;
     CKS(cudaMalloc((void**)&S->queue, sizeof(Task) * q));
     CKS(cudaMalloc((void**)&S->qseq, sizeof(u64) * q));
-    const size_t per = (size_t)(kStackMax - stack_entries(c, 32) > 0 ? kStackMax - stack_entries(c, 32) : 0);
+    const size_t per = gstack_entries(stack_entries(c, S->gs), S->gs);
     CKS(cudaMalloc((void**)&S->gstack, sizeof(ulonglong2) * std::max<size_t>(per * S->warps, 1)));
     CKS(cudaStreamCreateWithFlags(&S->stream, cudaStreamNonBlocking));
     CKS(cudaEventCreateWithFlags(&S->done_ev, cudaEventDisableTiming));
@@ -179,11 +186,11 @@ int launch_server(mcs_ctx* c, ServeState* S) {
     sp.queue = S->queue;
     sp.qseq = S->qseq;
     sp.qcap = S->qcap;
-    sp.stack_smem = stack_entries(c, 32);
+    sp.stack_smem = stack_entries(c, S->gs);
     sp.warp_smem_bytes = S->wsmem;
     sp.max_warps = S->warps;
     sp.gstack = S->gstack;
-    CKS(launch_search(sp, S->blocks, c->warps_per_block, false, false, S->stream));
+    CKS(launch_search(sp, S->blocks, c->warps_per_block, false, false, S->stream, S->gs));
     CKS(cudaEventRecord(S->done_ev, S->stream));
     S->running = true;
     return 0;

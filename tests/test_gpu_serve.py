@@ -14,13 +14,16 @@ import synth
 pytestmark = pytest.mark.gpu
 
 
-@pytest.fixture(scope="module")
-def solver():
+@pytest.fixture(scope="module", params=[32, 8], ids=["warp-searchers", "8-lane-searchers"])
+def solver(request):
+    """One context per serving searcher width (the server launch takes it at
+    the first submit)."""
     import torch
     if not torch.cuda.is_available():
         pytest.skip("no CUDA device")
     from paper_1908_06418_b300 import Solver
     s = Solver(0)
+    s.set_serve_group(request.param)
     yield s
     s.close()
 
@@ -98,3 +101,14 @@ def test_timeout_in_serving(solver):
     r = _wait(solver, [t])[0]
     assert r.status == MCS_TIMEOUT and r.size > 0
     assert oracle.verify(p.G.adj, p.H.adj, r.g_idx, r.h_idx) == 1
+
+
+def test_serve_group_is_fixed_once_serving(solver):
+    p = _requests(1, seed=58)[0]
+    t = solver.submit(p.G.adj, p.H.adj, p.G.labels, p.H.labels, timeout_s=20)
+    _wait(solver, [t])
+    with pytest.raises(ValueError):
+        solver.set_serve_group(16)
+    with pytest.raises(ValueError):
+        solver.set_serve_group(4)
+
