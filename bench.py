@@ -174,6 +174,21 @@ def oracle_sample(name: str, n_pairs: int, budget: float, offset: int = 0):
                        f"{min(cores, len(idx))} worker processes")
 
 
+def combine_ranks(total_ms, solved, nodes, dist=None, device="cpu"):
+    """Whole-job figures of a multi-rank run (one replica per rank): after a
+    barrier, the slowest rank's timed milliseconds and the work of all ranks
+    summed.  dist: torch.distributed (any backend) or None for one rank."""
+    if not dist:
+        return total_ms, solved, nodes
+    import torch
+    dist.barrier()
+    t = torch.tensor([total_ms], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    w = torch.tensor([solved, nodes], dtype=torch.float64, device=device)
+    dist.all_reduce(w)
+    return float(t.item()), int(w[0].item()), int(w[1].item())
+
+
 def apply_shape(solver, sh):
     """The autotuned launch shape of a group, else the library's defaults."""
     if sh:
@@ -420,16 +435,7 @@ def main():
             lats += l
             flush.fill_(k & 0xff)          # evict L2 between timed steps (untimed)
             torch.cuda.synchronize()
-    if dist:
-        dist.barrier()
-    total_ms = sum(step_ms)
-    if dist:
-        t = torch.tensor([total_ms], device=dev)
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        total_ms = float(t.item())
-        st = torch.tensor([solved_tot, nodes_tot], dtype=torch.float64, device=dev)
-        dist.all_reduce(st)
-        solved_tot, nodes_tot = int(st[0].item()), int(st[1].item())
+    total_ms, solved_tot, nodes_tot = combine_ranks(sum(step_ms), solved_tot, nodes_tot, dist, dev)
     value = solved_tot / (total_ms / 1e3)
     nodes_per_s = nodes_tot / (total_ms / 1e3)
 
