@@ -38,7 +38,8 @@ METRIC = "MCS pairs solved/sec (exact) on 1 B300"
 # the dominant search kernel, from a single-pass ncu capture of this
 # workload's launch (profiles/dram_search_kernel_c2.md); reported only while
 # the kernel source is the one the capture was taken with.
-TRAFFIC = {"c2": {"kernel_sha1": "baf0cb6351e7f6d6", "bytes": 1.22e9 + 5.28e9}}
+TRAFFIC = {"c2": {"kernel_sha1": "1fcd886be1aaa916", "bytes": 1.17e9 + 5.24e9},
+           "c3": {"kernel_sha1": "1fcd886be1aaa916", "bytes": 99.41e6 + 195.05e6}}
 UNIT = "pairs/s"
 
 
