@@ -445,6 +445,39 @@ __device__ __forceinline__ Scan scan_level(const Grp<GS>& g, const Stack& st, in
     return r;
 }
 
+// Learned order: the candidate u of `rrem` with the lowest rank in the row
+// rk[0..63] (ranks are distinct).  Each lane reads its contiguous 64/GS
+// entries of the row with one or two vector loads (the row is 64-byte
+// aligned), then the group takes the minimum of (rank << 6 | u).
+template <int GS>
+__device__ __forceinline__ int learned_pick(const uint8_t* rk, u64 rrem, const Grp<GS>& g) {
+    constexpr int C = kMaxN / GS;                      // entries per lane
+    const int u0 = g.q * C;
+    const u64 bits = (rrem >> u0) & (C == 64 ? ~0ull : ((1ull << (C & 63)) - 1ull));
+    unsigned kk = kKeyNone;
+    if (bits) {
+        uint32_t w[(C + 3) / 4];                       // the lane's ranks, 4 per word
+        if constexpr (C == 2) {
+            w[0] = __ldg(reinterpret_cast<const unsigned short*>(rk + u0));
+        } else if constexpr (C == 4) {
+            w[0] = __ldg(reinterpret_cast<const unsigned*>(rk + u0));
+        } else if constexpr (C == 8) {
+            const uint2 x = __ldg(reinterpret_cast<const uint2*>(rk + u0));
+            w[0] = x.x; w[1] = x.y;
+        } else {
+#pragma unroll
+            for (int h = 0; h < C / 16; ++h) {
+                const uint4 x = __ldg(reinterpret_cast<const uint4*>(rk + u0) + h);
+                w[4 * h] = x.x; w[4 * h + 1] = x.y; w[4 * h + 2] = x.z; w[4 * h + 3] = x.w;
+            }
+        }
+#pragma unroll
+        for (int b = 0; b < C; ++b)
+            if ((bits >> b) & 1ull) kk = min(kk, (((w[b >> 2] >> (8 * (b & 3))) & 0xffu) << 6) | (unsigned)(u0 + b));
+    }
+    return (int)(g.umin(kk) & 63u);
+}
+
 // Bounded wait for a ring slot's sequence number.
 __device__ __forceinline__ bool wait_seq(const u64* seq, u64 want) {
     for (int it = 0; it < kSpinLimit; ++it) {
@@ -1086,11 +1119,7 @@ __global__ void __launch_bounds__(256, (GS == 32 ? MCS_SEARCH_MINB : MCS_GROUP_M
                 int u;
                 if (LEARNED) {
                     // the remaining candidate with the best learned rank for v
-                    const uint8_t* rk = P.rank + ((size_t)pair * kMaxN + t.v) * kMaxN;
-                    unsigned kk = kKeyNone;
-                    for (int j = g.q; j < kMaxN; j += GS)
-                        if ((t.rrem >> j) & 1ull) kk = min(kk, ((unsigned)__ldg(rk + j) << 6) | (unsigned)j);
-                    u = (int)(g.umin(kk) & 63u);
+                    u = learned_pick<GS>(P.rank + ((size_t)pair * kMaxN + t.v) * kMaxN, t.rrem, g);
                 } else {
                     u = __ffsll(t.rrem) - 1;
                 }
