@@ -36,7 +36,6 @@ def build(force: bool = False, verbose: bool = False, extra=None, debug: bool = 
     lib = LIB_DEBUG if debug else LIB
     if not force and not _stale(lib):
         return lib
-    objs = []
     flags = ["-O3", "-std=c++17", "-lineinfo", "-Xcompiler", "-fPIC", *ARCH,
              "--expt-relaxed-constexpr"]
     if verbose:
@@ -46,10 +45,15 @@ def build(force: bool = False, verbose: bool = False, extra=None, debug: bool = 
         flags += ["-DMCS_DEBUG_BOUNDS"]
     build_dir = os.path.join(HERE, "_build", "debug" if debug else "release")
     os.makedirs(build_dir, exist_ok=True)
-    for s in SOURCES:
-        o = os.path.join(build_dir, s.replace(".cu", ".o"))
-        subprocess.check_call([nvcc(), "-c", os.path.join(CSRC, s), "-o", o, *flags])
-        objs.append(o)
+    # the translation units compile in parallel (the search kernel's
+    # instantiations dominate; the others overlap with it)
+    from concurrent.futures import ThreadPoolExecutor
+    objs = [os.path.join(build_dir, s.replace(".cu", ".o")) for s in SOURCES]
+    with ThreadPoolExecutor(max_workers=min(len(SOURCES), os.cpu_count() or 1)) as ex:
+        jobs = [ex.submit(subprocess.check_call, [nvcc(), "-c", os.path.join(CSRC, s), "-o", o, *flags])
+                for s, o in zip(SOURCES, objs)]
+        for j in jobs:
+            j.result()
     tmp = lib + ".tmp"
     subprocess.check_call([nvcc(), "-shared", *ARCH, *objs, "-o", tmp, "-lcudart"])
     os.replace(tmp, lib)
