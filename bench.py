@@ -446,18 +446,19 @@ def main():
     from paper_1908_06418_b300 import HostBatch
     hbs = [HostBatch([pairs[i] for i in g["idx"]], directed=bool(g["flags"] & MCS_DIRECTED)) for g in groups]
     e2e_ms, e2e_solved, h2d, d2h = [], 0, 0, 0
+    for g, hb in zip(groups, hbs):           # untimed: the bytes each call copies
+        apply_shape(solver, g.get("shape"))
+        solver.solve_host(hb, flags=g["flags"], timeout_s=a.timeout)
+        st = solver.last_stats()
+        h2d += st["h2d_bytes"]
+        d2h += st["d2h_bytes"]
     for k in range(max(1, min(a.steps, 3))):
         torch.cuda.synchronize()
         t0 = time.perf_counter()
         outs = []
         for g, hb in zip(groups, hbs):
-            sh = g.get("shape")
-            apply_shape(solver, sh)
+            apply_shape(solver, g.get("shape"))
             outs.append(solver.solve_host(hb, flags=g["flags"], timeout_s=a.timeout))
-            st = solver.last_stats()
-            if k == 0:
-                h2d += st["h2d_bytes"]
-                d2h += st["d2h_bytes"]
         e2e_ms.append((time.perf_counter() - t0) * 1e3)
         for g, res in zip(groups, outs):
             for j, i in enumerate(g["idx"]):

@@ -63,8 +63,18 @@ int launch_shape(mcs_ctx* c, bool directed, bool learned, bool narrow, int* bloc
     const int spb = c->warps_per_block * (32 / c->group_lanes);
     *wsmem = warp_smem_bytes(stack_entries(c, c->group_lanes), c->group_lanes);
     int smem_block = spb * *wsmem;
-    int per_sm = search_max_blocks_per_sm(c->warps_per_block, smem_block, directed, learned, c->group_lanes,
+    const uint64_t key = (uint64_t)c->warps_per_block | ((uint64_t)smem_block << 8) |
+                         ((uint64_t)c->group_lanes << 40) | ((uint64_t)directed << 48) |
+                         ((uint64_t)learned << 49) | ((uint64_t)narrow << 50);
+    auto it = c->occupancy.find(key);
+    int per_sm;
+    if (it != c->occupancy.end()) {
+        per_sm = it->second;
+    } else {
+        per_sm = search_max_blocks_per_sm(c->warps_per_block, smem_block, directed, learned, c->group_lanes,
                                           narrow);
+        c->occupancy[key] = per_sm;
+    }
     if (per_sm <= 0) return MCS_ERR_UNSUPPORTED;
     if (c->blocks_per_sm > 0) per_sm = std::min(per_sm, c->blocks_per_sm);
     *blocks = c->sms * per_sm;

@@ -3,6 +3,7 @@
 #pragma once
 #include <cstdint>
 #include <cuda_runtime.h>
+#include <unordered_map>
 
 namespace mcsk {
 
@@ -221,6 +222,9 @@ struct mcs_ctx {
     int serve_lanes = 32;         // lanes per searcher of the server launch: 32, 16 or 8
     int poll_nodes = 16;          // work-sharing poll interval (nodes, power of two)
     int steal_keep_q4 = 2;        // quarters of a donated level's candidates the donor keeps
+    // resident blocks per SM of each launch configuration already asked of the
+    // driver (key: warps per block, shared memory per block, kernel variant)
+    std::unordered_map<uint64_t, int> occupancy;
     // device arenas
     int pairs_cap = 0;
     PairGraph* graphs = nullptr;
