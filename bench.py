@@ -38,8 +38,8 @@ METRIC = "MCS pairs solved/sec (exact) on 1 B300"
 # the dominant search kernel, from a single-pass ncu capture of this
 # workload's launch (profiles/dram_search_kernel_c2.md); reported only while
 # the kernel source is the one the capture was taken with.
-TRAFFIC = {"c2": {"kernel_sha1": "1fcd886be1aaa916", "bytes": 1.17e9 + 5.24e9},
-           "c3": {"kernel_sha1": "1fcd886be1aaa916", "bytes": 99.41e6 + 195.05e6}}
+TRAFFIC = {"c2": {"kernel_sha1": "9c7ac2430a6e9883", "bytes": 1.21e9 + 5.30e9},
+           "c3": {"kernel_sha1": "9c7ac2430a6e9883", "bytes": 97.23e6 + 191.43e6}}
 UNIT = "pairs/s"
 
 

@@ -1305,19 +1305,25 @@ __global__ void __launch_bounds__(256, (GS == 32 ? MCS_SEARCH_MINB : MCS_GROUP_M
 // Raises a kernel's dynamic shared-memory limit on the current device when a
 // launch needs more than was set before (one driver call per new maximum,
 // not one per launch).  Per kernel instantiation: `Tag` is unique to it.
+// Returns false (with the runtime's error state cleared) when the device
+// cannot give the kernel that much shared memory.
 template <typename Tag>
-static void ensure_smem_limit(void (*k)(SearchParams), int smem) {
+static bool ensure_smem_limit(void (*k)(SearchParams), int smem) {
     constexpr int kDevs = 64;
     static std::atomic<int> set_bytes[kDevs];
     int dev = 0;
     cudaGetDevice(&dev);
-    if (dev >= 0 && dev < kDevs && set_bytes[dev].load(std::memory_order_relaxed) >= smem) return;
-    cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
+    if (dev >= 0 && dev < kDevs && set_bytes[dev].load(std::memory_order_relaxed) >= smem) return true;
+    if (cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, smem) != cudaSuccess) {
+        cudaGetLastError();            // expected for a shape that does not fit: reported as unsupported
+        return false;
+    }
     if (dev >= 0 && dev < kDevs) {
         int cur = set_bytes[dev].load();
         while (cur < smem && !set_bytes[dev].compare_exchange_weak(cur, smem)) {
         }
     }
+    return true;
 }
 
 template <bool DIR, bool LEARNED, bool SERVE, int GS, bool NARROW>
@@ -1327,7 +1333,7 @@ template <bool DIR, bool LEARNED, bool SERVE, int GS, bool NARROW>
 static cudaError_t launch_t(const SearchParams& p, int blocks, int wpb, cudaStream_t s) {
     size_t smem = (size_t)wpb * (32 / GS) * p.warp_smem_bytes;
     auto* k = search_kernel<DIR, LEARNED, SERVE, GS, NARROW>;
-    ensure_smem_limit<KernelTag<DIR, LEARNED, SERVE, GS, NARROW>>(k, (int)smem);
+    if (!ensure_smem_limit<KernelTag<DIR, LEARNED, SERVE, GS, NARROW>>(k, (int)smem)) return cudaErrorInvalidValue;
     k<<<blocks, wpb * 32, smem, s>>>(p);
     return cudaGetLastError();
 }
@@ -1365,8 +1371,11 @@ template <bool DIR, bool LEARNED, bool SERVE, int GS, bool NARROW>
 static int occupancy_t(int wpb, int smem) {
     int nb = 0;
     auto* k = search_kernel<DIR, LEARNED, SERVE, GS, NARROW>;
-    ensure_smem_limit<KernelTag<DIR, LEARNED, SERVE, GS, NARROW>>(k, smem);
-    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, k, wpb * 32, smem);
+    if (!ensure_smem_limit<KernelTag<DIR, LEARNED, SERVE, GS, NARROW>>(k, smem)) return 0;
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, k, wpb * 32, smem) != cudaSuccess) {
+        cudaGetLastError();
+        return 0;
+    }
     return nb;
 }
 
