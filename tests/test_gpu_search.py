@@ -380,3 +380,55 @@ def test_host_batch_call_matches_per_pair_objects(solver, directed, k):
         s = int(out["size"][i])
         g, h = out["g_idx"][i, :s], out["h_idx"][i, :s]
         assert oracle.verify(p.G.adj, p.H.adj, g, h, p.G.labels, p.H.labels) == 1
+
+
+@pytest.mark.parametrize("workload", ["c2", "c3"])
+def test_full_workload_in_the_tuned_launch_shape(solver, workload):
+    """The stored oracle results at full size, in the launch shapes the bench
+    applies (autotuner cache: searcher width, warps per block, work sharing),
+    through the device entry point as the bench times it."""
+    import torch
+    from paper_1908_06418_b300 import DeviceBatch
+    rows = {r["idx"]: r for r in _golden(f"{workload}_oracle.jsonl")}
+    pairs = synth.config2_pairs() if workload == "c2" else synth.config3_pairs()
+    try:
+        for directed in (True, False):
+            idx = [i for i, p in enumerate(pairs) if p.directed == directed]
+            if not idx:
+                continue
+            sub = [pairs[i] for i in idx]
+            solver.apply_tuned(sub, directed=directed) or solver.reset_launch()
+            b = DeviceBatch(sub, directed=directed)
+            n = len(sub)
+            size = torch.zeros(n, dtype=torch.int32, device=b.device)
+            status = torch.zeros(n, dtype=torch.int32, device=b.device)
+            nodes = torch.zeros(n, dtype=torch.int64, device=b.device)
+            mp = torch.zeros(n * 64, dtype=torch.int16, device=b.device)
+            rc = solver.solve_batch_device(n, b.d_n, b.d_adj_off, b.d_adj, b.d_lab_off, b.d_labels,
+                                           size, status, nodes, mp, flags=b.flags, timeout_s=600)
+            torch.cuda.synchronize()
+            assert rc == 0
+            sz, st = size.cpu().numpy(), status.cpu().numpy()
+            mp = mp.cpu().numpy().reshape(n, 64)
+            for j, i in enumerate(idx):
+                g = rows[i]
+                assert st[j] == 0, (i, st[j])
+                assert sz[j] == g["size"] if g["complete"] else sz[j] >= g["size"], (i, sz[j], g["size"])
+            for j in range(0, n, max(1, n // 64)):
+                p = sub[j]
+                gi = np.nonzero(mp[j] >= 0)[0]
+                assert len(gi) == sz[j]
+                assert oracle.verify(p.G.adj, p.H.adj, gi, mp[j][gi], p.G.labels, p.H.labels) == 1
+    finally:
+        solver.reset_launch()
+
+
+def test_empty_batches(solver):
+    import torch
+    from paper_1908_06418_b300 import HostBatch
+    assert solver.solve_batch([]) == []
+    out = solver.solve_host(HostBatch([]))
+    assert out["size"].size == 0
+    z = torch.zeros(1, dtype=torch.int32, device="cuda")
+    assert solver.solve_batch_device(0, None, None, None, None, None, z, z,
+                                     torch.zeros(1, dtype=torch.int64, device="cuda")) == 0
