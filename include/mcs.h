@@ -65,8 +65,8 @@ extern "C" {
                                     /* launches in a CUDA graph and replay the graph   */
                                     /* when called again with identical arguments      */
 #define MCS_NO_LEVEL_PRUNE    0x8u  /* diagnostic: do not re-test a level's bound      */
-                                    /* before each sibling, so that with one warp the  */
-                                    /* node count equals the sequential recursion's    */
+                                    /* before each sibling, so that with one searcher  */
+                                    /* the node count equals the sequential recursion's */
 #define MCS_WORD32            0x20u /* 32-bit node step: every graph of the call has at */
                                     /* most 32 vertices (others: MCS_ERR_ARG for that  */
                                     /* pair).  mcs_solve and mcs_solve_batch set it    */
@@ -225,7 +225,7 @@ int mcs_set_launch(mcs_ctx* ctx, int warps_per_block, int blocks_per_sm,
                    int smem_stack_entries);
 
 /* Restricts a solve to `warps` resident searchers in total (0 = the full
- * grid; a searcher is one warp unless mcs_set_search_group splits warps).
+ * grid; a searcher is a group of mcs_set_search_group lanes, 8 by default).
  * With warps == 1 the search order is deterministic. */
 int mcs_set_max_warps(mcs_ctx* ctx, int warps);
 
@@ -259,11 +259,13 @@ int mcs_set_serve_group(mcs_ctx* ctx, int lanes);
  * microseconds (for mcs_solve_batch_device: once its stream has passed the
  * launch, else the previous value), out[1] total nodes (host API calls only),
  * out[2] donated tasks, out[3] donated tasks taken up, out[4] child levels
- * that spilled past the shared-memory class cache, out[5] searchers launched,
+ * that spilled past the shared-memory class cache (searchers narrower than a
+ * warp keep the whole stack in global memory: every child level counts),
+ * out[5] searchers launched,
  * out[6] bytes copied host to device, out[7] bytes copied device to host
  * (out[6..7]: host API calls only), out[8] label classes read by node
  * expansions (the unit of algorithmic work), out[9] children cut by the bound
- * when created, out[10] / out[11] SM cycles summed over warps while working /
+ * when created, out[10] / out[11] SM cycles summed over searchers while working /
  * waiting for work, out[12..14] index violations recorded by an
  * MCS_DEBUG_BOUNDS build (count, first code, first source line; 0 in
  * release builds).  Returns the number of values written (<= n, <= 15). */
