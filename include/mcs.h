@@ -203,6 +203,17 @@ int mcs_order_train(mcs_ctx* ctx, int32_t npairs, const int32_t* d_n, const int6
                     const float* d_w, int32_t steps, int32_t batch, float lr, uint64_t seed,
                     float* h_loss_per_step);
 
+/* Scores of every candidate pair of a device-resident batch (layout of
+ * mcs_solve_batch_device) under the loaded model: d_scores[p][v][u]
+ * (npairs x 64 x 64 floats, device memory owned by the caller) receives the
+ * logit of (v, u) in original vertex ids for v < n_G(p), u < n_H(p); other
+ * entries are not written.  This is the all-pairs pass that
+ * MCS_ORDER_LEARNED runs before a search.  Asynchronous on `stream` (a
+ * cudaStream_t; NULL = the context's stream).  MCS_ERR_ARG without a model. */
+int mcs_order_score_grid(mcs_ctx* ctx, int32_t npairs, const int32_t* d_n, const int64_t* d_adj_off,
+                         const uint8_t* d_adj, const int64_t* d_lab_off, const int32_t* d_labels,
+                         uint32_t flags, float* d_scores, void* stream);
+
 /* Serving: admit one request; returns a ticket.  The search starts on the
  * device as soon as a slot and device memory are free; requests submitted
  * while others run join them (continuous batching). */

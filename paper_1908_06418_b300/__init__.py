@@ -53,7 +53,7 @@ EXPORTED_SYMBOLS = ["mcs_create", "mcs_destroy", "mcs_solve", "mcs_solve_batch",
                     "mcs_set_max_warps", "mcs_set_search_group", "mcs_set_serve_group", "mcs_set_steal",
                     "mcs_last_stats", "mcs_bench_popc", "mcs_strerror", "mcs_error_detail",
                     "mcs_solve_batch_noalloc", "mcs_set_order_model", "mcs_get_order_model",
-                    "mcs_order_eval", "mcs_order_train"]
+                    "mcs_order_eval", "mcs_order_train", "mcs_order_score_grid"]
 
 MCS_ORDER_NPARAMS = 22913
 
@@ -115,6 +115,8 @@ def load_library():
     lib.mcs_order_train.argtypes = [vp, i32, vp, vp, vp, vp, vp, u32, i32, vp, vp, vp,
                                     i32, i32, ctypes.c_float, ctypes.c_uint64, fp]
     lib.mcs_order_train.restype = ctypes.c_int
+    lib.mcs_order_score_grid.argtypes = [vp, i32, vp, vp, vp, vp, vp, u32, vp, vp]
+    lib.mcs_order_score_grid.restype = ctypes.c_int
     lib.mcs_error_detail.argtypes = []
     lib.mcs_error_detail.restype = ctypes.c_char_p
     lib.mcs_strerror.argtypes = [ctypes.c_int]
@@ -361,6 +363,22 @@ class Solver:
             out["grad"] = h_g
         if features:
             out["features"] = h_f
+        return out
+
+    def order_score_grid(self, batch: "DeviceBatch", out=None, stream=None):
+        """Scores of every candidate pair: a float32 tensor [npairs, 64, 64]
+        on the batch's device, entry [p, v, u] valid for v < n_G and u < n_H
+        (the rest is left as it was).  Asynchronous on `stream` (a
+        torch.cuda.Stream or a raw handle; None = the context's stream)."""
+        import torch
+        if out is None:
+            out = torch.zeros((batch.npairs, 64, 64), dtype=torch.float32, device=batch.device)
+        h = stream.cuda_stream if hasattr(stream, "cuda_stream") else stream
+        rc = self.lib.mcs_order_score_grid(self.ctx, batch.npairs, _ptr(batch.d_n), _ptr(batch.d_adj_off),
+                                           _ptr(batch.d_adj), _ptr(batch.d_lab_off), _ptr(batch.d_labels),
+                                           batch.flags, _ptr(out), h)
+        if rc:
+            raise RuntimeError(f"mcs_order_score_grid: {self.strerror(rc)}")
         return out
 
     def order_train(self, batch: "DeviceBatch", rows, y, w=None, steps=100, batch_size=4096,

@@ -8,10 +8,10 @@
 //   features_kernel  18 features per vertex: degree, label, histogram of the
 //                    neighbours' degrees in 16 bins
 //   mlp_fwd_kernel   x(v,u) = [f_G(v), f_H(u)] (36, padded to 48) -> 128 ->
-//                    128 -> 1 logit; both hidden layers are mma.sync
-//                    m16n8k16 (f16 in, f32 accumulate) with the layer-1 result
-//                    converted to layer-2 A fragments in registers
-//   bwd kernels      backward pass (head, two tensor-core GEMMs for dh1 and the
+//                    128 -> 1 logit; both hidden layers are tcgen05.mma
+//                    (kind::f16: f16 operands in shared memory, f32
+//                    accumulators in tensor memory), 128 rows per tile
+//   bwd kernels      backward pass (head, two mma.sync GEMMs for dh1 and the
 //                    weight gradients, column sums) and an Adam update
 //   keys / rank      per-pair vertex order keys (for the renumbering done by
 //                    the pack kernel) and per-v candidate ranks (for the search)
@@ -134,6 +134,7 @@ struct FwdParams {
     float* s;                // [nrows] logits
     __half* h1;              // training: [nrows][128]
     float* h2;               // training: [nrows][128]
+    int* err;                // set to 1 when a bounded wait gives up
 };
 
 __device__ __forceinline__ bool row_of(const FwdParams& P, long long r, int& p, int& v, int& u) {
@@ -146,116 +147,232 @@ __device__ __forceinline__ bool row_of(const FwdParams& P, long long r, int& p, 
     return v < P.n[2 * p] && u < P.n[2 * p + 1];
 }
 
-// x(row, k..k+1) for even k: G features, then H features, then zeros
-__device__ __forceinline__ uint32_t xpair(const __half* fg, const __half* fh, int k) {
-    if (k < kF) return *reinterpret_cast<const uint32_t*>(fg + k);
-    if (k < 2 * kF) return *reinterpret_cast<const uint32_t*>(fh + (k - kF));
-    return 0u;
+// ---- tcgen05 / TMEM / mbarrier primitives (inline PTX) -------------------
+__device__ __forceinline__ uint32_t smem_u32(const void* p) { return (uint32_t)__cvta_generic_to_shared(p); }
+__device__ __forceinline__ void tmem_alloc(uint32_t slot, uint32_t ncols) {
+    asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" :: "r"(slot), "r"(ncols) : "memory");
+}
+__device__ __forceinline__ void tmem_relinquish() {
+    asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
+}
+__device__ __forceinline__ void tmem_dealloc(uint32_t taddr, uint32_t ncols) {
+    asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" :: "r"(taddr), "r"(ncols) : "memory");
+}
+__device__ __forceinline__ void tc_before_sync() { asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory"); }
+__device__ __forceinline__ void tc_after_sync() { asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory"); }
+// generic-proxy shared-memory writes -> visible to the tensor core (async proxy)
+__device__ __forceinline__ void fence_async_smem() { asm volatile("fence.proxy.async.shared::cta;" ::: "memory"); }
+__device__ __forceinline__ void mbar_init(uint32_t a, uint32_t count) {
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" :: "r"(a), "r"(count) : "memory");
+}
+__device__ __forceinline__ void mbar_init_fence() {
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+}
+__device__ __forceinline__ bool mbar_try(uint32_t a, uint32_t parity) {
+    uint32_t ok;
+    asm volatile("{\n\t.reg .pred p;\n\tmbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n\t"
+                 "selp.u32 %0, 1, 0, p;\n}" : "=r"(ok) : "r"(a), "r"(parity) : "memory");
+    return ok != 0;
+}
+// bounded: gives up (false) after ~2^22 polls instead of spinning forever
+__device__ __forceinline__ bool mbar_wait(uint32_t a, uint32_t parity) {
+    for (uint32_t i = 0; i < (1u << 22); ++i)
+        if (mbar_try(a, parity)) return true;
+    return false;
+}
+// D[tmem] (+)= A[smem] * B[smem]^T, one elected thread; acc = 0 overwrites D
+__device__ __forceinline__ void umma_f16(uint32_t d, uint64_t adesc, uint64_t bdesc, uint32_t idesc, uint32_t acc) {
+    asm volatile("{\n\t.reg .pred p;\n\tsetp.ne.b32 p, %4, 0;\n\t"
+                 "tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n}"
+                 :: "r"(d), "l"(adesc), "l"(bdesc), "r"(idesc), "r"(acc) : "memory");
+}
+// arrives on the mbarrier once every MMA issued so far by this thread is done
+__device__ __forceinline__ void umma_commit(uint32_t bar) {
+    asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" :: "r"(bar) : "memory");
+}
+// 32 consecutive fp32 columns of this thread's TMEM lane; the wait carries the
+// registers so that no use is scheduled before the load has landed
+__device__ __forceinline__ void tmem_ld32(uint32_t taddr, uint32_t (&r)[32]) {
+    asm volatile("tcgen05.ld.sync.aligned.32x32b.x32.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15,%16,%17,%18,%19,%20,%21,%22,%23,%24,%25,%26,%27,%28,%29,%30,%31}, [%32];"
+                 : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7]), "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]), "=r"(r[14]), "=r"(r[15]), "=r"(r[16]), "=r"(r[17]), "=r"(r[18]), "=r"(r[19]), "=r"(r[20]), "=r"(r[21]), "=r"(r[22]), "=r"(r[23]), "=r"(r[24]), "=r"(r[25]), "=r"(r[26]), "=r"(r[27]), "=r"(r[28]), "=r"(r[29]), "=r"(r[30]), "=r"(r[31]) : "r"(taddr));
+    asm volatile("tcgen05.wait::ld.sync.aligned;" : "+r"(r[0]), "+r"(r[1]), "+r"(r[2]), "+r"(r[3]), "+r"(r[4]), "+r"(r[5]), "+r"(r[6]), "+r"(r[7]), "+r"(r[8]), "+r"(r[9]), "+r"(r[10]), "+r"(r[11]), "+r"(r[12]), "+r"(r[13]), "+r"(r[14]), "+r"(r[15]), "+r"(r[16]), "+r"(r[17]), "+r"(r[18]), "+r"(r[19]), "+r"(r[20]), "+r"(r[21]), "+r"(r[22]), "+r"(r[23]), "+r"(r[24]), "+r"(r[25]), "+r"(r[26]), "+r"(r[27]), "+r"(r[28]), "+r"(r[29]), "+r"(r[30]), "+r"(r[31]) :: "memory");
 }
 
+// Shared-memory operand layout for the MMAs: no swizzle, K-major.  The tile is
+// cut into 8-row x 16-byte core matrices (8 rows x 8 fp16); the cores of one
+// 8-row group are consecutive along K (128 B apart: the leading byte offset)
+// and consecutive 8-row groups are K/8 x 128 B apart (the stride byte offset).
+__device__ __forceinline__ int kmaj_off(int row, int kchunk, int kchunks) {
+    return (row >> 3) * (kchunks * 128) + kchunk * 128 + (row & 7) * 16;
+}
+// shared-memory matrix descriptor: start >> 4 | LBO >> 4 << 16 | SBO >> 4 << 32 |
+// version 1 (bit 46) | no swizzle (bits 61-63 = 0)
+__device__ __forceinline__ uint64_t kmaj_desc(uint32_t saddr, int kchunks) {
+    const uint64_t lbo = 128, sbo = (uint64_t)kchunks * 128;
+    return (uint64_t)((saddr >> 4) & 0x3FFFu) | ((lbo >> 4) << 16) | ((sbo >> 4) << 32) | (1ull << 46);
+}
+
+constexpr int kTile = 128;                            // rows per tile = MMA M = TMEM lanes
+constexpr uint32_t kTmemCols = 256;                   // layer 1: columns 0..127, layer 2: 128..255
+// instruction descriptor, kind::f16: D f32 (bits 4-5 = 1), A and B f16 (bits 7-12 = 0),
+// both K-major (bits 15-16 = 0), N >> 3 at bit 17, M >> 4 at bit 24
+constexpr uint32_t kIdesc = (1u << 4) | ((uint32_t)(kH >> 3) << 17) | ((uint32_t)(kTile >> 4) << 24);
+constexpr int kSW1 = 0;                               // W1t  128 x 48 fp16
+constexpr int kSW2 = kSW1 + kH * kIn * 2;             // W2t  128 x 128
+constexpr int kSA1 = kSW2 + kH * kH * 2;              // x    128 x 48
+constexpr int kSA2 = kSA1 + kTile * kIn * 2;          // h1   128 x 128
+constexpr int kSBias = kSA2 + kTile * kH * 2;         // b1, b2, w3 (fp32)
+constexpr int kSBar = kSBias + 3 * kH * 4;            // mbarrier, TMEM base address
+constexpr int kFwdSmem = kSBar + 16;
+// more than a third of the SM's shared memory: at most two CTAs (512 TMEM
+// columns) per SM, so the allocation never waits
+static_assert(3 * (kFwdSmem + 1024) > 228 * 1024, "TMEM columns could be oversubscribed");
+
+// One CTA (4 warps) computes 128 rows at a time, persistent over the tiles:
+// gather x into shared memory, layer 1 = 3 MMAs (K = 48) into TMEM, bias +
+// ReLU + fp16 by the thread owning the row into shared memory, layer 2 = 8
+// MMAs (K = 128), bias + ReLU + head dot product per thread (row t of the tile
+// is TMEM lane t, read by thread t).  Grid mode (P.rows == null) skips tiles
+// whose two rows v are both >= n_G.
 template <bool TRAIN>
-__global__ void __launch_bounds__(256) mlp_fwd_kernel(FwdParams P) {
-    extern __shared__ __align__(16) unsigned char sm[];
-    __half* sW1t = reinterpret_cast<__half*>(sm);           // 128 x 48
-    __half* sW2t = sW1t + kH * kIn;                         // 128 x 128
-    float* sb1 = reinterpret_cast<float*>(sW2t + kH * kH);
+__global__ void __launch_bounds__(kTile, 1) mlp_fwd_kernel(FwdParams P, long long ntiles) {
+    extern __shared__ __align__(1024) unsigned char sm[];
+    const int tid = threadIdx.x, warp = tid >> 5;
+    const uint32_t sbase = smem_u32(sm);
+    for (int i = tid; i < kH * (kIn / 8); i += kTile) {
+        const int n = i / (kIn / 8), kc = i % (kIn / 8);
+        *reinterpret_cast<uint4*>(sm + kSW1 + kmaj_off(n, kc, kIn / 8)) =
+            *reinterpret_cast<const uint4*>(P.W1t + n * kIn + kc * 8);
+    }
+    for (int i = tid; i < kH * (kH / 8); i += kTile) {
+        const int n = i / (kH / 8), kc = i % (kH / 8);
+        *reinterpret_cast<uint4*>(sm + kSW2 + kmaj_off(n, kc, kH / 8)) =
+            *reinterpret_cast<const uint4*>(P.W2t + n * kH + kc * 8);
+    }
+    float* sb1 = reinterpret_cast<float*>(sm + kSBias);
     float* sb2 = sb1 + kH;
     float* sw3 = sb2 + kH;
-    for (int i = threadIdx.x; i < kH * kIn / 2; i += blockDim.x)
-        reinterpret_cast<uint32_t*>(sW1t)[i] = reinterpret_cast<const uint32_t*>(P.W1t)[i];
-    for (int i = threadIdx.x; i < kH * kH / 2; i += blockDim.x)
-        reinterpret_cast<uint32_t*>(sW2t)[i] = reinterpret_cast<const uint32_t*>(P.W2t)[i];
-    for (int i = threadIdx.x; i < kH; i += blockDim.x) { sb1[i] = P.b1[i]; sb2[i] = P.b2[i]; sw3[i] = P.w3[i]; }
+    for (int i = tid; i < kH; i += kTile) { sb1[i] = P.b1[i]; sb2[i] = P.b2[i]; sw3[i] = P.w3[i]; }
+    const uint32_t bar = sbase + kSBar;
+    uint32_t* tslot = reinterpret_cast<uint32_t*>(sm + kSBar + 8);
+    if (tid == 0) { mbar_init(bar, 1); mbar_init_fence(); }
+    if (warp == 0) { tmem_alloc(smem_u32(tslot), kTmemCols); tmem_relinquish(); }
+    fence_async_smem();
+    tc_before_sync();
     __syncthreads();
+    tc_after_sync();
+    const uint32_t tmem = *tslot;
+    const uint32_t lane_off = (uint32_t)(warp * 32) << 16;   // warp w reads TMEM lanes 32w..32w+31
+    const uint32_t t1 = tmem + lane_off, t2 = tmem + 128 + lane_off;
     const float b3 = *P.b3;
-    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-    const int g = lane >> 2, tq = lane & 3;
-    const long long r0 = (long long)blockIdx.x * 128 + warp * 16;
-    const __half* fg[2];
-    const __half* fh[2];
-    bool ok[2];
-    long long rr[2];
-    for (int h = 0; h < 2; ++h) {
-        rr[h] = r0 + g + 8 * h;
+    uint32_t phase = 0;
+    for (long long t = blockIdx.x; t < ntiles; t += gridDim.x) {
+        if (!P.rows) {
+            const int p = (int)(t >> 5), v0 = (int)(t & 31) * 2;
+            if (v0 >= P.n[2 * p] || P.n[2 * p + 1] <= 0) continue;       // uniform over the CTA
+        }
+        const long long r = t * kTile + tid;
         int p = 0, v = 0, u = 0;
-        ok[h] = row_of(P, rr[h], p, v, u);
-        if (!ok[h]) { p = 0; v = 0; u = 0; }
-        fg[h] = P.feat16 + ((size_t)(2 * p) * kMaxN + v) * kFP;
-        fh[h] = P.feat16 + ((size_t)(2 * p + 1) * kMaxN + u) * kFP;
-    }
-    // ---- layer 1: [16 x 48] x [48 x 128]
-    float acc[16][4];
-#pragma unroll
-    for (int nt = 0; nt < 16; ++nt) acc[nt][0] = acc[nt][1] = acc[nt][2] = acc[nt][3] = 0.f;
-#pragma unroll
-    for (int kt = 0; kt < 3; ++kt) {
-        const int k0 = kt * 16 + 2 * tq;
-        uint32_t a[4];
-        a[0] = ok[0] ? xpair(fg[0], fh[0], k0) : 0u;
-        a[1] = ok[1] ? xpair(fg[1], fh[1], k0) : 0u;
-        a[2] = ok[0] ? xpair(fg[0], fh[0], k0 + 8) : 0u;
-        a[3] = ok[1] ? xpair(fg[1], fh[1], k0 + 8) : 0u;
-#pragma unroll
-        for (int nt = 0; nt < 16; ++nt) {
-            const __half* wb = sW1t + (nt * 8 + g) * kIn + k0;
-            mma16816(acc[nt], a, *reinterpret_cast<const uint32_t*>(wb),
-                     *reinterpret_cast<const uint32_t*>(wb + 8));
+        const bool ok = row_of(P, r, p, v, u);
+        // x = [f_G(v) (18), f_H(u) (18), 0 (12)] as 24 fp16 pairs, 6 core-matrix rows
+        uint4 c0 = make_uint4(0, 0, 0, 0), c1 = c0, c2 = c0, c3 = c0, c4 = c0;
+        if (ok) {
+            const __half* fg = P.feat16 + ((size_t)(2 * p) * kMaxN + v) * kFP;
+            const __half* fh = P.feat16 + ((size_t)(2 * p + 1) * kMaxN + u) * kFP;
+            const uint4 g0 = reinterpret_cast<const uint4*>(fg)[0], g1 = reinterpret_cast<const uint4*>(fg)[1];
+            const uint4 h0 = reinterpret_cast<const uint4*>(fh)[0], h1 = reinterpret_cast<const uint4*>(fh)[1];
+            const uint32_t g8 = reinterpret_cast<const uint32_t*>(fg)[8];
+            const uint32_t h8 = reinterpret_cast<const uint32_t*>(fh)[8];
+            c0 = g0; c1 = g1;
+            c2 = make_uint4(g8, h0.x, h0.y, h0.z);
+            c3 = make_uint4(h0.w, h1.x, h1.y, h1.z);
+            c4 = make_uint4(h1.w, h8, 0u, 0u);
         }
-    }
-    // ---- bias + ReLU, re-packed as layer-2 A fragments (k-tile = two n-tiles)
-    uint32_t a2[8][4];
+        unsigned char* a1 = sm + kSA1;
+        *reinterpret_cast<uint4*>(a1 + kmaj_off(tid, 0, kIn / 8)) = c0;
+        *reinterpret_cast<uint4*>(a1 + kmaj_off(tid, 1, kIn / 8)) = c1;
+        *reinterpret_cast<uint4*>(a1 + kmaj_off(tid, 2, kIn / 8)) = c2;
+        *reinterpret_cast<uint4*>(a1 + kmaj_off(tid, 3, kIn / 8)) = c3;
+        *reinterpret_cast<uint4*>(a1 + kmaj_off(tid, 4, kIn / 8)) = c4;
+        *reinterpret_cast<uint4*>(a1 + kmaj_off(tid, 5, kIn / 8)) = make_uint4(0, 0, 0, 0);
+        fence_async_smem();
+        tc_before_sync();
+        __syncthreads();
+        tc_after_sync();
+        if (tid == 0) {
 #pragma unroll
-    for (int kt = 0; kt < 8; ++kt) {
-        const int c0 = kt * 16 + 2 * tq;
-        a2[kt][0] = pack2(fmaxf(acc[2 * kt][0] + sb1[c0], 0.f), fmaxf(acc[2 * kt][1] + sb1[c0 + 1], 0.f));
-        a2[kt][1] = pack2(fmaxf(acc[2 * kt][2] + sb1[c0], 0.f), fmaxf(acc[2 * kt][3] + sb1[c0 + 1], 0.f));
-        a2[kt][2] = pack2(fmaxf(acc[2 * kt + 1][0] + sb1[c0 + 8], 0.f), fmaxf(acc[2 * kt + 1][1] + sb1[c0 + 9], 0.f));
-        a2[kt][3] = pack2(fmaxf(acc[2 * kt + 1][2] + sb1[c0 + 8], 0.f), fmaxf(acc[2 * kt + 1][3] + sb1[c0 + 9], 0.f));
-        if (TRAIN) {
-            if (ok[0]) {
-                *reinterpret_cast<uint32_t*>(P.h1 + rr[0] * kH + c0) = a2[kt][0];
-                *reinterpret_cast<uint32_t*>(P.h1 + rr[0] * kH + c0 + 8) = a2[kt][2];
+            for (int k = 0; k < kIn / 16; ++k)
+                umma_f16(tmem, kmaj_desc(sbase + kSA1 + k * 256, kIn / 8),
+                         kmaj_desc(sbase + kSW1 + k * 256, kIn / 8), kIdesc, k > 0);
+            umma_commit(bar);
+        }
+        if (__syncthreads_or(!mbar_wait(bar, phase))) { if (tid == 0) atomicExch(P.err, 1); break; }
+        phase ^= 1u;
+        tc_after_sync();
+        // ---- layer-1 epilogue: bias, ReLU, fp16 -> A operand of layer 2
+#pragma unroll
+        for (int cb = 0; cb < kH / 32; ++cb) {
+            uint32_t acc[32];
+            tmem_ld32(t1 + cb * 32, acc);
+#pragma unroll
+            for (int j = 0; j < 4; ++j) {
+                const int c = cb * 32 + j * 8;
+                const float4 bl = *reinterpret_cast<const float4*>(sb1 + c);
+                const float4 bh = *reinterpret_cast<const float4*>(sb1 + c + 4);
+                const float* a = reinterpret_cast<const float*>(acc) + j * 8;
+                const uint4 w = make_uint4(pack2(fmaxf(a[0] + bl.x, 0.f), fmaxf(a[1] + bl.y, 0.f)),
+                                           pack2(fmaxf(a[2] + bl.z, 0.f), fmaxf(a[3] + bl.w, 0.f)),
+                                           pack2(fmaxf(a[4] + bh.x, 0.f), fmaxf(a[5] + bh.y, 0.f)),
+                                           pack2(fmaxf(a[6] + bh.z, 0.f), fmaxf(a[7] + bh.w, 0.f)));
+                *reinterpret_cast<uint4*>(sm + kSA2 + kmaj_off(tid, cb * 4 + j, kH / 8)) = w;
+                if (TRAIN && ok) *reinterpret_cast<uint4*>(P.h1 + r * kH + c) = w;
             }
-            if (ok[1]) {
-                *reinterpret_cast<uint32_t*>(P.h1 + rr[1] * kH + c0) = a2[kt][1];
-                *reinterpret_cast<uint32_t*>(P.h1 + rr[1] * kH + c0 + 8) = a2[kt][3];
+        }
+        fence_async_smem();
+        tc_before_sync();
+        __syncthreads();
+        tc_after_sync();
+        if (tid == 0) {
+#pragma unroll
+            for (int k = 0; k < kH / 16; ++k)
+                umma_f16(tmem + 128, kmaj_desc(sbase + kSA2 + k * 256, kH / 8),
+                         kmaj_desc(sbase + kSW2 + k * 256, kH / 8), kIdesc, k > 0);
+            umma_commit(bar);
+        }
+        if (__syncthreads_or(!mbar_wait(bar, phase))) { if (tid == 0) atomicExch(P.err, 1); break; }
+        phase ^= 1u;
+        tc_after_sync();
+        // ---- layer-2 epilogue: bias, ReLU, head
+        float sacc = 0.f;
+#pragma unroll
+        for (int cb = 0; cb < kH / 32; ++cb) {
+            uint32_t acc[32];
+            tmem_ld32(t2 + cb * 32, acc);
+#pragma unroll
+            for (int j = 0; j < 8; ++j) {
+                const int c = cb * 32 + j * 4;
+                const float4 b = *reinterpret_cast<const float4*>(sb2 + c);
+                const float4 w = *reinterpret_cast<const float4*>(sw3 + c);
+                const float* a = reinterpret_cast<const float*>(acc) + j * 4;
+                const float4 h = make_float4(fmaxf(a[0] + b.x, 0.f), fmaxf(a[1] + b.y, 0.f),
+                                             fmaxf(a[2] + b.z, 0.f), fmaxf(a[3] + b.w, 0.f));
+                sacc = fmaf(h.x, w.x, sacc);
+                sacc = fmaf(h.y, w.y, sacc);
+                sacc = fmaf(h.z, w.z, sacc);
+                sacc = fmaf(h.w, w.w, sacc);
+                if (TRAIN && ok) *reinterpret_cast<float4*>(P.h2 + r * kH + c) = h;
             }
         }
+        if (ok) P.s[r] = sacc + b3;
+        // every warp's TMEM reads are done before the next tile's MMAs overwrite D
+        tc_before_sync();
+        __syncthreads();
+        tc_after_sync();
     }
-    // ---- layer 2: [16 x 128] x [128 x 128]
-#pragma unroll
-    for (int nt = 0; nt < 16; ++nt) acc[nt][0] = acc[nt][1] = acc[nt][2] = acc[nt][3] = 0.f;
-#pragma unroll
-    for (int kt = 0; kt < 8; ++kt) {
-#pragma unroll
-        for (int nt = 0; nt < 16; ++nt) {
-            const __half* wb = sW2t + (nt * 8 + g) * kH + kt * 16 + 2 * tq;
-            mma16816(acc[nt], a2[kt], *reinterpret_cast<const uint32_t*>(wb),
-                     *reinterpret_cast<const uint32_t*>(wb + 8));
-        }
-    }
-    // ---- bias + ReLU, head dot product (quad reduction over the 4 lanes of a row)
-    float s0 = 0.f, s1 = 0.f;
-#pragma unroll
-    for (int nt = 0; nt < 16; ++nt) {
-        const int c = nt * 8 + 2 * tq;
-        const float h00 = fmaxf(acc[nt][0] + sb2[c], 0.f), h01 = fmaxf(acc[nt][1] + sb2[c + 1], 0.f);
-        const float h10 = fmaxf(acc[nt][2] + sb2[c], 0.f), h11 = fmaxf(acc[nt][3] + sb2[c + 1], 0.f);
-        s0 += h00 * sw3[c] + h01 * sw3[c + 1];
-        s1 += h10 * sw3[c] + h11 * sw3[c + 1];
-        if (TRAIN) {
-            if (ok[0]) *reinterpret_cast<float2*>(P.h2 + rr[0] * kH + c) = make_float2(h00, h01);
-            if (ok[1]) *reinterpret_cast<float2*>(P.h2 + rr[1] * kH + c) = make_float2(h10, h11);
-        }
-    }
-    s0 += __shfl_xor_sync(0xffffffffu, s0, 1);
-    s0 += __shfl_xor_sync(0xffffffffu, s0, 2);
-    s1 += __shfl_xor_sync(0xffffffffu, s1, 1);
-    s1 += __shfl_xor_sync(0xffffffffu, s1, 2);
-    if (tq == 0) {
-        if (ok[0]) P.s[rr[0]] = s0 + b3;
-        if (ok[1]) P.s[rr[1]] = s1 + b3;
-    }
+    tc_before_sync();
+    __syncthreads();
+    tc_after_sync();
+    if (warp == 0) tmem_dealloc(tmem, kTmemCols);
 }
 
 // ---------------------------------------------------------------------------
@@ -517,6 +634,7 @@ struct MlpState {
     __half* W1t = nullptr;
     __half* W2t = nullptr;
     __half* W2h = nullptr;
+    int* err = nullptr;          // device flag: a bounded wait of the forward kernel gave up
     long long adam_t = 0;
     // scratch
     size_t feat_pairs = 0;
@@ -572,12 +690,13 @@ int mlp_state(mcs_ctx* c, MlpState** out) {
         CKM(cudaMalloc((void**)&m->W2t, sizeof(__half) * kH * kH));
         CKM(cudaMalloc((void**)&m->W2h, sizeof(__half) * kH * kH));
         CKM(cudaMalloc((void**)&m->loss, sizeof(float)));
+        CKM(cudaMalloc((void**)&m->err, sizeof(int)));
+        CKM(cudaMemset(m->err, 0, sizeof(int)));
     }
     *out = c->mlp;
     return 0;
 }
 
-size_t fwd_smem() { return sizeof(__half) * (kH * kIn + kH * kH) + sizeof(float) * 3 * kH; }
 
 int run_features(mcs_ctx* c, MlpState* m, int npairs, const int32_t* d_n, const int64_t* d_adj_off,
                  const uint8_t* d_adj, const int64_t* d_lab_off, const int32_t* d_labels,
@@ -604,17 +723,19 @@ int run_features(mcs_ctx* c, MlpState* m, int npairs, const int32_t* d_n, const 
 }
 
 template <bool TRAIN>
-int run_forward(MlpState* m, int npairs, long long nrows, const int32_t* rows, const int32_t* d_n,
-                float* out_s, cudaStream_t s) {
+int run_forward(const mcs_ctx* c, MlpState* m, int npairs, long long nrows, const int32_t* rows,
+                const int32_t* d_n, float* out_s, cudaStream_t s) {
     FwdParams P;
     P.nrows = nrows; P.npairs = npairs; P.rows = rows; P.n = d_n; P.feat16 = m->feat16;
     P.W1t = m->W1t; P.W2t = m->W2t;
     P.b1 = m->theta + kOffB1; P.b2 = m->theta + kOffB2; P.w3 = m->theta + kOffW3; P.b3 = m->theta + kOffB3;
     P.s = out_s; P.h1 = TRAIN ? m->h1 : nullptr; P.h2 = TRAIN ? m->h2 : nullptr;
-    const size_t sm = fwd_smem();
-    CKM(cudaFuncSetAttribute(mlp_fwd_kernel<TRAIN>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm));
-    const long long blocks = (nrows + 127) / 128;
-    if (blocks > 0) mlp_fwd_kernel<TRAIN><<<(unsigned)blocks, 256, sm, s>>>(P);
+    P.err = m->err;
+    CKM(cudaFuncSetAttribute(mlp_fwd_kernel<TRAIN>, cudaFuncAttributeMaxDynamicSharedMemorySize, kFwdSmem));
+    const long long ntiles = (nrows + kTile - 1) / kTile;
+    // persistent: two CTAs per SM (shared memory and TMEM admit two)
+    const long long grid = ntiles < 2LL * c->sms ? ntiles : 2LL * c->sms;
+    if (grid > 0) mlp_fwd_kernel<TRAIN><<<(unsigned)grid, kTile, kFwdSmem, s>>>(P, ntiles);
     CKM(cudaGetLastError());
     return 0;
 }
@@ -639,11 +760,11 @@ int ensure_train(MlpState* m, size_t B) {
 }
 
 // loss (sum over rows) and per-row gradient sums for the B rows in brows/by/bw
-int run_backward(MlpState* m, int npairs, int B, const int32_t* rows, const float* y, const float* w,
+int run_backward(const mcs_ctx* c, MlpState* m, int npairs, int B, const int32_t* rows, const float* y, const float* w,
                  cudaStream_t s) {
     CKM(cudaMemsetAsync(m->grad, 0, sizeof(float) * kNParams, s));
     CKM(cudaMemsetAsync(m->loss, 0, sizeof(float), s));
-    int rc = run_forward<true>(m, npairs, B, rows, nullptr, m->s, s);
+    int rc = run_forward<true>(c, m, npairs, B, rows, nullptr, m->s, s);
     if (rc) return rc;
     HeadParams hp;
     hp.nrows = B; hp.s = m->s; hp.y = y; hp.w = w; hp.h2 = m->h2; hp.w3 = m->theta + kOffW3;
@@ -697,6 +818,17 @@ int upload_model(mcs_ctx* c, MlpState* m, const float* params) {
     return 0;
 }
 
+// reads and clears the forward kernel's stall flag (the stream is idle)
+int check_stall(MlpState* m, cudaStream_t s) {
+    int e = 0;
+    CKM(cudaMemcpyAsync(&e, m->err, sizeof(int), cudaMemcpyDeviceToHost, s));
+    CKM(cudaStreamSynchronize(s));
+    if (!e) return 0;
+    CKM(cudaMemsetAsync(m->err, 0, sizeof(int), s));
+    snprintf(g_mlp_detail, sizeof(g_mlp_detail), "mlp_fwd_kernel: tensor-core completion wait gave up");
+    return MCS_ERR_DEVICE_STALL;
+}
+
 }  // namespace
 
 // Used by run_device (mcs_api.cu) for MCS_ORDER_LEARNED: features, scores of
@@ -712,7 +844,7 @@ int mcs_order_prepare(mcs_ctx* c, int npairs, const int32_t* d_n, const int64_t*
     size_t cap = m->score_rows;
     if ((rc = grow(m->S, cap, (size_t)npairs * 4096))) return rc;
     m->score_rows = cap;
-    if ((rc = run_forward<false>(m, npairs, (long long)npairs * 4096, nullptr, d_n, m->S, s))) return rc;
+    if ((rc = run_forward<false>(c, m, npairs, (long long)npairs * 4096, nullptr, d_n, m->S, s))) return rc;
     cap = m->vs_pairs;
     if ((rc = grow(m->vscore, cap, (size_t)npairs * 2 * kMaxN))) return rc;
     m->vs_pairs = cap;
@@ -788,15 +920,16 @@ int mcs_order_eval(mcs_ctx* c, int32_t npairs, const int32_t* d_n, const int64_t
     if (nrows > 0 && (h_scores || h_loss || h_grad)) {
         if ((rc = ensure_train(m, (size_t)nrows))) return rc;
         if (h_loss || h_grad) {
-            if ((rc = run_backward(m, npairs, nrows, d_rows, d_y, d_w, s))) return rc;
+            if ((rc = run_backward(c, m, npairs, nrows, d_rows, d_y, d_w, s))) return rc;
         } else {
-            if ((rc = run_forward<false>(m, npairs, nrows, d_rows, d_n, m->s, s))) return rc;
+            if ((rc = run_forward<false>(c, m, npairs, nrows, d_rows, d_n, m->s, s))) return rc;
         }
         if (h_scores) CKM(cudaMemcpyAsync(h_scores, m->s, sizeof(float) * nrows, cudaMemcpyDeviceToHost, s));
         if (h_grad) CKM(cudaMemcpyAsync(h_grad, m->grad, sizeof(float) * kNParams, cudaMemcpyDeviceToHost, s));
         if (h_loss) CKM(cudaMemcpyAsync(h_loss, m->loss, sizeof(float), cudaMemcpyDeviceToHost, s));
     }
     CKM(cudaStreamSynchronize(s));
+    if ((rc = check_stall(m, s))) return rc;
     // the device sums over rows; report means
     if (nrows > 0) {
         if (h_loss) *h_loss /= (float)nrows;
@@ -829,7 +962,7 @@ int mcs_order_train(mcs_ctx* c, int32_t npairs, const int32_t* d_n, const int64_
                                                           (unsigned long long)(m->adam_t + 1), m->brows,
                                                           m->by, m->bw);
         if (cudaGetLastError() != cudaSuccess) { rc = MCS_ERR_CUDA; break; }
-        if ((rc = run_backward(m, npairs, batch, m->brows, m->by, m->bw, s))) break;
+        if ((rc = run_backward(c, m, npairs, batch, m->brows, m->by, m->bw, s))) break;
         cudaMemcpyAsync(d_losses + t, m->loss, sizeof(float), cudaMemcpyDeviceToDevice, s);
         m->adam_t += 1;
         const float c1 = 1.f - powf(b1, (float)m->adam_t), c2 = 1.f - powf(b2, (float)m->adam_t);
@@ -846,7 +979,22 @@ int mcs_order_train(mcs_ctx* c, int32_t npairs, const int32_t* d_n, const int64_
             for (int t = 0; t < steps; ++t) h_loss_per_step[t] = losses[t] / (float)batch;
     }
     cudaFree(d_losses);
+    if (rc == 0) rc = check_stall(m, s);
     return rc;
+}
+
+int mcs_order_score_grid(mcs_ctx* c, int32_t npairs, const int32_t* d_n, const int64_t* d_adj_off,
+                         const uint8_t* d_adj, const int64_t* d_lab_off, const int32_t* d_labels,
+                         uint32_t flags, float* d_scores, void* stream) {
+    if (!c || npairs < 0 || (npairs > 0 && (!d_n || !d_adj_off || !d_adj || !d_scores))) return MCS_ERR_ARG;
+    if (!c->mlp || !c->mlp->has_model) return MCS_ERR_ARG;
+    if (npairs == 0) return 0;
+    if (cudaSetDevice(c->device) != cudaSuccess) return MCS_ERR_CUDA;
+    MlpState* m = c->mlp;
+    cudaStream_t s = stream ? (cudaStream_t)stream : c->stream;
+    int rc = run_features(c, m, npairs, d_n, d_adj_off, d_adj, d_lab_off, d_labels, flags, false, s);
+    if (rc) return rc;
+    return run_forward<false>(c, m, npairs, (long long)npairs * 4096, nullptr, d_n, d_scores, s);
 }
 
 }  // extern "C"

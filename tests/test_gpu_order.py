@@ -109,6 +109,51 @@ def test_forward_and_gradient_match_reference(solver):
         assert err <= 1e-2 * np.linalg.norm(ref) + 1e-7, (o, n, err, np.linalg.norm(ref))
 
 
+def test_forward_many_tiles_matches_reference(solver):
+    """Rows mode over many 128-row tiles of the tensor-core forward pass, with
+    a ragged last tile and pairs of every size up to 64 vertices."""
+    from paper_1908_06418_b300 import DeviceBatch
+    pairs = _pairs(24, 23, labelled=True, nmin=1, nmax=64)
+    rows, _ = _rows(pairs, 211, 8)                          # 5,064 rows: 39 full tiles + 72
+    theta = mlp.init_params(13) + np.random.default_rng(6).normal(0, 0.05, mlp.N_PARAMS)
+    theta[mlp.D_IN * mlp.H:mlp.D_PAD * mlp.H] = 0.0
+    theta32 = theta.astype(np.float32)
+    solver.set_order_model(theta32)
+    got = solver.order_eval(DeviceBatch(pairs), rows=rows, scores=True)["scores"]
+    s_ref, _ = mlp.forward(_device_view(theta32), _inputs(pairs, rows), round_h1_fp16=True)
+    assert np.max(np.abs(got - s_ref)) <= 2e-3 * max(1.0, np.max(np.abs(s_ref)))
+
+
+def test_grid_scores_match_reference(solver):
+    """The all-pairs pass (what MCS_ORDER_LEARNED runs before a search): every
+    valid (v, u) of every pair against the fp64 reference; entries outside
+    v < n_G, u < n_H are not written."""
+    import torch
+    from paper_1908_06418_b300 import DeviceBatch
+    pairs = _pairs(20, 25, labelled=True, nmin=1, nmax=64)
+    pairs[3] = synth.Pair(synth.Graph(np.zeros((64, 64), np.uint8), np.zeros(64, np.int32)), pairs[3].H)
+    pairs[5] = synth.Pair(pairs[5].G, synth.Graph(np.ones((1, 1), np.uint8), np.zeros(1, np.int32)))
+    theta = mlp.init_params(17) + np.random.default_rng(7).normal(0, 0.05, mlp.N_PARAMS)
+    theta[mlp.D_IN * mlp.H:mlp.D_PAD * mlp.H] = 0.0
+    theta32 = theta.astype(np.float32)
+    solver.set_order_model(theta32)
+    b = DeviceBatch(pairs)
+    sentinel = 12345.0
+    out = torch.full((len(pairs), 64, 64), sentinel, dtype=torch.float32, device=b.device)
+    solver.order_score_grid(b, out=out)
+    torch.cuda.synchronize()
+    got = out.cpu().numpy()
+    th = _device_view(theta32)
+    for i, p in enumerate(pairs):
+        rows = np.array([(i, v, u) for v in range(p.G.n) for u in range(p.H.n)], np.int32)
+        s_ref, _ = mlp.forward(th, _inputs(pairs, rows), round_h1_fp16=True)
+        g = got[i, :p.G.n, :p.H.n].reshape(-1)
+        assert np.max(np.abs(g - s_ref)) <= 2e-3 * max(1.0, np.max(np.abs(s_ref))), i
+        mask = np.ones((64, 64), bool)
+        mask[:p.G.n, :p.H.n] = False
+        assert np.all(got[i][mask] == sentinel), i
+
+
 def test_training_lowers_the_loss(solver):
     from paper_1908_06418_b300 import DeviceBatch
     pairs = _pairs(16, 31)
