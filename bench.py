@@ -534,6 +534,7 @@ def main():
         line["order_comparison"] = {"learned": one_pass(0), "plain": one_pass(MCS_ORDER_LEARNED),
                                     "note": "one pass each over the whole batch; exact either way, "
                                             "solved = proven within the per-pair limit"}
+        line["mlp"] = mlp_roofline(solver, groups, pairs, stream)
     if rank == 0 and not a.no_single:
         line["single_instance"] = single_instance_vs_batch(
             solver, pairs, a, batch_flags=MCS_ORDER_LEARNED if learned else 0)
@@ -548,6 +549,53 @@ def main():
     solver.close()
     if dist:
         dist.destroy_process_group()
+
+
+def mlp_roofline(solver, groups, pairs, stream, reps=20):
+    """The all-pairs scoring pass of the learned order (vertex features, then
+    the tcgen05 MLP forward over every (v, u) of every pair) on the bench's
+    batch, timed with CUDA events on its stream.  Algorithmic work counts the
+    valid rows only (v < n_G, u < n_H) at 2 x (36 x 128 + 128 x 128 + 128)
+    flops each (the unpadded network); the time includes the features kernel,
+    so the fraction is a lower bound for the forward kernel alone."""
+    import torch
+    from types import SimpleNamespace
+    peak, src = _tensor_peak()
+    outs, views = [], []
+    for g in groups:
+        views.append(SimpleNamespace(npairs=g["n"], d_n=g["d_n"], d_adj_off=g["d_adj_off"], d_adj=g["d_adj"],
+                                     d_lab_off=g["d_lab_off"], d_labels=g["d_labels"], flags=g["flags"],
+                                     device=g["d_n"].device))
+        outs.append(torch.empty((g["n"], 64, 64), dtype=torch.float32, device=g["d_n"].device))
+    for _ in range(3):
+        for v, o in zip(views, outs):
+            solver.order_score_grid(v, out=o, stream=stream)
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    for _ in range(reps):
+        for v, o in zip(views, outs):
+            solver.order_score_grid(v, out=o, stream=stream)
+    e1.record(stream)
+    stream.synchronize()
+    ms = e0.elapsed_time(e1) / reps
+    rows = sum(p.G.n * p.H.n for p in pairs)
+    tflops = rows * 2.0 * (36 * 128 + 128 * 128 + 128) / (ms * 1e-3) / 1e12
+    return {"bound": "tensor", "kernel": "mlp_fwd_kernel (tcgen05.mma kind::f16, TMEM accumulators)",
+            "rows": rows, "ms_per_pass": ms, "rows_per_s": rows / (ms * 1e-3),
+            "achieved": tflops, "peak": peak, "unit": "TFLOP/s", "frac": tflops / peak,
+            "peak_source": src,
+            "note": "features + forward per pass, inputs resident; fp16 operands, fp32 accumulation"}
+
+
+def _tensor_peak():
+    """Dense fp16 tensor peak: the measured bf16 burst figure (fp16 and bf16
+    run at the same nominal dense rate on this part)."""
+    path = os.path.join(os.path.dirname(os.path.abspath(__file__)), "MEASURED_PEAKS.json")
+    try:
+        with open(path) as f:
+            return float(json.load(f)["bf16_tflops"]), "of measured (bf16 burst; fp16 nominal ratio 1)"
+    except (OSError, KeyError, ValueError):
+        return 1800.0, "of fallback (1.8 PFLOP/s bf16 burst; fp16 nominal ratio 1)"
 
 
 # ---------------------------------------------------------------------------

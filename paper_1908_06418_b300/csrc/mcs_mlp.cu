@@ -198,6 +198,12 @@ __device__ __forceinline__ void tmem_ld32(uint32_t taddr, uint32_t (&r)[32]) {
     asm volatile("tcgen05.wait::ld.sync.aligned;" : "+r"(r[0]), "+r"(r[1]), "+r"(r[2]), "+r"(r[3]), "+r"(r[4]), "+r"(r[5]), "+r"(r[6]), "+r"(r[7]), "+r"(r[8]), "+r"(r[9]), "+r"(r[10]), "+r"(r[11]), "+r"(r[12]), "+r"(r[13]), "+r"(r[14]), "+r"(r[15]), "+r"(r[16]), "+r"(r[17]), "+r"(r[18]), "+r"(r[19]), "+r"(r[20]), "+r"(r[21]), "+r"(r[22]), "+r"(r[23]), "+r"(r[24]), "+r"(r[25]), "+r"(r[26]), "+r"(r[27]), "+r"(r[28]), "+r"(r[29]), "+r"(r[30]), "+r"(r[31]) :: "memory");
 }
 
+__device__ __forceinline__ void tmem_ld16(uint32_t taddr, uint32_t (&r)[16]) {
+    asm volatile("tcgen05.ld.sync.aligned.32x32b.x16.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15}, [%16];"
+                 : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7]), "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]), "=r"(r[14]), "=r"(r[15]) : "r"(taddr));
+    asm volatile("tcgen05.wait::ld.sync.aligned;" : "+r"(r[0]), "+r"(r[1]), "+r"(r[2]), "+r"(r[3]), "+r"(r[4]), "+r"(r[5]), "+r"(r[6]), "+r"(r[7]), "+r"(r[8]), "+r"(r[9]), "+r"(r[10]), "+r"(r[11]), "+r"(r[12]), "+r"(r[13]), "+r"(r[14]), "+r"(r[15]) :: "memory");
+}
+
 // Shared-memory operand layout for the MMAs: no swizzle, K-major.  The tile is
 // cut into 8-row x 16-byte core matrices (8 rows x 8 fp16); the cores of one
 // 8-row group are consecutive along K (128 B apart: the leading byte offset)
@@ -213,149 +219,195 @@ __device__ __forceinline__ uint64_t kmaj_desc(uint32_t saddr, int kchunks) {
 }
 
 constexpr int kTile = 128;                            // rows per tile = MMA M = TMEM lanes
-constexpr uint32_t kTmemCols = 256;                   // layer 1: columns 0..127, layer 2: 128..255
+constexpr int kWorkers = 4;                           // independent 128-row pipelines per CTA
+constexpr uint32_t kTmemCols = 512;                   // 128 per worker; layer 2 reuses layer 1's
+constexpr int kK2 = kH + 16;                          // layer-2 K: h1 (128), then [1, 0 x 15] for b2
 // instruction descriptor, kind::f16: D f32 (bits 4-5 = 1), A and B f16 (bits 7-12 = 0),
 // both K-major (bits 15-16 = 0), N >> 3 at bit 17, M >> 4 at bit 24
 constexpr uint32_t kIdesc = (1u << 4) | ((uint32_t)(kH >> 3) << 17) | ((uint32_t)(kTile >> 4) << 24);
-constexpr int kSW1 = 0;                               // W1t  128 x 48 fp16
-constexpr int kSW2 = kSW1 + kH * kIn * 2;             // W2t  128 x 128
-constexpr int kSA1 = kSW2 + kH * kH * 2;              // x    128 x 48
-constexpr int kSA2 = kSA1 + kTile * kIn * 2;          // h1   128 x 128
-constexpr int kSBias = kSA2 + kTile * kH * 2;         // b1, b2, w3 (fp32)
-constexpr int kSBar = kSBias + 3 * kH * 4;            // mbarrier, TMEM base address
-constexpr int kFwdSmem = kSBar + 16;
-// more than a third of the SM's shared memory: at most two CTAs (512 TMEM
-// columns) per SM, so the allocation never waits
-static_assert(3 * (kFwdSmem + 1024) > 228 * 1024, "TMEM columns could be oversubscribed");
+constexpr int kSW1 = 0;                               // [W1t | b1 at input 36]  128 x 48 fp16
+constexpr int kSW2 = kSW1 + kH * kIn * 2;             // [W2t | b2 at k = 128]   128 x 144
+constexpr int kSWork = kSW2 + kH * kK2 * 2;           // per worker: A operand, 128 x 144 (x aliases it)
+constexpr int kWBytes = kTile * kK2 * 2;
+constexpr int kSW3 = kSWork + kWorkers * kWBytes;     // w3 (fp32)
+constexpr int kSBar = kSW3 + kH * 4;                  // one mbarrier per worker, then the TMEM base
+constexpr int kFwdSmem = kSBar + 8 * kWorkers + 16;
+static_assert(kFwdSmem <= 227 * 1024, "shared memory per CTA");
+// more than half of the SM's shared memory: one CTA per SM, so its 512 TMEM
+// columns are the whole of the SM's tensor memory and the allocation never waits
+static_assert(2 * (kFwdSmem + 1024) > 228 * 1024, "TMEM columns could be oversubscribed");
 
-// One CTA (4 warps) computes 128 rows at a time, persistent over the tiles:
-// gather x into shared memory, layer 1 = 3 MMAs (K = 48) into TMEM, bias +
-// ReLU + fp16 by the thread owning the row into shared memory, layer 2 = 8
-// MMAs (K = 128), bias + ReLU + head dot product per thread (row t of the tile
-// is TMEM lane t, read by thread t).  Grid mode (P.rows == null) skips tiles
-// whose two rows v are both >= n_G.
+// barrier over the 128 threads of one worker (ids 1..kWorkers; 0 is __syncthreads)
+__device__ __forceinline__ void worker_sync(int wk) {
+    asm volatile("bar.sync %0, %1;" :: "r"(wk + 1), "r"(kTile) : "memory");
+}
+__device__ __forceinline__ bool worker_any(int wk, bool x) {
+    uint32_t out;
+    asm volatile("{\n\t.reg .pred p, q;\n\tsetp.ne.u32 p, %1, 0;\n\t"
+                 "bar.red.or.pred q, %2, %3, p;\n\tselp.u32 %0, 1, 0, q;\n}"
+                 : "=r"(out) : "r"((uint32_t)x), "r"(wk + 1), "r"(kTile) : "memory");
+    return out != 0;
+}
+__device__ __forceinline__ void worker_fence_sync(int wk) {
+    tc_before_sync();
+    worker_sync(wk);
+    tc_after_sync();
+}
+// (relu(lo), relu(hi)) rounded to fp16 and packed, lo in the low half
+__device__ __forceinline__ uint32_t relu_pack2(float lo, float hi) {
+    uint32_t d;
+    asm("cvt.rn.relu.f16x2.f32 %0, %1, %2;" : "=r"(d) : "f"(hi), "f"(lo));
+    return d;
+}
+
+// The next tile this worker computes after t (grid mode skips tiles whose
+// two rows v are both >= n_G), or ntiles.
+__device__ __forceinline__ long long next_tile(const FwdParams& P, long long t, long long stride, long long ntiles) {
+    for (; t < ntiles; t += stride) {
+        if (P.rows) return t;
+        const int p = (int)(t >> 5), v0 = (int)(t & 31) * 2;
+        if (v0 < P.n[2 * p] && P.n[2 * p + 1] > 0) return t;
+    }
+    return ntiles;
+}
+
+// The network input of one row as 5 core-matrix rows (the sixth is [1, 0..]):
+// x = [f_G(v) (18), f_H(u) (18), 1 (the b1 input), 0 (11)].
+struct XRow { uint4 c[5]; bool ok; };
+__device__ __forceinline__ XRow gather_x(const FwdParams& P, long long r) {
+    XRow x;
+    int p = 0, v = 0, u = 0;
+    x.ok = row_of(P, r, p, v, u);
+    const uint4 z = make_uint4(0, 0, 0, 0);
+    x.c[0] = x.c[1] = x.c[2] = x.c[3] = z;
+    x.c[4] = make_uint4(0, 0, 0x3C00u, 0);                // fp16 1.0 at input 36 (b1)
+    if (x.ok) {
+        const __half* fg = P.feat16 + ((size_t)(2 * p) * kMaxN + v) * kFP;
+        const __half* fh = P.feat16 + ((size_t)(2 * p + 1) * kMaxN + u) * kFP;
+        const uint4 g0 = reinterpret_cast<const uint4*>(fg)[0], g1 = reinterpret_cast<const uint4*>(fg)[1];
+        const uint4 h0 = reinterpret_cast<const uint4*>(fh)[0], h1 = reinterpret_cast<const uint4*>(fh)[1];
+        const uint32_t g8 = reinterpret_cast<const uint32_t*>(fg)[8];
+        const uint32_t h8 = reinterpret_cast<const uint32_t*>(fh)[8];
+        x.c[0] = g0; x.c[1] = g1;
+        x.c[2] = make_uint4(g8, h0.x, h0.y, h0.z);
+        x.c[3] = make_uint4(h0.w, h1.x, h1.y, h1.z);
+        x.c[4] = make_uint4(h1.w, h8, 0x3C00u, 0u);
+    }
+    return x;
+}
+
+// One CTA per SM, persistent: kWorkers groups of 4 warps each take 128-row
+// tiles independently (their own operand buffer, mbarrier and 128 TMEM
+// columns; the weights are shared).  Per tile: x into shared memory, layer 1
+// = 3 MMAs (K = 48, the bias through a constant-1 input) into TMEM, ReLU +
+// fp16 by the thread owning the row into shared memory, layer 2 = 9 MMAs
+// (K = 144: h1 and a constant-1 column for the bias) into the same columns,
+// ReLU + head dot product per thread (row t of the tile is TMEM lane t, read
+// by thread t of the worker: warp j of a worker reads lanes 32j..32j+31).
+// The next tile's inputs are loaded while the current one computes.  Biases
+// b1 and b2 therefore enter as fp16, like the weights.
 template <bool TRAIN>
-__global__ void __launch_bounds__(kTile, 1) mlp_fwd_kernel(FwdParams P, long long ntiles) {
+__global__ void __launch_bounds__(kTile * kWorkers, 1) mlp_fwd_kernel(FwdParams P, long long ntiles) {
     extern __shared__ __align__(1024) unsigned char sm[];
     const int tid = threadIdx.x, warp = tid >> 5;
+    const int wk = tid / kTile, rt = tid % kTile;
     const uint32_t sbase = smem_u32(sm);
-    for (int i = tid; i < kH * (kIn / 8); i += kTile) {
+    // weights with the biases as one more input: W1 column 36 = b1, W2 column 128 = b2
+    for (int i = tid; i < kH * (kIn / 8); i += kTile * kWorkers) {
         const int n = i / (kIn / 8), kc = i % (kIn / 8);
-        *reinterpret_cast<uint4*>(sm + kSW1 + kmaj_off(n, kc, kIn / 8)) =
-            *reinterpret_cast<const uint4*>(P.W1t + n * kIn + kc * 8);
+        uint4 w = *reinterpret_cast<const uint4*>(P.W1t + n * kIn + kc * 8);
+        if (kc == 4) w.z = (uint32_t)__half_as_ushort(__float2half_rn(P.b1[n]));   // inputs 36, 37
+        *reinterpret_cast<uint4*>(sm + kSW1 + kmaj_off(n, kc, kIn / 8)) = w;
     }
-    for (int i = tid; i < kH * (kH / 8); i += kTile) {
-        const int n = i / (kH / 8), kc = i % (kH / 8);
-        *reinterpret_cast<uint4*>(sm + kSW2 + kmaj_off(n, kc, kH / 8)) =
-            *reinterpret_cast<const uint4*>(P.W2t + n * kH + kc * 8);
+    for (int i = tid; i < kH * (kK2 / 8); i += kTile * kWorkers) {
+        const int n = i / (kK2 / 8), kc = i % (kK2 / 8);
+        uint4 w = make_uint4(0, 0, 0, 0);
+        if (kc < kH / 8) w = *reinterpret_cast<const uint4*>(P.W2t + n * kH + kc * 8);
+        else if (kc == kH / 8) w.x = (uint32_t)__half_as_ushort(__float2half_rn(P.b2[n]));
+        *reinterpret_cast<uint4*>(sm + kSW2 + kmaj_off(n, kc, kK2 / 8)) = w;
     }
-    float* sb1 = reinterpret_cast<float*>(sm + kSBias);
-    float* sb2 = sb1 + kH;
-    float* sw3 = sb2 + kH;
-    for (int i = tid; i < kH; i += kTile) { sb1[i] = P.b1[i]; sb2[i] = P.b2[i]; sw3[i] = P.w3[i]; }
-    const uint32_t bar = sbase + kSBar;
-    uint32_t* tslot = reinterpret_cast<uint32_t*>(sm + kSBar + 8);
-    if (tid == 0) { mbar_init(bar, 1); mbar_init_fence(); }
+    float* sw3 = reinterpret_cast<float*>(sm + kSW3);
+    for (int i = tid; i < kH; i += kTile * kWorkers) sw3[i] = P.w3[i];
+    uint32_t* tslot = reinterpret_cast<uint32_t*>(sm + kSBar + 8 * kWorkers);
+    if (tid < kWorkers) { mbar_init(sbase + kSBar + 8 * tid, 1); mbar_init_fence(); }
     if (warp == 0) { tmem_alloc(smem_u32(tslot), kTmemCols); tmem_relinquish(); }
     fence_async_smem();
     tc_before_sync();
     __syncthreads();
     tc_after_sync();
-    const uint32_t tmem = *tslot;
-    const uint32_t lane_off = (uint32_t)(warp * 32) << 16;   // warp w reads TMEM lanes 32w..32w+31
-    const uint32_t t1 = tmem + lane_off, t2 = tmem + 128 + lane_off;
+    const uint32_t tmem = *tslot + (uint32_t)(wk * kH);            // this worker's columns
+    const uint32_t tl = tmem + ((uint32_t)((warp & 3) * 32) << 16);  // this warp's lanes
+    const uint32_t bar = sbase + kSBar + 8 * wk;
+    const uint32_t sA = sbase + kSWork + wk * kWBytes;
+    unsigned char* a = sm + kSWork + wk * kWBytes;
     const float b3 = *P.b3;
+    const long long stride = (long long)gridDim.x * kWorkers;
     uint32_t phase = 0;
-    for (long long t = blockIdx.x; t < ntiles; t += gridDim.x) {
-        if (!P.rows) {
-            const int p = (int)(t >> 5), v0 = (int)(t & 31) * 2;
-            if (v0 >= P.n[2 * p] || P.n[2 * p + 1] <= 0) continue;       // uniform over the CTA
-        }
-        const long long r = t * kTile + tid;
-        int p = 0, v = 0, u = 0;
-        const bool ok = row_of(P, r, p, v, u);
-        // x = [f_G(v) (18), f_H(u) (18), 0 (12)] as 24 fp16 pairs, 6 core-matrix rows
-        uint4 c0 = make_uint4(0, 0, 0, 0), c1 = c0, c2 = c0, c3 = c0, c4 = c0;
-        if (ok) {
-            const __half* fg = P.feat16 + ((size_t)(2 * p) * kMaxN + v) * kFP;
-            const __half* fh = P.feat16 + ((size_t)(2 * p + 1) * kMaxN + u) * kFP;
-            const uint4 g0 = reinterpret_cast<const uint4*>(fg)[0], g1 = reinterpret_cast<const uint4*>(fg)[1];
-            const uint4 h0 = reinterpret_cast<const uint4*>(fh)[0], h1 = reinterpret_cast<const uint4*>(fh)[1];
-            const uint32_t g8 = reinterpret_cast<const uint32_t*>(fg)[8];
-            const uint32_t h8 = reinterpret_cast<const uint32_t*>(fh)[8];
-            c0 = g0; c1 = g1;
-            c2 = make_uint4(g8, h0.x, h0.y, h0.z);
-            c3 = make_uint4(h0.w, h1.x, h1.y, h1.z);
-            c4 = make_uint4(h1.w, h8, 0u, 0u);
-        }
-        unsigned char* a1 = sm + kSA1;
-        *reinterpret_cast<uint4*>(a1 + kmaj_off(tid, 0, kIn / 8)) = c0;
-        *reinterpret_cast<uint4*>(a1 + kmaj_off(tid, 1, kIn / 8)) = c1;
-        *reinterpret_cast<uint4*>(a1 + kmaj_off(tid, 2, kIn / 8)) = c2;
-        *reinterpret_cast<uint4*>(a1 + kmaj_off(tid, 3, kIn / 8)) = c3;
-        *reinterpret_cast<uint4*>(a1 + kmaj_off(tid, 4, kIn / 8)) = c4;
-        *reinterpret_cast<uint4*>(a1 + kmaj_off(tid, 5, kIn / 8)) = make_uint4(0, 0, 0, 0);
+    long long t = next_tile(P, (long long)blockIdx.x * kWorkers + wk, stride, ntiles);
+    XRow x = gather_x(P, t * kTile + rt);
+    while (t < ntiles) {
+        const long long r = t * kTile + rt;
+        const bool ok = x.ok;
+        // x (K = 48) in the first 128 x 48 of the buffer, as layer 1's A operand
+#pragma unroll
+        for (int j = 0; j < 5; ++j) *reinterpret_cast<uint4*>(a + kmaj_off(rt, j, kIn / 8)) = x.c[j];
+        *reinterpret_cast<uint4*>(a + kmaj_off(rt, 5, kIn / 8)) = make_uint4(0, 0, 0, 0);
         fence_async_smem();
-        tc_before_sync();
-        __syncthreads();
-        tc_after_sync();
-        if (tid == 0) {
+        worker_fence_sync(wk);
+        if (rt == 0) {
 #pragma unroll
             for (int k = 0; k < kIn / 16; ++k)
-                umma_f16(tmem, kmaj_desc(sbase + kSA1 + k * 256, kIn / 8),
-                         kmaj_desc(sbase + kSW1 + k * 256, kIn / 8), kIdesc, k > 0);
+                umma_f16(tmem, kmaj_desc(sA + k * 256, kIn / 8), kmaj_desc(sbase + kSW1 + k * 256, kIn / 8),
+                         kIdesc, k > 0);
             umma_commit(bar);
         }
-        if (__syncthreads_or(!mbar_wait(bar, phase))) { if (tid == 0) atomicExch(P.err, 1); break; }
+        const long long tn = next_tile(P, t + stride, stride, ntiles);
+        x = gather_x(P, tn * kTile + rt);                 // in flight during this tile
+        if (worker_any(wk, !mbar_wait(bar, phase))) { if (rt == 0) atomicExch(P.err, 1); break; }
         phase ^= 1u;
         tc_after_sync();
-        // ---- layer-1 epilogue: bias, ReLU, fp16 -> A operand of layer 2
+        // ---- layer-1 epilogue: ReLU, fp16 -> A operand of layer 2 (overwrites x)
 #pragma unroll
-        for (int cb = 0; cb < kH / 32; ++cb) {
-            uint32_t acc[32];
-            tmem_ld32(t1 + cb * 32, acc);
+        for (int cb = 0; cb < kH / 16; ++cb) {
+            uint32_t acc[16];
+            tmem_ld16(tl + cb * 16, acc);
 #pragma unroll
-            for (int j = 0; j < 4; ++j) {
-                const int c = cb * 32 + j * 8;
-                const float4 bl = *reinterpret_cast<const float4*>(sb1 + c);
-                const float4 bh = *reinterpret_cast<const float4*>(sb1 + c + 4);
-                const float* a = reinterpret_cast<const float*>(acc) + j * 8;
-                const uint4 w = make_uint4(pack2(fmaxf(a[0] + bl.x, 0.f), fmaxf(a[1] + bl.y, 0.f)),
-                                           pack2(fmaxf(a[2] + bl.z, 0.f), fmaxf(a[3] + bl.w, 0.f)),
-                                           pack2(fmaxf(a[4] + bh.x, 0.f), fmaxf(a[5] + bh.y, 0.f)),
-                                           pack2(fmaxf(a[6] + bh.z, 0.f), fmaxf(a[7] + bh.w, 0.f)));
-                *reinterpret_cast<uint4*>(sm + kSA2 + kmaj_off(tid, cb * 4 + j, kH / 8)) = w;
-                if (TRAIN && ok) *reinterpret_cast<uint4*>(P.h1 + r * kH + c) = w;
+            for (int j = 0; j < 2; ++j) {
+                const float* f = reinterpret_cast<const float*>(acc) + j * 8;
+                const uint4 w = make_uint4(relu_pack2(f[0], f[1]), relu_pack2(f[2], f[3]),
+                                           relu_pack2(f[4], f[5]), relu_pack2(f[6], f[7]));
+                *reinterpret_cast<uint4*>(a + kmaj_off(rt, cb * 2 + j, kK2 / 8)) = w;
+                if (TRAIN && ok) *reinterpret_cast<uint4*>(P.h1 + r * kH + cb * 16 + j * 8) = w;
             }
         }
+        *reinterpret_cast<uint4*>(a + kmaj_off(rt, kH / 8, kK2 / 8)) = make_uint4(0x3C00u, 0, 0, 0);
+        *reinterpret_cast<uint4*>(a + kmaj_off(rt, kH / 8 + 1, kK2 / 8)) = make_uint4(0, 0, 0, 0);
+        // h1 is in shared memory and every warp's TMEM reads are done: layer 2
+        // may overwrite the accumulator columns
         fence_async_smem();
-        tc_before_sync();
-        __syncthreads();
-        tc_after_sync();
-        if (tid == 0) {
+        worker_fence_sync(wk);
+        if (rt == 0) {
 #pragma unroll
-            for (int k = 0; k < kH / 16; ++k)
-                umma_f16(tmem + 128, kmaj_desc(sbase + kSA2 + k * 256, kH / 8),
-                         kmaj_desc(sbase + kSW2 + k * 256, kH / 8), kIdesc, k > 0);
+            for (int k = 0; k < kK2 / 16; ++k)
+                umma_f16(tmem, kmaj_desc(sA + k * 256, kK2 / 8), kmaj_desc(sbase + kSW2 + k * 256, kK2 / 8),
+                         kIdesc, k > 0);
             umma_commit(bar);
         }
-        if (__syncthreads_or(!mbar_wait(bar, phase))) { if (tid == 0) atomicExch(P.err, 1); break; }
+        if (worker_any(wk, !mbar_wait(bar, phase))) { if (rt == 0) atomicExch(P.err, 1); break; }
         phase ^= 1u;
         tc_after_sync();
-        // ---- layer-2 epilogue: bias, ReLU, head
+        // ---- layer-2 epilogue: ReLU, head
         float sacc = 0.f;
 #pragma unroll
-        for (int cb = 0; cb < kH / 32; ++cb) {
-            uint32_t acc[32];
-            tmem_ld32(t2 + cb * 32, acc);
+        for (int cb = 0; cb < kH / 16; ++cb) {
+            uint32_t acc[16];
+            tmem_ld16(tl + cb * 16, acc);
 #pragma unroll
-            for (int j = 0; j < 8; ++j) {
-                const int c = cb * 32 + j * 4;
-                const float4 b = *reinterpret_cast<const float4*>(sb2 + c);
+            for (int j = 0; j < 4; ++j) {
+                const int c = cb * 16 + j * 4;
                 const float4 w = *reinterpret_cast<const float4*>(sw3 + c);
-                const float* a = reinterpret_cast<const float*>(acc) + j * 4;
-                const float4 h = make_float4(fmaxf(a[0] + b.x, 0.f), fmaxf(a[1] + b.y, 0.f),
-                                             fmaxf(a[2] + b.z, 0.f), fmaxf(a[3] + b.w, 0.f));
+                const float* f = reinterpret_cast<const float*>(acc) + j * 4;
+                const float4 h = make_float4(fmaxf(f[0], 0.f), fmaxf(f[1], 0.f), fmaxf(f[2], 0.f), fmaxf(f[3], 0.f));
                 sacc = fmaf(h.x, w.x, sacc);
                 sacc = fmaf(h.y, w.y, sacc);
                 sacc = fmaf(h.z, w.z, sacc);
@@ -364,15 +416,14 @@ __global__ void __launch_bounds__(kTile, 1) mlp_fwd_kernel(FwdParams P, long lon
             }
         }
         if (ok) P.s[r] = sacc + b3;
-        // every warp's TMEM reads are done before the next tile's MMAs overwrite D
-        tc_before_sync();
-        __syncthreads();
-        tc_after_sync();
+        // the next tile overwrites the buffer and the columns just read
+        worker_fence_sync(wk);
+        t = tn;
     }
     tc_before_sync();
     __syncthreads();
     tc_after_sync();
-    if (warp == 0) tmem_dealloc(tmem, kTmemCols);
+    if (warp == 0) tmem_dealloc(*tslot, kTmemCols);
 }
 
 // ---------------------------------------------------------------------------
@@ -733,9 +784,10 @@ int run_forward(const mcs_ctx* c, MlpState* m, int npairs, long long nrows, cons
     P.err = m->err;
     CKM(cudaFuncSetAttribute(mlp_fwd_kernel<TRAIN>, cudaFuncAttributeMaxDynamicSharedMemorySize, kFwdSmem));
     const long long ntiles = (nrows + kTile - 1) / kTile;
-    // persistent: two CTAs per SM (shared memory and TMEM admit two)
-    const long long grid = ntiles < 2LL * c->sms ? ntiles : 2LL * c->sms;
-    if (grid > 0) mlp_fwd_kernel<TRAIN><<<(unsigned)grid, kTile, kFwdSmem, s>>>(P, ntiles);
+    // persistent: one CTA of kWorkers tile pipelines per SM
+    const long long need = (ntiles + kWorkers - 1) / kWorkers;
+    const long long grid = need < (long long)c->sms ? need : (long long)c->sms;
+    if (grid > 0) mlp_fwd_kernel<TRAIN><<<(unsigned)grid, kTile * kWorkers, kFwdSmem, s>>>(P, ntiles);
     CKM(cudaGetLastError());
     return 0;
 }
