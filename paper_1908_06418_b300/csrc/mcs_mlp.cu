@@ -66,6 +66,12 @@ struct FeatParams {
     __half* feat16;      // [npairs*2][64][kFP]
 };
 
+// One warp per graph, on bitsets: lane x (and x + 32) holds the out- and
+// in-neighbour sets of its vertex (self-loops excluded), built from coalesced
+// row reads and ballots.  degree = |out| (+ |in| if directed); the histogram
+// bin b of x counts the neighbours (out or in) whose degree, capped at 15, is
+// b: popc(nb(x) & bin_b), with bin_b a ballot over the warp.  All values are
+// small multiples of 1/16 or 1/4, exact in fp32.
 __global__ void features_kernel(FeatParams P) {
     const int lane = threadIdx.x & 31;
     const int gi = blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5);
@@ -75,44 +81,68 @@ __global__ void features_kernel(FeatParams P) {
     if (n < 0 || n > kMaxN) n = 0;
     const uint8_t* a = P.adj + P.adj_off[gi];
     const int32_t* lab = (P.labels && P.lab_off && P.lab_off[gi] >= 0) ? P.labels + P.lab_off[gi] : nullptr;
-    int deg[2];
-    for (int s = 0; s < 2; ++s) {
-        int x = lane + 32 * s, d = 0;
-        if (x < n)
-            for (int y = 0; y < n; ++y) {
-                if (y == x) continue;
-                d += a[x * n + y] != 0;
-                if (directed) d += a[y * n + x] != 0;
-            }
-        deg[s] = d;
-    }
-    float hist[2][16];
-    for (int s = 0; s < 2; ++s)
-        for (int b = 0; b < 16; ++b) hist[s][b] = 0.f;
-    for (int y = 0; y < n; ++y) {
-        const int dy = __shfl_sync(0xffffffffu, deg[y >> 5], y & 31);
-        const int by = dy < 15 ? dy : 15;
-        for (int s = 0; s < 2; ++s) {
-            int x = lane + 32 * s;
-            if (x < n && y != x) {
-                bool nb = a[x * n + y] != 0 || (directed && a[y * n + x] != 0);
-                if (nb) {
+    // out[s]: row of vertex lane + 32 s
+    unsigned long long out[2] = {0ull, 0ull};
+    for (int x0 = 0; x0 < n; x0 += 8) {
+        // eight rows' loads in flight before the votes
+        uint8_t blo[8], bhi[8];
 #pragma unroll
-                    for (int b = 0; b < 16; ++b) hist[s][b] += (b == by) ? 0.25f : 0.f;
-                }
-            }
+        for (int k = 0; k < 8; ++k) {
+            const int x = x0 + k;
+            blo[k] = (x < n && lane < n) ? a[(size_t)x * n + lane] : 0;
+            bhi[k] = (x < n && lane + 32 < n) ? a[(size_t)x * n + lane + 32] : 0;
+        }
+#pragma unroll
+        for (int k = 0; k < 8; ++k) {
+            const int x = x0 + k;
+            const unsigned lo = __ballot_sync(0xffffffffu, blo[k] != 0);
+            const unsigned hi = __ballot_sync(0xffffffffu, bhi[k] != 0);
+            const unsigned long long row = ((unsigned long long)hi << 32) | lo;
+            if (x < n && (x & 31) == lane) { if (x < 32) out[0] = row; else out[1] = row; }
         }
     }
+    unsigned long long in[2] = {0ull, 0ull};
+    if (directed) {
+        for (int y = 0; y < n; ++y) {
+            const unsigned long long ry = __shfl_sync(0xffffffffu, y < 32 ? out[0] : out[1], y & 31);
+            for (int s = 0; s < 2; ++s)
+                if ((ry >> (lane + 32 * s)) & 1ull) in[s] |= 1ull << y;
+        }
+    }
+    int deg[2];
+    unsigned long long nb[2];
     for (int s = 0; s < 2; ++s) {
-        int x = lane + 32 * s;
-        float f[kF];
-        f[0] = x < n ? deg[s] / 16.f : 0.f;
-        f[1] = (x < n && lab) ? (float)min(lab[x], 63) / 8.f : 0.f;
-        for (int b = 0; b < 16; ++b) f[2 + b] = x < n ? hist[s][b] : 0.f;
-        size_t row = (size_t)gi * kMaxN + x;
+        const int x = lane + 32 * s;
+        const unsigned long long self = 1ull << x;
+        const unsigned long long o = x < n ? out[s] & ~self : 0ull, i = x < n ? in[s] & ~self : 0ull;
+        deg[s] = __popcll(o) + (directed ? __popcll(i) : 0);
+        nb[s] = o | i;
+    }
+    float f[2][kF];
+    for (int s = 0; s < 2; ++s)
+        for (int k = 0; k < kF; ++k) f[s][k] = 0.f;
+    for (int b = 0; b < 16; ++b) {
+        const unsigned lo = __ballot_sync(0xffffffffu, lane < n && min(deg[0], 15) == b);
+        const unsigned hi = __ballot_sync(0xffffffffu, lane + 32 < n && min(deg[1], 15) == b);
+        const unsigned long long bin = ((unsigned long long)hi << 32) | lo;
+        for (int s = 0; s < 2; ++s) f[s][2 + b] = 0.25f * (float)__popcll(nb[s] & bin);
+    }
+    for (int s = 0; s < 2; ++s) {
+        const int x = lane + 32 * s;
+        if (x < n) {
+            f[s][0] = deg[s] / 16.f;
+            f[s][1] = lab ? (float)min(lab[x], 63) / 8.f : 0.f;
+        } else {
+            for (int k = 0; k < kF; ++k) f[s][k] = 0.f;
+        }
+        const size_t row = (size_t)gi * kMaxN + x;
         if (P.feat32)
-            for (int k = 0; k < kF; ++k) P.feat32[row * kF + k] = f[k];
-        for (int k = 0; k < kFP; ++k) P.feat16[row * kFP + k] = __float2half_rn(k < kF ? f[k] : 0.f);
+            for (int k = 0; k < kF; ++k) P.feat32[row * kF + k] = f[s][k];
+        uint32_t w[kFP / 2];
+        for (int k = 0; k < kFP / 2; ++k)
+            w[k] = 2 * k + 1 < kF ? pack2(f[s][2 * k], f[s][2 * k + 1]) : 0u;
+        uint4* dst = reinterpret_cast<uint4*>(P.feat16 + row * kFP);
+        for (int k = 0; k < kFP / 8; ++k) dst[k] = make_uint4(w[4 * k], w[4 * k + 1], w[4 * k + 2], w[4 * k + 3]);
     }
 }
 
