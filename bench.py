@@ -64,7 +64,7 @@ def workload(name: str):
     if name == "c4":
         return synth.config4_pairs(2048), dict(
             workload="learned ordering: 2048 bounded-valence pairs (random 3-/4-regular and perturbed "
-                     "2D meshes, n U{40..64}), 1 s per pair, order network data/order_mlp_bvg.npy",
+                     "2D meshes, n U{40..64}), order network data/order_mlp_bvg.npy (per-pair limit: timeout_s)",
             pairs=2048)
     raise SystemExit(f"unknown workload {name}")
 
