@@ -13,6 +13,10 @@ fastest setting for the workload's bucket
 (directed or not, labelled or not, largest vertex count rounded up to 32 /
 48 / 64) in ``data/tune_cache.json``.  ``Solver.apply_tuned(pairs)`` applies
 the cached shape for a batch's bucket.
+
+Buckets whose pairs run into the per-pair limit (the bounded-valence batch:
+no pair is proven within a second) are ranked by search nodes per second
+over a fixed limit instead of by time to solve (``objective="nodes"``).
 """
 from __future__ import annotations
 
@@ -78,31 +82,64 @@ def time_shape(solver, batch, n, shape, reps, timeout_s):
     return best
 
 
+def rate_shape(solver, batch, n, shape, reps, timeout_s):
+    """Best search-node rate (nodes per microsecond of kernel time) of the
+    shape over `reps` device solves that stop at the per-pair limit; None if
+    a call fails."""
+    import torch
+    dev = batch.device
+    out = dict(size=torch.zeros(n, dtype=torch.int32, device=dev),
+               status=torch.zeros(n, dtype=torch.int32, device=dev),
+               nodes=torch.zeros(n, dtype=torch.int64, device=dev))
+    solver.set_launch(shape["warps_per_block"], shape["blocks_per_sm"] or -1, shape["smem_stack_entries"],
+                      search_group=shape["search_group"])
+    solver.set_steal(shape.get("poll_nodes", -1), shape.get("steal_keep_quarters", -1))
+    stream = torch.cuda.Stream(dev)
+    best = None
+    for r in range(reps + 1):
+        rc = solver.solve_batch_device(n, batch.d_n, batch.d_adj_off, batch.d_adj, batch.d_lab_off,
+                                       batch.d_labels, out["size"], out["status"], out["nodes"],
+                                       flags=batch.flags, timeout_s=timeout_s, stream=stream.cuda_stream)
+        stream.synchronize()
+        if rc < 0:
+            return None
+        st = solver.last_stats()
+        if r > 0 and st["kernel_us"] > 0:
+            rate = int(out["nodes"].sum().item()) / st["kernel_us"]
+            best = rate if best is None else max(best, rate)
+    return best
+
+
 def tune(name: str, pairs, directed: bool, reps: int = 2, timeout_s: float = 120.0,
-         cache_path: str = CACHE) -> dict:
+         cache_path: str = CACHE, objective: str = "time") -> dict:
+    """objective "time": fastest batch solve (ms); "nodes": highest search-node
+    rate over solves cut at `timeout_s` per pair (nodes per microsecond)."""
     from . import Solver, DeviceBatch
     batch = DeviceBatch(pairs, directed=directed)
+    measure = time_shape if objective == "time" else rate_shape
+    field = "ms" if objective == "time" else "nodes_per_us"
+    pick = min if objective == "time" else max
     results = []
     with Solver(0) as s:
         for shape in SHAPES:
-            t = time_shape(s, batch, len(pairs), shape, reps, timeout_s)
-            results.append(dict(shape, ms=t))
+            t = measure(s, batch, len(pairs), shape, reps, timeout_s)
+            results.append(dict(shape, **{field: t}))
             print(name, shape, t, flush=True)
-        ok = [r for r in results if r["ms"] is not None]
-        best = {k: min(ok, key=lambda r: r["ms"])[k] for k in KEYS}
+        ok = [r for r in results if r[field] is not None]
+        best = {k: pick(ok, key=lambda r: r[field])[k] for k in KEYS}
         steal = []
         for st in STEAL:
             shape = dict(best, **st)
-            t = time_shape(s, batch, len(pairs), shape, reps, timeout_s)
-            steal.append(dict(shape, ms=t))
+            t = measure(s, batch, len(pairs), shape, reps, timeout_s)
+            steal.append(dict(shape, **{field: t}))
             print(name, shape, t, flush=True)
-    ok = [r for r in steal if r["ms"] is not None]
-    best = min(ok, key=lambda r: r["ms"])
+    ok = [r for r in steal if r[field] is not None]
+    best = pick(ok, key=lambda r: r[field])
     cache = load_cache(cache_path)
     key = bucket(pairs, directed)
     cache[key] = dict(best, workload=name, measured=time.strftime("%Y-%m-%d"),
-                      sweep=[{k: r[k] for k in KEYS + ("ms",)} for r in results],
-                      steal_sweep=[{k: r[k] for k in ("poll_nodes", "steal_keep_quarters", "ms")} for r in steal])
+                      sweep=[{k: r[k] for k in KEYS + (field,)} for r in results],
+                      steal_sweep=[{k: r[k] for k in ("poll_nodes", "steal_keep_quarters", field)} for r in steal])
     os.makedirs(os.path.dirname(cache_path), exist_ok=True)
     with open(cache_path, "w") as f:
         json.dump(cache, f, indent=1)
@@ -127,6 +164,10 @@ def main():
             tune(w, synth.config3_pairs(), False, a.reps, cache_path=a.cache)
         elif w == "c1":
             tune(w, synth.config1_like(64), False, a.reps, cache_path=a.cache)
+        elif w == "c4":
+            # no pair is proven within the limit: rank shapes by node rate over 0.3 s per pair
+            tune(w, synth.config4_pairs(2048), False, a.reps, timeout_s=0.3, cache_path=a.cache,
+                 objective="nodes")
         else:
             raise SystemExit(f"unknown workload {w}")
 
