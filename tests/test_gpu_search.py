@@ -423,6 +423,49 @@ def test_full_workload_in_the_tuned_launch_shape(solver, workload):
         solver.reset_launch()
 
 
+@pytest.mark.parametrize("learned", [False, True])
+def test_bounded_valence_batch_in_the_tuned_launch_shape(solver, learned):
+    """The 2,048 bounded-valence pairs (n 40-64) at full size, in the launch
+    shape the bench applies, cut at 0.2 s per pair (no pair of this family is
+    proven within seconds, by the GPU or the oracle).  Every result is a
+    verified common induced subgraph with status OK or TIMEOUT; with the
+    degree order each size is at least the oracle's first-dive incumbent (the
+    first leaf of the same depth-first order, reached within 65 nodes)."""
+    import os
+    import torch
+    from paper_1908_06418_b300 import DeviceBatch, MCS_OK, MCS_TIMEOUT, MCS_ORDER_LEARNED
+    pairs = synth.config4_pairs(2048)
+    if learned:
+        here = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+        solver.set_order_model(np.load(os.path.join(here, "paper_1908_06418_b300", "data",
+                                                    "order_mlp_bvg.npy")).astype(np.float32))
+    try:
+        assert solver.apply_tuned(pairs) is not None
+        b = DeviceBatch(pairs)
+        n = len(pairs)
+        size = torch.zeros(n, dtype=torch.int32, device=b.device)
+        status = torch.zeros(n, dtype=torch.int32, device=b.device)
+        nodes = torch.zeros(n, dtype=torch.int64, device=b.device)
+        mp = torch.zeros(n * 64, dtype=torch.int16, device=b.device)
+        rc = solver.solve_batch_device(n, b.d_n, b.d_adj_off, b.d_adj, b.d_lab_off, b.d_labels,
+                                       size, status, nodes, mp,
+                                       flags=b.flags | (MCS_ORDER_LEARNED if learned else 0), timeout_s=0.2)
+        torch.cuda.synchronize()
+        assert rc in (MCS_OK, MCS_TIMEOUT)
+        sz, st = size.cpu().numpy(), status.cpu().numpy()
+        mp = mp.cpu().numpy().reshape(n, 64)
+        assert set(np.unique(st)) <= {MCS_OK, MCS_TIMEOUT}
+        for j, p in enumerate(pairs):
+            gi = np.nonzero(mp[j] >= 0)[0]
+            assert len(gi) == sz[j], j
+            assert oracle.verify(p.G.adj, p.H.adj, gi, mp[j][gi]) == 1, j
+            if not learned:
+                first = oracle.mcs(p.G.adj, p.H.adj, node_limit=65).size
+                assert sz[j] >= first, (j, sz[j], first)
+    finally:
+        solver.reset_launch()
+
+
 def test_empty_batches(solver):
     import torch
     from paper_1908_06418_b300 import HostBatch
