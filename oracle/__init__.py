@@ -5,6 +5,8 @@ and by the CPU-baseline leg of ``bench.py``; never by the product package.
 It shares no code with the CUDA path.
 
 * ``mcs``        -- sequential recursive McSplit (Section II-B, Algorithm 1, Eq. 1)
+* ``mcs_goal``   -- one goal-directed McSplit search (Section IV, top-down strategy)
+* ``mcs_topdown``-- the top-down strategy: goal sizes min(|V_G|,|V_H|), one less, ...
 * ``bruteforce`` -- exhaustive injective partial mappings (definition, Section II-A)
 * ``clique``     -- maximum clique of the modular product graph (textbook reduction)
 * ``verify``     -- checks a mapping is a common induced subgraph (Section II-A)
@@ -36,9 +38,8 @@ def _load():
     global _lib
     if _lib is not None:
         return _lib
-    if not os.path.exists(_LIB_PATH):
-        from . import build as _b
-        _b.build()
+    from . import build as _b
+    _b.build()                      # rebuilds only when oracle.cpp is newer
     lib = ctypes.CDLL(_LIB_PATH)
     g = [ctypes.c_int, _u8p, _i32p, ctypes.c_int, _u8p, _i32p]
     lib.oracle_verify.argtypes = g + [ctypes.c_int, _i32p, _i32p]
@@ -46,6 +47,11 @@ def _load():
     lib.oracle_mcs.argtypes = g + [ctypes.c_int, ctypes.c_int64, ctypes.c_double,
                                    _i32p, _i32p, _i64p, ctypes.POINTER(ctypes.c_int)]
     lib.oracle_mcs.restype = ctypes.c_int
+    lib.oracle_mcs_goal.argtypes = g + [ctypes.c_int, ctypes.c_int, ctypes.c_int, ctypes.c_int64,
+                                        ctypes.c_double, _i32p, _i32p, _i64p, ctypes.POINTER(ctypes.c_int)]
+    lib.oracle_mcs_goal.restype = ctypes.c_int
+    lib.oracle_mcs_topdown.argtypes = lib.oracle_mcs.argtypes
+    lib.oracle_mcs_topdown.restype = ctypes.c_int
     lib.oracle_bruteforce.argtypes = g + [_i32p, _i32p]
     lib.oracle_bruteforce.restype = ctypes.c_int
     lib.oracle_clique.argtypes = g + [_i32p, _i32p]
@@ -92,6 +98,45 @@ def mcs(adjG, adjH, labG=None, labH=None, directed: bool = False,
     k = lib.oracle_mcs(*ga, *ha, int(directed), int(node_limit), float(time_limit_s),
                        og.ctypes.data_as(_i32p), oh.ctypes.data_as(_i32p),
                        ctypes.byref(nodes), ctypes.byref(st))
+    return OracleResult(int(k), og[:k].copy(), oh[:k].copy(), int(nodes.value), st.value == 0)
+
+
+def mcs_goal(adjG, adjH, floor: int, cap: int, labG=None, labH=None, directed: bool = False,
+             node_limit: int = 0, time_limit_s: float = 0.0) -> OracleResult:
+    """One goal-directed search (Section IV): only mappings larger than
+    `floor` are recorded and the search stops once one of size `cap` is
+    found.  size == 0 means no mapping beat the floor; `complete` is False
+    only when a limit stopped the search."""
+    lib = _load()
+    ga, keep1 = _gargs(adjG, labG)
+    ha, keep2 = _gargs(adjH, labH)
+    n = max(1, min(ga[0], ha[0]))
+    og = np.zeros(n, np.int32)
+    oh = np.zeros(n, np.int32)
+    nodes = ctypes.c_int64(0)
+    st = ctypes.c_int(0)
+    k = lib.oracle_mcs_goal(*ga, *ha, int(directed), int(floor), int(cap), int(node_limit),
+                            float(time_limit_s), og.ctypes.data_as(_i32p), oh.ctypes.data_as(_i32p),
+                            ctypes.byref(nodes), ctypes.byref(st))
+    return OracleResult(int(k), og[:k].copy(), oh[:k].copy(), int(nodes.value), st.value == 0)
+
+
+def mcs_topdown(adjG, adjH, labG=None, labH=None, directed: bool = False,
+                node_limit: int = 0, time_limit_s: float = 0.0) -> OracleResult:
+    """The top-down strategy (Section IV): goal-directed searches for the goal
+    sizes min(|V_G|,|V_H|), one less, ... until one is reached; `nodes` sums
+    all of them."""
+    lib = _load()
+    ga, keep1 = _gargs(adjG, labG)
+    ha, keep2 = _gargs(adjH, labH)
+    n = max(1, min(ga[0], ha[0]))
+    og = np.zeros(n, np.int32)
+    oh = np.zeros(n, np.int32)
+    nodes = ctypes.c_int64(0)
+    st = ctypes.c_int(0)
+    k = lib.oracle_mcs_topdown(*ga, *ha, int(directed), int(node_limit), float(time_limit_s),
+                               og.ctypes.data_as(_i32p), oh.ctypes.data_as(_i32p),
+                               ctypes.byref(nodes), ctypes.byref(st))
     return OracleResult(int(k), og[:k].copy(), oh[:k].copy(), int(nodes.value), st.value == 0)
 
 

@@ -16,6 +16,12 @@
 //   oracle_branch_log  oracle_mcs instrumented to record, per branching
 //                      decision, which candidate pairs (v,u) lay on an optimal
 //                      extension (training signal for the ordering network)
+//   oracle_mcs_goal    one goal-directed search (Section IV, top-down
+//                      strategy): the incumbent starts at a floor with no
+//                      mapping, and the search stops once it reaches a cap
+//   oracle_mcs_topdown the top-down strategy of Section IV: one goal-directed
+//                      search per goal size min(|V_G|,|V_H|), one less, ...,
+//                      until a goal is reached
 //
 // Readings where the paper is silent (the McSplit publication it cites fixes
 // them; none of them changes the optimum, only the traversal):
@@ -110,6 +116,15 @@ struct McSplit {
     std::vector<std::pair<int, int>> M, best;
     std::vector<BranchRecord>* log = nullptr;
     int log_max_depth = 0;
+    // Goal-directed search (Section IV): the incumbent size starts at `floor`
+    // without a mapping (a solution must beat it to be recorded), and the
+    // search stops as soon as the incumbent reaches `cap` (a solution of the
+    // goal size was found).  The plain search has floor 0 and no cap.
+    int floor = 0;
+    int cap = 1 << 30;
+    bool reached = false;
+
+    int incumbent() const { return std::max((int)best.size(), floor); }
 
     McSplit(const OGraph& g, const OGraph& h, bool d, int64_t nl, double tl)
         : G(g), H(h), directed(d), node_limit(nl), time_limit(tl),
@@ -160,8 +175,11 @@ struct McSplit {
     void solve(std::vector<LabelClass> cl, int depth) {
         ++nodes;
         if (aborted || out_of_budget()) { aborted = true; return; }
-        if (M.size() > best.size()) best = M;                 // incumbent (Algorithm 1)
-        if (bound(cl) <= (int)best.size()) return;            // prune (Algorithm 1, Eq. 1)
+        if ((int)M.size() > incumbent()) {                    // incumbent (Algorithm 1)
+            best = M;
+            if ((int)best.size() >= cap) { reached = true; return; }   // goal reached (Section IV)
+        }
+        if (bound(cl) <= incumbent()) return;                 // prune (Algorithm 1, Eq. 1)
         // selectLabelClass (Algorithm 1): smallest max(|L|,|R|), ties to the
         // class with the lowest-numbered left vertex.
         int c = -1, ckey = 0, cmin = 0;
@@ -192,7 +210,7 @@ struct McSplit {
                 rec->sub_nodes.push_back(nodes - before);
                 rec->sub_best.push_back((int)best.size() > best_before ? (int)best.size() : -1);
             }
-            if (aborted) return;
+            if (aborted || reached) return;
         }
         // "G = G \ v" (Algorithm 1): v stays unmatched; only this class loses it.
         auto& L = cl[c].L;
@@ -371,6 +389,80 @@ int oracle_mcs(int nG, const uint8_t* adjG, const int32_t* labG,
     }
     if (nodes) *nodes = s.nodes;
     if (status) *status = s.aborted ? 1 : 0;
+    return k;
+}
+
+// One goal-directed McSplit search (Section IV, top-down strategy): the
+// incumbent size starts at `floor` with no mapping, so only a mapping larger
+// than `floor` is recorded, and the search stops once the incumbent reaches
+// `cap`.  Returns the size of the best mapping recorded (0 when none beat the
+// floor) and writes it like oracle_mcs; *status = 0 when the search ended by
+// itself (completed, or stopped at the cap), 1 when a limit stopped it.
+int oracle_mcs_goal(int nG, const uint8_t* adjG, const int32_t* labG,
+                    int nH, const uint8_t* adjH, const int32_t* labH,
+                    int directed, int floor, int cap, int64_t node_limit, double time_limit_s,
+                    int32_t* out_g, int32_t* out_h, int64_t* nodes, int* status) {
+    OGraph g0 = make_graph(nG, adjG, labG), h0 = make_graph(nH, adjH, labH);
+    std::vector<int> og = degree_order(g0, directed != 0), oh = degree_order(h0, directed != 0);
+    OGraph G = relabel(g0, og), H = relabel(h0, oh);
+    McSplit s(G, H, directed != 0, node_limit, time_limit_s);
+    s.floor = floor;
+    s.cap = cap;
+    s.solve(initial_classes(G, H), 0);
+    int k = (int)s.best.size();
+    for (int i = 0; i < k; ++i) {
+        if (out_g) out_g[i] = og[s.best[i].first];
+        if (out_h) out_h[i] = oh[s.best[i].second];
+    }
+    if (nodes) *nodes = s.nodes;
+    if (status) *status = s.aborted ? 1 : 0;
+    return k;
+}
+
+// The top-down strategy (Section IV): goal-directed searches for the goal
+// sizes k = min(|V_G|, |V_H|), k - 1, ..., 1, each with floor k - 1 and cap k,
+// from the root; the first goal reached is the maximum (every larger goal was
+// proven unreachable).  With an empty graph it is the plain search.  Returns
+// the size (0 when no goal is reached), the mapping as oracle_mcs, *nodes
+// summed over the goal searches, *status as oracle_mcs (1: a limit stopped it;
+// then the size is that of a recorded mapping, 0 when none).
+int oracle_mcs_topdown(int nG, const uint8_t* adjG, const int32_t* labG,
+                       int nH, const uint8_t* adjH, const int32_t* labH,
+                       int directed, int64_t node_limit, double time_limit_s,
+                       int32_t* out_g, int32_t* out_h, int64_t* nodes, int* status) {
+    OGraph g0 = make_graph(nG, adjG, labG), h0 = make_graph(nH, adjH, labH);
+    std::vector<int> og = degree_order(g0, directed != 0), oh = degree_order(h0, directed != 0);
+    OGraph G = relabel(g0, og), H = relabel(h0, oh);
+    const int kmax = std::min(nG, nH);
+    const auto t0 = std::chrono::steady_clock::now();
+    int64_t total = 0;
+    int k = 0, st = 0;
+    std::vector<std::pair<int, int>> best;
+    for (int goal = kmax; goal >= (kmax > 0 ? 1 : 0); --goal) {
+        double left = 0.0;
+        if (time_limit_s > 0) {
+            left = time_limit_s - std::chrono::duration<double>(std::chrono::steady_clock::now() - t0).count();
+            if (left <= 0) { st = 1; break; }
+        }
+        int64_t nl = 0;
+        if (node_limit > 0) {
+            nl = node_limit - total;
+            if (nl <= 0) { st = 1; break; }
+        }
+        McSplit s(G, H, directed != 0, nl, left);
+        if (kmax > 0) { s.floor = goal - 1; s.cap = goal; }
+        s.solve(initial_classes(G, H), 0);
+        total += s.nodes;
+        if (!s.best.empty() || kmax == 0) { best = s.best; k = (int)best.size(); }
+        if (s.aborted) { st = 1; break; }
+        if (k > 0 || kmax == 0) break;          // the goal was reached
+    }
+    for (int i = 0; i < k; ++i) {
+        if (out_g) out_g[i] = og[best[i].first];
+        if (out_h) out_h[i] = oh[best[i].second];
+    }
+    if (nodes) *nodes = total;
+    if (status) *status = st;
     return k;
 }
 

@@ -226,3 +226,71 @@ def test_config1_golden_matches_generator():
     p = synth.config1_pair()
     assert rows[0]["digest"] == pair_digest(p)
     assert rows[0]["size"] == oracle.mcs(p.G.adj, p.H.adj).size == 13
+
+
+# --------------------------------------------------------------------------
+# goal-directed search and the top-down strategy (Section IV)
+# --------------------------------------------------------------------------
+@pytest.mark.parametrize("directed,k", [(False, 0), (True, 0), (False, 3), (True, 2)])
+def test_topdown_vs_bruteforce(directed, k):
+    """Top-down reaches the same optimum as exhaustive enumeration (a
+    different traversal: goal searches from min(|V_G|,|V_H|) down)."""
+    rs = np.random.default_rng(61 + 7 * k + (500 if directed else 0))
+    for s in range(120):
+        nG, nH = int(rs.integers(0, 10)), int(rs.integers(0, 10))
+        p = float(rs.uniform(0.1, 0.7))
+        a, b, la, lb = _rand_pair(s + 7000 + (5000 if directed else 0) + 100 * k, nG, nH, p, directed, k)
+        r = oracle.mcs_topdown(a, b, la, lb, directed=directed)
+        kb, _, _ = oracle.bruteforce(a, b, la, lb)
+        assert r.complete
+        assert r.size == kb, (s, nG, nH, p)
+        assert len(r.g_idx) == r.size
+        assert oracle.verify(a, b, r.g_idx, r.h_idx, la, lb) == 1
+
+
+@pytest.mark.parametrize("directed,k", [(False, 0), (True, 2)])
+def test_goal_search_decides_each_goal(directed, k):
+    """A goal search with floor g-1 and cap g records a mapping (of size
+    exactly g) iff a common induced subgraph of g vertices exists, i.e. iff
+    the optimum found by exhaustive enumeration is >= g."""
+    rs = np.random.default_rng(83 + k)
+    for s in range(40):
+        nG, nH = int(rs.integers(1, 9)), int(rs.integers(1, 9))
+        a, b, la, lb = _rand_pair(s + 8000 + 100 * k, nG, nH, float(rs.uniform(0.2, 0.6)), directed, k)
+        opt, _, _ = oracle.bruteforce(a, b, la, lb)
+        for goal in range(1, min(nG, nH) + 2):
+            r = oracle.mcs_goal(a, b, goal - 1, goal, la, lb, directed=directed)
+            assert r.complete
+            if opt >= goal:
+                assert r.size == goal, (s, goal, opt)
+                assert oracle.verify(a, b, r.g_idx, r.h_idx, la, lb) == 1
+            else:
+                assert r.size == 0, (s, goal, opt)
+
+
+def test_topdown_on_an_induced_subgraph_stops_at_the_first_goal():
+    """When G is an induced subgraph of H the first goal, |V_G|, is reached:
+    top-down is exactly one goal search, and it maps all of G."""
+    rs = np.random.default_rng(97)
+    for s in range(20):
+        n = int(rs.integers(6, 16))
+        _, b, _, _ = _rand_pair(s + 9000, n, n + 6, 0.35)
+        keep = np.sort(rs.permutation(n + 6)[:n])
+        a = b[np.ix_(keep, keep)].copy()
+        r = oracle.mcs_topdown(a, b)
+        one = oracle.mcs_goal(a, b, n - 1, n)
+        assert r.size == n and one.size == n
+        assert r.nodes == one.nodes
+        assert oracle.verify(a, b, r.g_idx, r.h_idx) == 1
+
+
+def test_topdown_nodes_sum_over_goal_searches():
+    """Top-down's node count is the sum over the goal searches it ran, from
+    min(|V_G|,|V_H|) down to the optimum."""
+    for s in range(12):
+        a, b, _, _ = _rand_pair(s + 9500, 11, 13, 0.4)
+        r = oracle.mcs_topdown(a, b)
+        opt = oracle.mcs(a, b).size
+        assert r.size == opt
+        total = sum(oracle.mcs_goal(a, b, g - 1, g).nodes for g in range(11, opt - 1, -1))
+        assert r.nodes == total
