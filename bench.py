@@ -1,6 +1,6 @@
 """Benchmark: exact MCS pairs solved/sec and search nodes/sec on one B300.
 
-    python bench.py [--gpus N] [--steps K] [--warmup W] [--workload c2|c3|c1]
+    python bench.py [--gpus N] [--steps K] [--warmup W] [--workload c2|c3|c1|c4|c5|td]
                     [--impl ours|reference]
 
 A step solves one whole workload batch: every pair of the workload, each to a
@@ -11,6 +11,12 @@ persistent launches (one directed, one undirected) with all inputs resident in
 HBM.  Timing: CUDA events on the launching stream around each step; the L2
 cache (126 MB) is flushed by writing a 512 MB buffer between steps, outside
 the timed events.  `value` = pairs solved / summed step time.
+
+Other workloads: c3 (4,096 labelled pairs), c1 (one small pair), c4 (2,048
+bounded-valence pairs, learned order, 1 s per pair), c5 (serving on a Poisson
+stream), td (96 bounded-valence pairs with a 90 % planted core, solved with
+the top-down strategy of Section IV; the line adds the plain search of the
+same batch).
 
 `--impl reference` times the CPU oracle (plain sequential McSplit) on the
 host cores on a bounded sample of the same workload; it is the reference arm
@@ -66,6 +72,10 @@ def workload(name: str):
             workload="learned ordering: 2048 bounded-valence pairs (random 3-/4-regular and perturbed "
                      "2D meshes, n U{40..64}), order network data/order_mlp_bvg.npy (per-pair limit: timeout_s)",
             pairs=2048)
+    if name == "td":
+        return [synth.planted_bvg_pair(i, 40, 64, cid=62) for i in range(4, 480, 5)], dict(
+            workload="top-down strategy (Section IV): 96 bounded-valence pairs with a planted common "
+                     "core of 90% of n (3-regular or mesh core), n U{40..64}; MCS_TOP_DOWN", pairs=96)
     raise SystemExit(f"unknown workload {name}")
 
 
@@ -149,8 +159,8 @@ def _oracle_one(args):
     pairs, _ = workload(name)
     p = pairs[idx]
     t = time.time()
-    r = oracle.mcs(p.G.adj, p.H.adj, p.G.labels, p.H.labels, directed=p.directed,
-                   time_limit_s=budget)
+    run = oracle.mcs_topdown if name == "td" else oracle.mcs
+    r = run(p.G.adj, p.H.adj, p.G.labels, p.H.labels, directed=p.directed, time_limit_s=budget)
     return idx, r.size, r.complete, r.nodes, time.time() - t
 
 
@@ -211,7 +221,7 @@ def single_instance_vs_batch(solver, pairs, a, batch_flags=0):
     import torch
     from paper_1908_06418_b300 import MCS_OK, MCS_DIRECTED, HostBatch
     n = len(pairs)
-    k = {"c2": 24, "c2s": 8, "c3": 256, "c1": 1, "c4": 8}.get(a.workload, min(n, 64))
+    k = {"c2": 24, "c2s": 8, "c3": 256, "c1": 1, "c4": 8, "td": 8}.get(a.workload, min(n, 64))
     idx = list(range(0, n, max(1, n // k)))[:k]
     sample = [pairs[i] for i in idx]
     # one pair per call
@@ -318,13 +328,15 @@ def main():
     if world > 1:
         import torch.distributed as dist
         dist.init_process_group("nccl")
-    from paper_1908_06418_b300 import Solver, pack_host, MCS_DIRECTED, MCS_OK, MCS_WORD32, MCS_ORDER_LEARNED
+    from paper_1908_06418_b300 import (Solver, pack_host, MCS_DIRECTED, MCS_OK, MCS_WORD32, MCS_ORDER_LEARNED,
+                                       MCS_TOP_DOWN)
 
     pairs, cfg = workload(a.workload)
     gold = golden_sizes(a.workload)
     dev = torch.device("cuda", local)
     solver = Solver(local)
     learned = a.workload == "c4"
+    topdown = a.workload == "td"
     if learned:       # the candidate order of the trained network (exactness unchanged)
         solver.set_order_model(np.load(os.path.join(ROOT, "paper_1908_06418_b300", "data",
                                                     "order_mlp_bvg.npy")).astype(np.float32))
@@ -342,7 +354,7 @@ def main():
         narrow = all(max(pairs[i].G.n, pairs[i].H.n) <= 32 for i in idx)
         h = pack_host([pairs[i] for i in idx])
         g = dict(idx=idx, flags=(MCS_DIRECTED if directed else 0) | (MCS_WORD32 if narrow else 0)
-                 | (MCS_ORDER_LEARNED if learned else 0), n=len(idx),
+                 | (MCS_ORDER_LEARNED if learned else 0) | (MCS_TOP_DOWN if topdown else 0), n=len(idx),
                  d_n=torch.from_numpy(h["n"]).to(dev),
                  d_adj_off=torch.from_numpy(h["adj_off"]).to(dev),
                  d_adj=torch.from_numpy(h["adj"]).to(dev),
@@ -512,8 +524,8 @@ def main():
             "e2e": {"value": e2e_value, "unit": UNIT, "h2d_bytes_per_step": int(h2d),
                     "d2h_bytes_per_step": int(d2h)},
             "roofline": roof, "clocks": csum}
-    if rank == 0 and learned:
-        # the same batch with the learned order and with the plain degree order
+    if rank == 0 and (learned or topdown):
+        # the same batch with and without the strategy under test
         def one_pass(flag_clear):
             torch.cuda.synchronize()
             e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
@@ -530,14 +542,27 @@ def main():
             sz = np.concatenate([g["size"].cpu().numpy() for g in groups])
             nd = sum(int(g["nodes"].sum().item()) for g in groups)
             return {"ms": e0.elapsed_time(e1), "solved": int((st == MCS_OK).sum()),
-                    "mean_size": float(sz.mean()), "nodes": nd}
-        line["order_comparison"] = {"learned": one_pass(0), "plain": one_pass(MCS_ORDER_LEARNED),
-                                    "note": "one pass each over the whole batch; exact either way, "
-                                            "solved = proven within the per-pair limit"}
-        line["mlp"] = mlp_roofline(solver, groups, pairs, stream)
+                    "mean_size": float(sz.mean()), "nodes": nd, "_sizes": sz, "_status": st}
+        if learned:
+            cmp = {"learned": one_pass(0), "plain": one_pass(MCS_ORDER_LEARNED)}
+            key = "order_comparison"
+        else:
+            cmp = {"top_down": one_pass(0), "plain": one_pass(MCS_TOP_DOWN)}
+            key = "strategy_comparison"
+            # both are exact: where both proved their result the sizes must agree
+            a_, b_ = cmp["top_down"], cmp["plain"]
+            both = (a_["_status"] == MCS_OK) & (b_["_status"] == MCS_OK)
+            if not np.array_equal(a_["_sizes"][both], b_["_sizes"][both]):
+                raise SystemExit("PARITY FAILURE: top-down and plain optima differ")
+        for v in cmp.values():
+            v.pop("_sizes"); v.pop("_status")
+        line[key] = dict(cmp, note="one pass each over the whole batch; exact either way, "
+                                   "solved = proven within the per-pair limit")
+        if learned:
+            line["mlp"] = mlp_roofline(solver, groups, pairs, stream)
     if rank == 0 and not a.no_single:
         line["single_instance"] = single_instance_vs_batch(
-            solver, pairs, a, batch_flags=MCS_ORDER_LEARNED if learned else 0)
+            solver, pairs, a, batch_flags=(MCS_ORDER_LEARNED if learned else 0) | (MCS_TOP_DOWN if topdown else 0))
     if rank == 0 and not a.no_cpu_baseline:
         cb = oracle_sample(a.workload, 8 if a.workload.startswith("c2") else 64,
                            a.timeout if a.workload == "c4" else (25.0 if a.workload.startswith("c2") else 2.0))

@@ -71,6 +71,12 @@ extern "C" {
                                     /* most 32 vertices (others: MCS_ERR_ARG for that  */
                                     /* pair).  mcs_solve and mcs_solve_batch set it    */
                                     /* themselves when all graphs fit                  */
+#define MCS_TOP_DOWN          0x40u /* top-down strategy (Section IV): goal-directed  */
+                                    /* searches for min(n_G,n_H), one less, ... from  */
+                                    /* the root until a goal is reached; the first    */
+                                    /* goal reached is the optimum.  A time limit     */
+                                    /* before that reports size 0 (MCS_TIMEOUT).      */
+                                    /* Batch calls only (mcs_submit: unsupported).    */
 
 typedef struct mcs_ctx mcs_ctx;
 

@@ -18,7 +18,7 @@ import numpy as np
 __all__ = ["Solver", "Result", "MCS_OK", "MCS_TIMEOUT", "MCS_PENDING", "MCS_ERR_ARG",
            "MCS_ERR_NOMEM", "MCS_ERR_CUDA", "MCS_ERR_DEVICE_STALL", "MCS_ERR_UNSUPPORTED",
            "MCS_DIRECTED", "MCS_ORDER_LEARNED", "MCS_NO_MAPPING", "MCS_NO_LEVEL_PRUNE",
-           "MCS_MAX_N", "MCS_GRAPH_REPLAY", "MCS_WORD32", "lib_path", "load_library", "EXPORTED_SYMBOLS",
+           "MCS_MAX_N", "MCS_GRAPH_REPLAY", "MCS_WORD32", "MCS_TOP_DOWN", "lib_path", "load_library", "EXPORTED_SYMBOLS",
            "DeviceBatch", "HostBatch", "pack_host"]
 
 MCS_MAX_N = 64
@@ -26,6 +26,7 @@ MCS_OK, MCS_TIMEOUT, MCS_PENDING = 0, 1, 2
 MCS_ERR_ARG, MCS_ERR_NOMEM, MCS_ERR_CUDA, MCS_ERR_DEVICE_STALL, MCS_ERR_UNSUPPORTED = -1, -2, -3, -4, -5
 MCS_DIRECTED, MCS_ORDER_LEARNED, MCS_NO_MAPPING, MCS_NO_LEVEL_PRUNE = 0x1, 0x2, 0x4, 0x8
 MCS_WORD32 = 0x20
+MCS_TOP_DOWN = 0x40
 MCS_GRAPH_REPLAY = 0x10
 
 _HERE = os.path.dirname(os.path.abspath(__file__))

@@ -32,15 +32,20 @@ struct PairGraph {
 
 // Per-pair search state.
 struct PairState {
-    int32_t inc;           // incumbent size (atomicMax)
+    int32_t inc;           // incumbent size (atomicMax); starts at `floor`
     int32_t open;          // tasks of this pair that exist (queued or running)
     int32_t status;        // MCS_PENDING until finalised, or MCS_ERR_ARG
-    int32_t abort;         // 1 once the pair timed out
+    int32_t abort;         // 0 running, 1 time limit hit, 2 goal reached (stop, optimal)
     u64 nodes;
     u64 t_start, deadline; // globaltimer ns
     u64 ticket;            // serve mode: the request's ticket
     u64 timeout_ns;        // serve mode: the request's limit (from its root's start)
+    // Goal-directed search (top-down strategy, Section IV): only mappings
+    // larger than `floor` are recorded, and the pair stops once the incumbent
+    // reaches `cap`.  Plain search: floor 0, cap kNoCap.
+    int32_t floor, cap;
 };
+constexpr int32_t kNoCap = 1 << 30;
 
 // A unit of work: one level of a pair's search tree (a node, its classes,
 // the chosen left vertex v and the candidate set still to try).

@@ -274,7 +274,12 @@ __global__ void pack_kernel(PackParams P) {
     const bool ok = pack_pair_warp(g, directed, k0, k1, pg, s_key[wib], lane) && fits;
     if (lane == 0) {
         PairState& st = P.state[p];
-        st.inc = 0;
+        // top-down: the first goal is min(|V_G|, |V_H|) (Section IV)
+        const int kmax = min(max(g[0].n, 0), max(g[1].n, 0));
+        const bool td = (P.flags & MCS_TOP_DOWN) && ok && kmax > 0;
+        st.floor = td ? kmax - 1 : 0;
+        st.cap = td ? kmax : kNoCap;
+        st.inc = st.floor;
         st.open = 1;
         st.status = ok ? MCS_PENDING : MCS_ERR_ARG;
         st.abort = 0;
@@ -558,6 +563,31 @@ __device__ void finalize_served(const SearchParams& P, int pair, int status, int
     g.sync();
 }
 
+// Top-down (Section IV), one lane: the goal fl + 1 was not reached, so the
+// pair searches again from its root with the goal fl (floor fl - 1, cap fl).
+// Out of line: it runs once per goal, and inlined it would cost the node loop
+// registers.  False if the bounded wait for a ring slot expired.
+__device__ __noinline__ bool requeue_next_goal(const SearchParams& P, int pair, int fl) {
+    PairState& ps = P.state[pair];
+    ps.floor = fl - 1;
+    ps.cap = fl;
+    ps.inc = fl - 1;
+    ps.open = 1;
+    __threadfence();
+    const uint32_t qmask = P.qcap - 1;
+    const u64 t = atomicAdd(&P.ctl->q_tail, 1ull);
+    if (!wait_seq(P.qseq + (t & qmask), t)) return false;
+    Task* dst = P.queue + (t & qmask);
+    dst->h.pair = pair;
+    dst->h.flags = kTaskFresh;
+    dst->h.depth = 0;
+    dst->h.C = 0;
+    __threadfence();
+    P.qseq[t & qmask] = t + 1;
+    atomicMax(&P.ctl->last_progress, gtimer());
+    return true;
+}
+
 // Finish the pair: write size, status, nodes and the mapping (original numbers).
 template <bool SERVE, int GS>
 __device__ void finalize_pair(const SearchParams& P, int pair, const Grp<GS>& g, int16_t* smap) {
@@ -565,18 +595,34 @@ __device__ void finalize_pair(const SearchParams& P, int pair, const Grp<GS>& g,
     PairState& ps = P.state[pair];
     const PairGraph& pg = P.graphs[pair];
     // read by lane 0 and broadcast (see the note at task install)
-    int status = 0, k = 0, ab = 0;
+    int status = 0, k = 0, ab = 0, fl = 0;
     if (g.q == 0) {
         status = vload(&ps.status);
         k = vload(&ps.inc);
         ab = vload(&ps.abort);
+        fl = vload(&ps.floor);
     }
     status = g.shfl(status, 0);
     k = g.shfl(k, 0);
     ab = g.shfl(ab, 0);
+    fl = g.shfl(fl, 0);
+    if (status == MCS_PENDING && ab != 1 && fl > 0 && k <= fl) {
+        // Top-down (Section IV): the goal fl + 1 is unreachable -- the whole
+        // tree was searched without beating the floor.  Search again from the
+        // root with the next smaller goal; the pair's time limit keeps running.
+        int ok = 1;
+        if (g.q == 0) ok = requeue_next_goal(P, pair, fl) ? 1 : 0;
+        ok = g.shfl(ok, 0);
+        if (ok) { g.sync(); return; }
+        // the ring slot never freed (recorded below): finish the pair instead
+        if (g.q == 0) atomicCAS(&P.ctl->error, 0, MCS_ERR_DEVICE_STALL);
+        k = fl;
+    }
     if (status == MCS_PENDING) {
         if (!DBG_OK(P.ctl, k >= 0 && k < kLevels, 7, k)) k = 0;
-        status = ab ? MCS_TIMEOUT : MCS_OK;
+        // a floor without a mapping above it (time limit during a goal search) reports nothing
+        if (fl > 0 && k <= fl) k = 0;
+        status = ab == 1 ? MCS_TIMEOUT : MCS_OK;
         if constexpr (SERVE) { finalize_served<GS>(P, pair, status, k, g, smap); return; }
         if (P.out_map) {
             const uint16_t* slot = P.best + ((size_t)pair * kLevels + k) * kMaxN;
@@ -676,6 +722,7 @@ __device__ void serve_pack(const SearchParams& P, int slot, int lane, long long*
     if (lane == 0) {
         PairState& ps = P.state[slot];
         ps.inc = 0; ps.open = 1; ps.abort = 0; ps.nodes = 0;
+        ps.floor = 0; ps.cap = kNoCap;
         ps.t_start = 0; ps.deadline = 0; ps.ticket = rtk; ps.timeout_ns = rt;
         ps.status = ok ? MCS_PENDING : MCS_ERR_ARG;
     }
@@ -1005,8 +1052,10 @@ __global__ void __launch_bounds__(256, (GS == 32 ? MCS_SEARCH_MINB : MCS_GROUP_M
             }
             if (g.q == 0) {
                 u64 now = gtimer();
-                ps.t_start = now;
-                ps.deadline = now + (SERVE ? vload(&ps.timeout_ns) : P.timeout_ns);
+                if (vload(&ps.t_start) == 0) {     // the first root (top-down re-enqueues it per goal)
+                    ps.t_start = now;
+                    ps.deadline = now + (SERVE ? vload(&ps.timeout_ns) : P.timeout_ns);
+                }
                 atomicMax(&ctl->last_progress, now);
             }
         }
@@ -1205,6 +1254,19 @@ __global__ void __launch_bounds__(256, (GS == 32 ? MCS_SEARCH_MINB : MCS_GROUP_M
                     } else {
                         inc = old;
                     }
+                    // goal reached (top-down, Section IV; the cap is read only when the
+                    // incumbent grows): the pair is solved -- every searcher on it stops
+                    // at its next poll, this one now (depth -1 is below every task's)
+                    if (__builtin_expect((P.flags & MCS_TOP_DOWN) != 0, 0)) {
+                        int cap = 0;
+                        if (g.q == 0) cap = vload(&ps.cap);
+                        cap = g.shfl(cap, 0);
+                        if (inc >= cap) {
+                            if (g.q == 0) atomicCAS(&ps.abort, 0, 2);
+                            t.d = -1;
+                            return;
+                        }
+                    }
                 }
                 if (dm + sum <= inc) { ++pruned; return; }    // child pruned by Eq. 1
                 const unsigned kmin = g.umin(best);
@@ -1264,7 +1326,7 @@ __global__ void __launch_bounds__(256, (GS == 32 ? MCS_SEARCH_MINB : MCS_GROUP_M
                 p_abort = vload(&ps.abort);
                 p_hungry = vload(&ctl->q_head) > vload(&ctl->q_tail);   // a searcher waits
                 if (!p_abort && (tick & 255) == 0 && gtimer() > vload(&ps.deadline)) {
-                    ps.abort = 1;                      // per-pair time limit
+                    atomicCAS(&ps.abort, 0, 1);        // per-pair time limit (a reached goal stays)
                     p_abort = 1;
                 }
                 if (cvisits >= (1u << 31)) { atomicAdd(&ctl->class_visits, (u64)cvisits); cvisits = 0; }
