@@ -7,6 +7,7 @@ It shares no code with the CUDA path.
 * ``mcs``        -- sequential recursive McSplit (Section II-B, Algorithm 1, Eq. 1)
 * ``mcs_goal``   -- one goal-directed McSplit search (Section IV, top-down strategy)
 * ``mcs_topdown``-- the top-down strategy: goal sizes min(|V_G|,|V_H|), one less, ...
+* ``mcs_deadend``-- dead-end forecasting with a bound increase and a binary search (Section IV)
 * ``bruteforce`` -- exhaustive injective partial mappings (definition, Section II-A)
 * ``clique``     -- maximum clique of the modular product graph (textbook reduction)
 * ``verify``     -- checks a mapping is a common induced subgraph (Section II-A)
@@ -52,6 +53,9 @@ def _load():
     lib.oracle_mcs_goal.restype = ctypes.c_int
     lib.oracle_mcs_topdown.argtypes = lib.oracle_mcs.argtypes
     lib.oracle_mcs_topdown.restype = ctypes.c_int
+    lib.oracle_mcs_deadend.argtypes = g + [ctypes.c_int, ctypes.c_int64, ctypes.c_int, ctypes.c_int64,
+                                           ctypes.c_double, _i32p, _i32p, _i64p, ctypes.POINTER(ctypes.c_int)]
+    lib.oracle_mcs_deadend.restype = ctypes.c_int
     lib.oracle_bruteforce.argtypes = g + [_i32p, _i32p]
     lib.oracle_bruteforce.restype = ctypes.c_int
     lib.oracle_clique.argtypes = g + [_i32p, _i32p]
@@ -136,6 +140,26 @@ def mcs_topdown(adjG, adjH, labG=None, labH=None, directed: bool = False,
     st = ctypes.c_int(0)
     k = lib.oracle_mcs_topdown(*ga, *ha, int(directed), int(node_limit), float(time_limit_s),
                                og.ctypes.data_as(_i32p), oh.ctypes.data_as(_i32p),
+                               ctypes.byref(nodes), ctypes.byref(st))
+    return OracleResult(int(k), og[:k].copy(), oh[:k].copy(), int(nodes.value), st.value == 0)
+
+
+def mcs_deadend(adjG, adjH, threshold: int, doubling: bool = False, labG=None, labH=None,
+                directed: bool = False, node_limit: int = 0, time_limit_s: float = 0.0) -> OracleResult:
+    """Dead-end forecasting (Section IV): the plain search raises its
+    incumbent size by one (or doubles it) after `threshold` nodes without a
+    new incumbent; an unreachable raised value becomes an upper bound that a
+    binary search of goal-directed searches closes."""
+    lib = _load()
+    ga, keep1 = _gargs(adjG, labG)
+    ha, keep2 = _gargs(adjH, labH)
+    n = max(1, min(ga[0], ha[0]))
+    og = np.zeros(n, np.int32)
+    oh = np.zeros(n, np.int32)
+    nodes = ctypes.c_int64(0)
+    st = ctypes.c_int(0)
+    k = lib.oracle_mcs_deadend(*ga, *ha, int(directed), int(threshold), int(bool(doubling)), int(node_limit),
+                               float(time_limit_s), og.ctypes.data_as(_i32p), oh.ctypes.data_as(_i32p),
                                ctypes.byref(nodes), ctypes.byref(st))
     return OracleResult(int(k), og[:k].copy(), oh[:k].copy(), int(nodes.value), st.value == 0)
 

@@ -22,6 +22,11 @@
 //   oracle_mcs_topdown the top-down strategy of Section IV: one goal-directed
 //                      search per goal size min(|V_G|,|V_H|), one less, ...,
 //                      until a goal is reached
+//   oracle_mcs_deadend dead-end forecasting with a bound increase and a binary
+//                      search (Section IV): the plain search raises its
+//                      incumbent size by 1 (or doubles it) after a number of
+//                      nodes without improvement; an unreachable raised value
+//                      is an upper bound, closed by goal-directed searches
 //
 // Readings where the paper is silent (the McSplit publication it cites fixes
 // them; none of them changes the optimum, only the traversal):
@@ -123,6 +128,12 @@ struct McSplit {
     int floor = 0;
     int cap = 1 << 30;
     bool reached = false;
+    // Dead-end forecast (Section IV): after `dead_threshold` nodes without a
+    // new incumbent the incumbent size is raised -- by one, or doubled -- as
+    // if a mapping of that size were known (0: off).
+    int64_t dead_threshold = 0;
+    bool dead_double = false;
+    int64_t since = 0;
 
     int incumbent() const { return std::max((int)best.size(), floor); }
 
@@ -175,9 +186,16 @@ struct McSplit {
     void solve(std::vector<LabelClass> cl, int depth) {
         ++nodes;
         if (aborted || out_of_budget()) { aborted = true; return; }
+        ++since;
         if ((int)M.size() > incumbent()) {                    // incumbent (Algorithm 1)
             best = M;
+            since = 0;
             if ((int)best.size() >= cap) { reached = true; return; }   // goal reached (Section IV)
+        }
+        if (dead_threshold > 0 && since >= dead_threshold) {  // dead end forecast (Section IV)
+            const int inc = incumbent();
+            floor = dead_double ? std::max(inc + 1, 2 * inc) : inc + 1;
+            since = 0;
         }
         if (bound(cl) <= incumbent()) return;                 // prune (Algorithm 1, Eq. 1)
         // selectLabelClass (Algorithm 1): smallest max(|L|,|R|), ties to the
@@ -457,6 +475,61 @@ int oracle_mcs_topdown(int nG, const uint8_t* adjG, const int32_t* labG,
         if (s.aborted) { st = 1; break; }
         if (k > 0 || kmax == 0) break;          // the goal was reached
     }
+    for (int i = 0; i < k; ++i) {
+        if (out_g) out_g[i] = og[best[i].first];
+        if (out_h) out_h[i] = oh[best[i].second];
+    }
+    if (nodes) *nodes = total;
+    if (status) *status = st;
+    return k;
+}
+
+// Dead-end forecasting with a bound increase (Section IV).  The plain search
+// runs with the forecast on (raise by one, or double when `doubling`, after
+// `threshold` nodes without a new incumbent).  When it ends, a recorded
+// mapping larger than the last raised value is optimal.  Otherwise the raised
+// value U is an upper bound and the best recorded mapping size L a lower
+// bound, and a binary search closes [L, U]: a goal-directed search (floor
+// m - 1, cap m) for m = ceil((L + U) / 2) sets L = m when it reaches m, else
+// U = m - 1.  Returns the optimum with its mapping as oracle_mcs; *nodes sums
+// all searches; *status 1 when a limit stopped it (then the size is the best
+// recorded mapping's).
+int oracle_mcs_deadend(int nG, const uint8_t* adjG, const int32_t* labG,
+                       int nH, const uint8_t* adjH, const int32_t* labH,
+                       int directed, int64_t threshold, int doubling,
+                       int64_t node_limit, double time_limit_s,
+                       int32_t* out_g, int32_t* out_h, int64_t* nodes, int* status) {
+    OGraph g0 = make_graph(nG, adjG, labG), h0 = make_graph(nH, adjH, labH);
+    std::vector<int> og = degree_order(g0, directed != 0), oh = degree_order(h0, directed != 0);
+    OGraph G = relabel(g0, og), H = relabel(h0, oh);
+    const auto t0 = std::chrono::steady_clock::now();
+    auto left = [&](double lim) {
+        return lim > 0 ? lim - std::chrono::duration<double>(std::chrono::steady_clock::now() - t0).count() : 0.0;
+    };
+    McSplit s(G, H, directed != 0, node_limit, time_limit_s);
+    s.dead_threshold = threshold;
+    s.dead_double = doubling != 0;
+    s.solve(initial_classes(G, H), 0);
+    int64_t total = s.nodes;
+    int st = s.aborted ? 1 : 0;
+    std::vector<std::pair<int, int>> best = s.best;
+    int lo = (int)best.size();
+    int hi = std::max(lo, s.floor);
+    while (!st && lo < hi) {
+        const int m = (lo + hi + 1) / 2;
+        const double tl = left(time_limit_s);
+        const int64_t nl = node_limit > 0 ? node_limit - total : 0;
+        if ((time_limit_s > 0 && tl <= 0) || (node_limit > 0 && nl <= 0)) { st = 1; break; }
+        McSplit q(G, H, directed != 0, nl, tl);
+        q.floor = m - 1;
+        q.cap = m;
+        q.solve(initial_classes(G, H), 0);
+        total += q.nodes;
+        if ((int)q.best.size() >= m) { lo = m; best = q.best; }
+        else if (q.aborted) st = 1;
+        else hi = m - 1;
+    }
+    const int k = (int)best.size();
     for (int i = 0; i < k; ++i) {
         if (out_g) out_g[i] = og[best[i].first];
         if (out_h) out_h[i] = oh[best[i].second];

@@ -294,3 +294,46 @@ def test_topdown_nodes_sum_over_goal_searches():
         assert r.size == opt
         total = sum(oracle.mcs_goal(a, b, g - 1, g).nodes for g in range(11, opt - 1, -1))
         assert r.nodes == total
+
+
+@pytest.mark.parametrize("threshold,doubling", [(1, False), (3, False), (20, False), (1, True), (7, True)])
+def test_deadend_vs_bruteforce(threshold, doubling):
+    """Dead-end forecasting reaches the optimum of exhaustive enumeration
+    whatever the threshold: raised bounds that are unreachable are closed by
+    the binary search, reachable ones are overtaken by a larger mapping."""
+    rs = np.random.default_rng(131 + threshold + (50 if doubling else 0))
+    for s in range(80):
+        directed = bool(s % 3 == 0)
+        k = 3 if s % 4 == 1 else 0
+        nG, nH = int(rs.integers(0, 10)), int(rs.integers(0, 10))
+        a, b, la, lb = _rand_pair(s + 10000 + 97 * threshold, nG, nH, float(rs.uniform(0.1, 0.7)), directed, k)
+        r = oracle.mcs_deadend(a, b, threshold, doubling, la, lb, directed=directed)
+        kb, _, _ = oracle.bruteforce(a, b, la, lb)
+        assert r.complete
+        assert r.size == kb, (s, threshold, doubling, r.size, kb)
+        assert len(r.g_idx) == r.size
+        assert oracle.verify(a, b, r.g_idx, r.h_idx, la, lb) == 1
+
+
+def test_deadend_with_a_huge_threshold_is_the_plain_search():
+    """A threshold that is never reached leaves the plain search unchanged,
+    node for node."""
+    for s in range(15):
+        a, b, _, _ = _rand_pair(s + 11000, 12, 14, 0.4)
+        r = oracle.mcs_deadend(a, b, 1 << 40)
+        o = oracle.mcs(a, b)
+        assert r.size == o.size and r.nodes == o.nodes
+
+
+def test_deadend_raises_change_the_traversal_on_larger_pairs():
+    """On pairs whose plain search runs long after its last improvement, a
+    small threshold raises the bound (the traversal differs from the plain
+    one) and the optimum is unchanged."""
+    changed = 0
+    for s in range(10):
+        a, b, _, _ = _rand_pair(s + 12000, 16, 18, 0.5)
+        o = oracle.mcs(a, b)
+        r = oracle.mcs_deadend(a, b, 50)
+        assert r.size == o.size
+        changed += r.nodes != o.nodes
+    assert changed >= 5
