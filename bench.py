@@ -15,8 +15,8 @@ the timed events.  `value` = pairs solved / summed step time.
 Other workloads: c3 (4,096 labelled pairs), c1 (one small pair), c4 (2,048
 bounded-valence pairs, learned order, 1 s per pair), c5 (serving on a Poisson
 stream), td (96 bounded-valence pairs with a 90 % planted core, solved with
-the top-down strategy of Section IV; the line adds the plain search of the
-same batch).
+the top-down strategy of Section IV; the line adds the plain search and the
+dead-end forecast of the same batch).
 
 `--impl reference` times the CPU oracle (plain sequential McSplit) on the
 host cores on a bounded sample of the same workload; it is the reference arm
@@ -329,7 +329,7 @@ def main():
         import torch.distributed as dist
         dist.init_process_group("nccl")
     from paper_1908_06418_b300 import (Solver, pack_host, MCS_DIRECTED, MCS_OK, MCS_WORD32, MCS_ORDER_LEARNED,
-                                       MCS_TOP_DOWN)
+                                       MCS_TOP_DOWN, MCS_DEAD_END)
 
     pairs, cfg = workload(a.workload)
     gold = golden_sizes(a.workload)
@@ -526,7 +526,7 @@ def main():
             "roofline": roof, "clocks": csum}
     if rank == 0 and (learned or topdown):
         # the same batch with and without the strategy under test
-        def one_pass(flag_clear):
+        def one_pass(flag_clear, flag_set=0):
             torch.cuda.synchronize()
             e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
             e0.record(stream)
@@ -534,7 +534,8 @@ def main():
                 apply_shape(solver, g.get("shape"))
                 solver.solve_batch_device(g["n"], g["d_n"], g["d_adj_off"], g["d_adj"], g["d_lab_off"],
                                           g["d_labels"], g["size"], g["status"], g["nodes"], g["map"],
-                                          g["usec"], flags=g["flags"] & ~flag_clear, timeout_s=a.timeout,
+                                          g["usec"], flags=(g["flags"] & ~flag_clear) | flag_set,
+                                          timeout_s=a.timeout,
                                           stream=stream.cuda_stream)
             e1.record(stream)
             torch.cuda.synchronize()
@@ -547,13 +548,15 @@ def main():
             cmp = {"learned": one_pass(0), "plain": one_pass(MCS_ORDER_LEARNED)}
             key = "order_comparison"
         else:
-            cmp = {"top_down": one_pass(0), "plain": one_pass(MCS_TOP_DOWN)}
+            cmp = {"top_down": one_pass(0), "plain": one_pass(MCS_TOP_DOWN),
+                   "dead_end": one_pass(MCS_TOP_DOWN, MCS_DEAD_END)}
             key = "strategy_comparison"
             # both are exact: where both proved their result the sizes must agree
-            a_, b_ = cmp["top_down"], cmp["plain"]
-            both = (a_["_status"] == MCS_OK) & (b_["_status"] == MCS_OK)
-            if not np.array_equal(a_["_sizes"][both], b_["_sizes"][both]):
-                raise SystemExit("PARITY FAILURE: top-down and plain optima differ")
+            for other in ("top_down", "dead_end"):
+                a_, b_ = cmp[other], cmp["plain"]
+                both = (a_["_status"] == MCS_OK) & (b_["_status"] == MCS_OK)
+                if not np.array_equal(a_["_sizes"][both], b_["_sizes"][both]):
+                    raise SystemExit(f"PARITY FAILURE: {other} and plain optima differ")
         for v in cmp.values():
             v.pop("_sizes"); v.pop("_status")
         line[key] = dict(cmp, note="one pass each over the whole batch; exact either way, "

@@ -77,6 +77,14 @@ extern "C" {
                                     /* goal reached is the optimum.  A time limit     */
                                     /* before that reports size 0 (MCS_TIMEOUT).      */
                                     /* Batch calls only (mcs_submit: unsupported).    */
+#define MCS_DEAD_END          0x80u /* dead-end forecast (Section IV): after          */
+                                    /* mcs_set_dead_end's threshold of nodes without  */
+                                    /* a new incumbent, the pair's incumbent size is  */
+                                    /* raised by one (or doubled); an unreachable     */
+                                    /* raised value bounds the optimum, and a binary  */
+                                    /* search of goal-directed searches from the root */
+                                    /* closes the gap.  Exact.  Not with MCS_TOP_DOWN */
+                                    /* (MCS_ERR_ARG); batch calls only.               */
 
 typedef struct mcs_ctx mcs_ctx;
 
@@ -271,6 +279,13 @@ int mcs_set_search_group(mcs_ctx* ctx, int lanes);
  * mcs_submit on the context: MCS_ERR_UNSUPPORTED afterwards (unless the
  * value is unchanged); other values: MCS_ERR_ARG. */
 int mcs_set_serve_group(mcs_ctx* ctx, int lanes);
+
+/* MCS_DEAD_END parameters: threshold_nodes (>= 1; -1 restores the default
+ * 2^22) is the number of search nodes of a pair, counted over all its
+ * searchers at their polls, without a new incumbent before the incumbent size
+ * is raised; doubling 1 doubles it, 0 (default) adds one, -1 restores the
+ * default.  Applies to later calls.  MCS_ERR_ARG for other values. */
+int mcs_set_dead_end(mcs_ctx* ctx, long long threshold_nodes, int doubling);
 
 /* Statistics of the last solve on this context: out[0] search-kernel
  * microseconds (for mcs_solve_batch_device: once its stream has passed the

@@ -132,6 +132,8 @@ int run_device(mcs_ctx* c, int npairs, const int32_t* d_n, const int64_t* d_adj_
                int32_t* d_status, uint64_t* d_nodes, int16_t* d_map, float* d_usec,
                cudaStream_t s, bool timed) {
     if (npairs < 0) return MCS_ERR_ARG;
+    // the two goal-directed strategies of Section IV are alternatives
+    if ((flags & MCS_TOP_DOWN) && (flags & MCS_DEAD_END)) return MCS_ERR_ARG;
     if (npairs == 0) return 0;
     const bool directed = (flags & MCS_DIRECTED) != 0;
     int rc = 0;
@@ -200,6 +202,8 @@ int run_device(mcs_ctx* c, int npairs, const int32_t* d_n, const int64_t* d_adj_
     sp.rank = rank;
     sp.poll_mask = (uint32_t)c->poll_nodes - 1;
     sp.steal_keep_q4 = c->steal_keep_q4;
+    sp.dead_nodes = (u64)c->dead_nodes;
+    sp.dead_double = c->dead_double;
     sp.out_size = d_size;
     sp.out_status = d_status;
     sp.out_nodes = reinterpret_cast<u64*>(d_nodes);
@@ -290,6 +294,13 @@ int mcs_set_steal(mcs_ctx* c, int poll_nodes, int keep_quarters) {
     if (keep_quarters < -1 || keep_quarters > 3) return MCS_ERR_ARG;
     if (poll_nodes) c->poll_nodes = poll_nodes > 0 ? poll_nodes : (int)kPollMaskDefault + 1;
     if (keep_quarters) c->steal_keep_q4 = keep_quarters > 0 ? keep_quarters : kStealKeepDefault;
+    return 0;
+}
+
+int mcs_set_dead_end(mcs_ctx* c, long long threshold_nodes, int doubling) {
+    if (!c || threshold_nodes == 0 || threshold_nodes < -1 || doubling < -1 || doubling > 1) return MCS_ERR_ARG;
+    c->dead_nodes = threshold_nodes > 0 ? threshold_nodes : (1LL << 22);
+    c->dead_double = doubling > 0 ? 1 : 0;
     return 0;
 }
 

@@ -44,6 +44,10 @@ struct PairState {
     // larger than `floor` are recorded, and the pair stops once the incumbent
     // reaches `cap`.  Plain search: floor 0, cap kNoCap.
     int32_t floor, cap;
+    int32_t real;          // size of the largest recorded mapping (atomicMax)
+    int32_t lo, hi;        // dead-end mode: bounds of the binary search over goals
+    int32_t pad_;
+    u64 dead;              // dead-end mode: nodes since the last new incumbent (approx.)
 };
 constexpr int32_t kNoCap = 1 << 30;
 
@@ -144,6 +148,8 @@ struct SearchParams {
     const uint8_t* rank;           // learned order: [npairs][kMaxN][kMaxN] rank of u for v, or null
     uint32_t poll_mask;            // work sharing: poll every poll_mask + 1 nodes (power of two)
     int32_t steal_keep_q4;         // a donor keeps ceil(k * q / 4) of k candidates (1..3)
+    u64 dead_nodes;                // MCS_DEAD_END: nodes without a new incumbent before a raise
+    int32_t dead_double;           // MCS_DEAD_END: 1 doubles the incumbent size, 0 adds one
     // outputs
     int32_t* out_size;
     int32_t* out_status;
@@ -227,6 +233,8 @@ struct mcs_ctx {
     int serve_lanes = 32;         // lanes per searcher of the server launch: 32, 16 or 8
     int poll_nodes = 16;          // work-sharing poll interval (nodes, power of two)
     int steal_keep_q4 = 2;        // quarters of a donated level's candidates the donor keeps
+    long long dead_nodes = 1LL << 22;   // MCS_DEAD_END: nodes without a new incumbent before a raise
+    int dead_double = 0;          // MCS_DEAD_END: 1 doubles the incumbent size, 0 adds one
     // resident blocks per SM of each launch configuration already asked of the
     // driver (key: warps per block, shared memory per block, kernel variant)
     std::unordered_map<uint64_t, int> occupancy;

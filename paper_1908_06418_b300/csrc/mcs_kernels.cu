@@ -280,6 +280,9 @@ __global__ void pack_kernel(PackParams P) {
         st.floor = td ? kmax - 1 : 0;
         st.cap = td ? kmax : kNoCap;
         st.inc = st.floor;
+        st.real = 0;
+        st.lo = st.hi = 0;
+        st.dead = 0;
         st.open = 1;
         st.status = ok ? MCS_PENDING : MCS_ERR_ARG;
         st.abort = 0;
@@ -563,15 +566,16 @@ __device__ void finalize_served(const SearchParams& P, int pair, int status, int
     g.sync();
 }
 
-// Top-down (Section IV), one lane: the goal fl + 1 was not reached, so the
-// pair searches again from its root with the goal fl (floor fl - 1, cap fl).
-// Out of line: it runs once per goal, and inlined it would cost the node loop
-// registers.  False if the bounded wait for a ring slot expired.
-__device__ __noinline__ bool requeue_next_goal(const SearchParams& P, int pair, int fl) {
+// Goal-directed search (Section IV), one lane: the pair searches again from
+// its root for the goal `cap` (only mappings larger than `floor` = cap - 1 are
+// recorded).  Out of line: it runs once per goal, and inlined it would cost
+// the node loop registers.  False if the bounded wait for a ring slot expired.
+__device__ __noinline__ bool requeue_goal(const SearchParams& P, int pair, int floor, int cap) {
     PairState& ps = P.state[pair];
-    ps.floor = fl - 1;
-    ps.cap = fl;
-    ps.inc = fl - 1;
+    ps.floor = floor;
+    ps.cap = cap;
+    ps.inc = floor;
+    ps.abort = 0;
     ps.open = 1;
     __threadfence();
     const uint32_t qmask = P.qcap - 1;
@@ -595,33 +599,57 @@ __device__ void finalize_pair(const SearchParams& P, int pair, const Grp<GS>& g,
     PairState& ps = P.state[pair];
     const PairGraph& pg = P.graphs[pair];
     // read by lane 0 and broadcast (see the note at task install)
-    int status = 0, k = 0, ab = 0, fl = 0;
+    int status = 0, k = 0, ab = 0, fl = 0, cp = 0, lo = 0, hi = 0;
     if (g.q == 0) {
         status = vload(&ps.status);
-        k = vload(&ps.inc);
+        k = vload(&ps.real);
         ab = vload(&ps.abort);
         fl = vload(&ps.floor);
+        cp = vload(&ps.cap);
+        lo = vload(&ps.lo);
+        hi = vload(&ps.hi);
     }
     status = g.shfl(status, 0);
     k = g.shfl(k, 0);
     ab = g.shfl(ab, 0);
     fl = g.shfl(fl, 0);
-    if (status == MCS_PENDING && ab != 1 && fl > 0 && k <= fl) {
-        // Top-down (Section IV): the goal fl + 1 is unreachable -- the whole
-        // tree was searched without beating the floor.  Search again from the
-        // root with the next smaller goal; the pair's time limit keeps running.
+    cp = g.shfl(cp, 0);
+    lo = g.shfl(lo, 0);
+    hi = g.shfl(hi, 0);
+    // Goal-directed strategies (Section IV): decide whether the pair is
+    // settled, else the goal of its next search from the root (0: none).
+    int next_goal = 0;
+    if (status == MCS_PENDING && ab != 1) {
+        if ((P.flags & MCS_TOP_DOWN) && cp < kNoCap && k < cp && fl > 0) {
+            next_goal = fl;                       // top-down: goal fl + 1 unreachable, try fl
+        } else if (P.flags & MCS_DEAD_END) {
+            if (cp == kNoCap) {
+                // the search with raised bounds ended: a mapping at least the last
+                // raised value is optimal, else that value bounds the optimum
+                lo = k;
+                hi = k >= fl ? k : fl;
+            } else if (k >= cp) {
+                lo = cp;                          // the probed goal was reached
+            } else {
+                hi = cp - 1;                      // the probed goal is unreachable
+            }
+            if (lo < hi) next_goal = (lo + hi + 1) / 2;
+        }
+    }
+    if (next_goal > 0) {
         int ok = 1;
-        if (g.q == 0) ok = requeue_next_goal(P, pair, fl) ? 1 : 0;
+        if (g.q == 0) {
+            ps.lo = lo;
+            ps.hi = hi;
+            ok = requeue_goal(P, pair, next_goal - 1, next_goal) ? 1 : 0;
+        }
         ok = g.shfl(ok, 0);
         if (ok) { g.sync(); return; }
-        // the ring slot never freed (recorded below): finish the pair instead
+        // the ring slot never freed (recorded below): finish with what is known
         if (g.q == 0) atomicCAS(&P.ctl->error, 0, MCS_ERR_DEVICE_STALL);
-        k = fl;
     }
     if (status == MCS_PENDING) {
         if (!DBG_OK(P.ctl, k >= 0 && k < kLevels, 7, k)) k = 0;
-        // a floor without a mapping above it (time limit during a goal search) reports nothing
-        if (fl > 0 && k <= fl) k = 0;
         status = ab == 1 ? MCS_TIMEOUT : MCS_OK;
         if constexpr (SERVE) { finalize_served<GS>(P, pair, status, k, g, smap); return; }
         if (P.out_map) {
@@ -722,7 +750,7 @@ __device__ void serve_pack(const SearchParams& P, int slot, int lane, long long*
     if (lane == 0) {
         PairState& ps = P.state[slot];
         ps.inc = 0; ps.open = 1; ps.abort = 0; ps.nodes = 0;
-        ps.floor = 0; ps.cap = kNoCap;
+        ps.floor = 0; ps.cap = kNoCap; ps.real = 0; ps.lo = ps.hi = 0; ps.dead = 0;
         ps.t_start = 0; ps.deadline = 0; ps.ticket = rtk; ps.timeout_ns = rt;
         ps.status = ok ? MCS_PENDING : MCS_ERR_ARG;
     }
@@ -1251,6 +1279,10 @@ __global__ void __launch_bounds__(256, (GS == 32 ? MCS_SEARCH_MINB : MCS_GROUP_M
                     if (old < dm) {
                         write_best<GS>(P, pair, w, t.d, v, u, g);
                         inc = dm;
+                        if (g.q == 0) {
+                            atomicMax(&ps.real, dm);        // a recorded mapping of size dm
+                            if (P.flags & MCS_DEAD_END) ps.dead = 0;
+                        }
                     } else {
                         inc = old;
                     }
@@ -1328,6 +1360,21 @@ __global__ void __launch_bounds__(256, (GS == 32 ? MCS_SEARCH_MINB : MCS_GROUP_M
                 if (!p_abort && (tick & 255) == 0 && gtimer() > vload(&ps.deadline)) {
                     atomicCAS(&ps.abort, 0, 1);        // per-pair time limit (a reached goal stays)
                     p_abort = 1;
+                }
+                if ((P.flags & MCS_DEAD_END) && p_abort == 0) {
+                    // dead-end forecast (Section IV): the searcher whose poll takes the
+                    // pair's count of nodes without a new incumbent past the threshold
+                    // raises the incumbent size, as if a mapping of that size were known
+                    const u64 step = (u64)P.poll_mask + 1;
+                    const u64 before = atomicAdd((unsigned long long*)&ps.dead, (unsigned long long)step);
+                    if (before < P.dead_nodes && before + step >= P.dead_nodes && vload(&ps.cap) == kNoCap) {
+                        const int cur = vload(&ps.inc);
+                        const int r = min(P.dead_double ? max(cur + 1, 2 * cur) : cur + 1, kMaxN);
+                        atomicMax(&ps.floor, r);
+                        atomicMax(&ps.inc, r);
+                        atomicExch((unsigned long long*)&ps.dead, 0ull);
+                        p_inc = max(p_inc, r);
+                    }
                 }
                 if (cvisits >= (1u << 31)) { atomicAdd(&ctl->class_visits, (u64)cvisits); cvisits = 0; }
                 if (pruned >= (1u << 31)) { atomicAdd(&ctl->pruned, (u64)pruned); pruned = 0; }

@@ -159,6 +159,8 @@ int launch_server(mcs_ctx* c, ServeState* S) {
     memset(&sp, 0, sizeof(sp));
     sp.poll_mask = kPollMaskDefault;
     sp.steal_keep_q4 = kStealKeepDefault;
+    sp.dead_nodes = 0;
+    sp.dead_double = 0;
     sp.serving = 1;
     sp.sv.host_written = dev_view(S->h_written);
     sp.sv.ring = dev_view(S->h_ring);
@@ -258,7 +260,7 @@ extern "C" {
 int mcs_submit(mcs_ctx* c, const mcs_graph* G, const mcs_graph* H, uint32_t flags, double timeout_s,
                uint64_t* ticket) {
     if (!c || !ticket || check_graph_s(G) || check_graph_s(H)) return MCS_ERR_ARG;
-    if (flags & (MCS_DIRECTED | MCS_ORDER_LEARNED | MCS_TOP_DOWN)) return MCS_ERR_UNSUPPORTED;
+    if (flags & (MCS_DIRECTED | MCS_ORDER_LEARNED | MCS_TOP_DOWN | MCS_DEAD_END)) return MCS_ERR_UNSUPPORTED;
     if (cudaSetDevice(c->device) != cudaSuccess) return MCS_ERR_CUDA;
     ServeState* S = nullptr;
     int rc = serve_state(c, &S);

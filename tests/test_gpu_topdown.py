@@ -115,3 +115,82 @@ def test_topdown_is_rejected_by_the_server(solver):
     a = synth.er_undirected(10, 0.3, synth.rng_for(3700, 0, 0))
     with pytest.raises(Exception):
         solver.submit(a, a, flags=MCS_TOP_DOWN)
+
+
+# --------------------------------------------------------------------------
+# dead-end forecasting with a bound increase and a binary search (Section IV)
+# --------------------------------------------------------------------------
+def _golden(name):
+    import json
+    import os
+    here = os.path.dirname(os.path.abspath(__file__))
+    with open(os.path.join(here, "golden", name)) as f:
+        return [json.loads(l) for l in f if l.strip()]
+
+
+@pytest.mark.parametrize("threshold,doubling", [(64, 0), (1024, 0), (64, 1), (4096, 1)])
+def test_deadend_labelled_batch_equals_stored_oracle(solver, threshold, doubling):
+    """512 pairs of the labelled batch with thresholds low enough that pairs
+    raise their bound (and some raise it past the optimum, which the binary
+    search must then recover): every size equals the stored oracle optimum."""
+    from paper_1908_06418_b300 import MCS_DEAD_END
+    rows = {r["idx"]: r for r in _golden("c3_oracle.jsonl")}
+    pairs = synth.config3_pairs()[:512]
+    solver.set_dead_end(threshold, doubling)
+    try:
+        res = solver.solve_batch(pairs, flags=MCS_DEAD_END, timeout_s=60)
+    finally:
+        solver.set_dead_end(-1, -1)
+    for i, (p, r) in enumerate(zip(pairs, res)):
+        g = rows[i]
+        assert r.status == 0, (i, r.status)
+        assert r.size == g["size"] if g["complete"] else r.size >= g["size"], (i, r.size, g["size"])
+        assert oracle.verify(p.G.adj, p.H.adj, r.g_idx, r.h_idx, p.G.labels, p.H.labels) == 1, i
+
+
+@pytest.mark.parametrize("directed,k", [(False, 0), (True, 0), (False, 3)])
+def test_deadend_small_threshold_batch_equals_oracle(solver, directed, k):
+    from paper_1908_06418_b300 import MCS_DEAD_END
+    pairs = _pairs(120, 8, 24, 3800 + k + (50 if directed else 0), directed, k)
+    solver.set_dead_end(32, 0)
+    try:
+        res = solver.solve_batch(pairs, flags=MCS_DEAD_END, directed=directed, timeout_s=60)
+    finally:
+        solver.set_dead_end(-1, -1)
+    for i, (p, r) in enumerate(zip(pairs, res)):
+        o = oracle.mcs(p.G.adj, p.H.adj, p.G.labels, p.H.labels, directed=directed)
+        assert r.status == 0 and r.size == o.size, (i, r.size, o.size)
+        assert oracle.verify(p.G.adj, p.H.adj, r.g_idx, r.h_idx, p.G.labels, p.H.labels) == 1, i
+
+
+def test_deadend_never_reached_is_the_plain_search(solver):
+    """With a threshold no pair reaches, a lone searcher walks the plain
+    search tree node for node."""
+    from paper_1908_06418_b300 import MCS_DEAD_END, MCS_NO_LEVEL_PRUNE
+    pairs = _pairs(20, 4, 16, 3900)
+    solver.set_max_warps(1)
+    solver.set_dead_end(1 << 50, 0)
+    try:
+        for p in pairs:
+            r = solver.solve(p.G.adj, p.H.adj, flags=MCS_DEAD_END | MCS_NO_LEVEL_PRUNE, timeout_s=30)
+            o = oracle.mcs(p.G.adj, p.H.adj)
+            assert r.status == 0 and r.size == o.size and r.nodes == o.nodes
+    finally:
+        solver.set_max_warps(0)
+        solver.set_dead_end(-1, -1)
+
+
+def test_deadend_parameters_and_flag_combination(solver):
+    import torch
+    from paper_1908_06418_b300 import MCS_DEAD_END, MCS_TOP_DOWN, MCS_ERR_ARG, DeviceBatch
+    for bad in ((0, 0), (-2, 0), (100, 2), (100, -2)):
+        with pytest.raises(ValueError):
+            solver.set_dead_end(*bad)
+    pairs = _pairs(4, 6, 10, 3950)
+    b = DeviceBatch(pairs)
+    n = len(pairs)
+    out = [torch.zeros(n, dtype=torch.int32, device=b.device), torch.zeros(n, dtype=torch.int32, device=b.device),
+           torch.zeros(n, dtype=torch.int64, device=b.device)]
+    rc = solver.solve_batch_device(n, b.d_n, b.d_adj_off, b.d_adj, b.d_lab_off, b.d_labels, *out,
+                                   flags=b.flags | MCS_DEAD_END | MCS_TOP_DOWN, timeout_s=10)
+    assert rc == MCS_ERR_ARG
