@@ -8,6 +8,7 @@ It shares no code with the CUDA path.
 * ``mcs_goal``   -- one goal-directed McSplit search (Section IV, top-down strategy)
 * ``mcs_topdown``-- the top-down strategy: goal sizes min(|V_G|,|V_H|), one less, ...
 * ``mcs_deadend``-- dead-end forecasting with a bound increase and a binary search (Section IV)
+* ``hr_order`` / ``mcs_hr`` -- the static component + Hellerman-Rarick-style order (Section IV-A)
 * ``bruteforce`` -- exhaustive injective partial mappings (definition, Section II-A)
 * ``clique``     -- maximum clique of the modular product graph (textbook reduction)
 * ``verify``     -- checks a mapping is a common induced subgraph (Section II-A)
@@ -56,6 +57,10 @@ def _load():
     lib.oracle_mcs_deadend.argtypes = g + [ctypes.c_int, ctypes.c_int64, ctypes.c_int, ctypes.c_int64,
                                            ctypes.c_double, _i32p, _i32p, _i64p, ctypes.POINTER(ctypes.c_int)]
     lib.oracle_mcs_deadend.restype = ctypes.c_int
+    lib.oracle_hr_order.argtypes = [ctypes.c_int, _u8p, ctypes.c_int, _i32p]
+    lib.oracle_hr_order.restype = None
+    lib.oracle_mcs_hr.argtypes = lib.oracle_mcs.argtypes
+    lib.oracle_mcs_hr.restype = ctypes.c_int
     lib.oracle_bruteforce.argtypes = g + [_i32p, _i32p]
     lib.oracle_bruteforce.restype = ctypes.c_int
     lib.oracle_clique.argtypes = g + [_i32p, _i32p]
@@ -161,6 +166,33 @@ def mcs_deadend(adjG, adjH, threshold: int, doubling: bool = False, labG=None, l
     k = lib.oracle_mcs_deadend(*ga, *ha, int(directed), int(threshold), int(bool(doubling)), int(node_limit),
                                float(time_limit_s), og.ctypes.data_as(_i32p), oh.ctypes.data_as(_i32p),
                                ctypes.byref(nodes), ctypes.byref(st))
+    return OracleResult(int(k), og[:k].copy(), oh[:k].copy(), int(nodes.value), st.value == 0)
+
+
+def hr_order(adj, directed: bool = False) -> np.ndarray:
+    """The static order of Section IV-A for one graph: perm[position] = vertex."""
+    lib = _load()
+    a = np.ascontiguousarray(adj, dtype=np.uint8)
+    n = int(a.shape[0])
+    out = np.zeros(max(n, 1), np.int32)
+    lib.oracle_hr_order(n, a.ctypes.data_as(_u8p), int(directed), out.ctypes.data_as(_i32p))
+    return out[:n].copy()
+
+
+def mcs_hr(adjG, adjH, labG=None, labH=None, directed: bool = False,
+           node_limit: int = 0, time_limit_s: float = 0.0) -> OracleResult:
+    """McSplit with the static order of Section IV-A instead of the degree order."""
+    lib = _load()
+    ga, keep1 = _gargs(adjG, labG)
+    ha, keep2 = _gargs(adjH, labH)
+    n = max(1, min(ga[0], ha[0]))
+    og = np.zeros(n, np.int32)
+    oh = np.zeros(n, np.int32)
+    nodes = ctypes.c_int64(0)
+    st = ctypes.c_int(0)
+    k = lib.oracle_mcs_hr(*ga, *ha, int(directed), int(node_limit), float(time_limit_s),
+                          og.ctypes.data_as(_i32p), oh.ctypes.data_as(_i32p),
+                          ctypes.byref(nodes), ctypes.byref(st))
     return OracleResult(int(k), og[:k].copy(), oh[:k].copy(), int(nodes.value), st.value == 0)
 
 

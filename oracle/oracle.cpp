@@ -22,6 +22,10 @@
 //   oracle_mcs_topdown the top-down strategy of Section IV: one goal-directed
 //                      search per goal size min(|V_G|,|V_H|), one less, ...,
 //                      until a goal is reached
+//   oracle_hr_order    the static vertex order of the portfolio section
+//                      (connected components, then a Hellerman-Rarick-style
+//                      column order inside each); oracle_mcs_hr runs McSplit
+//                      with it in place of the degree order
 //   oracle_mcs_deadend dead-end forecasting with a bound increase and a binary
 //                      search (Section IV): the plain search raises its
 //                      incumbent size by 1 (or doubles it) after a number of
@@ -79,6 +83,99 @@ std::vector<int> degree_order(const OGraph& g, bool directed) {
     for (int i = 0; i < g.n; ++i) ord[i] = i;
     std::stable_sort(ord.begin(), ord.end(),
                      [&](int x, int y) { return deg[x] > deg[y]; });
+    return ord;
+}
+
+// Static order of the portfolio modifications (Section IV-A: block structure
+// of the adjacency matrix).  Readings where the text is rough:
+//   * components are weakly connected (arcs in either direction), self-loops
+//     ignored; a component's "rows" are its vertices with an out-arc, its
+//     "columns" those with an in-arc; components go in decreasing
+//     rows/columns ratio (0/0 counts as 0, r/0 with r > 0 as infinite), then
+//     decreasing size, then increasing lowest vertex;
+//   * inside a component the active submatrix starts as its nonzero rows and
+//     columns; each step takes the shortest nonempty active rows (fewest
+//     nonzeros in active columns), picks the active column with a nonzero in
+//     the most of them (ties: lowest vertex), gives it the next position and
+//     removes it from the active columns; rows leave once empty.  When no
+//     active row is left, the remaining active columns follow in increasing
+//     order, then the component's vertices without an in-arc.
+// Returns ord with ord[position] = original vertex.
+std::vector<int> hr_order(const OGraph& g, bool directed) {
+    const int n = g.n;
+    auto arc = [&](int i, int j) { return i != j && (g.edge(i, j) || (!directed && g.edge(j, i))); };
+    std::vector<int> comp(n, -1);
+    std::vector<std::vector<int>> comps;
+    for (int s = 0; s < n; ++s) {
+        if (comp[s] >= 0) continue;
+        std::vector<int> c{s}, stack{s};
+        comp[s] = (int)comps.size();
+        while (!stack.empty()) {
+            int x = stack.back();
+            stack.pop_back();
+            for (int y = 0; y < n; ++y)
+                if (comp[y] < 0 && (arc(x, y) || arc(y, x))) { comp[y] = comp[s]; c.push_back(y); stack.push_back(y); }
+        }
+        std::sort(c.begin(), c.end());
+        comps.push_back(c);
+    }
+    struct Key { long long rows, cols; int size, low; int idx; };
+    std::vector<Key> keys;
+    for (int i = 0; i < (int)comps.size(); ++i) {
+        Key k{0, 0, (int)comps[i].size(), comps[i][0], i};
+        for (int x : comps[i]) {
+            bool r = false, c = false;
+            for (int y = 0; y < n; ++y) { r |= arc(x, y); c |= arc(y, x); }
+            k.rows += r; k.cols += c;
+        }
+        keys.push_back(k);
+    }
+    auto ratio_gt = [](const Key& a, const Key& b) {        // a.rows/a.cols > b.rows/b.cols
+        auto inf = [](const Key& k) { return k.cols == 0 && k.rows > 0; };
+        if (inf(a) || inf(b)) return inf(a) && !inf(b);
+        const long long an = a.cols ? a.rows : 0, ad = a.cols ? a.cols : 1;
+        const long long bn = b.cols ? b.rows : 0, bd = b.cols ? b.cols : 1;
+        return an * bd > bn * ad;
+    };
+    std::sort(keys.begin(), keys.end(), [&](const Key& a, const Key& b) {
+        if (ratio_gt(a, b)) return true;
+        if (ratio_gt(b, a)) return false;
+        if (a.size != b.size) return a.size > b.size;
+        return a.low < b.low;
+    });
+    std::vector<int> ord;
+    for (const Key& k : keys) {
+        const std::vector<int>& c = comps[k.idx];
+        std::vector<char> colact(n, 0), placed(n, 0);
+        for (int x : c)
+            for (int y : c) if (arc(y, x)) colact[x] = 1;
+        for (;;) {
+            int minlen = 1 << 30;
+            std::vector<int> len(n, 0);
+            for (int r : c) {
+                for (int x : c) if (colact[x] && arc(r, x)) ++len[r];
+                if (len[r] > 0) minlen = std::min(minlen, len[r]);
+            }
+            bool any_col = false;
+            for (int x : c) any_col |= colact[x] != 0;
+            if (!any_col) break;
+            if (minlen == (1 << 30)) {                       // no active row: the rest in order
+                for (int x : c) if (colact[x]) { ord.push_back(x); placed[x] = 1; colact[x] = 0; }
+                break;
+            }
+            int best = -1, bestc = -1;
+            for (int x : c) {
+                if (!colact[x]) continue;
+                int cnt = 0;
+                for (int r : c) if (len[r] == minlen && arc(r, x)) ++cnt;
+                if (cnt > bestc) { bestc = cnt; best = x; }
+            }
+            ord.push_back(best);
+            placed[best] = 1;
+            colact[best] = 0;
+        }
+        for (int x : c) if (!placed[x]) ord.push_back(x);
+    }
     return ord;
 }
 
@@ -536,6 +633,34 @@ int oracle_mcs_deadend(int nG, const uint8_t* adjG, const int32_t* labG,
     }
     if (nodes) *nodes = total;
     if (status) *status = st;
+    return k;
+}
+
+// The static order of hr_order for one graph: out_perm[position] = vertex.
+void oracle_hr_order(int n, const uint8_t* adj, int directed, int32_t* out_perm) {
+    OGraph g = make_graph(n, adj, nullptr);
+    std::vector<int> ord = hr_order(g, directed != 0);
+    for (int i = 0; i < n; ++i) out_perm[i] = ord[i];
+}
+
+// oracle_mcs with the hr_order renumbering of both graphs in place of the
+// degree order (everything else identical).
+int oracle_mcs_hr(int nG, const uint8_t* adjG, const int32_t* labG,
+                  int nH, const uint8_t* adjH, const int32_t* labH,
+                  int directed, int64_t node_limit, double time_limit_s,
+                  int32_t* out_g, int32_t* out_h, int64_t* nodes, int* status) {
+    OGraph g0 = make_graph(nG, adjG, labG), h0 = make_graph(nH, adjH, labH);
+    std::vector<int> og = hr_order(g0, directed != 0), oh = hr_order(h0, directed != 0);
+    OGraph G = relabel(g0, og), H = relabel(h0, oh);
+    McSplit s(G, H, directed != 0, node_limit, time_limit_s);
+    s.solve(initial_classes(G, H), 0);
+    int k = (int)s.best.size();
+    for (int i = 0; i < k; ++i) {
+        if (out_g) out_g[i] = og[s.best[i].first];
+        if (out_h) out_h[i] = oh[s.best[i].second];
+    }
+    if (nodes) *nodes = s.nodes;
+    if (status) *status = s.aborted ? 1 : 0;
     return k;
 }
 

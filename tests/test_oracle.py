@@ -337,3 +337,69 @@ def test_deadend_raises_change_the_traversal_on_larger_pairs():
         assert r.size == o.size
         changed += r.nodes != o.nodes
     assert changed >= 5
+
+
+# --------------------------------------------------------------------------
+# static component + Hellerman-Rarick-style order (Section IV-A)
+# --------------------------------------------------------------------------
+def test_hr_order_hand_derived_cases():
+    """Orders derived by hand from the procedure of Section IV-A (components
+    by decreasing rows/columns ratio, then size; inside a component the
+    column meeting most of the shortest active rows goes next):
+    path 0-1-2-3-4: shortest rows {0,4} -> column 1 (tie with 3, lower
+    first); then rows {2,4} -> 3; then rows {1,3} -> 2; then 0, 4.
+    star 0-{1,2,3,4}, edge 6-7, isolated 5: the star (ratio 1, size 5), its
+    centre first; then the edge; the isolated vertex (ratio 0) last.
+    triangle 0-1-2 beside the 4-cycle 3-4-5-6: the larger component first,
+    3 (all rows tie), then 5 (meets both shortest rows 4 and 6), 4, 6.
+    arcs 0->1->2 and 3->4, vertex 5: columns are in-arcs, so 1, 2, then the
+    vertex without an in-arc, 0."""
+    def E(n, edges):
+        a = np.zeros((n, n), np.uint8)
+        for i, j in edges:
+            a[i, j] = a[j, i] = 1
+        return a
+    assert oracle.hr_order(E(5, [(0, 1), (1, 2), (2, 3), (3, 4)])).tolist() == [1, 3, 2, 0, 4]
+    assert oracle.hr_order(E(8, [(0, 1), (0, 2), (0, 3), (0, 4), (6, 7)])).tolist() == [0, 1, 2, 3, 4, 6, 7, 5]
+    assert oracle.hr_order(E(7, [(0, 1), (1, 2), (0, 2), (3, 4), (4, 5), (5, 6), (6, 3)])).tolist() == \
+        [3, 5, 4, 6, 0, 1, 2]
+    d = np.zeros((6, 6), np.uint8)
+    d[0, 1] = d[1, 2] = d[3, 4] = 1
+    assert oracle.hr_order(d, directed=True).tolist() == [1, 2, 0, 4, 3, 5]
+
+
+def test_hr_order_is_a_permutation_with_contiguous_components():
+    rs = np.random.default_rng(141)
+    for s in range(60):
+        n = int(rs.integers(1, 40))
+        directed = bool(s % 2)
+        f = synth.er_directed if directed else synth.er_undirected
+        a = f(n, float(rs.uniform(0.02, 0.3)), synth.rng_for(141, s, 0))
+        perm = oracle.hr_order(a, directed=directed)
+        assert sorted(perm.tolist()) == list(range(n))
+        und = ((a | a.T) != 0).astype(np.int64)
+        np.fill_diagonal(und, 0)
+        # component label of each vertex (closure by repeated squaring)
+        reach = (und + np.eye(n, dtype=np.int64)) > 0
+        for _ in range(7):
+            reach = (reach.astype(np.int64) @ reach.astype(np.int64)) > 0
+        lab = [int(np.argmax(reach[x])) for x in range(n)]
+        seq = [lab[x] for x in perm]
+        seen = set()
+        for i, c in enumerate(seq):
+            if i and c != seq[i - 1]:
+                assert c not in seen, (s, seq)
+            seen.add(c)
+
+
+@pytest.mark.parametrize("directed,k", [(False, 0), (True, 0), (False, 3)])
+def test_mcs_with_hr_order_vs_bruteforce(directed, k):
+    """The order changes the traversal only: the optimum is enumeration's."""
+    rs = np.random.default_rng(151 + k + (7 if directed else 0))
+    for s in range(100):
+        nG, nH = int(rs.integers(0, 10)), int(rs.integers(0, 10))
+        a, b, la, lb = _rand_pair(s + 13000 + 100 * k, nG, nH, float(rs.uniform(0.1, 0.7)), directed, k)
+        r = oracle.mcs_hr(a, b, la, lb, directed=directed)
+        kb, _, _ = oracle.bruteforce(a, b, la, lb)
+        assert r.complete and r.size == kb
+        assert oracle.verify(a, b, r.g_idx, r.h_idx, la, lb) == 1
