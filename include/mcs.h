@@ -76,7 +76,8 @@ extern "C" {
                                     /* the root until a goal is reached; the first    */
                                     /* goal reached is the optimum.  A time limit     */
                                     /* before that reports size 0 (MCS_TIMEOUT).      */
-                                    /* Batch calls only (mcs_submit: unsupported).    */
+                                    /* Batch calls only (mcs_submit: unsupported);   */
+                                    /* not with MCS_ORDER_LEARNED (unsupported).      */
 #define MCS_DEAD_END          0x80u /* dead-end forecast (Section IV): after          */
                                     /* mcs_set_dead_end's threshold of nodes without  */
                                     /* a new incumbent, the pair's incumbent size is  */
@@ -84,7 +85,8 @@ extern "C" {
                                     /* raised value bounds the optimum, and a binary  */
                                     /* search of goal-directed searches from the root */
                                     /* closes the gap.  Exact.  Not with MCS_TOP_DOWN */
-                                    /* (MCS_ERR_ARG); batch calls only.               */
+                                    /* (MCS_ERR_ARG); batch calls only; not with      */
+                                    /* MCS_ORDER_LEARNED (MCS_ERR_UNSUPPORTED).       */
 
 typedef struct mcs_ctx mcs_ctx;
 

@@ -593,7 +593,10 @@ __device__ __noinline__ bool requeue_goal(const SearchParams& P, int pair, int f
 }
 
 // Finish the pair: write size, status, nodes and the mapping (original numbers).
-template <bool SERVE, int GS>
+// GOAL: a launch of a goal-directed strategy (MCS_TOP_DOWN, MCS_DEAD_END):
+// the size is the largest recorded mapping, and a pair may be searched again
+// from its root with another goal instead of being finished.
+template <bool SERVE, int GS, bool GOAL>
 __device__ void finalize_pair(const SearchParams& P, int pair, const Grp<GS>& g, int16_t* smap) {
     __threadfence();
     PairState& ps = P.state[pair];
@@ -602,23 +605,28 @@ __device__ void finalize_pair(const SearchParams& P, int pair, const Grp<GS>& g,
     int status = 0, k = 0, ab = 0, fl = 0, cp = 0, lo = 0, hi = 0;
     if (g.q == 0) {
         status = vload(&ps.status);
-        k = vload(&ps.real);
         ab = vload(&ps.abort);
-        fl = vload(&ps.floor);
-        cp = vload(&ps.cap);
-        lo = vload(&ps.lo);
-        hi = vload(&ps.hi);
+        if constexpr (GOAL) {
+            k = vload(&ps.real);
+            fl = vload(&ps.floor);
+            cp = vload(&ps.cap);
+            lo = vload(&ps.lo);
+            hi = vload(&ps.hi);
+        } else {
+            k = vload(&ps.inc);
+        }
     }
     status = g.shfl(status, 0);
     k = g.shfl(k, 0);
     ab = g.shfl(ab, 0);
+    // Goal-directed strategies (Section IV): decide whether the pair is
+    // settled, else the goal of its next search from the root (0: none).
+    int next_goal = 0;
+    if constexpr (GOAL) {
     fl = g.shfl(fl, 0);
     cp = g.shfl(cp, 0);
     lo = g.shfl(lo, 0);
     hi = g.shfl(hi, 0);
-    // Goal-directed strategies (Section IV): decide whether the pair is
-    // settled, else the goal of its next search from the root (0: none).
-    int next_goal = 0;
     if (status == MCS_PENDING && ab != 1) {
         if ((P.flags & MCS_TOP_DOWN) && cp < kNoCap && k < cp && fl > 0) {
             next_goal = fl;                       // top-down: goal fl + 1 unreachable, try fl
@@ -635,6 +643,7 @@ __device__ void finalize_pair(const SearchParams& P, int pair, const Grp<GS>& g,
             }
             if (lo < hi) next_goal = (lo + hi + 1) / 2;
         }
+    }
     }
     if (next_goal > 0) {
         int ok = 1;
@@ -686,7 +695,7 @@ __device__ void finalize_pair(const SearchParams& P, int pair, const Grp<GS>& g,
 
 // A task of `pair` ended: publish node count, drop the open count and finalise
 // the pair if this was its last task.
-template <bool SERVE, int GS>
+template <bool SERVE, int GS, bool GOAL>
 __device__ __forceinline__ void end_task(const SearchParams& P, int pair, u64& nodes, const Grp<GS>& g,
                                          int16_t* smap) {
     int last = 0;
@@ -697,7 +706,7 @@ __device__ __forceinline__ void end_task(const SearchParams& P, int pair, u64& n
     }
     nodes = 0;
     last = g.shfl(last, 0);
-    if (last) finalize_pair<SERVE, GS>(P, pair, g, smap);
+    if (last) finalize_pair<SERVE, GS, GOAL>(P, pair, g, smap);
 }
 
 // Serve mode: copies request `slot` out of mapped host memory into its device
@@ -963,10 +972,14 @@ __device__ __forceinline__ bool donate(const SearchParams& P, int pair, int d0, 
 #define MCS_GROUP_MINB 4
 #endif
 
-template <bool DIR, bool LEARNED, bool SERVE, int GS, bool NARROW>
+// GOAL: the goal-directed strategies of Section IV (MCS_TOP_DOWN, MCS_DEAD_END)
+// are compiled into their own instantiation, so that the plain search carries
+// none of their bookkeeping.
+template <bool DIR, bool LEARNED, bool SERVE, int GS, bool NARROW, bool GOAL>
 __global__ void __launch_bounds__(256, (GS == 32 ? MCS_SEARCH_MINB : MCS_GROUP_MINB)) search_kernel(SearchParams P) {
     static_assert(GS == 2 || GS == 4 || GS == 8 || GS == 16 || GS == 32, "searcher group size");
     static_assert(!SERVE || GS >= 8, "serve mode keeps the level arrays and result scratch in shared memory");
+    static_assert(!GOAL || (!SERVE && !LEARNED), "goal-directed searches: batch launches, degree or static order");
     extern __shared__ __align__(16) unsigned char smem[];
     constexpr int GPW = 32 / GS;                       // searchers per warp
     const int lane = threadIdx.x & 31;
@@ -1075,12 +1088,12 @@ __global__ void __launch_bounds__(256, (GS == 32 ? MCS_SEARCH_MINB : MCS_GROUP_M
             if (pstat != MCS_PENDING) {                   // malformed input: report and skip
                 g.sync();
                 if (g.q == 0) { P.qseq[qh & qmask] = qh + P.qcap; ps.open = 0; }
-                finalize_pair<SERVE, GS>(P, pair, g, smap);
+                finalize_pair<SERVE, GS, GOAL>(P, pair, g, smap);
                 continue;
             }
             if (g.q == 0) {
                 u64 now = gtimer();
-                if (vload(&ps.t_start) == 0) {     // the first root (top-down re-enqueues it per goal)
+                if (!GOAL || vload(&ps.t_start) == 0) {   // the first root (goal searches re-enqueue it)
                     ps.t_start = now;
                     ps.deadline = now + (SERVE ? vload(&ps.timeout_ns) : P.timeout_ns);
                 }
@@ -1148,7 +1161,7 @@ __global__ void __launch_bounds__(256, (GS == 32 ? MCS_SEARCH_MINB : MCS_GROUP_M
         const long long c_busy = clock64();
         if (g.q == 0) cyc[1] += (u64)(c_busy - c_idle);
         if (ab0) {
-            end_task<SERVE, GS>(P, pair, nodes, g, smap);
+            end_task<SERVE, GS, GOAL>(P, pair, nodes, g, smap);
             if (g.q == 0) cyc[0] += (u64)(clock64() - c_busy);
             continue;
         }
@@ -1159,7 +1172,7 @@ __global__ void __launch_bounds__(256, (GS == 32 ? MCS_SEARCH_MINB : MCS_GROUP_M
             const Scan sc = scan_level<typename std::conditional<NARROW, uint32_t, u64>::type, GS>(g, st, 0, t.C, -1);
             t.bound = sc.sum;
             if (t.bound <= inc) {
-                end_task<SERVE, GS>(P, pair, nodes, g, smap);
+                end_task<SERVE, GS, GOAL>(P, pair, nodes, g, smap);
                 if (g.q == 0) cyc[0] += (u64)(clock64() - c_busy);
                 continue;
             }
@@ -1279,17 +1292,19 @@ __global__ void __launch_bounds__(256, (GS == 32 ? MCS_SEARCH_MINB : MCS_GROUP_M
                     if (old < dm) {
                         write_best<GS>(P, pair, w, t.d, v, u, g);
                         inc = dm;
-                        if (g.q == 0) {
-                            atomicMax(&ps.real, dm);        // a recorded mapping of size dm
-                            if (P.flags & MCS_DEAD_END) ps.dead = 0;
+                        if constexpr (GOAL) {
+                            if (g.q == 0) {
+                                atomicMax(&ps.real, dm);        // a recorded mapping of size dm
+                                if (P.flags & MCS_DEAD_END) ps.dead = 0;
+                            }
                         }
                     } else {
                         inc = old;
                     }
-                    // goal reached (top-down, Section IV; the cap is read only when the
-                    // incumbent grows): the pair is solved -- every searcher on it stops
-                    // at its next poll, this one now (depth -1 is below every task's)
-                    if (__builtin_expect((P.flags & MCS_TOP_DOWN) != 0, 0)) {
+                    // goal reached (Section IV; the cap is read only when the incumbent
+                    // grows): the pair is solved -- every searcher on it stops at its
+                    // next poll, this one now (depth -1 is below every task's)
+                    if constexpr (GOAL) {
                         int cap = 0;
                         if (g.q == 0) cap = vload(&ps.cap);
                         cap = g.shfl(cap, 0);
@@ -1358,10 +1373,11 @@ __global__ void __launch_bounds__(256, (GS == 32 ? MCS_SEARCH_MINB : MCS_GROUP_M
                 p_abort = vload(&ps.abort);
                 p_hungry = vload(&ctl->q_head) > vload(&ctl->q_tail);   // a searcher waits
                 if (!p_abort && (tick & 255) == 0 && gtimer() > vload(&ps.deadline)) {
-                    atomicCAS(&ps.abort, 0, 1);        // per-pair time limit (a reached goal stays)
+                    if constexpr (GOAL) atomicCAS(&ps.abort, 0, 1);   // time limit (a reached goal stays)
+                    else ps.abort = 1;                 // per-pair time limit
                     p_abort = 1;
                 }
-                if ((P.flags & MCS_DEAD_END) && p_abort == 0) {
+                if (GOAL && (P.flags & MCS_DEAD_END) && p_abort == 0) {
                     // dead-end forecast (Section IV): the searcher whose poll takes the
                     // pair's count of nodes without a new incumbent past the threshold
                     // raises the incumbent size, as if a mapping of that size were known
@@ -1397,7 +1413,7 @@ __global__ void __launch_bounds__(256, (GS == 32 ? MCS_SEARCH_MINB : MCS_GROUP_M
             if constexpr (NARROW) node_step(uint32_t{});
             else node_step(u64{});
         }
-        end_task<SERVE, GS>(P, pair, nodes, g, smap);
+        end_task<SERVE, GS, GOAL>(P, pair, nodes, g, smap);
         if (g.q == 0) cyc[0] += (u64)(clock64() - c_busy);
     }
     if (g.q == 0) {
@@ -1435,31 +1451,32 @@ static bool ensure_smem_limit(void (*k)(SearchParams), int smem) {
     return true;
 }
 
-template <bool DIR, bool LEARNED, bool SERVE, int GS, bool NARROW>
+template <bool DIR, bool LEARNED, bool SERVE, int GS, bool NARROW, bool GOAL>
 struct KernelTag {};
 
-template <bool DIR, bool LEARNED, bool SERVE, int GS, bool NARROW>
+template <bool DIR, bool LEARNED, bool SERVE, int GS, bool NARROW, bool GOAL = false>
 static cudaError_t launch_t(const SearchParams& p, int blocks, int wpb, cudaStream_t s) {
     size_t smem = (size_t)wpb * (32 / GS) * p.warp_smem_bytes;
-    auto* k = search_kernel<DIR, LEARNED, SERVE, GS, NARROW>;
-    if (!ensure_smem_limit<KernelTag<DIR, LEARNED, SERVE, GS, NARROW>>(k, (int)smem)) return cudaErrorInvalidValue;
+    auto* k = search_kernel<DIR, LEARNED, SERVE, GS, NARROW, GOAL>;
+    if (!ensure_smem_limit<KernelTag<DIR, LEARNED, SERVE, GS, NARROW, GOAL>>(k, (int)smem))
+        return cudaErrorInvalidValue;
     k<<<blocks, wpb * 32, smem, s>>>(p);
     return cudaGetLastError();
 }
 
-template <bool DIR, bool LEARNED, bool NARROW>
+template <bool DIR, bool LEARNED, bool NARROW, bool GOAL>
 static cudaError_t launch_g(const SearchParams& p, int blocks, int wpb, int gs, cudaStream_t s) {
-    if (gs == 2) return launch_t<DIR, LEARNED, false, 2, NARROW>(p, blocks, wpb, s);
-    if (gs == 4) return launch_t<DIR, LEARNED, false, 4, NARROW>(p, blocks, wpb, s);
-    if (gs == 8) return launch_t<DIR, LEARNED, false, 8, NARROW>(p, blocks, wpb, s);
-    if (gs == 16) return launch_t<DIR, LEARNED, false, 16, NARROW>(p, blocks, wpb, s);
-    return launch_t<DIR, LEARNED, false, 32, NARROW>(p, blocks, wpb, s);
+    if (gs == 2) return launch_t<DIR, LEARNED, false, 2, NARROW, GOAL>(p, blocks, wpb, s);
+    if (gs == 4) return launch_t<DIR, LEARNED, false, 4, NARROW, GOAL>(p, blocks, wpb, s);
+    if (gs == 8) return launch_t<DIR, LEARNED, false, 8, NARROW, GOAL>(p, blocks, wpb, s);
+    if (gs == 16) return launch_t<DIR, LEARNED, false, 16, NARROW, GOAL>(p, blocks, wpb, s);
+    return launch_t<DIR, LEARNED, false, 32, NARROW, GOAL>(p, blocks, wpb, s);
 }
 
-template <bool DIR, bool LEARNED>
+template <bool DIR, bool LEARNED, bool GOAL = false>
 static cudaError_t launch_w(const SearchParams& p, int blocks, int wpb, int gs, bool narrow, cudaStream_t s) {
-    return narrow ? launch_g<DIR, LEARNED, true>(p, blocks, wpb, gs, s)
-                  : launch_g<DIR, LEARNED, false>(p, blocks, wpb, gs, s);
+    return narrow ? launch_g<DIR, LEARNED, true, GOAL>(p, blocks, wpb, gs, s)
+                  : launch_g<DIR, LEARNED, false, GOAL>(p, blocks, wpb, gs, s);
 }
 
 cudaError_t launch_search(const SearchParams& p, int blocks, int warps_per_block, bool directed,
@@ -1470,17 +1487,25 @@ cudaError_t launch_search(const SearchParams& p, int blocks, int warps_per_block
         return launch_t<false, false, true, 32, false>(p, blocks, warps_per_block, s);
     }
     const bool narrow = (p.flags & MCS_WORD32) != 0;
+    if (p.flags & (MCS_TOP_DOWN | MCS_DEAD_END)) {
+        // goal-directed strategies (the caller rejects them with the learned order)
+        if (learned) return cudaErrorNotSupported;
+        return directed ? launch_w<true, false, true>(p, blocks, warps_per_block, gs, narrow, s)
+                        : launch_w<false, false, true>(p, blocks, warps_per_block, gs, narrow, s);
+    }
     if (directed) return learned ? launch_w<true, true>(p, blocks, warps_per_block, gs, narrow, s)
                                  : launch_w<true, false>(p, blocks, warps_per_block, gs, narrow, s);
     return learned ? launch_w<false, true>(p, blocks, warps_per_block, gs, narrow, s)
                    : launch_w<false, false>(p, blocks, warps_per_block, gs, narrow, s);
 }
 
+// Occupancy of the plain instantiation; the goal-directed one has the same
+// launch bounds (register cap) and shared memory.
 template <bool DIR, bool LEARNED, bool SERVE, int GS, bool NARROW>
 static int occupancy_t(int wpb, int smem) {
     int nb = 0;
-    auto* k = search_kernel<DIR, LEARNED, SERVE, GS, NARROW>;
-    if (!ensure_smem_limit<KernelTag<DIR, LEARNED, SERVE, GS, NARROW>>(k, smem)) return 0;
+    auto* k = search_kernel<DIR, LEARNED, SERVE, GS, NARROW, false>;
+    if (!ensure_smem_limit<KernelTag<DIR, LEARNED, SERVE, GS, NARROW, false>>(k, smem)) return 0;
     if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, k, wpb * 32, smem) != cudaSuccess) {
         cudaGetLastError();
         return 0;
