@@ -295,6 +295,9 @@ def main():
     ap.add_argument("--steps", type=int, default=5)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--workload", default="c2")
+    ap.add_argument("--order", default="degree", choices=["degree", "hr"],
+                    help="vertex order of the search: degree (default) or the static component + "
+                         "Hellerman-Rarick-style order of Section IV-A (MCS_ORDER_HR; not with c4's learned order)")
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--timeout", type=float, default=None,
                     help="per-pair limit in seconds (default 600; c4: 1)")
@@ -329,13 +332,14 @@ def main():
         import torch.distributed as dist
         dist.init_process_group("nccl")
     from paper_1908_06418_b300 import (Solver, pack_host, MCS_DIRECTED, MCS_OK, MCS_WORD32, MCS_ORDER_LEARNED,
-                                       MCS_TOP_DOWN, MCS_DEAD_END)
+                                       MCS_TOP_DOWN, MCS_DEAD_END, MCS_ORDER_HR)
 
     pairs, cfg = workload(a.workload)
     gold = golden_sizes(a.workload)
     dev = torch.device("cuda", local)
     solver = Solver(local)
-    learned = a.workload == "c4"
+    learned = a.workload == "c4" and a.order == "degree"
+    hr = a.order == "hr"
     topdown = a.workload == "td"
     if learned:       # the candidate order of the trained network (exactness unchanged)
         solver.set_order_model(np.load(os.path.join(ROOT, "paper_1908_06418_b300", "data",
@@ -354,7 +358,8 @@ def main():
         narrow = all(max(pairs[i].G.n, pairs[i].H.n) <= 32 for i in idx)
         h = pack_host([pairs[i] for i in idx])
         g = dict(idx=idx, flags=(MCS_DIRECTED if directed else 0) | (MCS_WORD32 if narrow else 0)
-                 | (MCS_ORDER_LEARNED if learned else 0) | (MCS_TOP_DOWN if topdown else 0), n=len(idx),
+                 | (MCS_ORDER_LEARNED if learned else 0) | (MCS_TOP_DOWN if topdown else 0)
+                 | (MCS_ORDER_HR if hr else 0), n=len(idx),
                  d_n=torch.from_numpy(h["n"]).to(dev),
                  d_adj_off=torch.from_numpy(h["adj_off"]).to(dev),
                  d_adj=torch.from_numpy(h["adj"]).to(dev),
@@ -518,6 +523,7 @@ def main():
             "p99_latency_ms": float(np.percentile(lats, 99)) if lats else None,
             "solved_per_step": solved_tot / a.steps / world,
             "config": dict(cfg, parallelism=f"replicas x{world}", l2="flushed between steps (512 MB write)",
+                           vertex_order=("learned" if learned else a.order),
                            timeout_s=a.timeout, launch_shapes=shapes),
             "gpu_launches": launches_per_step * a.steps,
             "search_ms_per_step": sum(search_ms) / len(search_ms),

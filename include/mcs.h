@@ -78,6 +78,12 @@ extern "C" {
                                     /* before that reports size 0 (MCS_TIMEOUT).      */
                                     /* Batch calls only (mcs_submit: unsupported);   */
                                     /* not with MCS_ORDER_LEARNED (unsupported).      */
+#define MCS_ORDER_HR          0x100u /* static vertex order of Section IV-A instead of */
+                                     /* the degree order: weakly connected components */
+                                     /* (decreasing rows/columns ratio, then size),   */
+                                     /* inside each a Hellerman-Rarick-style column   */
+                                     /* order.  Exact either way.  Not with           */
+                                     /* MCS_ORDER_LEARNED (MCS_ERR_ARG); batch calls. */
 #define MCS_DEAD_END          0x80u /* dead-end forecast (Section IV): after          */
                                     /* mcs_set_dead_end's threshold of nodes without  */
                                     /* a new incumbent, the pair's incumbent size is  */

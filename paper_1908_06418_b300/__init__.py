@@ -18,7 +18,7 @@ import numpy as np
 __all__ = ["Solver", "Result", "MCS_OK", "MCS_TIMEOUT", "MCS_PENDING", "MCS_ERR_ARG",
            "MCS_ERR_NOMEM", "MCS_ERR_CUDA", "MCS_ERR_DEVICE_STALL", "MCS_ERR_UNSUPPORTED",
            "MCS_DIRECTED", "MCS_ORDER_LEARNED", "MCS_NO_MAPPING", "MCS_NO_LEVEL_PRUNE",
-           "MCS_MAX_N", "MCS_GRAPH_REPLAY", "MCS_WORD32", "MCS_TOP_DOWN", "MCS_DEAD_END", "lib_path", "load_library", "EXPORTED_SYMBOLS",
+           "MCS_MAX_N", "MCS_GRAPH_REPLAY", "MCS_WORD32", "MCS_TOP_DOWN", "MCS_DEAD_END", "MCS_ORDER_HR", "lib_path", "load_library", "EXPORTED_SYMBOLS",
            "DeviceBatch", "HostBatch", "pack_host"]
 
 MCS_MAX_N = 64
@@ -28,6 +28,7 @@ MCS_DIRECTED, MCS_ORDER_LEARNED, MCS_NO_MAPPING, MCS_NO_LEVEL_PRUNE = 0x1, 0x2, 
 MCS_WORD32 = 0x20
 MCS_TOP_DOWN = 0x40
 MCS_DEAD_END = 0x80
+MCS_ORDER_HR = 0x100
 MCS_GRAPH_REPLAY = 0x10
 
 _HERE = os.path.dirname(os.path.abspath(__file__))

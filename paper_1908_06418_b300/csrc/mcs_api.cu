@@ -134,6 +134,8 @@ int run_device(mcs_ctx* c, int npairs, const int32_t* d_n, const int64_t* d_adj_
     if (npairs < 0) return MCS_ERR_ARG;
     // the two goal-directed strategies of Section IV are alternatives
     if ((flags & MCS_TOP_DOWN) && (flags & MCS_DEAD_END)) return MCS_ERR_ARG;
+    // one vertex order per call
+    if ((flags & MCS_ORDER_HR) && (flags & MCS_ORDER_LEARNED)) return MCS_ERR_ARG;
     // goal-directed searches are compiled for the degree (or static) order only
     if ((flags & (MCS_TOP_DOWN | MCS_DEAD_END)) && (flags & MCS_ORDER_LEARNED)) return MCS_ERR_UNSUPPORTED;
     if (npairs == 0) return 0;

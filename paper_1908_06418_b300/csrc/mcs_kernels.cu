@@ -67,6 +67,12 @@ __device__ __forceinline__ uint8_t ld_cg(const uint8_t* p) {
     return (uint8_t)r;
 }
 
+__device__ __forceinline__ u64 shfl_xor64(u64 x, int m) {
+    unsigned lo = (unsigned)x, hi = (unsigned)(x >> 32);
+    lo = __shfl_xor_sync(FULL, lo, m);
+    hi = __shfl_xor_sync(FULL, hi, m);
+    return ((u64)hi << 32) | lo;
+}
 __device__ __forceinline__ u64 shfl64(u64 x, int src) {
     unsigned lo = (unsigned)x, hi = (unsigned)(x >> 32);
     lo = __shfl_sync(FULL, lo, src);
@@ -83,11 +89,161 @@ struct GraphIn {
     const int32_t* lab;
 };
 
+// Component ordering of the static order below: a before b when a's
+// rows/columns ratio is larger (r/0 with r > 0 is infinite, 0/0 is 0), then
+// when a is larger, then when its lowest vertex is lower.
+struct CompKey { int rows, cols, size, low; };
+__device__ __forceinline__ bool comp_ratio_gt(const CompKey& a, const CompKey& b) {
+    const bool ia = a.cols == 0 && a.rows > 0, ib = b.cols == 0 && b.rows > 0;
+    if (ia || ib) return ia && !ib;
+    const int an = a.cols ? a.rows : 0, ad = a.cols ? a.cols : 1;
+    const int bn = b.cols ? b.rows : 0, bd = b.cols ? b.cols : 1;
+    return an * bd > bn * ad;
+}
+__device__ __forceinline__ bool comp_before(const CompKey& a, const CompKey& b) {
+    if (comp_ratio_gt(a, b)) return true;
+    if (comp_ratio_gt(b, a)) return false;
+    if (a.size != b.size) return a.size > b.size;
+    return a.low < b.low;
+}
+
+// The static vertex order of the portfolio modifications (Section IV-A), for
+// MCS_ORDER_HR: weakly connected components in decreasing rows/columns ratio
+// (rows: vertices with an out-arc, columns: with an in-arc), then size, then
+// lowest vertex; inside a component, repeatedly the active column with a
+// nonzero in the most of the shortest nonempty active rows (ties: lowest
+// vertex) takes the next position; when no active row is left the remaining
+// active columns follow in increasing order, then the component's vertices
+// without an in-arc.  One warp; lane l holds vertices l and l + 32 (orow /
+// icol: out- and in-neighbours without the vertex itself).  pos[s] receives
+// the position of vertex lane + 32 s.  scratch: 64 words of shared memory.
+// Every loop is bounded by the vertex count.
+__device__ void hr_positions(int n, const u64 (&orow)[2], const u64 (&icol)[2], u64* scratch, int lane,
+                             int (&pos)[2]) {
+    u64 R[2];
+    for (int s = 0; s < 2; ++s) {
+        const int x = lane + 32 * s;
+        R[s] = x < n ? (orow[s] | icol[s] | (1ull << x)) : 0ull;
+        if (x < n) scratch[x] = R[s];
+    }
+    __syncwarp();
+    // reach sets by repeated squaring: paths of up to 2^6 = 64 arcs
+    for (int it = 0; it < 6; ++it) {
+        u64 nr[2];
+        for (int s = 0; s < 2; ++s) {
+            u64 acc = R[s], m = R[s];
+            while (m) { const int y = __ffsll((long long)m) - 1; m &= m - 1; acc |= scratch[y]; }
+            nr[s] = acc;
+        }
+        __syncwarp();
+        for (int s = 0; s < 2; ++s) {
+            const int x = lane + 32 * s;
+            R[s] = nr[s];
+            if (x < n) scratch[x] = nr[s];
+        }
+        __syncwarp();
+    }
+    const u64 rownz = (u64)__ballot_sync(FULL, lane < n && orow[0] != 0) |
+                      ((u64)__ballot_sync(FULL, lane + 32 < n && orow[1] != 0) << 32);
+    const u64 colnz = (u64)__ballot_sync(FULL, lane < n && icol[0] != 0) |
+                      ((u64)__ballot_sync(FULL, lane + 32 < n && icol[1] != 0) << 32);
+    CompKey ck[2];
+    for (int s = 0; s < 2; ++s) {
+        ck[s].size = __popcll(R[s]);
+        ck[s].rows = __popcll(R[s] & rownz);
+        ck[s].cols = __popcll(R[s] & colnz);
+        ck[s].low = R[s] ? __ffsll((long long)R[s]) - 1 : 64;
+    }
+    // offset of each vertex's component: sizes of the components ordered before it
+    int off[2] = {0, 0};
+    for (int j = 0; j < n; ++j) {
+        CompKey cj;
+        cj.size = __shfl_sync(FULL, ck[j >> 5].size, j & 31);
+        cj.rows = __shfl_sync(FULL, ck[j >> 5].rows, j & 31);
+        cj.cols = __shfl_sync(FULL, ck[j >> 5].cols, j & 31);
+        cj.low = __shfl_sync(FULL, ck[j >> 5].low, j & 31);
+        if (cj.low != j) continue;                      // warp-uniform: j represents its component
+        for (int s = 0; s < 2; ++s)
+            if (lane + 32 * s < n && comp_before(cj, ck[s])) off[s] += cj.size;
+    }
+    pos[0] = pos[1] = -1;
+    int cur = 0;
+    for (int comp = 0; cur < n && comp < kMaxN; ++comp) {
+        // the component placed next: the one whose offset is cur
+        const unsigned b0 = __ballot_sync(FULL, lane < n && off[0] == cur);
+        const unsigned b1 = __ballot_sync(FULL, lane + 32 < n && off[1] == cur);
+        if (!b0 && !b1) break;                          // (cannot happen: offsets are prefix sums)
+        const int src = b0 ? __ffs(b0) - 1 : 32 + __ffs(b1) - 1;
+        const u64 cm = shfl64(src < 32 ? R[0] : R[1], src & 31);
+        u64 colact = cm & colnz, placed = 0;
+        for (int step = 0; colact && step < kMaxN; ++step) {
+            int len[2];
+            bool act[2];
+            for (int s = 0; s < 2; ++s) {
+                const int x = lane + 32 * s;
+                len[s] = (x < n && ((cm >> x) & 1)) ? __popcll(orow[s] & colact) : 0;
+                act[s] = len[s] > 0;
+            }
+            const unsigned mn = __reduce_min_sync(FULL, (unsigned)min(act[0] ? len[0] : 255, act[1] ? len[1] : 255));
+            if (mn == 255) {                            // no active row: the rest of the columns in order
+                for (int s = 0; s < 2; ++s) {
+                    const int x = lane + 32 * s;
+                    if (x < n && ((colact >> x) & 1)) pos[s] = cur + __popcll(colact & ((1ull << x) - 1));
+                }
+                cur += __popcll(colact);
+                placed |= colact;
+                colact = 0;
+                break;
+            }
+            const u64 S = (u64)__ballot_sync(FULL, act[0] && len[0] == (int)mn) |
+                          ((u64)__ballot_sync(FULL, act[1] && len[1] == (int)mn) << 32);
+            unsigned key = 0;
+            for (int s = 0; s < 2; ++s) {
+                const int x = lane + 32 * s;
+                if (x < n && ((colact >> x) & 1))
+                    key = max(key, ((unsigned)__popcll(icol[s] & S) << 7) | (unsigned)(127 - x));
+            }
+            const unsigned best = __reduce_max_sync(FULL, key);
+            if (best == 0) break;                       // (cannot happen: colact is not empty)
+            const int c = 127 - (int)(best & 127);
+            if ((c & 31) == lane) pos[c >> 5] = cur;
+            ++cur;
+            colact &= ~(1ull << c);
+            placed |= 1ull << c;
+        }
+        const u64 rest = cm & ~placed;                  // vertices without an in-arc, in order
+        for (int s = 0; s < 2; ++s) {
+            const int x = lane + 32 * s;
+            if (x < n && ((rest >> x) & 1)) pos[s] = cur + __popcll(rest & ((1ull << x) - 1));
+        }
+        cur += __popcll(rest);
+    }
+    // every position 0..n-1 taken exactly once, else (never expected) the identity order
+    u64 mine = 0;
+    bool dup = false;
+    for (int s = 0; s < 2; ++s) {
+        const int x = lane + 32 * s;
+        if (x < n) {
+            if (pos[s] < 0 || pos[s] >= n) dup = true;
+            else mine |= 1ull << pos[s];
+        }
+    }
+    u64 all = mine;
+    int total = __popcll(mine);
+    for (int o = 16; o > 0; o >>= 1) {
+        all |= shfl_xor64(all, o);
+        total += __shfl_xor_sync(FULL, total, o);
+    }
+    const bool good = !__any_sync(FULL, dup) && total == n && all == (n == 64 ? ~0ull : ((1ull << n) - 1));
+    if (!good) { pos[0] = lane; pos[1] = lane + 32; }
+}
+
 // Lane l handles vertices l and l + 32.  Returns false (warp-uniform) if the
-// graph is malformed.
+// graph is malformed.  hr: the static order of hr_positions instead of the
+// degree order (scratch: 64 words of shared memory).
 __device__ bool pack_graph(const GraphIn& g, bool directed, const float* key,
                            u64* out_rows, u64* in_rows, uint8_t* perm,
-                           long long* vkey /* per lane: 2 entries */, int lane) {
+                           long long* vkey /* per lane: 2 entries */, int lane, bool hr, u64* scratch) {
     const int n = g.n;
     bool ok = (n >= 0 && n <= kMaxN);
     // content checks: entries 0/1, symmetric when undirected, labels >= 0
@@ -128,6 +284,23 @@ __device__ bool pack_graph(const GraphIn& g, bool directed, const float* key,
     }
     // rank: earlier if higher degree (or lower caller key), ties to lower index
     int rank[2];
+    if (hr) {
+        u64 orow[2], icol[2];
+        for (int s = 0; s < 2; ++s) {
+            const int i = lane + 32 * s;
+            u64 o = 0, in = 0;
+            if (i < n)
+                for (int j = 0; j < n; ++j) {
+                    if (j == i) continue;
+                    if (g.a[i * n + j]) o |= 1ull << j;
+                    if (g.a[j * n + i]) in |= 1ull << j;
+                }
+            orow[s] = o;
+            icol[s] = directed ? in : o;
+        }
+        hr_positions(n, orow, icol, scratch, lane, rank);
+        __syncwarp();
+    } else
     for (int s = 0; s < 2; ++s) {
         int i = lane + 32 * s;
         int r = 0;
@@ -172,7 +345,7 @@ __device__ bool pack_graph(const GraphIn& g, bool directed, const float* key,
 // initial label classes into pg.  skey is 2 x 64 long long of shared scratch.
 // Returns false (warp-uniform) when an input graph is malformed.
 __device__ bool pack_pair_warp(const GraphIn (&g)[2], bool directed, const float* key0,
-                               const float* key1, PairGraph& pg, long long* skey, int lane) {
+                               const float* key1, PairGraph& pg, long long* skey, int lane, bool hr = false) {
     bool ok = true;
     long long vk[2][2];
     for (int side = 0; side < 2 && ok; ++side) {
@@ -180,7 +353,8 @@ __device__ bool pack_pair_warp(const GraphIn (&g)[2], bool directed, const float
         u64* orows = side ? pg.hout : pg.gout;
         u64* irows = side ? pg.hin : pg.gin;
         uint8_t* perm = side ? pg.permH : pg.permG;
-        ok = pack_graph(g[side], directed, side ? key1 : key0, orows, irows, perm, vk[side], lane);
+        ok = pack_graph(g[side], directed, side ? key1 : key0, orows, irows, perm, vk[side], lane, hr,
+                        reinterpret_cast<u64*>(skey));
     }
     __syncwarp();
     const int nG = g[0].n, nH = g[1].n;
@@ -271,7 +445,7 @@ __global__ void pack_kernel(PackParams P) {
     const float* k1 = P.vscore ? P.vscore + ((size_t)p * 2 + 1) * kMaxN : nullptr;
     // the 32-bit node step holds graphs of at most 32 vertices
     const bool fits = !(P.flags & MCS_WORD32) || (g[0].n <= 32 && g[1].n <= 32);
-    const bool ok = pack_pair_warp(g, directed, k0, k1, pg, s_key[wib], lane) && fits;
+    const bool ok = pack_pair_warp(g, directed, k0, k1, pg, s_key[wib], lane, (P.flags & MCS_ORDER_HR) != 0) && fits;
     if (lane == 0) {
         PairState& st = P.state[p];
         // top-down: the first goal is min(|V_G|, |V_H|) (Section IV)

@@ -260,7 +260,8 @@ extern "C" {
 int mcs_submit(mcs_ctx* c, const mcs_graph* G, const mcs_graph* H, uint32_t flags, double timeout_s,
                uint64_t* ticket) {
     if (!c || !ticket || check_graph_s(G) || check_graph_s(H)) return MCS_ERR_ARG;
-    if (flags & (MCS_DIRECTED | MCS_ORDER_LEARNED | MCS_TOP_DOWN | MCS_DEAD_END)) return MCS_ERR_UNSUPPORTED;
+    if (flags & (MCS_DIRECTED | MCS_ORDER_LEARNED | MCS_ORDER_HR | MCS_TOP_DOWN | MCS_DEAD_END))
+        return MCS_ERR_UNSUPPORTED;
     if (cudaSetDevice(c->device) != cudaSuccess) return MCS_ERR_CUDA;
     ServeState* S = nullptr;
     int rc = serve_state(c, &S);
