@@ -44,8 +44,8 @@ METRIC = "MCS pairs solved/sec (exact) on 1 B300"
 # the dominant search kernel, from a single-pass ncu capture of this
 # workload's launch (profiles/dram_search_kernel_c2.md); reported only while
 # the kernel source is the one the capture was taken with.
-TRAFFIC = {"c2": {"kernel_sha1": "9c7ac2430a6e9883", "bytes": 1.21e9 + 5.30e9},
-           "c3": {"kernel_sha1": "9c7ac2430a6e9883", "bytes": 97.23e6 + 191.43e6}}
+TRAFFIC = {"c2": {"kernel_sha1": "8a1098cd8250ad62", "bytes": 1.21e9 + 5.29e9},
+           "c3": {"kernel_sha1": "8a1098cd8250ad62", "bytes": 96.91e6 + 193.70e6}}
 UNIT = "pairs/s"
 
 
