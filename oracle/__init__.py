@@ -8,6 +8,7 @@ It shares no code with the CUDA path.
 * ``mcs_goal``   -- one goal-directed McSplit search (Section IV, top-down strategy)
 * ``mcs_topdown``-- the top-down strategy: goal sizes min(|V_G|,|V_H|), one less, ...
 * ``mcs_deadend``-- dead-end forecasting with a bound increase and a binary search (Section IV)
+* ``mcs_restart``-- randomized restarts over an explicit stack of pending branches (Section IV-A)
 * ``hr_order`` / ``mcs_hr`` -- the static component + Hellerman-Rarick-style order (Section IV-A)
 * ``bruteforce`` -- exhaustive injective partial mappings (definition, Section II-A)
 * ``clique``     -- maximum clique of the modular product graph (textbook reduction)
@@ -61,6 +62,10 @@ def _load():
     lib.oracle_hr_order.restype = None
     lib.oracle_mcs_hr.argtypes = lib.oracle_mcs.argtypes
     lib.oracle_mcs_hr.restype = ctypes.c_int
+    lib.oracle_mcs_restart.argtypes = g + [ctypes.c_int, ctypes.c_int64, ctypes.c_uint64, ctypes.c_int64,
+                                           ctypes.c_double, _i32p, _i32p, _i64p, ctypes.POINTER(ctypes.c_int),
+                                           _i64p]
+    lib.oracle_mcs_restart.restype = ctypes.c_int
     lib.oracle_bruteforce.argtypes = g + [_i32p, _i32p]
     lib.oracle_bruteforce.restype = ctypes.c_int
     lib.oracle_clique.argtypes = g + [_i32p, _i32p]
@@ -194,6 +199,25 @@ def mcs_hr(adjG, adjH, labG=None, labH=None, directed: bool = False,
                           og.ctypes.data_as(_i32p), oh.ctypes.data_as(_i32p),
                           ctypes.byref(nodes), ctypes.byref(st))
     return OracleResult(int(k), og[:k].copy(), oh[:k].copy(), int(nodes.value), st.value == 0)
+
+
+def mcs_restart(adjG, adjH, min_nodes: int = 1, seed: int = 0, labG=None, labH=None,
+                directed: bool = False, node_limit: int = 0, time_limit_s: float = 0.0):
+    """Randomized restarts (Section IV-A) on an explicit stack of pending
+    branches; returns (OracleResult, number of restarts)."""
+    lib = _load()
+    ga, keep1 = _gargs(adjG, labG)
+    ha, keep2 = _gargs(adjH, labH)
+    n = max(1, min(ga[0], ha[0]))
+    og = np.zeros(n, np.int32)
+    oh = np.zeros(n, np.int32)
+    nodes = ctypes.c_int64(0)
+    st = ctypes.c_int(0)
+    rs = ctypes.c_int64(0)
+    k = lib.oracle_mcs_restart(*ga, *ha, int(directed), int(min_nodes), int(seed) & (2**64 - 1),
+                               int(node_limit), float(time_limit_s), og.ctypes.data_as(_i32p),
+                               oh.ctypes.data_as(_i32p), ctypes.byref(nodes), ctypes.byref(st), ctypes.byref(rs))
+    return OracleResult(int(k), og[:k].copy(), oh[:k].copy(), int(nodes.value), st.value == 0), int(rs.value)
 
 
 def bruteforce(adjG, adjH, labG=None, labH=None) -> Tuple[int, np.ndarray, np.ndarray]:

@@ -26,6 +26,12 @@
 //                      (connected components, then a Hellerman-Rarick-style
 //                      column order inside each); oracle_mcs_hr runs McSplit
 //                      with it in place of the degree order
+//   oracle_mcs_restart randomized restarts (Section IV-A): McSplit on an
+//                      explicit stack of pending branches (the record of what
+//                      is left to visit); when the node count has doubled
+//                      since the last new incumbent, the pending branches are
+//                      put in a random order and the search goes on from the
+//                      first of them
 //   oracle_mcs_deadend dead-end forecasting with a bound increase and a binary
 //                      search (Section IV): the plain search raises its
 //                      incumbent size by 1 (or doubles it) after a number of
@@ -661,6 +667,105 @@ int oracle_mcs_hr(int nG, const uint8_t* adjG, const int32_t* labG,
     }
     if (nodes) *nodes = s.nodes;
     if (status) *status = s.aborted ? 1 : 0;
+    return k;
+}
+
+// SplitMix64 (Steele, Lea, Flood 2014), one output per counter value.
+static uint64_t splitmix64(uint64_t x) {
+    x += 0x9E3779B97F4A7C15ull;
+    x = (x ^ (x >> 30)) * 0xBF58476D1CE4E5B9ull;
+    x = (x ^ (x >> 27)) * 0x94D049BB133111EBull;
+    return x ^ (x >> 31);
+}
+
+// Randomized restarts (Section IV-A).  The recursion of oracle_mcs written as
+// an explicit stack of pending branches: a branch is a node already entered
+// (incumbent test, Eq. 1 bound, class and v chosen) with the candidates u
+// still to try and whether its "v unmatched" branch is still to do.  The
+// stack is the record of every part of the tree not yet visited, so the order
+// in which branches are taken does not change the optimum.  A restart fires
+// when the node count reaches twice the count at the last new incumbent (and
+// at least min_nodes): the pending branches are reordered by the keys
+// splitmix64(seed + restart index * 2^32 + position) and the search goes on.
+// Returns the optimum and mapping as oracle_mcs; *restarts counts restarts.
+int oracle_mcs_restart(int nG, const uint8_t* adjG, const int32_t* labG,
+                       int nH, const uint8_t* adjH, const int32_t* labH,
+                       int directed, int64_t min_nodes, uint64_t seed,
+                       int64_t node_limit, double time_limit_s,
+                       int32_t* out_g, int32_t* out_h, int64_t* nodes, int* status, int64_t* restarts) {
+    OGraph g0 = make_graph(nG, adjG, labG), h0 = make_graph(nH, adjH, labH);
+    std::vector<int> og = degree_order(g0, directed != 0), oh = degree_order(h0, directed != 0);
+    OGraph G = relabel(g0, og), H = relabel(h0, oh);
+    McSplit s(G, H, directed != 0, node_limit, time_limit_s);   // filter, bound and limits
+    struct Branch {
+        std::vector<LabelClass> cl;
+        std::vector<std::pair<int, int>> M;
+        int c, v;
+        std::vector<int> cand;          // candidates u still to try, next at the back
+        bool unmatched;                 // the "v unmatched" branch is still to do
+    };
+    std::vector<Branch> stack;
+    int64_t mark = 0, nrestart = 0;
+    // node entry (Algorithm 1): incumbent, Eq. 1 bound, selection; a branch when not pruned
+    auto enter = [&](std::vector<LabelClass> cl, std::vector<std::pair<int, int>> M) {
+        ++s.nodes;
+        if (s.aborted || s.out_of_budget()) { s.aborted = true; return; }
+        s.M = M;
+        if (M.size() > s.best.size()) { s.best = M; mark = s.nodes; }
+        if (s.bound(cl) <= (int)s.best.size()) return;
+        int c = -1, ckey = 0, cmin = 0;
+        for (int i = 0; i < (int)cl.size(); ++i) {
+            int key = (int)std::max(cl[i].L.size(), cl[i].R.size());
+            int mn = *std::min_element(cl[i].L.begin(), cl[i].L.end());
+            if (c < 0 || key < ckey || (key == ckey && mn < cmin)) { c = i; ckey = key; cmin = mn; }
+        }
+        std::vector<int> cand = cl[c].R;
+        std::sort(cand.rbegin(), cand.rend());            // ascending order, taken from the back
+        stack.push_back(Branch{std::move(cl), std::move(M), c, cmin, std::move(cand), true});
+    };
+    enter(initial_classes(G, H), {});
+    while (!stack.empty() && !s.aborted) {
+        if (s.nodes >= std::max(min_nodes, 2 * mark) && stack.size() > 1) {
+            // restart: a random order of the pending branches (every one is kept)
+            std::vector<std::pair<uint64_t, size_t>> key(stack.size());
+            for (size_t i = 0; i < stack.size(); ++i)
+                key[i] = {splitmix64(seed + ((uint64_t)nrestart << 32) + i), i};
+            std::sort(key.begin(), key.end());
+            std::vector<Branch> shuffled;
+            for (auto& k : key) shuffled.push_back(std::move(stack[k.second]));
+            stack = std::move(shuffled);
+            ++nrestart;
+            mark = s.nodes;
+        }
+        Branch& b = stack.back();
+        if (!b.cand.empty()) {
+            const int u = b.cand.back();
+            b.cand.pop_back();
+            std::vector<LabelClass> child = s.filter(b.cl, b.v, u);
+            std::vector<std::pair<int, int>> M = b.M;
+            M.emplace_back(b.v, u);
+            enter(std::move(child), std::move(M));
+        } else if (b.unmatched) {
+            b.unmatched = false;
+            std::vector<LabelClass> cl = b.cl;
+            auto& L = cl[b.c].L;
+            L.erase(std::find(L.begin(), L.end(), b.v));
+            if (L.empty()) cl.erase(cl.begin() + b.c);
+            std::vector<std::pair<int, int>> M = b.M;
+            stack.pop_back();
+            enter(std::move(cl), std::move(M));
+        } else {
+            stack.pop_back();
+        }
+    }
+    const int k = (int)s.best.size();
+    for (int i = 0; i < k; ++i) {
+        if (out_g) out_g[i] = og[s.best[i].first];
+        if (out_h) out_h[i] = oh[s.best[i].second];
+    }
+    if (nodes) *nodes = s.nodes;
+    if (status) *status = s.aborted ? 1 : 0;
+    if (restarts) *restarts = nrestart;
     return k;
 }
 

@@ -403,3 +403,49 @@ def test_mcs_with_hr_order_vs_bruteforce(directed, k):
         kb, _, _ = oracle.bruteforce(a, b, la, lb)
         assert r.complete and r.size == kb
         assert oracle.verify(a, b, r.g_idx, r.h_idx, la, lb) == 1
+
+
+# --------------------------------------------------------------------------
+# randomized restarts over an explicit stack of pending branches (Section IV-A)
+# --------------------------------------------------------------------------
+@pytest.mark.parametrize("directed,k", [(False, 0), (True, 0), (False, 3)])
+def test_restart_stack_without_restarts_is_the_recursion(directed, k):
+    """With no restart firing, the explicit stack walks the recursive
+    search's tree node for node."""
+    rs = np.random.default_rng(171 + k)
+    for s in range(30):
+        nG, nH = int(rs.integers(0, 15)), int(rs.integers(0, 15))
+        a, b, la, lb = _rand_pair(s + 14000 + 100 * k, nG, nH, float(rs.uniform(0.1, 0.6)), directed, k)
+        r, n = oracle.mcs_restart(a, b, 1 << 60, 0, la, lb, directed=directed)
+        o = oracle.mcs(a, b, la, lb, directed=directed)
+        assert n == 0 and r.size == o.size and r.nodes == o.nodes
+
+
+@pytest.mark.parametrize("min_nodes,seed", [(1, 0), (1, 12345), (8, 7), (64, 99)])
+def test_restart_vs_bruteforce(min_nodes, seed):
+    """Restarts reorder the pending branches, which hold every part of the
+    tree not yet visited: the optimum is enumeration's for any seed."""
+    rs = np.random.default_rng(181 + min_nodes + seed % 1000)
+    total = 0
+    for s in range(80):
+        directed = bool(s % 3 == 0)
+        k = 3 if s % 4 == 1 else 0
+        nG, nH = int(rs.integers(0, 10)), int(rs.integers(0, 10))
+        a, b, la, lb = _rand_pair(s + 15000 + min_nodes, nG, nH, float(rs.uniform(0.1, 0.7)), directed, k)
+        r, n = oracle.mcs_restart(a, b, min_nodes, seed, la, lb, directed=directed)
+        kb, _, _ = oracle.bruteforce(a, b, la, lb)
+        assert r.complete and r.size == kb, (s, r.size, kb)
+        assert oracle.verify(a, b, r.g_idx, r.h_idx, la, lb) == 1
+        total += n
+    assert total > 0
+
+
+def test_restarts_fire_and_keep_the_optimum_on_larger_pairs():
+    fired = 0
+    for s in range(10):
+        a, b, _, _ = _rand_pair(s + 16000, 16, 18, 0.5)
+        o = oracle.mcs(a, b)
+        r, n = oracle.mcs_restart(a, b, 256, s)
+        assert r.size == o.size
+        fired += n > 0
+    assert fired >= 5
