@@ -15,8 +15,8 @@ the timed events.  `value` = pairs solved / summed step time.
 Other workloads: c3 (4,096 labelled pairs), c1 (one small pair), c4 (2,048
 bounded-valence pairs, learned order, 1 s per pair), c5 (serving on a Poisson
 stream), td (96 bounded-valence pairs with a 90 % planted core, solved with
-the top-down strategy of Section IV; the line adds the plain search and the
-dead-end forecast of the same batch).
+the top-down strategy of Section IV; the line adds the plain search, the
+dead-end forecast and randomized restarts on the same batch).
 
 `--impl reference` times the CPU oracle (plain sequential McSplit) on the
 host cores on a bounded sample of the same workload; it is the reference arm
@@ -332,7 +332,7 @@ def main():
         import torch.distributed as dist
         dist.init_process_group("nccl")
     from paper_1908_06418_b300 import (Solver, pack_host, MCS_DIRECTED, MCS_OK, MCS_WORD32, MCS_ORDER_LEARNED,
-                                       MCS_TOP_DOWN, MCS_DEAD_END, MCS_ORDER_HR)
+                                       MCS_TOP_DOWN, MCS_DEAD_END, MCS_ORDER_HR, MCS_RESTART)
 
     pairs, cfg = workload(a.workload)
     gold = golden_sizes(a.workload)
@@ -555,10 +555,11 @@ def main():
             key = "order_comparison"
         else:
             cmp = {"top_down": one_pass(0), "plain": one_pass(MCS_TOP_DOWN),
-                   "dead_end": one_pass(MCS_TOP_DOWN, MCS_DEAD_END)}
+                   "dead_end": one_pass(MCS_TOP_DOWN, MCS_DEAD_END),
+                   "restart": one_pass(MCS_TOP_DOWN, MCS_RESTART)}
             key = "strategy_comparison"
             # both are exact: where both proved their result the sizes must agree
-            for other in ("top_down", "dead_end"):
+            for other in ("top_down", "dead_end", "restart"):
                 a_, b_ = cmp[other], cmp["plain"]
                 both = (a_["_status"] == MCS_OK) & (b_["_status"] == MCS_OK)
                 if not np.array_equal(a_["_sizes"][both], b_["_sizes"][both]):

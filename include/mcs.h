@@ -84,6 +84,16 @@ extern "C" {
                                      /* inside each a Hellerman-Rarick-style column   */
                                      /* order.  Exact either way.  Not with           */
                                      /* MCS_ORDER_LEARNED (MCS_ERR_ARG); batch calls. */
+#define MCS_RESTART           0x200u /* randomized restarts (Section IV-A): once a    */
+                                     /* pair's node count has doubled since its last  */
+                                     /* new incumbent (and passed mcs_set_restart's   */
+                                     /* minimum), one searcher puts every open branch */
+                                     /* of its stack back in the work ring in a      */
+                                     /* random order and starts afresh; the pending   */
+                                     /* branches keep the record of what is left, so  */
+                                     /* the result stays exact.  Not with             */
+                                     /* MCS_TOP_DOWN / MCS_DEAD_END (MCS_ERR_ARG) or  */
+                                     /* MCS_ORDER_LEARNED (unsupported); batch calls. */
 #define MCS_DEAD_END          0x80u /* dead-end forecast (Section IV): after          */
                                     /* mcs_set_dead_end's threshold of nodes without  */
                                     /* a new incumbent, the pair's incumbent size is  */
@@ -294,6 +304,12 @@ int mcs_set_serve_group(mcs_ctx* ctx, int lanes);
  * is raised; doubling 1 doubles it, 0 (default) adds one, -1 restores the
  * default.  Applies to later calls.  MCS_ERR_ARG for other values. */
 int mcs_set_dead_end(mcs_ctx* ctx, long long threshold_nodes, int doubling);
+
+/* MCS_RESTART parameters: min_nodes (>= 1; -1 restores the default 2^20) is
+ * the number of search nodes of a pair, counted over all its searchers at
+ * their polls, before its first restart; seed selects the random order of the
+ * spilled branches.  Applies to later calls.  MCS_ERR_ARG for other values. */
+int mcs_set_restart(mcs_ctx* ctx, long long min_nodes, unsigned long long seed);
 
 /* Statistics of the last solve on this context: out[0] search-kernel
  * microseconds (for mcs_solve_batch_device: once its stream has passed the

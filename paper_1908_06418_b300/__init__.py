@@ -18,7 +18,7 @@ import numpy as np
 __all__ = ["Solver", "Result", "MCS_OK", "MCS_TIMEOUT", "MCS_PENDING", "MCS_ERR_ARG",
            "MCS_ERR_NOMEM", "MCS_ERR_CUDA", "MCS_ERR_DEVICE_STALL", "MCS_ERR_UNSUPPORTED",
            "MCS_DIRECTED", "MCS_ORDER_LEARNED", "MCS_NO_MAPPING", "MCS_NO_LEVEL_PRUNE",
-           "MCS_MAX_N", "MCS_GRAPH_REPLAY", "MCS_WORD32", "MCS_TOP_DOWN", "MCS_DEAD_END", "MCS_ORDER_HR", "lib_path", "load_library", "EXPORTED_SYMBOLS",
+           "MCS_MAX_N", "MCS_GRAPH_REPLAY", "MCS_WORD32", "MCS_TOP_DOWN", "MCS_DEAD_END", "MCS_ORDER_HR", "MCS_RESTART", "lib_path", "load_library", "EXPORTED_SYMBOLS",
            "DeviceBatch", "HostBatch", "pack_host"]
 
 MCS_MAX_N = 64
@@ -29,6 +29,7 @@ MCS_WORD32 = 0x20
 MCS_TOP_DOWN = 0x40
 MCS_DEAD_END = 0x80
 MCS_ORDER_HR = 0x100
+MCS_RESTART = 0x200
 MCS_GRAPH_REPLAY = 0x10
 
 _HERE = os.path.dirname(os.path.abspath(__file__))
@@ -54,7 +55,7 @@ class _Result(ctypes.Structure):
 EXPORTED_SYMBOLS = ["mcs_create", "mcs_destroy", "mcs_solve", "mcs_solve_batch",
                     "mcs_solve_batch_device", "mcs_submit", "mcs_poll", "mcs_set_launch",
                     "mcs_set_max_warps", "mcs_set_search_group", "mcs_set_serve_group", "mcs_set_steal",
-                    "mcs_set_dead_end",
+                    "mcs_set_dead_end", "mcs_set_restart",
                     "mcs_last_stats", "mcs_bench_popc", "mcs_strerror", "mcs_error_detail",
                     "mcs_solve_batch_noalloc", "mcs_set_order_model", "mcs_get_order_model",
                     "mcs_order_eval", "mcs_order_train", "mcs_order_score_grid"]
@@ -97,6 +98,8 @@ def load_library():
     lib.mcs_set_max_warps.restype = ctypes.c_int
     lib.mcs_set_dead_end.argtypes = [vp, ctypes.c_longlong, ctypes.c_int]
     lib.mcs_set_dead_end.restype = ctypes.c_int
+    lib.mcs_set_restart.argtypes = [vp, ctypes.c_longlong, ctypes.c_ulonglong]
+    lib.mcs_set_restart.restype = ctypes.c_int
     lib.mcs_set_search_group.argtypes = [vp, ctypes.c_int]
     lib.mcs_set_search_group.restype = ctypes.c_int
     lib.mcs_set_serve_group.argtypes = [vp, ctypes.c_int]
@@ -228,6 +231,13 @@ class Solver:
         rc = self.lib.mcs_set_dead_end(self.ctx, int(threshold_nodes), int(doubling))
         if rc:
             raise ValueError(f"mcs_set_dead_end: {self.strerror(rc)}")
+
+    def set_restart(self, min_nodes: int = -1, seed: int = 0):
+        """MCS_RESTART parameters: nodes of a pair before its first restart
+        (-1: default 2^20) and the seed of the random branch order."""
+        rc = self.lib.mcs_set_restart(self.ctx, int(min_nodes), int(seed) & (2**64 - 1))
+        if rc:
+            raise ValueError(f"mcs_set_restart: {self.strerror(rc)}")
 
     def set_search_group(self, lanes: int):
         """Lanes per searcher: 32 (one search per warp), 16, 8, 4 or 2."""

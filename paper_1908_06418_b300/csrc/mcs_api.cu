@@ -134,10 +134,12 @@ int run_device(mcs_ctx* c, int npairs, const int32_t* d_n, const int64_t* d_adj_
     if (npairs < 0) return MCS_ERR_ARG;
     // the two goal-directed strategies of Section IV are alternatives
     if ((flags & MCS_TOP_DOWN) && (flags & MCS_DEAD_END)) return MCS_ERR_ARG;
+    if ((flags & MCS_RESTART) && (flags & (MCS_TOP_DOWN | MCS_DEAD_END))) return MCS_ERR_ARG;
     // one vertex order per call
     if ((flags & MCS_ORDER_HR) && (flags & MCS_ORDER_LEARNED)) return MCS_ERR_ARG;
     // goal-directed searches are compiled for the degree (or static) order only
-    if ((flags & (MCS_TOP_DOWN | MCS_DEAD_END)) && (flags & MCS_ORDER_LEARNED)) return MCS_ERR_UNSUPPORTED;
+    if ((flags & (MCS_TOP_DOWN | MCS_DEAD_END | MCS_RESTART)) && (flags & MCS_ORDER_LEARNED))
+        return MCS_ERR_UNSUPPORTED;
     if (npairs == 0) return 0;
     const bool directed = (flags & MCS_DIRECTED) != 0;
     int rc = 0;
@@ -208,6 +210,8 @@ int run_device(mcs_ctx* c, int npairs, const int32_t* d_n, const int64_t* d_adj_
     sp.steal_keep_q4 = c->steal_keep_q4;
     sp.dead_nodes = (u64)c->dead_nodes;
     sp.dead_double = c->dead_double;
+    sp.restart_min = (u64)c->restart_min;
+    sp.restart_seed = (u64)c->restart_seed;
     sp.out_size = d_size;
     sp.out_status = d_status;
     sp.out_nodes = reinterpret_cast<u64*>(d_nodes);
@@ -305,6 +309,13 @@ int mcs_set_dead_end(mcs_ctx* c, long long threshold_nodes, int doubling) {
     if (!c || threshold_nodes == 0 || threshold_nodes < -1 || doubling < -1 || doubling > 1) return MCS_ERR_ARG;
     c->dead_nodes = threshold_nodes > 0 ? threshold_nodes : (1LL << 22);
     c->dead_double = doubling > 0 ? 1 : 0;
+    return 0;
+}
+
+int mcs_set_restart(mcs_ctx* c, long long min_nodes, unsigned long long seed) {
+    if (!c || min_nodes == 0 || min_nodes < -1) return MCS_ERR_ARG;
+    c->restart_min = min_nodes > 0 ? min_nodes : (1LL << 20);
+    c->restart_seed = seed;
     return 0;
 }
 

@@ -46,8 +46,9 @@ struct PairState {
     int32_t floor, cap;
     int32_t real;          // size of the largest recorded mapping (atomicMax)
     int32_t lo, hi;        // dead-end mode: bounds of the binary search over goals
-    int32_t pad_;
+    int32_t restarts;      // restart mode: restarts so far (part of the random order's counter)
     u64 dead;              // dead-end mode: nodes since the last new incumbent (approx.)
+    u64 live, mark;        // restart mode: nodes so far and at the last new incumbent (approx.)
 };
 constexpr int32_t kNoCap = 1 << 30;
 
@@ -150,6 +151,8 @@ struct SearchParams {
     int32_t steal_keep_q4;         // a donor keeps ceil(k * q / 4) of k candidates (1..3)
     u64 dead_nodes;                // MCS_DEAD_END: nodes without a new incumbent before a raise
     int32_t dead_double;           // MCS_DEAD_END: 1 doubles the incumbent size, 0 adds one
+    u64 restart_min;               // MCS_RESTART: no restart before this many nodes of a pair
+    u64 restart_seed;              // MCS_RESTART: seed of the random order of spilled branches
     // outputs
     int32_t* out_size;
     int32_t* out_status;
@@ -235,6 +238,8 @@ struct mcs_ctx {
     int steal_keep_q4 = 2;        // quarters of a donated level's candidates the donor keeps
     long long dead_nodes = 1LL << 22;   // MCS_DEAD_END: nodes without a new incumbent before a raise
     int dead_double = 0;          // MCS_DEAD_END: 1 doubles the incumbent size, 0 adds one
+    long long restart_min = 1LL << 20;   // MCS_RESTART: nodes of a pair before its first restart
+    unsigned long long restart_seed = 0; // MCS_RESTART: seed of the random branch order
     // resident blocks per SM of each launch configuration already asked of the
     // driver (key: warps per block, shared memory per block, kernel variant)
     std::unordered_map<uint64_t, int> occupancy;

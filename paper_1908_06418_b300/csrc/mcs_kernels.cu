@@ -457,6 +457,8 @@ __global__ void pack_kernel(PackParams P) {
         st.real = 0;
         st.lo = st.hi = 0;
         st.dead = 0;
+        st.live = st.mark = 0;
+        st.restarts = 0;
         st.open = 1;
         st.status = ok ? MCS_PENDING : MCS_ERR_ARG;
         st.abort = 0;
@@ -934,6 +936,7 @@ __device__ void serve_pack(const SearchParams& P, int slot, int lane, long long*
         PairState& ps = P.state[slot];
         ps.inc = 0; ps.open = 1; ps.abort = 0; ps.nodes = 0;
         ps.floor = 0; ps.cap = kNoCap; ps.real = 0; ps.lo = ps.hi = 0; ps.dead = 0;
+        ps.live = ps.mark = 0; ps.restarts = 0;
         ps.t_start = 0; ps.deadline = 0; ps.ticket = rtk; ps.timeout_ns = rt;
         ps.status = ok ? MCS_PENDING : MCS_ERR_ARG;
     }
@@ -1132,6 +1135,86 @@ __device__ __forceinline__ bool donate(const SearchParams& P, int pair, int d0, 
     if (ds == t.d) {
         t.rrem = rr & ~give;
         t.flags = fl & ~gflags;
+    }
+    return true;
+}
+
+// SplitMix64 (Steele, Lea, Flood 2014), one output per counter value.
+__device__ __forceinline__ u64 splitmix64(u64 x) {
+    x += 0x9E3779B97F4A7C15ull;
+    x = (x ^ (x >> 30)) * 0xBF58476D1CE4E5B9ull;
+    x = (x ^ (x >> 27)) * 0x94D049BB133111EBull;
+    return x ^ (x >> 31);
+}
+
+// Randomized restart (Section IV-A, MCS_RESTART): this searcher gives up its
+// position in the tree.  Every open level of its stack -- remaining
+// candidates and, if still to do, the "v unmatched" branch -- goes to the
+// ring as a task, so the pending branches are the record of what is left to
+// visit and nothing is lost; the levels are spilled in a random order (an
+// affine permutation x -> (a x + b) mod 2^k of the level span, a odd, from
+// SplitMix64 of the seed, the pair and its restart count), and whoever takes
+// them next continues from there.  The caller then ends its task.  Returns
+// false if a bounded wait for a ring slot expired.
+template <int GS, typename Stack>
+__device__ __noinline__ bool spill_all(const SearchParams& P, int pair, int d0, const Top& t, int inc,
+                                       const WarpSmem& w, const Stack& st, const Grp<GS>& g) {
+    Control* ctl = P.ctl;
+    const uint32_t qmask = P.qcap - 1;
+    if (g.q == 0) {
+        w.rrem[t.d] = t.rrem;
+        w.info[t.d] = pack_info(t.base, t.C, t.v, t.flags, t.bound);
+    }
+    g.sync();
+    int nr = 0;
+    if (g.q == 0) nr = atomicAdd(&P.state[pair].restarts, 1);
+    nr = g.shfl(nr, 0);
+    const int span = t.d - d0 + 1;
+    int m = 1;
+    while (m < span) m <<= 1;
+    const u64 r = splitmix64(P.restart_seed + ((u64)(unsigned)pair << 32) + (u64)(unsigned)nr);
+    const unsigned a = (unsigned)(r >> 32) | 1u, b = (unsigned)r;
+    for (int i = 0; i < m; ++i) {
+        const int d = d0 + (int)((a * (unsigned)i + b) & (unsigned)(m - 1));
+        if (d > t.d) continue;
+        const u64 inf = w.info[d];
+        const u64 rr = w.rrem[d];
+        const int fl = (int)((inf >> 32) & 0xff), bd = (int)((inf >> 40) & 0xff);
+        if (!((rr != 0 || (fl & kTaskPending)) && bd > inc)) continue;   // nothing left above the bound
+        u64 ticket = 0;
+        int ok = 0;
+        if (g.q == 0) {
+            ticket = atomicAdd(&ctl->q_tail, 1ull);
+            atomicAdd(&P.state[pair].open, 1);
+            ok = wait_seq(P.qseq + (ticket & qmask), ticket) ? 1 : -1;
+        }
+        ok = g.shfl(ok, 0);
+        if (ok < 0) {
+            if (g.q == 0) atomicCAS(&ctl->error, 0, MCS_ERR_DEVICE_STALL);
+            return false;
+        }
+        ticket = g.shfl64(ticket, 0);
+        Task* dst = P.queue + (ticket & qmask);
+        const int C = (int)((inf >> 16) & 0xff);
+        const int bs = (int)(inf & 0xffff);
+        for (int i2 = g.q; i2 < C; i2 += GS) dst->cls[i2] = *st.at(bs + i2);
+        for (int i2 = g.q; i2 < d; i2 += GS) { dst->Mg[i2] = w.Mg[i2]; dst->Mh[i2] = w.Mh[i2]; }
+        if (g.q == 0) {
+            dst->h.pair = pair;
+            dst->h.depth = d;
+            dst->h.C = C;
+            dst->h.v = (int)((inf >> 24) & 0xff);
+            dst->h.rrem = rr;
+            dst->h.flags = fl & kTaskPending;
+            dst->h.bound = bd;
+        }
+        g.sync();
+        __threadfence();
+        if (g.q == 0) {
+            P.qseq[ticket & qmask] = ticket + 1;   // publish
+            atomicMax(&ctl->last_progress, gtimer());
+        }
+        g.sync();
     }
     return true;
 }
@@ -1470,6 +1553,7 @@ __global__ void __launch_bounds__(256, (GS == 32 ? MCS_SEARCH_MINB : MCS_GROUP_M
                             if (g.q == 0) {
                                 atomicMax(&ps.real, dm);        // a recorded mapping of size dm
                                 if (P.flags & MCS_DEAD_END) ps.dead = 0;
+                                if (P.flags & MCS_RESTART) ps.mark = vload(&ps.live);
                             }
                         }
                     } else {
@@ -1539,7 +1623,7 @@ __global__ void __launch_bounds__(256, (GS == 32 ? MCS_SEARCH_MINB : MCS_GROUP_M
                 t.bound = dm + sum;
         };
 
-        int p_inc = 0, p_abort = 0, p_hungry = 0;
+        int p_inc = 0, p_abort = 0, p_hungry = 0, p_restart = 0;
         while (t.d >= d0) {
             ++tick;
             if ((tick & P.poll_mask) == 0 && g.q == 0) {
@@ -1550,6 +1634,20 @@ __global__ void __launch_bounds__(256, (GS == 32 ? MCS_SEARCH_MINB : MCS_GROUP_M
                     if constexpr (GOAL) atomicCAS(&ps.abort, 0, 1);   // time limit (a reached goal stays)
                     else ps.abort = 1;                 // per-pair time limit
                     p_abort = 1;
+                }
+                if (GOAL && (P.flags & MCS_RESTART) && p_abort == 0) {
+                    // randomized restart (Section IV-A) once the pair's node count has
+                    // doubled since its last new incumbent (and passed restart_min); the
+                    // searcher whose poll wins the mark update restarts
+                    const u64 step = (u64)P.poll_mask + 1;
+                    const u64 now = atomicAdd((unsigned long long*)&ps.live, (unsigned long long)step) + step;
+                    const u64 mk = vload(&ps.mark);
+                    // room for a whole stack of spilled branches: unclaimed tasks stay
+                    // under half the ring (else this restart waits for the next doubling)
+                    const long long pend = (long long)vload(&ctl->q_tail) - (long long)vload(&ctl->q_head);
+                    if (now >= P.restart_min && now >= 2 * mk && pend + 2 * kLevels < (long long)(P.qcap / 2) &&
+                        atomicCAS((unsigned long long*)&ps.mark, (unsigned long long)mk, (unsigned long long)now) == mk)
+                        p_restart = 1;
                 }
                 if (GOAL && (P.flags & MCS_DEAD_END) && p_abort == 0) {
                     // dead-end forecast (Section IV): the searcher whose poll takes the
@@ -1575,6 +1673,14 @@ __global__ void __launch_bounds__(256, (GS == 32 ? MCS_SEARCH_MINB : MCS_GROUP_M
                 const int hungry = g.shfl(p_hungry, 0);
                 inc = max(inc, g_inc);
                 if (ab) break;
+                if constexpr (GOAL) {
+                    const int rst = g.shfl(p_restart, 0);
+                    p_restart = 0;
+                    if (rst) {                         // restart: every open level to the ring
+                        spill_all<GS>(P, pair, d0, t, inc, w, st, g);
+                        break;
+                    }
+                }
                 // ---- donate the shallowest open level to a waiting searcher ----
                 if (hungry && !donate<GS>(P, pair, d0, t, inc, w, st, g, donated)) break;
             }
@@ -1661,7 +1767,7 @@ cudaError_t launch_search(const SearchParams& p, int blocks, int warps_per_block
         return launch_t<false, false, true, 32, false>(p, blocks, warps_per_block, s);
     }
     const bool narrow = (p.flags & MCS_WORD32) != 0;
-    if (p.flags & (MCS_TOP_DOWN | MCS_DEAD_END)) {
+    if (p.flags & (MCS_TOP_DOWN | MCS_DEAD_END | MCS_RESTART)) {
         // goal-directed strategies (the caller rejects them with the learned order)
         if (learned) return cudaErrorNotSupported;
         return directed ? launch_w<true, false, true>(p, blocks, warps_per_block, gs, narrow, s)

@@ -82,6 +82,7 @@ extern "C" int mcs_solve_batch_noalloc(int32_t npairs, const int32_t* d_n,
     if (!d_n || !d_adj_off || !d_adj || !d_size || !d_status || !d_nodes) return MCS_ERR_ARG;
     if (flags & MCS_ORDER_LEARNED) return MCS_ERR_UNSUPPORTED;
     if ((flags & MCS_TOP_DOWN) && (flags & MCS_DEAD_END)) return MCS_ERR_ARG;
+    if ((flags & MCS_RESTART) && (flags & (MCS_TOP_DOWN | MCS_DEAD_END))) return MCS_ERR_ARG;
     int dev = 0;
     if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= kMaxDevices) return MCS_ERR_CUDA;
     unsigned char* base = nullptr;
@@ -135,6 +136,8 @@ extern "C" int mcs_solve_batch_noalloc(int32_t npairs, const int32_t* d_n,
     sp.steal_keep_q4 = kStealKeepDefault;
     sp.dead_nodes = 1ull << 22;
     sp.dead_double = 0;
+    sp.restart_min = 1ull << 20;
+    sp.restart_seed = 0;
     sp.npairs = npairs;
     sp.flags = flags;
     sp.timeout_ns = (u64)(tmo * 1e9);

@@ -161,6 +161,8 @@ int launch_server(mcs_ctx* c, ServeState* S) {
     sp.steal_keep_q4 = kStealKeepDefault;
     sp.dead_nodes = 0;
     sp.dead_double = 0;
+    sp.restart_min = 0;
+    sp.restart_seed = 0;
     sp.serving = 1;
     sp.sv.host_written = dev_view(S->h_written);
     sp.sv.ring = dev_view(S->h_ring);
@@ -260,7 +262,7 @@ extern "C" {
 int mcs_submit(mcs_ctx* c, const mcs_graph* G, const mcs_graph* H, uint32_t flags, double timeout_s,
                uint64_t* ticket) {
     if (!c || !ticket || check_graph_s(G) || check_graph_s(H)) return MCS_ERR_ARG;
-    if (flags & (MCS_DIRECTED | MCS_ORDER_LEARNED | MCS_ORDER_HR | MCS_TOP_DOWN | MCS_DEAD_END))
+    if (flags & (MCS_DIRECTED | MCS_ORDER_LEARNED | MCS_ORDER_HR | MCS_TOP_DOWN | MCS_DEAD_END | MCS_RESTART))
         return MCS_ERR_UNSUPPORTED;
     if (cudaSetDevice(c->device) != cudaSuccess) return MCS_ERR_CUDA;
     ServeState* S = nullptr;

@@ -194,3 +194,86 @@ def test_deadend_parameters_and_flag_combination(solver):
     rc = solver.solve_batch_device(n, b.d_n, b.d_adj_off, b.d_adj, b.d_lab_off, b.d_labels, *out,
                                    flags=b.flags | MCS_DEAD_END | MCS_TOP_DOWN, timeout_s=10)
     assert rc == MCS_ERR_ARG
+
+
+# --------------------------------------------------------------------------
+# randomized restarts (Section IV-A)
+# --------------------------------------------------------------------------
+@pytest.mark.parametrize("min_nodes,seed", [(64, 0), (4096, 77)])
+def test_restart_labelled_batch_equals_stored_oracle(solver, min_nodes, seed):
+    """Restarts that fire after a few polls: every open branch of the
+    restarting searcher goes back to the ring, and no part of the tree may
+    be lost -- the sizes equal the stored oracle optima."""
+    from paper_1908_06418_b300 import MCS_RESTART
+    rows = {r["idx"]: r for r in _golden("c3_oracle.jsonl")}
+    pairs = synth.config3_pairs()[:512]
+    solver.set_restart(min_nodes, seed)
+    try:
+        res = solver.solve_batch(pairs, flags=MCS_RESTART, timeout_s=60)
+    finally:
+        solver.set_restart(-1, 0)
+    for i, (p, r) in enumerate(zip(pairs, res)):
+        g = rows[i]
+        assert r.status == 0, (i, r.status)
+        assert r.size == g["size"] if g["complete"] else r.size >= g["size"], (i, r.size, g["size"])
+        assert oracle.verify(p.G.adj, p.H.adj, r.g_idx, r.h_idx, p.G.labels, p.H.labels) == 1, i
+
+
+@pytest.mark.parametrize("directed,k", [(False, 0), (True, 0), (False, 3)])
+def test_restart_small_minimum_batch_equals_oracle(solver, directed, k):
+    from paper_1908_06418_b300 import MCS_RESTART
+    pairs = _pairs(120, 8, 24, 4500 + k + (50 if directed else 0), directed, k)
+    solver.set_restart(32, 5)
+    try:
+        res = solver.solve_batch(pairs, flags=MCS_RESTART, directed=directed, timeout_s=60)
+    finally:
+        solver.set_restart(-1, 0)
+    for i, (p, r) in enumerate(zip(pairs, res)):
+        o = oracle.mcs(p.G.adj, p.H.adj, p.G.labels, p.H.labels, directed=directed)
+        assert r.status == 0 and r.size == o.size, (i, r.size, o.size)
+        assert oracle.verify(p.G.adj, p.H.adj, r.g_idx, r.h_idx, p.G.labels, p.H.labels) == 1, i
+
+
+def test_restart_lone_searcher(solver):
+    """A lone searcher: with a minimum no pair reaches it walks the plain tree
+    node for node; with restarts firing its traversal changes (its spilled
+    branches come back from the ring in another order) and the optimum does
+    not."""
+    from paper_1908_06418_b300 import MCS_RESTART, MCS_NO_LEVEL_PRUNE
+    pairs = _pairs(16, 12, 18, 4600, pmin=0.3, pmax=0.5)
+    solver.set_max_warps(1)
+    changed = 0
+    try:
+        for p in pairs:
+            o = oracle.mcs(p.G.adj, p.H.adj)
+            solver.set_restart(1 << 50, 0)
+            r = solver.solve(p.G.adj, p.H.adj, flags=MCS_RESTART | MCS_NO_LEVEL_PRUNE, timeout_s=30)
+            assert r.status == 0 and r.size == o.size and r.nodes == o.nodes
+            solver.set_restart(64, 3)
+            r = solver.solve(p.G.adj, p.H.adj, flags=MCS_RESTART | MCS_NO_LEVEL_PRUNE, timeout_s=30)
+            assert r.status == 0 and r.size == o.size
+            assert oracle.verify(p.G.adj, p.H.adj, r.g_idx, r.h_idx) == 1
+            changed += r.nodes != o.nodes
+    finally:
+        solver.set_max_warps(0)
+        solver.set_restart(-1, 0)
+    assert changed >= len(pairs) // 2
+
+
+def test_restart_parameters_and_flag_combinations(solver):
+    import torch
+    from paper_1908_06418_b300 import (MCS_RESTART, MCS_TOP_DOWN, MCS_DEAD_END, MCS_ORDER_LEARNED,
+                                       MCS_ERR_ARG, MCS_ERR_UNSUPPORTED, DeviceBatch)
+    for bad in (0, -2):
+        with pytest.raises(ValueError):
+            solver.set_restart(bad, 0)
+    pairs = _pairs(4, 6, 10, 4700)
+    b = DeviceBatch(pairs)
+    n = len(pairs)
+    out = [torch.zeros(n, dtype=torch.int32, device=b.device), torch.zeros(n, dtype=torch.int32, device=b.device),
+           torch.zeros(n, dtype=torch.int64, device=b.device)]
+    for extra, want in ((MCS_TOP_DOWN, MCS_ERR_ARG), (MCS_DEAD_END, MCS_ERR_ARG),
+                        (MCS_ORDER_LEARNED, MCS_ERR_UNSUPPORTED)):
+        rc = solver.solve_batch_device(n, b.d_n, b.d_adj_off, b.d_adj, b.d_lab_off, b.d_labels, *out,
+                                       flags=b.flags | MCS_RESTART | extra, timeout_s=10)
+        assert rc == want, (extra, rc)
