@@ -44,8 +44,8 @@ METRIC = "MCS pairs solved/sec (exact) on 1 B300"
 # the dominant search kernel, from a single-pass ncu capture of this
 # workload's launch (profiles/dram_search_kernel_c2.md); reported only while
 # the kernel source is the one the capture was taken with.
-TRAFFIC = {"c2": {"kernel_sha1": "8a1098cd8250ad62", "bytes": 1.21e9 + 5.29e9},
-           "c3": {"kernel_sha1": "8a1098cd8250ad62", "bytes": 96.91e6 + 193.70e6}}
+TRAFFIC = {"c2": {"kernel_sha1": "bd0f42f3a1f70798", "bytes": 1.18e9 + 5.24e9},
+           "c3": {"kernel_sha1": "bd0f42f3a1f70798", "bytes": 98.94e6 + 194.31e6}}
 UNIT = "pairs/s"
 
 
