@@ -769,10 +769,11 @@ __device__ __noinline__ bool requeue_goal(const SearchParams& P, int pair, int f
 }
 
 // Finish the pair: write size, status, nodes and the mapping (original numbers).
-// GOAL: a launch of a goal-directed strategy (MCS_TOP_DOWN, MCS_DEAD_END):
-// the size is the largest recorded mapping, and a pair may be searched again
-// from its root with another goal instead of being finished.
-template <bool SERVE, int GS, bool GOAL>
+// GOAL (nonzero): a launch of a strategy of Section IV (MCS_TOP_DOWN,
+// MCS_DEAD_END, MCS_RESTART): the size is the largest recorded mapping, and a
+// pair may be searched again from its root with another goal instead of being
+// finished.
+template <bool SERVE, int GS, int GOAL>
 __device__ void finalize_pair(const SearchParams& P, int pair, const Grp<GS>& g, int16_t* smap) {
     __threadfence();
     PairState& ps = P.state[pair];
@@ -871,7 +872,7 @@ __device__ void finalize_pair(const SearchParams& P, int pair, const Grp<GS>& g,
 
 // A task of `pair` ended: publish node count, drop the open count and finalise
 // the pair if this was its last task.
-template <bool SERVE, int GS, bool GOAL>
+template <bool SERVE, int GS, int GOAL>
 __device__ __forceinline__ void end_task(const SearchParams& P, int pair, u64& nodes, const Grp<GS>& g,
                                          int16_t* smap) {
     int last = 0;
@@ -1229,10 +1230,11 @@ __device__ __noinline__ bool spill_all(const SearchParams& P, int pair, int d0, 
 #define MCS_GROUP_MINB 4
 #endif
 
-// GOAL: the goal-directed strategies of Section IV (MCS_TOP_DOWN, MCS_DEAD_END)
-// are compiled into their own instantiation, so that the plain search carries
-// none of their bookkeeping.
-template <bool DIR, bool LEARNED, bool SERVE, int GS, bool NARROW, bool GOAL>
+// GOAL: the strategies of Section IV are compiled into instantiations of
+// their own, so that the plain search (0) carries none of their bookkeeping:
+// 1 top-down goal sizes (MCS_TOP_DOWN), 2 dead-end forecasting and
+// randomized restarts (MCS_DEAD_END, MCS_RESTART).
+template <bool DIR, bool LEARNED, bool SERVE, int GS, bool NARROW, int GOAL>
 __global__ void __launch_bounds__(256, (GS == 32 ? MCS_SEARCH_MINB : MCS_GROUP_MINB)) search_kernel(SearchParams P) {
     static_assert(GS == 2 || GS == 4 || GS == 8 || GS == 16 || GS == 32, "searcher group size");
     static_assert(!SERVE || GS >= 8, "serve mode keeps the level arrays and result scratch in shared memory");
@@ -1552,8 +1554,8 @@ __global__ void __launch_bounds__(256, (GS == 32 ? MCS_SEARCH_MINB : MCS_GROUP_M
                         if constexpr (GOAL) {
                             if (g.q == 0) {
                                 atomicMax(&ps.real, dm);        // a recorded mapping of size dm
-                                if (P.flags & MCS_DEAD_END) ps.dead = 0;
-                                if (P.flags & MCS_RESTART) ps.mark = vload(&ps.live);
+                                if (GOAL == 2 && (P.flags & MCS_DEAD_END)) ps.dead = 0;
+                                if (GOAL == 2 && (P.flags & MCS_RESTART)) ps.mark = vload(&ps.live);
                             }
                         }
                     } else {
@@ -1635,7 +1637,7 @@ __global__ void __launch_bounds__(256, (GS == 32 ? MCS_SEARCH_MINB : MCS_GROUP_M
                     else ps.abort = 1;                 // per-pair time limit
                     p_abort = 1;
                 }
-                if (GOAL && (P.flags & MCS_RESTART) && p_abort == 0) {
+                if (GOAL == 2 && (P.flags & MCS_RESTART) && p_abort == 0) {
                     // randomized restart (Section IV-A) once the pair's node count has
                     // doubled since its last new incumbent (and passed restart_min); the
                     // searcher whose poll wins the mark update restarts
@@ -1649,7 +1651,7 @@ __global__ void __launch_bounds__(256, (GS == 32 ? MCS_SEARCH_MINB : MCS_GROUP_M
                         atomicCAS((unsigned long long*)&ps.mark, (unsigned long long)mk, (unsigned long long)now) == mk)
                         p_restart = 1;
                 }
-                if (GOAL && (P.flags & MCS_DEAD_END) && p_abort == 0) {
+                if (GOAL == 2 && (P.flags & MCS_DEAD_END) && p_abort == 0) {
                     // dead-end forecast (Section IV): the searcher whose poll takes the
                     // pair's count of nodes without a new incumbent past the threshold
                     // raises the incumbent size, as if a mapping of that size were known
@@ -1673,7 +1675,7 @@ __global__ void __launch_bounds__(256, (GS == 32 ? MCS_SEARCH_MINB : MCS_GROUP_M
                 const int hungry = g.shfl(p_hungry, 0);
                 inc = max(inc, g_inc);
                 if (ab) break;
-                if constexpr (GOAL) {
+                if constexpr (GOAL == 2) {
                     const int rst = g.shfl(p_restart, 0);
                     p_restart = 0;
                     if (rst) {                         // restart: every open level to the ring
@@ -1731,10 +1733,10 @@ static bool ensure_smem_limit(void (*k)(SearchParams), int smem) {
     return true;
 }
 
-template <bool DIR, bool LEARNED, bool SERVE, int GS, bool NARROW, bool GOAL>
+template <bool DIR, bool LEARNED, bool SERVE, int GS, bool NARROW, int GOAL>
 struct KernelTag {};
 
-template <bool DIR, bool LEARNED, bool SERVE, int GS, bool NARROW, bool GOAL = false>
+template <bool DIR, bool LEARNED, bool SERVE, int GS, bool NARROW, int GOAL = 0>
 static cudaError_t launch_t(const SearchParams& p, int blocks, int wpb, cudaStream_t s) {
     size_t smem = (size_t)wpb * (32 / GS) * p.warp_smem_bytes;
     auto* k = search_kernel<DIR, LEARNED, SERVE, GS, NARROW, GOAL>;
@@ -1744,7 +1746,7 @@ static cudaError_t launch_t(const SearchParams& p, int blocks, int wpb, cudaStre
     return cudaGetLastError();
 }
 
-template <bool DIR, bool LEARNED, bool NARROW, bool GOAL>
+template <bool DIR, bool LEARNED, bool NARROW, int GOAL>
 static cudaError_t launch_g(const SearchParams& p, int blocks, int wpb, int gs, cudaStream_t s) {
     if (gs == 2) return launch_t<DIR, LEARNED, false, 2, NARROW, GOAL>(p, blocks, wpb, s);
     if (gs == 4) return launch_t<DIR, LEARNED, false, 4, NARROW, GOAL>(p, blocks, wpb, s);
@@ -1753,7 +1755,7 @@ static cudaError_t launch_g(const SearchParams& p, int blocks, int wpb, int gs, 
     return launch_t<DIR, LEARNED, false, 32, NARROW, GOAL>(p, blocks, wpb, s);
 }
 
-template <bool DIR, bool LEARNED, bool GOAL = false>
+template <bool DIR, bool LEARNED, int GOAL = 0>
 static cudaError_t launch_w(const SearchParams& p, int blocks, int wpb, int gs, bool narrow, cudaStream_t s) {
     return narrow ? launch_g<DIR, LEARNED, true, GOAL>(p, blocks, wpb, gs, s)
                   : launch_g<DIR, LEARNED, false, GOAL>(p, blocks, wpb, gs, s);
@@ -1770,8 +1772,11 @@ cudaError_t launch_search(const SearchParams& p, int blocks, int warps_per_block
     if (p.flags & (MCS_TOP_DOWN | MCS_DEAD_END | MCS_RESTART)) {
         // goal-directed strategies (the caller rejects them with the learned order)
         if (learned) return cudaErrorNotSupported;
-        return directed ? launch_w<true, false, true>(p, blocks, warps_per_block, gs, narrow, s)
-                        : launch_w<false, false, true>(p, blocks, warps_per_block, gs, narrow, s);
+        if (p.flags & MCS_TOP_DOWN)
+            return directed ? launch_w<true, false, 1>(p, blocks, warps_per_block, gs, narrow, s)
+                            : launch_w<false, false, 1>(p, blocks, warps_per_block, gs, narrow, s);
+        return directed ? launch_w<true, false, 2>(p, blocks, warps_per_block, gs, narrow, s)
+                        : launch_w<false, false, 2>(p, blocks, warps_per_block, gs, narrow, s);
     }
     if (directed) return learned ? launch_w<true, true>(p, blocks, warps_per_block, gs, narrow, s)
                                  : launch_w<true, false>(p, blocks, warps_per_block, gs, narrow, s);
