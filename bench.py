@@ -44,8 +44,8 @@ METRIC = "MCS pairs solved/sec (exact) on 1 B300"
 # the dominant search kernel, from a single-pass ncu capture of this
 # workload's launch (profiles/dram_search_kernel_c2.md); reported only while
 # the kernel source is the one the capture was taken with.
-TRAFFIC = {"c2": {"kernel_sha1": "bd0f42f3a1f70798", "bytes": 1.18e9 + 5.24e9},
-           "c3": {"kernel_sha1": "bd0f42f3a1f70798", "bytes": 98.94e6 + 194.31e6}}
+TRAFFIC = {"c2": {"kernel_sha1": "de3f4df5bb2549c2", "bytes": 1.19e9 + 5.28e9},
+           "c3": {"kernel_sha1": "de3f4df5bb2549c2", "bytes": 99.89e6 + 197.09e6}}
 UNIT = "pairs/s"
 
 
