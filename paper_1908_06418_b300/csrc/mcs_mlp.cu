@@ -11,8 +11,10 @@
 //                    128 -> 1 logit; both hidden layers are tcgen05.mma
 //                    (kind::f16: f16 operands in shared memory, f32
 //                    accumulators in tensor memory), 128 rows per tile
-//   bwd kernels      backward pass (head, two mma.sync GEMMs for dh1 and the
-//                    weight gradients, column sums) and an Adam update
+//   bwd kernels      backward pass: a head kernel (logit gradient, w3, b2, b3,
+//                    loss), then mlp_bwd_kernel -- dz1 and the W2, W1 and b1
+//                    gradients as tcgen05.mma on 128-row tiles -- and an
+//                    Adam update
 //   keys / rank      per-pair vertex order keys (for the renumbering done by
 //                    the pack kernel) and per-v candidate ranks (for the search)
 #include <cmath>
@@ -36,19 +38,9 @@ static_assert(kNParams == MCS_ORDER_NPARAMS, "parameter layout out of date");
 constexpr int kOffW1 = 0, kOffB1 = kIn * kH, kOffW2 = kOffB1 + kH, kOffB2 = kOffW2 + kH * kH,
               kOffW3 = kOffB2 + kH, kOffB3 = kOffW3 + kH;
 
-__device__ __forceinline__ void mma16816(float (&d)[4], const uint32_t (&a)[4], uint32_t b0, uint32_t b1) {
-    asm volatile(
-        "mma.sync.aligned.m16n8k16.row.col.f32.f16.f16.f32 {%0,%1,%2,%3}, {%4,%5,%6,%7}, {%8,%9}, "
-        "{%0,%1,%2,%3};"
-        : "+f"(d[0]), "+f"(d[1]), "+f"(d[2]), "+f"(d[3])
-        : "r"(a[0]), "r"(a[1]), "r"(a[2]), "r"(a[3]), "r"(b0), "r"(b1));
-}
 __device__ __forceinline__ uint32_t pack2(float lo, float hi) {
     __half2 h = __floats2half2_rn(lo, hi);
     return *reinterpret_cast<uint32_t*>(&h);
-}
-__device__ __forceinline__ uint32_t pack2h(__half lo, __half hi) {
-    return (uint32_t)__half_as_ushort(lo) | ((uint32_t)__half_as_ushort(hi) << 16);
 }
 
 // ---------------------------------------------------------------------------
@@ -204,10 +196,18 @@ __device__ __forceinline__ bool mbar_try(uint32_t a, uint32_t parity) {
                  "selp.u32 %0, 1, 0, p;\n}" : "=r"(ok) : "r"(a), "r"(parity) : "memory");
     return ok != 0;
 }
-// bounded: gives up (false) after ~2^22 polls instead of spinning forever
+__device__ __forceinline__ unsigned long long global_ns() {
+    unsigned long long t;
+    asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
+    return t;
+}
+// bounded: gives up (false) after ~2 s (or 2^22 polls) instead of waiting forever
 __device__ __forceinline__ bool mbar_wait(uint32_t a, uint32_t parity) {
-    for (uint32_t i = 0; i < (1u << 22); ++i)
+    const unsigned long long t0 = global_ns();
+    for (uint32_t i = 0; i < (1u << 22); ++i) {
         if (mbar_try(a, parity)) return true;
+        if ((i & 255) == 255 && global_ns() - t0 > 2000000000ull) return false;
+    }
     return false;
 }
 // D[tmem] (+)= A[smem] * B[smem]^T, one elected thread; acc = 0 overwrites D
@@ -501,117 +501,153 @@ __global__ void bwd_head_kernel(HeadParams P, int rows_per_block) {
     if (c == 0) { atomicAdd(P.g_b3, gb3); atomicAdd(P.loss, ls); }
 }
 
-// Generic tensor-core GEMM: C(m,n) (+)= sum_k A(m,k) B(k,n); one warp per
-// 16 x 64 output tile and K chunk.  A.pair(m,k) packs A(m,k), A(m,k+1);
-// B.pair(k,n) packs B(k,n), B(k+1,n) (k even, zero outside the matrix).
-template <class AF, class BF, class CF>
-__global__ void gemm_kernel(int M, int N, int K, int kchunk, AF A, BF B, CF C) {
-    const int lane = threadIdx.x & 31, g = lane >> 2, tq = lane & 3;
-    const int m0 = blockIdx.x * 16, n0 = blockIdx.y * 64;
-    const int kb = blockIdx.z * kchunk, ke = min(K, kb + kchunk);
-    float acc[8][4];
-#pragma unroll
-    for (int nt = 0; nt < 8; ++nt) acc[nt][0] = acc[nt][1] = acc[nt][2] = acc[nt][3] = 0.f;
-    for (int k0 = kb; k0 < ke; k0 += 16) {
-        uint32_t a[4];
-        a[0] = A.pair(m0 + g, k0 + 2 * tq, M, ke);
-        a[1] = A.pair(m0 + g + 8, k0 + 2 * tq, M, ke);
-        a[2] = A.pair(m0 + g, k0 + 2 * tq + 8, M, ke);
-        a[3] = A.pair(m0 + g + 8, k0 + 2 * tq + 8, M, ke);
-#pragma unroll
-        for (int nt = 0; nt < 8; ++nt) {
-            const int n = n0 + nt * 8 + g;
-            mma16816(acc[nt], a, B.pair(k0 + 2 * tq, n, N, ke), B.pair(k0 + 2 * tq + 8, n, N, ke));
-        }
-    }
-#pragma unroll
-    for (int nt = 0; nt < 8; ++nt) {
-        const int n = n0 + nt * 8 + 2 * tq;
-        C.put(m0 + g, n, acc[nt][0], M, N);
-        C.put(m0 + g, n + 1, acc[nt][1], M, N);
-        C.put(m0 + g + 8, n, acc[nt][2], M, N);
-        C.put(m0 + g + 8, n + 1, acc[nt][3], M, N);
-    }
+// ---------------------------------------------------------------------------
+// backward GEMMs on the 5th-generation tensor cores (one 128-row tile per CTA)
+// ---------------------------------------------------------------------------
+// For the rows r of a tile (dz2, h1 from the forward pass, x gathered again):
+//   dz1[r][j]   = (sum_o dz2[r][o] W2[j][o]) * (h1[r][j] > 0)      MMA 1 (M r, N j, K o)
+//   gW2[i][o]  += sum_r h1[r][i] dz2[r][o]                          MMA 2 (M i, N o, K r)
+//   gW1[i][j]  += sum_r x[r][i] dz1[r][j]                           MMA 3 (M i, N j, K r)
+// x[r][36] = 1 is the b1 input of the forward pass, so row 36 of MMA 3 is the
+// b1 gradient (the sum of dz1 over the rows).  Every operand is K-major in
+// shared memory (the layout of the forward pass); the transposed ones (h1,
+// dz2, x, dz1 with the rows r as K) are written element by element by the
+// thread that owns row r.  Accumulators in TMEM: MMA 1 columns 0-127, MMA 2
+// 128-255, MMA 3 256-383; each CTA adds its tile's weight gradients to the
+// global sums with atomics.
+struct BwdParams {
+    FwdParams fp;            // rows, feature table, pair count, row count (for gather_x)
+    const __half* W2h;       // [in][out] (as stored in the parameters)
+    const __half* h1;        // [nrows][128]
+    const __half* dz2;       // [nrows][128]
+    float* g_W1;             // [48][128] (rows 36.. not written)
+    float* g_b1;             // [128]
+    float* g_W2;             // [128][128]
+    int* err;
+};
+constexpr int kBOpBytes = kTile * kH * 2;           // one 128 x 128 fp16 operand
+constexpr int kBW2 = 0, kBDz2 = kBOpBytes, kBH1T = 2 * kBOpBytes, kBDz2T = 3 * kBOpBytes,
+              kBXT = 4 * kBOpBytes, kBDz1T = 5 * kBOpBytes, kBBar = 6 * kBOpBytes;
+constexpr int kBwdSmem = kBBar + 16;
+static_assert(kBwdSmem <= 227 * 1024, "shared memory per CTA");
+static_assert(2 * (kBwdSmem + 1024) > 228 * 1024, "one CTA per SM: its 512 TMEM columns never wait");
+
+// element (m, k) of a 128-row K-major fp16 operand with K = 128
+__device__ __forceinline__ void put_t(unsigned char* base, int m, int k, __half v) {
+    *reinterpret_cast<__half*>(base + kmaj_off(m, k >> 3, kH / 8) + (k & 7) * 2) = v;
 }
 
-__device__ __forceinline__ __half hz() { return __ushort_as_half((unsigned short)0); }
-
-// row-major fp16 matrix, pairs along the second index (contiguous)
-struct RowPairA {
-    const __half* p; int ld;
-    __device__ uint32_t pair(int m, int k, int M, int K) const {
-        if (m >= M || k >= K) return 0u;
-        if (k + 1 < K) return *reinterpret_cast<const uint32_t*>(p + (size_t)m * ld + k);
-        return pack2h(p[(size_t)m * ld + k], hz());
+__global__ void __launch_bounds__(kTile, 1) mlp_bwd_kernel(BwdParams P) {
+    extern __shared__ __align__(1024) unsigned char sm[];
+    const int tid = threadIdx.x, warp = tid >> 5;
+    const uint32_t sbase = smem_u32(sm);
+    const long long r = (long long)blockIdx.x * kTile + tid;       // this thread's row
+    const bool ok = r < P.fp.nrows;
+    for (int i = tid; i < kH * (kH / 8); i += kTile) {               // W2h rows: n = in, k = out
+        const int n = i / (kH / 8), kc = i % (kH / 8);
+        *reinterpret_cast<uint4*>(sm + kBW2 + kmaj_off(n, kc, kH / 8)) =
+            *reinterpret_cast<const uint4*>(P.W2h + n * kH + kc * 8);
     }
-};
-// B(k, n) = W[n][k]: fp16 matrix stored [n][k]; pairs along k contiguous
-struct NKPairB {
-    const __half* p; int ld;
-    __device__ uint32_t pair(int k, int n, int N, int K) const {
-        if (n >= N || k >= K) return 0u;
-        if (k + 1 < K) return *reinterpret_cast<const uint32_t*>(p + (size_t)n * ld + k);
-        return pack2h(p[(size_t)n * ld + k], hz());
+    // dz2: row r of MMA 1's A, and column r of MMA 2's B
+    const __half hz = __ushort_as_half((unsigned short)0);
+    for (int c = 0; c < kH / 8; ++c) {
+        uint4 v = make_uint4(0, 0, 0, 0);
+        if (ok) v = *reinterpret_cast<const uint4*>(P.dz2 + r * kH + c * 8);
+        *reinterpret_cast<uint4*>(sm + kBDz2 + kmaj_off(tid, c, kH / 8)) = v;
+        const __half* e = reinterpret_cast<const __half*>(&v);
+        for (int q = 0; q < 8; ++q) put_t(sm + kBDz2T, c * 8 + q, tid, e[q]);
     }
-};
-// A(m, k) = X[k][m] (X stored [k][m]); pairs along k are strided
-struct TransA {
-    const __half* p; int ld;
-    __device__ uint32_t pair(int m, int k, int M, int K) const {
-        if (m >= M || k >= K) return 0u;
-        __half lo = p[(size_t)k * ld + m];
-        __half hi = (k + 1 < K) ? p[(size_t)(k + 1) * ld + m] : hz();
-        return pack2h(lo, hi);
+    // h1: column r of MMA 2's A
+    for (int c = 0; c < kH / 8; ++c) {
+        uint4 v = make_uint4(0, 0, 0, 0);
+        if (ok) v = *reinterpret_cast<const uint4*>(P.h1 + r * kH + c * 8);
+        const __half* e = reinterpret_cast<const __half*>(&v);
+        for (int q = 0; q < 8; ++q) put_t(sm + kBH1T, c * 8 + q, tid, e[q]);
     }
-};
-// B(k, n) = X[k][n] (X stored [k][n]); pairs along k are strided
-struct KNPairB {
-    const __half* p; int ld;
-    __device__ uint32_t pair(int k, int n, int N, int K) const {
-        if (n >= N || k >= K) return 0u;
-        __half lo = p[(size_t)k * ld + n];
-        __half hi = (k + 1 < K) ? p[(size_t)(k + 1) * ld + n] : hz();
-        return pack2h(lo, hi);
+    // x (48 inputs, the rest of the 128 rows zero): column r of MMA 3's A
+    {
+        const XRow x = gather_x(P.fp, r);
+        for (int c = 0; c < 5; ++c) {
+            const __half* e = reinterpret_cast<const __half*>(&x.c[c]);
+            for (int q = 0; q < 8; ++q) put_t(sm + kBXT, c * 8 + q, tid, x.ok ? e[q] : hz);
+        }
+        for (int i = 40; i < kH; ++i) put_t(sm + kBXT, i, tid, hz);
     }
-};
-// A(i, r) = x(row r, input i): gathered from the feature table
-struct InputTA {
-    const int32_t* rows; const __half* feat; int npairs;
-    __device__ __half at(int i, int r) const {
-        const int p = rows[3 * r], v = rows[3 * r + 1], u = rows[3 * r + 2];
-        if (p < 0 || p >= npairs || v < 0 || v >= kMaxN || u < 0 || u >= kMaxN) return hz();
-        if (i < kF) return feat[((size_t)(2 * p) * kMaxN + v) * kFP + i];
-        if (i < 2 * kF) return feat[((size_t)(2 * p + 1) * kMaxN + u) * kFP + (i - kF)];
-        return hz();
+    const uint32_t bar = sbase + kBBar;
+    uint32_t* tslot = reinterpret_cast<uint32_t*>(sm + kBBar + 8);
+    if (tid == 0) { mbar_init(bar, 1); mbar_init_fence(); }
+    if (warp == 0) { tmem_alloc(smem_u32(tslot), 512); tmem_relinquish(); }
+    fence_async_smem();
+    tc_before_sync();
+    __syncthreads();
+    tc_after_sync();
+    const uint32_t tmem = *tslot;
+    const uint32_t lanes = (uint32_t)(warp * 32) << 16;
+    bool stalled = false;
+    if (tid == 0) {
+#pragma unroll
+        for (int k = 0; k < kH / 16; ++k) {
+            umma_f16(tmem, kmaj_desc(sbase + kBDz2 + k * 256, kH / 8), kmaj_desc(sbase + kBW2 + k * 256, kH / 8),
+                     kIdesc, k > 0);
+            umma_f16(tmem + 128, kmaj_desc(sbase + kBH1T + k * 256, kH / 8),
+                     kmaj_desc(sbase + kBDz2T + k * 256, kH / 8), kIdesc, k > 0);
+        }
+        umma_commit(bar);
     }
-    __device__ uint32_t pair(int m, int k, int M, int K) const {
-        if (m >= M || k >= K) return 0u;
-        return pack2h(at(m, k), k + 1 < K ? at(m, k + 1) : hz());
+    if (__syncthreads_or(!mbar_wait(bar, 0))) stalled = true;
+    tc_after_sync();
+    if (!stalled) {
+        // dz1 = MMA 1 * (h1 > 0): column r of MMA 3's B
+        for (int cb = 0; cb < kH / 16; ++cb) {
+            uint32_t acc[16];
+            tmem_ld16(tmem + lanes + cb * 16, acc);
+            uint4 hv[2] = {make_uint4(0, 0, 0, 0), make_uint4(0, 0, 0, 0)};
+            if (ok) {
+                hv[0] = *reinterpret_cast<const uint4*>(P.h1 + r * kH + cb * 16);
+                hv[1] = *reinterpret_cast<const uint4*>(P.h1 + r * kH + cb * 16 + 8);
+            }
+            const __half* h = reinterpret_cast<const __half*>(hv);
+            for (int q = 0; q < 16; ++q) {
+                const float d = __uint_as_float(acc[q]);
+                put_t(sm + kBDz1T, cb * 16 + q, tid, __float2half_rn(__half2float(h[q]) > 0.f ? d : 0.f));
+            }
+        }
+        fence_async_smem();
+        tc_before_sync();
+        __syncthreads();
+        tc_after_sync();
+        if (tid == 0) {
+#pragma unroll
+            for (int k = 0; k < kH / 16; ++k)
+                umma_f16(tmem + 256, kmaj_desc(sbase + kBXT + k * 256, kH / 8),
+                         kmaj_desc(sbase + kBDz1T + k * 256, kH / 8), kIdesc, k > 0);
+            umma_commit(bar);
+        }
+        // MMA 2 is done: row tid of gW2 (input tid) to the global sums
+        for (int cb = 0; cb < kH / 16; ++cb) {
+            uint32_t acc[16];
+            tmem_ld16(tmem + 128 + lanes + cb * 16, acc);
+            for (int q = 0; q < 16; ++q) atomicAdd(P.g_W2 + tid * kH + cb * 16 + q, __uint_as_float(acc[q]));
+        }
+        if (__syncthreads_or(!mbar_wait(bar, 1))) stalled = true;
+        tc_after_sync();
+        // inputs 0..35 and the b1 input (36) sit in TMEM lanes 0..36: warps 0 and 1
+        // load (tcgen05.ld is a whole-warp instruction), rows 0..36 add
+        if (!stalled && warp < 2) {
+            float* dst = tid < 2 * kF ? P.g_W1 + tid * kH : P.g_b1;
+            for (int cb = 0; cb < kH / 16; ++cb) {
+                uint32_t acc[16];
+                tmem_ld16(tmem + 256 + lanes + cb * 16, acc);
+                if (tid <= 2 * kF)
+                    for (int q = 0; q < 16; ++q) atomicAdd(dst + cb * 16 + q, __uint_as_float(acc[q]));
+            }
+        }
     }
-};
-// dz1 = acc * (h1 > 0), stored fp16 [r][i]
-struct StoreDz1 {
-    __half* dz1; const __half* h1;
-    __device__ void put(int m, int n, float v, int M, int N) const {
-        if (m >= M || n >= N) return;
-        const size_t o = (size_t)m * kH + n;
-        dz1[o] = __float2half_rn(__half2float(h1[o]) > 0.f ? v : 0.f);
-    }
-};
-struct AtomicAddC {
-    float* g; int ld;
-    __device__ void put(int m, int n, float v, int M, int N) const {
-        if (m >= M || n >= N) return;
-        atomicAdd(g + (size_t)m * ld + n, v);
-    }
-};
-
-// column sums of dz1 -> g_b1
-__global__ void colsum_kernel(const __half* x, int nrows, float* out) {
-    const int c = threadIdx.x;
-    float acc = 0.f;
-    for (int r = blockIdx.x; r < nrows; r += gridDim.x) acc += __half2float(x[(size_t)r * kH + c]);
-    atomicAdd(out + c, acc);
+    if (stalled && tid == 0) atomicExch(P.err, 1);
+    tc_before_sync();
+    __syncthreads();
+    tc_after_sync();
+    if (warp == 0) tmem_dealloc(tmem, 512);
 }
 
 // Adam (Kingma & Ba): per-row gradient sums are divided by the batch size
@@ -731,7 +767,6 @@ struct MlpState {
     __half* h1 = nullptr;
     float* h2 = nullptr;
     __half* dz2 = nullptr;
-    __half* dz1 = nullptr;
     float* s = nullptr;
     int32_t* brows = nullptr;
     float* by = nullptr;
@@ -826,12 +861,11 @@ int ensure_train(MlpState* m, size_t B) {
     if (B <= m->train_rows && m->h1) return 0;
     size_t cap = 0;
     int rc;
-    cudaFree(m->h1); cudaFree(m->h2); cudaFree(m->dz2); cudaFree(m->dz1); cudaFree(m->s);
+    cudaFree(m->h1); cudaFree(m->h2); cudaFree(m->dz2); cudaFree(m->s);
     cudaFree(m->brows); cudaFree(m->by); cudaFree(m->bw);
-    m->h1 = m->dz2 = m->dz1 = nullptr; m->h2 = m->s = m->by = m->bw = nullptr; m->brows = nullptr;
+    m->h1 = m->dz2 = nullptr; m->h2 = m->s = m->by = m->bw = nullptr; m->brows = nullptr;
     if ((rc = grow(m->h1, cap, B * kH))) return rc; cap = 0;
     if ((rc = grow(m->dz2, cap, B * kH))) return rc; cap = 0;
-    if ((rc = grow(m->dz1, cap, B * kH))) return rc; cap = 0;
     if ((rc = grow(m->h2, cap, B * kH))) return rc; cap = 0;
     if ((rc = grow(m->s, cap, B))) return rc; cap = 0;
     if ((rc = grow(m->brows, cap, 3 * B))) return rc; cap = 0;
@@ -855,35 +889,13 @@ int run_backward(const mcs_ctx* c, MlpState* m, int npairs, int B, const int32_t
     const int rpb = 64;
     bwd_head_kernel<<<(B + rpb - 1) / rpb, kH, 0, s>>>(hp, rpb);
     CKM(cudaGetLastError());
-    // dz1 = (dz2 W2^T) * relu'(z1):  M = B, N = 128 (in), K = 128 (out)
-    {
-        RowPairA A{m->dz2, kH};
-        NKPairB Bm{m->W2h, kH};
-        StoreDz1 C{m->dz1, m->h1};
-        dim3 grid((B + 15) / 16, kH / 64, 1);
-        gemm_kernel<<<grid, 32, 0, s>>>(B, kH, kH, kH, A, Bm, C);
-        CKM(cudaGetLastError());
-    }
-    // g_W2[in][out] = h1^T dz2:  M = 128, N = 128, K = B (split over K)
-    const int kchunk = 256;
-    {
-        TransA A{m->h1, kH};
-        KNPairB Bm{m->dz2, kH};
-        AtomicAddC C{m->grad + kOffW2, kH};
-        dim3 grid(kH / 16, kH / 64, (B + kchunk - 1) / kchunk);
-        gemm_kernel<<<grid, 32, 0, s>>>(kH, kH, B, kchunk, A, Bm, C);
-        CKM(cudaGetLastError());
-    }
-    // g_W1[in][out] = x^T dz1:  M = 48, N = 128, K = B
-    {
-        InputTA A{rows, m->feat16, npairs};
-        KNPairB Bm{m->dz1, kH};
-        AtomicAddC C{m->grad + kOffW1, kH};
-        dim3 grid(kIn / 16, kH / 64, (B + kchunk - 1) / kchunk);
-        gemm_kernel<<<grid, 32, 0, s>>>(kIn, kH, B, kchunk, A, Bm, C);
-        CKM(cudaGetLastError());
-    }
-    colsum_kernel<<<128, kH, 0, s>>>(m->dz1, B, m->grad + kOffB1);
+    // dz1, the W2 and W1 gradients and the b1 gradient: one tensor-core kernel per 128-row tile
+    BwdParams bp;
+    bp.fp.nrows = B; bp.fp.npairs = npairs; bp.fp.rows = rows; bp.fp.n = nullptr; bp.fp.feat16 = m->feat16;
+    bp.W2h = m->W2h; bp.h1 = m->h1; bp.dz2 = m->dz2;
+    bp.g_W1 = m->grad + kOffW1; bp.g_b1 = m->grad + kOffB1; bp.g_W2 = m->grad + kOffW2; bp.err = m->err;
+    CKM(cudaFuncSetAttribute(mlp_bwd_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, kBwdSmem));
+    if (B > 0) mlp_bwd_kernel<<<(B + kTile - 1) / kTile, kTile, kBwdSmem, s>>>(bp);
     CKM(cudaGetLastError());
     return 0;
 }
@@ -953,7 +965,7 @@ void mcs_order_free(mcs_ctx* c) {
     MlpState* m = c->mlp;
     if (!m) return;
     void* ps[] = {m->theta, m->adam_m, m->adam_v, m->grad, m->W1t, m->W2t, m->W2h, m->feat16,
-                  m->feat32, m->S, m->vscore, m->rank, m->h1, m->h2, m->dz2, m->dz1, m->s,
+                  m->feat32, m->S, m->vscore, m->rank, m->h1, m->h2, m->dz2, m->s,
                   m->brows, m->by, m->bw, m->loss};
     for (void* p : ps) cudaFree(p);
     delete m;
