@@ -15,7 +15,7 @@ the timed events.  `value` = pairs solved / summed step time.
 Other workloads: c3 (4,096 labelled pairs), c1 (one small pair), c4 (2,048
 bounded-valence pairs, learned order, 1 s per pair), c5 (serving on a Poisson
 stream), td (96 bounded-valence pairs with a 90 % planted core, solved with
-the top-down strategy of Section IV; the line adds the plain search, the
+the top-down strategy of Section IV-A; the line adds the plain search, the
 dead-end forecast and randomized restarts on the same batch).
 
 `--impl reference` times the CPU oracle (plain sequential McSplit) on the
@@ -74,7 +74,7 @@ def workload(name: str):
             pairs=2048)
     if name == "td":
         return [synth.planted_bvg_pair(i, 40, 64, cid=62) for i in range(4, 480, 5)], dict(
-            workload="top-down strategy (Section IV): 96 bounded-valence pairs with a planted common "
+            workload="top-down strategy (Section IV-A): 96 bounded-valence pairs with a planted common "
                      "core of 90% of n (3-regular or mesh core), n U{40..64}; MCS_TOP_DOWN", pairs=96)
     raise SystemExit(f"unknown workload {name}")
 

@@ -71,7 +71,7 @@ extern "C" {
                                     /* most 32 vertices (others: MCS_ERR_ARG for that  */
                                     /* pair).  mcs_solve and mcs_solve_batch set it    */
                                     /* themselves when all graphs fit                  */
-#define MCS_TOP_DOWN          0x40u /* top-down strategy (Section IV): goal-directed  */
+#define MCS_TOP_DOWN          0x40u /* top-down strategy (Section IV-A): goal-directed  */
                                     /* searches for min(n_G,n_H), one less, ... from  */
                                     /* the root until a goal is reached; the first    */
                                     /* goal reached is the optimum.  A time limit     */
@@ -94,7 +94,7 @@ extern "C" {
                                      /* the result stays exact.  Not with             */
                                      /* MCS_TOP_DOWN / MCS_DEAD_END (MCS_ERR_ARG) or  */
                                      /* MCS_ORDER_LEARNED (unsupported); batch calls. */
-#define MCS_DEAD_END          0x80u /* dead-end forecast (Section IV): after          */
+#define MCS_DEAD_END          0x80u /* dead-end forecast (Section IV-A): after          */
                                     /* mcs_set_dead_end's threshold of nodes without  */
                                     /* a new incumbent, the pair's incumbent size is  */
                                     /* raised by one (or doubled); an unreachable     */

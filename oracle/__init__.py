@@ -5,9 +5,9 @@ and by the CPU-baseline leg of ``bench.py``; never by the product package.
 It shares no code with the CUDA path.
 
 * ``mcs``        -- sequential recursive McSplit (Section II-B, Algorithm 1, Eq. 1)
-* ``mcs_goal``   -- one goal-directed McSplit search (Section IV, top-down strategy)
+* ``mcs_goal``   -- one goal-directed McSplit search (Section IV-A, top-down strategy)
 * ``mcs_topdown``-- the top-down strategy: goal sizes min(|V_G|,|V_H|), one less, ...
-* ``mcs_deadend``-- dead-end forecasting with a bound increase and a binary search (Section IV)
+* ``mcs_deadend``-- dead-end forecasting with a bound increase and a binary search (Section IV-A)
 * ``mcs_restart``-- randomized restarts over an explicit stack of pending branches (Section IV-A)
 * ``hr_order`` / ``mcs_hr`` -- the static component + Hellerman-Rarick-style order (Section IV-A)
 * ``bruteforce`` -- exhaustive injective partial mappings (definition, Section II-A)
@@ -117,7 +117,7 @@ def mcs(adjG, adjH, labG=None, labH=None, directed: bool = False,
 
 def mcs_goal(adjG, adjH, floor: int, cap: int, labG=None, labH=None, directed: bool = False,
              node_limit: int = 0, time_limit_s: float = 0.0) -> OracleResult:
-    """One goal-directed search (Section IV): only mappings larger than
+    """One goal-directed search (Section IV-A): only mappings larger than
     `floor` are recorded and the search stops once one of size `cap` is
     found.  size == 0 means no mapping beat the floor; `complete` is False
     only when a limit stopped the search."""
@@ -137,7 +137,7 @@ def mcs_goal(adjG, adjH, floor: int, cap: int, labG=None, labH=None, directed: b
 
 def mcs_topdown(adjG, adjH, labG=None, labH=None, directed: bool = False,
                 node_limit: int = 0, time_limit_s: float = 0.0) -> OracleResult:
-    """The top-down strategy (Section IV): goal-directed searches for the goal
+    """The top-down strategy (Section IV-A): goal-directed searches for the goal
     sizes min(|V_G|,|V_H|), one less, ... until one is reached; `nodes` sums
     all of them."""
     lib = _load()
@@ -156,7 +156,7 @@ def mcs_topdown(adjG, adjH, labG=None, labH=None, directed: bool = False,
 
 def mcs_deadend(adjG, adjH, threshold: int, doubling: bool = False, labG=None, labH=None,
                 directed: bool = False, node_limit: int = 0, time_limit_s: float = 0.0) -> OracleResult:
-    """Dead-end forecasting (Section IV): the plain search raises its
+    """Dead-end forecasting (Section IV-A): the plain search raises its
     incumbent size by one (or doubles it) after `threshold` nodes without a
     new incumbent; an unreachable raised value becomes an upper bound that a
     binary search of goal-directed searches closes."""

@@ -16,10 +16,10 @@
 //   oracle_branch_log  oracle_mcs instrumented to record, per branching
 //                      decision, which candidate pairs (v,u) lay on an optimal
 //                      extension (training signal for the ordering network)
-//   oracle_mcs_goal    one goal-directed search (Section IV, top-down
+//   oracle_mcs_goal    one goal-directed search (Section IV-A, top-down
 //                      strategy): the incumbent starts at a floor with no
 //                      mapping, and the search stops once it reaches a cap
-//   oracle_mcs_topdown the top-down strategy of Section IV: one goal-directed
+//   oracle_mcs_topdown the top-down strategy of Section IV-A: one goal-directed
 //                      search per goal size min(|V_G|,|V_H|), one less, ...,
 //                      until a goal is reached
 //   oracle_hr_order    the static vertex order of the portfolio section
@@ -33,7 +33,7 @@
 //                      put in a random order and the search goes on from the
 //                      first of them
 //   oracle_mcs_deadend dead-end forecasting with a bound increase and a binary
-//                      search (Section IV): the plain search raises its
+//                      search (Section IV-A): the plain search raises its
 //                      incumbent size by 1 (or doubles it) after a number of
 //                      nodes without improvement; an unreachable raised value
 //                      is an upper bound, closed by goal-directed searches
@@ -224,14 +224,14 @@ struct McSplit {
     std::vector<std::pair<int, int>> M, best;
     std::vector<BranchRecord>* log = nullptr;
     int log_max_depth = 0;
-    // Goal-directed search (Section IV): the incumbent size starts at `floor`
+    // Goal-directed search (Section IV-A): the incumbent size starts at `floor`
     // without a mapping (a solution must beat it to be recorded), and the
     // search stops as soon as the incumbent reaches `cap` (a solution of the
     // goal size was found).  The plain search has floor 0 and no cap.
     int floor = 0;
     int cap = 1 << 30;
     bool reached = false;
-    // Dead-end forecast (Section IV): after `dead_threshold` nodes without a
+    // Dead-end forecast (Section IV-A): after `dead_threshold` nodes without a
     // new incumbent the incumbent size is raised -- by one, or doubled -- as
     // if a mapping of that size were known (0: off).
     int64_t dead_threshold = 0;
@@ -293,9 +293,9 @@ struct McSplit {
         if ((int)M.size() > incumbent()) {                    // incumbent (Algorithm 1)
             best = M;
             since = 0;
-            if ((int)best.size() >= cap) { reached = true; return; }   // goal reached (Section IV)
+            if ((int)best.size() >= cap) { reached = true; return; }   // goal reached (Section IV-A)
         }
-        if (dead_threshold > 0 && since >= dead_threshold) {  // dead end forecast (Section IV)
+        if (dead_threshold > 0 && since >= dead_threshold) {  // dead end forecast (Section IV-A)
             const int inc = incumbent();
             floor = dead_double ? std::max(inc + 1, 2 * inc) : inc + 1;
             since = 0;
@@ -513,7 +513,7 @@ int oracle_mcs(int nG, const uint8_t* adjG, const int32_t* labG,
     return k;
 }
 
-// One goal-directed McSplit search (Section IV, top-down strategy): the
+// One goal-directed McSplit search (Section IV-A, top-down strategy): the
 // incumbent size starts at `floor` with no mapping, so only a mapping larger
 // than `floor` is recorded, and the search stops once the incumbent reaches
 // `cap`.  Returns the size of the best mapping recorded (0 when none beat the
@@ -540,7 +540,7 @@ int oracle_mcs_goal(int nG, const uint8_t* adjG, const int32_t* labG,
     return k;
 }
 
-// The top-down strategy (Section IV): goal-directed searches for the goal
+// The top-down strategy (Section IV-A): goal-directed searches for the goal
 // sizes k = min(|V_G|, |V_H|), k - 1, ..., 1, each with floor k - 1 and cap k,
 // from the root; the first goal reached is the maximum (every larger goal was
 // proven unreachable).  With an empty graph it is the plain search.  Returns
@@ -587,7 +587,7 @@ int oracle_mcs_topdown(int nG, const uint8_t* adjG, const int32_t* labG,
     return k;
 }
 
-// Dead-end forecasting with a bound increase (Section IV).  The plain search
+// Dead-end forecasting with a bound increase (Section IV-A).  The plain search
 // runs with the forecast on (raise by one, or double when `doubling`, after
 // `threshold` nodes without a new incumbent).  When it ends, a recorded
 // mapping larger than the last raised value is optimal.  Otherwise the raised

@@ -132,7 +132,7 @@ int run_device(mcs_ctx* c, int npairs, const int32_t* d_n, const int64_t* d_adj_
                int32_t* d_status, uint64_t* d_nodes, int16_t* d_map, float* d_usec,
                cudaStream_t s, bool timed) {
     if (npairs < 0) return MCS_ERR_ARG;
-    // the two goal-directed strategies of Section IV are alternatives
+    // the two goal-directed strategies of Section IV-A are alternatives
     if ((flags & MCS_TOP_DOWN) && (flags & MCS_DEAD_END)) return MCS_ERR_ARG;
     if ((flags & MCS_RESTART) && (flags & (MCS_TOP_DOWN | MCS_DEAD_END))) return MCS_ERR_ARG;
     // one vertex order per call

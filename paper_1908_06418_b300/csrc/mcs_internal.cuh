@@ -40,7 +40,7 @@ struct PairState {
     u64 t_start, deadline; // globaltimer ns
     u64 ticket;            // serve mode: the request's ticket
     u64 timeout_ns;        // serve mode: the request's limit (from its root's start)
-    // Goal-directed search (top-down strategy, Section IV): only mappings
+    // Goal-directed search (top-down strategy, Section IV-A): only mappings
     // larger than `floor` are recorded, and the pair stops once the incumbent
     // reaches `cap`.  Plain search: floor 0, cap kNoCap.
     int32_t floor, cap;

@@ -1,4 +1,4 @@
-"""The top-down strategy (Section IV) on the GPU against the oracle: the
+"""The top-down strategy (Section IV-A) on the GPU against the oracle: the
 optimum must equal the plain search's, a lone searcher must walk the oracle's
 goal searches node for node, and time limits must report verified mappings."""
 import numpy as np
@@ -118,7 +118,7 @@ def test_topdown_is_rejected_by_the_server(solver):
 
 
 # --------------------------------------------------------------------------
-# dead-end forecasting with a bound increase and a binary search (Section IV)
+# dead-end forecasting with a bound increase and a binary search (Section IV-A)
 # --------------------------------------------------------------------------
 def _golden(name):
     import json

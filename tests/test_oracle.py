@@ -229,7 +229,7 @@ def test_config1_golden_matches_generator():
 
 
 # --------------------------------------------------------------------------
-# goal-directed search and the top-down strategy (Section IV)
+# goal-directed search and the top-down strategy (Section IV-A)
 # --------------------------------------------------------------------------
 @pytest.mark.parametrize("directed,k", [(False, 0), (True, 0), (False, 3), (True, 2)])
 def test_topdown_vs_bruteforce(directed, k):
