@@ -76,14 +76,15 @@ extern "C" {
                                     /* the root until a goal is reached; the first    */
                                     /* goal reached is the optimum.  A time limit     */
                                     /* before that reports size 0 (MCS_TIMEOUT).      */
-                                    /* Batch calls only (mcs_submit: unsupported);   */
-                                    /* not with MCS_ORDER_LEARNED (unsupported).      */
+                                    /* mcs_solve and the batch calls; mcs_submit and  */
+                                    /* MCS_ORDER_LEARNED: MCS_ERR_UNSUPPORTED.        */
 #define MCS_ORDER_HR          0x100u /* static vertex order of Section IV-A instead of */
                                      /* the degree order: weakly connected components */
                                      /* (decreasing rows/columns ratio, then size),   */
                                      /* inside each a Hellerman-Rarick-style column   */
                                      /* order.  Exact either way.  Not with           */
-                                     /* MCS_ORDER_LEARNED (MCS_ERR_ARG); batch calls. */
+                                     /* MCS_ORDER_LEARNED (MCS_ERR_ARG) or mcs_submit */
+                                     /* (MCS_ERR_UNSUPPORTED).                        */
 #define MCS_RESTART           0x200u /* randomized restarts (Section IV-A): once a    */
                                      /* pair's node count has doubled since its last  */
                                      /* new incumbent (and passed mcs_set_restart's   */
@@ -92,8 +93,9 @@ extern "C" {
                                      /* random order and starts afresh; the pending   */
                                      /* branches keep the record of what is left, so  */
                                      /* the result stays exact.  Not with             */
-                                     /* MCS_TOP_DOWN / MCS_DEAD_END (MCS_ERR_ARG) or  */
-                                     /* MCS_ORDER_LEARNED (unsupported); batch calls. */
+                                     /* MCS_TOP_DOWN / MCS_DEAD_END (MCS_ERR_ARG);    */
+                                     /* with MCS_ORDER_LEARNED or in mcs_submit:      */
+                                     /* MCS_ERR_UNSUPPORTED.                          */
 #define MCS_DEAD_END          0x80u /* dead-end forecast (Section IV-A): after          */
                                     /* mcs_set_dead_end's threshold of nodes without  */
                                     /* a new incumbent, the pair's incumbent size is  */
@@ -101,8 +103,8 @@ extern "C" {
                                     /* raised value bounds the optimum, and a binary  */
                                     /* search of goal-directed searches from the root */
                                     /* closes the gap.  Exact.  Not with MCS_TOP_DOWN */
-                                    /* (MCS_ERR_ARG); batch calls only; not with      */
-                                    /* MCS_ORDER_LEARNED (MCS_ERR_UNSUPPORTED).       */
+                                    /* (MCS_ERR_ARG); with MCS_ORDER_LEARNED or in    */
+                                    /* mcs_submit: MCS_ERR_UNSUPPORTED.               */
 
 typedef struct mcs_ctx mcs_ctx;
 
