@@ -6,12 +6,25 @@ size comes from the CPU oracle; nothing here touches the CUDA path.
     python tests/golden/make_oracle_golden.py c2 --budget 1800 --workers 5
     python tests/golden/make_oracle_golden.py c3 --budget 10 --workers 6
     python tests/golden/make_oracle_golden.py c4 --budget 10 --count 256
-    python tests/golden/make_oracle_golden.py c5 --budget 1 --count 2000
+    python tests/golden/make_oracle_golden.py c5 --budget 60 --count 800
+    python tests/golden/make_oracle_golden.py c4p --budget 300 --workers 3
+    python tests/golden/make_oracle_golden.py planted --budget 300 --workers 2
 
 Output: ``tests/golden/<cfg>_oracle.jsonl``, one JSON object per pair with the
 pair index, a digest of both adjacency matrices (to detect generator drift),
 the size, whether the search completed within the budget (size proven
 optimal), the node count, seconds and the mapping in original vertex ids.
+
+``c4p`` is the planted-core form of the bounded-valence workload: 96 pairs of
+40 to 64 vertices whose graphs share a common induced core of 90 % of n (the
+way the ARG ``mcsXX`` pairs are built).  Unrelated bounded-valence pairs of
+that size are beyond the oracle's reach, so these give the workload an exact
+check.  They are solved with the oracle's top-down strategy (Section IV-A),
+which is exact and finishes fastest when the optimum is near min(n_G, n_H).
+
+``planted`` is the held-out planted-core family the ordering network is
+measured on: 160 bounded-valence pairs of 24 to 34 vertices with cores of 10
+to 90 % of n, solved with the plain oracle.
 """
 from __future__ import annotations
 
@@ -51,10 +64,21 @@ def load_pairs(cfg: str, count: int):
         return synth.config3_pairs(count=count or 4096)
     if cfg == "c4":
         return synth.config4_pairs(count=count or 2048)
+    if cfg == "c4p":
+        return c4p_pairs()
+    if cfg == "planted":
+        import synth
+        return [synth.planted_bvg_pair(i, 24, 34, cid=47) for i in range(count or 160)]
     if cfg == "c5":
         return [r.pair for r in itertools.islice(synth.config5_requests(count=count or 2000),
                                                   count or 2000)]
     raise ValueError(cfg)
+
+
+def c4p_pairs():
+    """Planted-core bounded-valence pairs, 40 to 64 vertices, core 90 % of n."""
+    import synth
+    return [synth.planted_bvg_pair(i, 40, 64, cid=62) for i in range(4, 480, 5)]
 
 
 def _work(args):
@@ -62,8 +86,8 @@ def _work(args):
     import oracle
     p = load_pairs(cfg, count)[idx] if cfg in ("c1", "c2") else _cached(cfg, count)[idx]
     t = time.time()
-    r = oracle.mcs(p.G.adj, p.H.adj, p.G.labels, p.H.labels, directed=p.directed,
-                   time_limit_s=budget)
+    run = oracle.mcs_topdown if cfg == "c4p" else oracle.mcs
+    r = run(p.G.adj, p.H.adj, p.G.labels, p.H.labels, directed=p.directed, time_limit_s=budget)
     dt = time.time() - t
     return dict(idx=idx, tag=p.tag, nG=p.G.n, nH=p.H.n, directed=p.directed,
                 digest=pair_digest(p), size=r.size, complete=bool(r.complete),
