@@ -37,13 +37,17 @@ import numpy as np
 
 ROOT = os.path.dirname(os.path.abspath(__file__))
 sys.path.insert(0, ROOT)
+MCS_MAX_N = 256          # include/mcs.h: stride of the device mapping outputs
 
 METRIC = "MCS pairs solved/sec (exact) on 1 B300"
 
 # DRAM bytes (dram__bytes_read.sum + dram__bytes_write.sum) of one launch of
 # the dominant search kernel, from a single-pass ncu capture of this
-# workload's launch (profiles/dram_search_kernel_c2.md); reported only while
-# the kernel source is the one the capture was taken with.
+# workload's launch:
+#   ncu --metrics dram__bytes_read.sum,dram__bytes_write.sum --clock-control none
+#       -k regex:search_kernel -s <warm-up launches> -c 1
+#       python bench.py --workload <w> --steps 1 --warmup 1 --no-cpu-baseline --no-single
+# Reported only while the kernel source is the one the capture was taken with.
 TRAFFIC = {"c2": {"kernel_sha1": "de3f4df5bb2549c2", "bytes": 1.19e9 + 5.28e9},
            "c3": {"kernel_sha1": "de3f4df5bb2549c2", "bytes": 99.89e6 + 197.09e6}}
 UNIT = "pairs/s"
@@ -164,25 +168,42 @@ def _oracle_one(args):
     return idx, r.size, r.complete, r.nodes, time.time() - t
 
 
-def oracle_sample(name: str, n_pairs: int, budget: float, offset: int = 0):
-    """Runs the oracle over a bounded sample (every k-th pair) on all host cores."""
-    pairs, _ = workload(name)
+def host_cpu():
+    """(usable host cores, CPU model) of this machine."""
     cores = len(os.sched_getaffinity(0))
+    model = "unknown"
+    try:
+        for line in open("/proc/cpuinfo"):
+            if line.startswith("model name"):
+                model = line.split(":", 1)[1].strip()
+                break
+    except OSError:
+        pass
+    return cores, model
+
+
+def oracle_sample(name: str, n_pairs: int, budget: float, offset: int = 0):
+    """Runs the oracle over a bounded sample (every k-th pair) with one worker
+    process per usable host core; the sample has at least one pair per core
+    (up to the workload's size), so every core works."""
+    pairs, _ = workload(name)
+    cores, model = host_cpu()
+    n_pairs = min(len(pairs), max(n_pairs, cores))
     step = max(1, len(pairs) // n_pairs)
-    idx = [(offset + i * step) % len(pairs) for i in range(min(n_pairs, len(pairs)))]
+    idx = [(offset + i * step) % len(pairs) for i in range(n_pairs)]
     gold = golden_sizes(name)
     ctx = mp.get_context("spawn")
     t = time.time()
-    with ctx.Pool(min(cores, len(idx))) as pool:
-        res = pool.map(_oracle_one, [(name, i, budget) for i in idx])
+    with ctx.Pool(cores) as pool:
+        res = pool.map(_oracle_one, [(name, i, budget) for i in idx], chunksize=1)
     wall = time.time() - t
     solved = sum(1 for (i, k, c, n, s) in res if c and (i not in gold or gold[i][0] == k or not gold[i][1]))
     nodes = sum(n for (_, _, _, n, _) in res)
     lat = sorted(s for (_, _, c, _, s) in res if c)
-    return dict(solved=solved, tried=len(idx), wall=wall, nodes=nodes, cores=min(cores, len(idx)),
+    return dict(solved=solved, tried=len(idx), wall=wall, nodes=nodes, cores=cores, cpu_model=model,
                 p99=(float(np.percentile(lat, 99)) if lat else None),
                 sample=f"{len(idx)} of {len(pairs)} pairs (every {step}th), {budget:g} s budget per pair, "
-                       f"{min(cores, len(idx))} worker processes")
+                       f"one worker process per host core ({cores} cores, {model})")
 
 
 def combine_ranks(total_ms, solved, nodes, dist=None, device="cpu"):
@@ -281,7 +302,7 @@ def run_reference(a):
             "nodes_per_s": tot_nodes / tot_wall if tot_wall else 0.0,
             "config": dict(cfg, sample=last["sample"]),
             "cpu_baseline": {"value": val, "unit": UNIT, "cores": last["cores"], "kind": "oracle",
-                             "sample": last["sample"]},
+                             "cpu_model": last["cpu_model"], "sample": last["sample"]},
             "e2e": {"value": val, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
     print(json.dumps(line), flush=True)
 
@@ -289,7 +310,7 @@ def run_reference(a):
 # ---------------------------------------------------------------------------
 # our arm
 # ---------------------------------------------------------------------------
-def main():
+def parse_args(argv=None):
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
     ap.add_argument("--steps", type=int, default=5)
@@ -305,23 +326,35 @@ def main():
     ap.add_argument("--no-tune", action="store_true", help="ignore the autotuner cache")
     ap.add_argument("--no-single", action="store_true",
                     help="skip the single-instance (one pair per call) comparison")
+    ap.add_argument("--no-batched", action="store_true",
+                    help="default run: skip the batched (c3) key")
+    ap.add_argument("--no-served", action="store_true",
+                    help="default run: skip the served (c5) key")
+    ap.add_argument("--no-race", action="store_true",
+                    help="default run: skip the GPU + CPU race sample (race key)")
     ap.add_argument("--requests", type=int, default=100000, help="c5: requests in the stream")
     ap.add_argument("--rate-frac", type=float, default=0.5, help="c5: arrival rate / saturated rate")
     ap.add_argument("--rate", type=float, default=0.0, help="c5: absolute arrival rate (requests/s), "
                                                              "instead of --rate-frac")
-    ap.add_argument("--single-sample", type=int, default=2000, help="c5: single-instance baseline sample")
+    ap.add_argument("--single-sample", type=int, default=300, help="c5: single-instance baseline sample")
     ap.add_argument("--serve-lanes", type=int, default=0,
                     help="c5: lanes per searcher of the server (8, 16 or 32; default: the library's, 32)")
-    a = ap.parse_args()
+    a = ap.parse_args(argv)
     if a.timeout is None:
         a.timeout = 1.0 if a.workload == "c4" else 600.0
+    return a
+
+
+def main():
+    a = parse_args()
     if a.impl == "reference":
         run_reference(a)
         return
     if a.workload == "c5":
-        run_serving(a)
+        print(json.dumps(run_serving(a)), flush=True)
         return
 
+    import copy
     import torch
     rank = int(os.environ.get("RANK", "0"))
     world = int(os.environ.get("WORLD_SIZE", "1"))
@@ -331,16 +364,47 @@ def main():
     if world > 1:
         import torch.distributed as dist
         dist.init_process_group("nccl")
-    from paper_1908_06418_b300 import (Solver, pack_host, MCS_DIRECTED, MCS_OK, MCS_WORD32, MCS_ORDER_LEARNED,
+    from paper_1908_06418_b300 import Solver
+    solver = Solver(local)
+    line = measure(a, a.workload, solver, local, rank, world, dist)
+    # the default run (one GPU) also measures the batched form (the 4,096
+    # labelled pairs) and the served form (the Poisson stream of requests);
+    # under several ranks only the replicated headline workload runs
+    if world == 1 and a.workload == "c2" and not a.no_batched:
+        b = copy.copy(a)
+        b.workload = "c3"
+        sub = measure(b, "c3", solver, local, rank, world, None)
+        line["batched"] = {k: sub[k] for k in ("metric", "value", "unit", "ms_per_step", "steps", "warmup",
+                                                "nodes_per_s", "p50_latency_ms", "p99_latency_ms",
+                                                "solved_per_step", "config", "gpu_launches", "e2e",
+                                                "roofline", "clocks", "single_instance", "cpu_baseline")
+                           if k in sub}
+    if world == 1 and a.workload == "c2" and not a.no_race:
+        line["race"] = race_sample(solver, a)
+    solver.close()
+    if world == 1 and a.workload == "c2" and not a.no_served:
+        line["served"] = run_serving(a)
+    if rank == 0:
+        print(json.dumps(line), flush=True)
+    if dist:
+        dist.destroy_process_group()
+
+
+def measure(a, name, solver, local, rank, world, dist):
+    """One workload on the device: K timed steps after W warm-up steps (each
+    step solves every pair of the workload), then the same workload end to end
+    through the host C ABI, the roofline of the dominant kernel, and the
+    comparisons.  Returns the bench line (dict)."""
+    import torch
+    from paper_1908_06418_b300 import (pack_host, MCS_DIRECTED, MCS_OK, MCS_WORD32, MCS_ORDER_LEARNED,
                                        MCS_TOP_DOWN, MCS_DEAD_END, MCS_ORDER_HR, MCS_RESTART)
 
-    pairs, cfg = workload(a.workload)
-    gold = golden_sizes(a.workload)
+    pairs, cfg = workload(name)
+    gold = golden_sizes(name)
     dev = torch.device("cuda", local)
-    solver = Solver(local)
-    learned = a.workload == "c4" and a.order == "degree"
+    learned = name == "c4" and a.order == "degree"
     hr = a.order == "hr"
-    topdown = a.workload == "td"
+    topdown = name == "td"
     if learned:       # the candidate order of the trained network (exactness unchanged)
         solver.set_order_model(np.load(os.path.join(ROOT, "paper_1908_06418_b300", "data",
                                                     "order_mlp_bvg.npy")).astype(np.float32))
@@ -369,7 +433,7 @@ def main():
                  status=torch.zeros(len(idx), dtype=torch.int32, device=dev),
                  nodes=torch.zeros(len(idx), dtype=torch.int64, device=dev),
                  usec=torch.zeros(len(idx), dtype=torch.float32, device=dev),
-                 map=torch.zeros(len(idx) * 64, dtype=torch.int16, device=dev))
+                 map=torch.zeros(len(idx) * MCS_MAX_N, dtype=torch.int16, device=dev))
         groups.append(g)
     # launch shapes recorded by the autotuner for each group's bucket
     shapes = []
@@ -504,7 +568,7 @@ def main():
     import hashlib
     ksha = hashlib.sha1(open(os.path.join(ROOT, "paper_1908_06418_b300", "csrc", "mcs_kernels.cu"),
                              "rb").read()).hexdigest()[:16]
-    tr = TRAFFIC.get(a.workload)
+    tr = TRAFFIC.get(name)
     traffic = tr["bytes"] if tr and tr["kernel_sha1"] == ksha else None
     roof = {"bound": "alu", "achieved": achieved, "peak": popc_peak, "unit": "Gpopc/s",
             "frac": achieved / popc_peak, "traffic": traffic,
@@ -574,16 +638,48 @@ def main():
         line["single_instance"] = single_instance_vs_batch(
             solver, pairs, a, batch_flags=(MCS_ORDER_LEARNED if learned else 0) | (MCS_TOP_DOWN if topdown else 0))
     if rank == 0 and not a.no_cpu_baseline:
-        cb = oracle_sample(a.workload, 8 if a.workload.startswith("c2") else 64,
-                           a.timeout if a.workload == "c4" else (25.0 if a.workload.startswith("c2") else 2.0))
+        cb = oracle_sample(name, 8 if name.startswith("c2") else 64,
+                           a.timeout if name == "c4" else (25.0 if name.startswith("c2") else 2.0))
         line["cpu_baseline"] = {"value": cb["solved"] / cb["wall"], "unit": UNIT, "cores": cb["cores"],
-                                "kind": "oracle", "sample": cb["sample"],
+                                "cpu_model": cb["cpu_model"], "kind": "oracle", "sample": cb["sample"],
                                 "nodes_per_s": cb["nodes"] / cb["wall"]}
-    if rank == 0:
-        print(json.dumps(line), flush=True)
-    solver.close()
-    if dist:
-        dist.destroy_process_group()
+    return line
+
+
+def race_sample(solver, a, n_req=200):
+    """The GPU + CPU race (MCS_RACE) on single pairs: the C1 pair and the
+    first n_req requests of the serving stream (n 16..56), each solved by
+    mcs_solve with and without the race, in the single-pair launch shape.
+    Reports how often each side finished its proof first and the summed
+    solve times; sizes must agree where both are proven."""
+    import itertools
+    import synth
+    from paper_1908_06418_b300 import MCS_OK, MCS_RACE
+    pairs = [synth.config1_pair()] + [r.pair for r in itertools.islice(synth.config5_requests(count=n_req), n_req)]
+    solver.set_launch(4, -1, 256, search_group=32)
+    solver.set_steal(-1, -1)
+    wins = {0: 0, 1: 0, 2: 0}
+    t_plain = t_race = 0.0
+    lat_plain, lat_race = [], []
+    for p in pairs:
+        t0 = time.perf_counter()
+        r0 = solver.solve(p.G.adj, p.H.adj, p.G.labels, p.H.labels, timeout_s=1.0)
+        t1 = time.perf_counter()
+        r1 = solver.solve(p.G.adj, p.H.adj, p.G.labels, p.H.labels, flags=MCS_RACE, timeout_s=1.0)
+        t2 = time.perf_counter()
+        wins[int(solver.last_stats()["race_winner"])] += 1
+        t_plain += t1 - t0
+        t_race += t2 - t1
+        lat_plain.append((t1 - t0) * 1e3)
+        lat_race.append((t2 - t1) * 1e3)
+        if r0.status == MCS_OK and r1.status == MCS_OK and r0.size != r1.size:
+            raise SystemExit(f"PARITY FAILURE race vs plain: {r1.size} vs {r0.size}")
+    solver.reset_launch()
+    return {"pairs": len(pairs), "cpu_first": wins[1], "gpu_first": wins[2], "neither_within_1s": wins[0],
+            "plain_s": t_plain, "race_s": t_race,
+            "plain_p50_ms": float(np.percentile(lat_plain, 50)), "race_p50_ms": float(np.percentile(lat_race, 50)),
+            "plain_p99_ms": float(np.percentile(lat_plain, 99)), "race_p99_ms": float(np.percentile(lat_race, 99)),
+            "how": "mcs_solve per pair (C1 pair + first serving requests), 1 s limit, with and without MCS_RACE"}
 
 
 def mlp_roofline(solver, groups, pairs, stream, reps=20):
@@ -637,6 +733,12 @@ def _tensor_peak():
 # serving (continuous batching) on a Poisson stream
 # ---------------------------------------------------------------------------
 def run_serving(a):
+    """The served form: a Poisson stream of config-5 requests (n log-uniform
+    16..56, 0-8 label classes, 1 s limit each) through mcs_submit/mcs_poll,
+    at a fraction of the batch solver's saturated rate (or --rate); latency =
+    arrival -> result on the host.  Beside it, the plain single-instance form
+    (one mcs_solve per request, FIFO at the same arrival times) on a sample.
+    Returns the line (dict)."""
     import itertools
     import torch
     import synth
@@ -654,6 +756,11 @@ def run_serving(a):
     if a.serve_lanes:
         solver.set_serve_group(a.serve_lanes)    # before the first submit creates the server
     reqs = list(synth.config5_requests(count=n_req, rate_per_s=rate))
+    # bytes each request moves: its two matrices (and labels) in, its result out
+    h2d = sum(q.pair.G.n ** 2 + q.pair.H.n ** 2 + 4 * ((q.pair.G.labels is not None) * q.pair.G.n +
+                                                         (q.pair.H.labels is not None) * q.pair.H.n)
+              for q in reqs)
+    gold = golden_sizes("c5")             # stored oracle optima of the stream's first requests
     lat, status = [], []
     out = {}
     i = 0
@@ -674,6 +781,8 @@ def run_serving(a):
                     lat.append(time.perf_counter() - t0 - reqs[j].arrival_s)
                     status.append(r.status)
                     done.append(tk)
+                    if r.status == MCS_OK and j in gold and gold[j][1] and r.size != gold[j][0]:
+                        raise SystemExit(f"PARITY FAILURE request {j}: served {r.size} oracle {gold[j][0]}")
             for tk in done:
                 del out[tk]
             if not done and i < n_req:
@@ -709,10 +818,13 @@ def run_serving(a):
             "single_instance": {"pairs_per_s": m / sum(serv), "p50_latency_ms": float(np.percentile(lat1, 50)),
                                 "p99_latency_ms": float(np.percentile(lat1, 99)), "sample": m,
                                 "how": "mcs_solve per request in arrival order; FIFO queue at the same arrival times"},
-            "e2e": {"value": solved / wall, "unit": "pairs/s", "h2d_bytes_per_step": None, "d2h_bytes_per_step": None},
+            "e2e": {"value": solved / wall, "unit": "pairs/s", "h2d_bytes_per_step": int(h2d),
+                    "d2h_bytes_per_step": int(len(status) * (24 + 2 * 64)),
+                    "note": "one step = the whole stream; requests are read by the device from mapped "
+                            "pinned host memory and results written back there"},
             "clocks": clk.summary()}
-    print(json.dumps(line), flush=True)
     solver.close()
+    return line
 
 
 if __name__ == "__main__":

@@ -12,7 +12,13 @@
  * MCS_OK is the proven optimum.
  *
  * Graph encoding (all entry points):
- *   n       number of vertices, 0 <= n <= MCS_MAX_N
+ *   n       number of vertices, 0 <= n <= MCS_MAX_N (256: the paper's solvers
+ *           stop at 254, Section III-B).  Graphs of up to 64 vertices run on
+ *           one-word bit sets; larger ones on two or four words per vertex
+ *           set (mcs_solve and mcs_solve_batch choose per pair; the device
+ *           entry point takes them with MCS_WIDE).  Serving, the ordering
+ *           network, the strategies of Section IV-A and the allocation-free
+ *           call take graphs of up to 64 vertices.
  *   adj     n*n bytes, row major, adj[i*n + j] == 1 iff arc i -> j, else 0.
  *           Without MCS_DIRECTED the matrix must be symmetric.  Diagonal
  *           entries are self-loops; they are allowed and must be matched.
@@ -40,7 +46,7 @@
 extern "C" {
 #endif
 
-#define MCS_MAX_N 64
+#define MCS_MAX_N 256
 
 /* status / return codes */
 #define MCS_OK                 0   /* optimum found and proven                        */
@@ -96,6 +102,26 @@ extern "C" {
                                      /* MCS_TOP_DOWN / MCS_DEAD_END (MCS_ERR_ARG);    */
                                      /* with MCS_ORDER_LEARNED or in mcs_submit:      */
                                      /* MCS_ERR_UNSUPPORTED.                          */
+#define MCS_WIDE              0x400u /* mcs_solve_batch_device: graphs of up to       */
+                                     /* MCS_MAX_N vertices (four 64-bit words per     */
+                                     /* vertex set); without it a graph of more than  */
+                                     /* 64 vertices is MCS_ERR_ARG for its pair.      */
+                                     /* Degree order only: with MCS_ORDER_LEARNED,     */
+                                     /* MCS_ORDER_HR, MCS_TOP_DOWN, MCS_DEAD_END,      */
+                                     /* MCS_RESTART or MCS_GRAPH_REPLAY the call is    */
+                                     /* MCS_ERR_UNSUPPORTED (mcs_solve_batch reports   */
+                                     /* it per pair for pairs over 64 vertices)        */
+#define MCS_RACE              0x800u /* mcs_solve only: race the GPU search against a  */
+                                     /* sequential CPU McSplit of the same pair on a   */
+                                     /* host thread (the portfolio of Section IV with  */
+                                     /* two contenders).  Each side publishes its best */
+                                     /* size in host-mapped memory and prunes against  */
+                                     /* the larger of the two; the first to finish its */
+                                     /* proof stops the other, and the larger mapping  */
+                                     /* is returned (exact).  Graphs of at most 64     */
+                                     /* vertices, degree order; mcs_last_stats out[15] */
+                                     /* tells which side finished first.  Other entry  */
+                                     /* points, and other strategies: UNSUPPORTED.     */
 #define MCS_DEAD_END          0x80u /* dead-end forecast (Section IV-A): after          */
                                     /* mcs_set_dead_end's threshold of nodes without  */
                                     /* a new incumbent, the pair's incumbent size is  */
@@ -125,24 +151,33 @@ typedef struct {
     double seconds;          /* device time from the pair's start to its proof    */
 } mcs_result;
 
-/* Creates a context on CUDA device `device`.  flags: reserved, pass 0.
- * Returns NULL on failure (no device, allocation failure). */
+/* Creates a context on CUDA device `device`: the state behind every solve
+ * below (the paper's solver runs one search per process, Section III; a
+ * context holds one CUDA stream and the device arenas of its searches).
+ * flags: reserved, pass 0.  Returns NULL on failure (no device, allocation
+ * failure). */
 mcs_ctx* mcs_create(int device, uint32_t flags);
 void mcs_destroy(mcs_ctx* ctx);
 
-/* Solves one pair.  timeout_s <= 0 means no limit (an internal cap of one
- * hour still bounds every device wait).  Returns out->status. */
+/* Solves one pair: a maximum common induced subgraph of G and H as defined
+ * in Section II-A, found and proven by the branch and bound of Algorithm 1
+ * (Section II-B) with the bound of Eq. 1.  out->size is its size and
+ * out->g_idx / h_idx its vertex pairs (original numbering).  timeout_s <= 0
+ * means no limit (an internal cap of one hour still bounds every device
+ * wait).  Returns out->status. */
 int mcs_solve(mcs_ctx* ctx, const mcs_graph* G, const mcs_graph* H,
               uint32_t flags, double timeout_s, mcs_result* out);
 
-/* Solves npairs pairs (G[i], H[i]) in one persistent launch.  timeout_s is
- * per pair, counted from the moment the pair's search starts.  Returns the
- * worst (lowest negative, else highest) per-pair status. */
+/* Solves npairs pairs (G[i], H[i]) -- each the problem of Section II-A by
+ * Algorithm 1 and Eq. 1, as mcs_solve -- in one persistent launch.
+ * timeout_s is per pair, counted from the moment the pair's search starts.
+ * Returns the worst (lowest negative, else highest) per-pair status. */
 int mcs_solve_batch(mcs_ctx* ctx, const mcs_graph* G, const mcs_graph* H,
                     int32_t npairs, uint32_t flags, double timeout_s,
                     mcs_result* out);
 
-/* Device-resident batch: every pointer is a device pointer; nothing is
+/* Device-resident batch (the problem of Section II-A by Algorithm 1 and
+ * Eq. 1, as mcs_solve_batch): every pointer is a device pointer; nothing is
  * copied between host and device and the call does not synchronise.
  *   d_n[2p], d_n[2p+1]            vertex counts of G_p and H_p
  *   d_adj_off[2p], d_adj_off[2p+1] byte offsets of their matrices in d_adj
@@ -180,12 +215,16 @@ int mcs_solve_batch_device(mcs_ctx* ctx, int32_t npairs,
  * no cudaMalloc/cudaFree and uses no allocating library routine.
  *
  * Limits: at most MCS_NOALLOC_MAX_PAIRS pairs per call (more returns
- * MCS_ERR_ARG and enqueues nothing) and at most MCS_NOALLOC_MAX_WARPS search
- * warps (one block of 4 warps per SM).
+ * MCS_ERR_ARG and enqueues nothing), at most MCS_NOALLOC_MAX_WARPS search
+ * warps (one block of 4 warps per SM), and graphs of at most 64 vertices
+ * (a larger one makes its pair MCS_ERR_ARG; MCS_WIDE: MCS_ERR_UNSUPPORTED).
  *
  * The first call on a device looks up the array's device address
- * (cudaGetSymbolAddress, with that device current) and caches it; make that
- * first call before any stream capture begins.  Every call uses the same
+ * (cudaGetSymbolAddress, with that device current) and caches it, and loads
+ * every kernel variant the entry point can launch (any accepted flags) with
+ * its shared-memory limit set; make that first call before any stream capture
+ * begins.  MCS_ORDER_LEARNED is not available here (MCS_ERR_UNSUPPORTED).
+ * Every call uses the same
  * array and overwrites what the previous call left there (the kernels
  * re-initialise all state they read), so calls whose executions overlap on
  * the GPU -- on different streams, or from different host threads on one
@@ -248,15 +287,22 @@ int mcs_order_score_grid(mcs_ctx* ctx, int32_t npairs, const int32_t* d_n, const
                          const uint8_t* d_adj, const int64_t* d_lab_off, const int32_t* d_labels,
                          uint32_t flags, float* d_scores, void* stream);
 
-/* Serving: admit one request; returns a ticket.  The search starts on the
- * device as soon as a slot and device memory are free; requests submitted
- * while others run join them (continuous batching). */
+/* Serving: admit one request -- one pair, solved as in mcs_solve (Section
+ * II-A, Algorithm 1, Eq. 1) -- and return its ticket.  The search starts on
+ * the device as soon as a slot and device memory are free; requests
+ * submitted while others run join them (continuous batching).  The paper
+ * serves no request stream (its portfolio runs one instance at a time,
+ * Section IV); this is the continuous-batching form of the same search.
+ * Undirected requests with the degree order only (other flags:
+ * MCS_ERR_UNSUPPORTED). */
 int mcs_submit(mcs_ctx* ctx, const mcs_graph* G, const mcs_graph* H,
                uint32_t flags, double timeout_s, uint64_t* ticket);
 
 /* Returns MCS_PENDING until the request finishes, then its status, and fills
- * `out` (mapping buffers as in mcs_result).  A finished ticket is released by
- * the first poll that reports it. */
+ * `out` with its result (Section II-A: size and vertex pairs; mapping buffers
+ * as in mcs_result).  A finished ticket is released by the first poll that
+ * reports it.  A request lost by a failed server launch returns that
+ * launch's error (MCS_ERR_DEVICE_STALL or MCS_ERR_CUDA) and is released. */
 int mcs_poll(mcs_ctx* ctx, uint64_t ticket, mcs_result* out);
 
 /* Launch shape used by every solve on this context: warps per block (1..8,
@@ -292,6 +338,23 @@ int mcs_set_steal(mcs_ctx* ctx, int poll_nodes, int keep_quarters);
  * setting (mcs_set_serve_group). */
 int mcs_set_search_group(mcs_ctx* ctx, int lanes);
 
+/* How searchers narrower than a warp share it in plain batch solves
+ * (mcs_solve_batch[_device], mcs_solve, without MCS_TOP_DOWN, MCS_DEAD_END or
+ * MCS_RESTART):
+ *   MCS_MODE_FREE (default): each searcher runs its own loop, and the warp
+ *     serialises the searchers' diverging branches;
+ *   MCS_MODE_LOCKSTEP: the searchers of a warp advance together, one node
+ *     of each per pass (the "v unmatched" step and a child (v, u) are the
+ *     same predicated split pass), so the warp issues one instruction
+ *     stream for all of them.  Measured slower on the B300 (the searchers'
+ *     memory waits add up instead of overlapping).
+ * Results are the same either way (a lone searcher visits the same nodes).
+ * Whole-warp searchers, goal-directed strategies and the server launch are
+ * not affected.  MCS_ERR_ARG for other values. */
+#define MCS_MODE_FREE      0
+#define MCS_MODE_LOCKSTEP  1
+int mcs_set_search_mode(mcs_ctx* ctx, int mode);
+
 /* Lanes per searcher of the server launch behind mcs_submit / mcs_poll:
  * 32 (default; the best throughput and p50 latency measured on the
  * config-5 stream), 16 or 8.  The first warp of the server always admits
@@ -326,8 +389,49 @@ int mcs_set_restart(mcs_ctx* ctx, long long min_nodes, unsigned long long seed);
  * when created, out[10] / out[11] SM cycles summed over searchers while working /
  * waiting for work, out[12..14] index violations recorded by an
  * MCS_DEBUG_BOUNDS build (count, first code, first source line; 0 in
- * release builds).  Returns the number of values written (<= n, <= 15). */
+ * release builds), out[15] for an MCS_RACE solve the side that finished its
+ * proof first (0 neither, 1 the CPU, 2 the GPU), out[16] the CPU side's
+ * search nodes.  Returns the number of values written (<= n, <= 17). */
 int mcs_last_stats(mcs_ctx* ctx, double* out, int n);
+
+/* ---- failure injection (diagnostics; the paper has no counterpart) ------
+ * Makes the library's failure paths run on demand in tests, without faulting
+ * the GPU: every device-side wait of the search is bounded, and these hooks
+ * make one of them run out, or make a host-side call fail as if the system
+ * had refused it.  `value` applies to the context's later calls (a graph
+ * captured by MCS_GRAPH_REPLAY keeps the values it was captured with); 0
+ * turns a fault off.  Returns MCS_ERR_ARG for an unknown kind or a negative
+ * value.
+ *   MCS_FAULT_ALLOC          the value-th device or pinned-host allocation of a
+ *                            batch solve from now fails once, as if out of
+ *                            memory: that call returns MCS_ERR_NOMEM and the
+ *                            next call allocates again
+ *   MCS_FAULT_CUDA           the next `value` batch solves fail at their first
+ *                            kernel launch with MCS_ERR_CUDA (nothing of that
+ *                            call runs on the device; mcs_error_detail names it)
+ *   MCS_FAULT_STALL_MS       limit, in milliseconds, of an idle searcher's wait
+ *                            for work without progress anywhere in the launch
+ *                            (default: the time limit + 2 s); also applies to
+ *                            the server launch of mcs_submit
+ *   MCS_FAULT_SPIN_LIMIT     iterations of a wait for a free work-ring slot
+ *                            before it gives up (default 2^22)
+ *   MCS_FAULT_WITHHOLD_EXIT  the searcher that ends a launch posts `value`
+ *                            fewer exit tokens: as many searchers wait for work
+ *                            that never comes until MCS_FAULT_STALL_MS expires
+ *   MCS_FAULT_BLOCK_RING     1: work-ring slots other than the pair roots never
+ *                            become free, so every hand-over of work waits
+ *                            until MCS_FAULT_SPIN_LIMIT runs out
+ * An expired wait makes the call (mcs_solve_batch, or mcs_poll for each
+ * request of a failed server launch) return MCS_ERR_DEVICE_STALL; pairs that
+ * finished before it keep their results, the others report MCS_PENDING; the
+ * context stays usable. */
+#define MCS_FAULT_ALLOC          1
+#define MCS_FAULT_CUDA           2
+#define MCS_FAULT_STALL_MS       3
+#define MCS_FAULT_SPIN_LIMIT     4
+#define MCS_FAULT_WITHHOLD_EXIT  5
+#define MCS_FAULT_BLOCK_RING     6
+int mcs_set_fault(mcs_ctx* ctx, int kind, long long value);
 
 /* Micro-benchmark of the integer pipe the search is bound by: sustained
  * 32-bit population counts per second over the whole device (8 independent

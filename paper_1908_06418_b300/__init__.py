@@ -18,10 +18,11 @@ import numpy as np
 __all__ = ["Solver", "Result", "MCS_OK", "MCS_TIMEOUT", "MCS_PENDING", "MCS_ERR_ARG",
            "MCS_ERR_NOMEM", "MCS_ERR_CUDA", "MCS_ERR_DEVICE_STALL", "MCS_ERR_UNSUPPORTED",
            "MCS_DIRECTED", "MCS_ORDER_LEARNED", "MCS_NO_MAPPING", "MCS_NO_LEVEL_PRUNE",
-           "MCS_MAX_N", "MCS_GRAPH_REPLAY", "MCS_WORD32", "MCS_TOP_DOWN", "MCS_DEAD_END", "MCS_ORDER_HR", "MCS_RESTART", "lib_path", "load_library", "EXPORTED_SYMBOLS",
+           "MCS_MAX_N", "MCS_GRAPH_REPLAY", "MCS_WIDE", "MCS_RACE", "MCS_MODE_FREE", "MCS_MODE_LOCKSTEP", "MCS_FAULT_ALLOC", "MCS_FAULT_CUDA", "MCS_FAULT_STALL_MS",
+           "MCS_FAULT_SPIN_LIMIT", "MCS_FAULT_WITHHOLD_EXIT", "MCS_FAULT_BLOCK_RING", "MCS_WORD32", "MCS_TOP_DOWN", "MCS_DEAD_END", "MCS_ORDER_HR", "MCS_RESTART", "lib_path", "load_library", "EXPORTED_SYMBOLS",
            "DeviceBatch", "HostBatch", "pack_host"]
 
-MCS_MAX_N = 64
+MCS_MAX_N = 256      # vertices per graph; also the stride of the device mapping outputs
 MCS_OK, MCS_TIMEOUT, MCS_PENDING = 0, 1, 2
 MCS_ERR_ARG, MCS_ERR_NOMEM, MCS_ERR_CUDA, MCS_ERR_DEVICE_STALL, MCS_ERR_UNSUPPORTED = -1, -2, -3, -4, -5
 MCS_DIRECTED, MCS_ORDER_LEARNED, MCS_NO_MAPPING, MCS_NO_LEVEL_PRUNE = 0x1, 0x2, 0x4, 0x8
@@ -31,6 +32,12 @@ MCS_DEAD_END = 0x80
 MCS_ORDER_HR = 0x100
 MCS_RESTART = 0x200
 MCS_GRAPH_REPLAY = 0x10
+MCS_WIDE = 0x400     # mcs_solve_batch_device: graphs of more than 64 vertices
+MCS_RACE = 0x800     # mcs_solve: GPU search raced against a CPU McSplit
+MCS_MODE_FREE, MCS_MODE_LOCKSTEP = 0, 1     # mcs_set_search_mode
+# failure-injection kinds of mcs_set_fault (test hooks)
+MCS_FAULT_ALLOC, MCS_FAULT_CUDA, MCS_FAULT_STALL_MS = 1, 2, 3
+MCS_FAULT_SPIN_LIMIT, MCS_FAULT_WITHHOLD_EXIT, MCS_FAULT_BLOCK_RING = 4, 5, 6
 
 _HERE = os.path.dirname(os.path.abspath(__file__))
 
@@ -55,7 +62,7 @@ class _Result(ctypes.Structure):
 EXPORTED_SYMBOLS = ["mcs_create", "mcs_destroy", "mcs_solve", "mcs_solve_batch",
                     "mcs_solve_batch_device", "mcs_submit", "mcs_poll", "mcs_set_launch",
                     "mcs_set_max_warps", "mcs_set_search_group", "mcs_set_serve_group", "mcs_set_steal",
-                    "mcs_set_dead_end", "mcs_set_restart",
+                    "mcs_set_dead_end", "mcs_set_restart", "mcs_set_fault", "mcs_set_search_mode",
                     "mcs_last_stats", "mcs_bench_popc", "mcs_strerror", "mcs_error_detail",
                     "mcs_solve_batch_noalloc", "mcs_set_order_model", "mcs_get_order_model",
                     "mcs_order_eval", "mcs_order_train", "mcs_order_score_grid"]
@@ -100,6 +107,10 @@ def load_library():
     lib.mcs_set_dead_end.restype = ctypes.c_int
     lib.mcs_set_restart.argtypes = [vp, ctypes.c_longlong, ctypes.c_ulonglong]
     lib.mcs_set_restart.restype = ctypes.c_int
+    lib.mcs_set_search_mode.argtypes = [vp, ctypes.c_int]
+    lib.mcs_set_search_mode.restype = ctypes.c_int
+    lib.mcs_set_fault.argtypes = [vp, ctypes.c_int, ctypes.c_longlong]
+    lib.mcs_set_fault.restype = ctypes.c_int
     lib.mcs_set_search_group.argtypes = [vp, ctypes.c_int]
     lib.mcs_set_search_group.restype = ctypes.c_int
     lib.mcs_set_serve_group.argtypes = [vp, ctypes.c_int]
@@ -239,6 +250,24 @@ class Solver:
         if rc:
             raise ValueError(f"mcs_set_restart: {self.strerror(rc)}")
 
+    def set_search_mode(self, mode: int):
+        """MCS_MODE_FREE (default) or MCS_MODE_LOCKSTEP: how searchers
+        narrower than a warp share it in plain batch solves."""
+        rc = self.lib.mcs_set_search_mode(self.ctx, int(mode))
+        if rc:
+            raise ValueError(self.strerror(rc))
+
+    def set_fault(self, kind: int, value: int):
+        """Failure injection (mcs_set_fault): MCS_FAULT_* kind, value 0 = off."""
+        rc = self.lib.mcs_set_fault(self.ctx, int(kind), int(value))
+        if rc:
+            raise ValueError(f"mcs_set_fault: {self.strerror(rc)}")
+
+    def clear_faults(self):
+        for k in (MCS_FAULT_ALLOC, MCS_FAULT_CUDA, MCS_FAULT_STALL_MS, MCS_FAULT_SPIN_LIMIT,
+                  MCS_FAULT_WITHHOLD_EXIT, MCS_FAULT_BLOCK_RING):
+            self.set_fault(k, 0)
+
     def set_search_group(self, lanes: int):
         """Lanes per searcher: 32 (one search per warp), 16, 8, 4 or 2."""
         rc = self.lib.mcs_set_search_group(self.ctx, int(lanes))
@@ -258,13 +287,13 @@ class Solver:
         return e
 
     def last_stats(self) -> dict:
-        buf = (ctypes.c_double * 15)()
-        self.lib.mcs_last_stats(self.ctx, buf, 15)
+        buf = (ctypes.c_double * 17)()
+        self.lib.mcs_last_stats(self.ctx, buf, 17)
         return dict(kernel_us=buf[0], nodes=buf[1], donated=buf[2], stolen=buf[3],
                     spilled=buf[4], warps=buf[5], h2d_bytes=buf[6], d2h_bytes=buf[7],
                     class_visits=buf[8], pruned=buf[9], busy_cycles=buf[10],
                     idle_cycles=buf[11], dbg_count=buf[12], dbg_code=buf[13],
-                    dbg_line=buf[14])
+                    dbg_line=buf[14], race_winner=buf[15], race_cpu_nodes=buf[16])
 
     def bench_popc(self) -> float:
         """Measured device-wide 32-bit popcount rate (per second)."""
@@ -279,9 +308,11 @@ class Solver:
 
     # -- solving ----------------------------------------------------------
     def solve_batch(self, pairs: Sequence, flags: int = 0, timeout_s: float = 0.0,
-                    directed: Optional[bool] = None) -> List[Result]:
+                    directed: Optional[bool] = None, raise_errors: bool = True) -> List[Result]:
         """pairs: sequence of (adjG, adjH, labG, labH) tuples or objects with
-        .G.adj/.G.labels/.H.adj/.H.labels (and optionally .directed)."""
+        .G.adj/.G.labels/.H.adj/.H.labels (and optionally .directed).  The
+        call's return code is kept in ``last_rc``; with raise_errors=False an
+        error code other than MCS_ERR_ARG is returned there instead of raised."""
         keep = _Keep()
         n = len(pairs)
         Gs = (_Graph * max(n, 1))()
@@ -306,7 +337,8 @@ class Solver:
         if directed:
             flags |= MCS_DIRECTED
         rc = self.lib.mcs_solve_batch(self.ctx, Gs, Hs, n, flags, float(timeout_s), Rs)
-        if rc < 0 and rc not in (MCS_ERR_ARG,):
+        self.last_rc = int(rc)
+        if rc < 0 and rc not in (MCS_ERR_ARG,) and raise_errors:
             raise RuntimeError(f"mcs_solve_batch: {self.strerror(rc)} ({rc}): "
                                f"{self.lib.mcs_error_detail().decode()}")
         out = []
@@ -339,8 +371,24 @@ class Solver:
 
     def solve(self, adjG, adjH, labG=None, labH=None, directed: bool = False,
               flags: int = 0, timeout_s: float = 0.0) -> Result:
-        return self.solve_batch([(adjG, adjH, labG, labH)],
-                                flags | (MCS_DIRECTED if directed else 0), timeout_s)[0]
+        """One pair through mcs_solve (the entry point that also takes MCS_RACE)."""
+        keep = _Keep()
+        G = keep.graph(adjG, labG)
+        H = keep.graph(adjH, labH)
+        cap = max(1, min(G.n, H.n))
+        gi = np.zeros(cap, np.int16)
+        hi = np.zeros(cap, np.int16)
+        r = _Result()
+        r.g_idx = gi.ctypes.data_as(ctypes.POINTER(ctypes.c_int16))
+        r.h_idx = hi.ctypes.data_as(ctypes.POINTER(ctypes.c_int16))
+        rc = self.lib.mcs_solve(self.ctx, ctypes.byref(G), ctypes.byref(H),
+                                int(flags | (MCS_DIRECTED if directed else 0)), float(timeout_s), ctypes.byref(r))
+        self.last_rc = int(rc)
+        if rc < 0 and rc != MCS_ERR_ARG:
+            raise RuntimeError(f"mcs_solve: {self.strerror(rc)} ({rc}): {self.lib.mcs_error_detail().decode()}")
+        k = r.npairs
+        return Result(int(r.size), int(r.status), gi[:k].astype(np.int32), hi[:k].astype(np.int32),
+                      int(r.nodes), float(r.seconds))
 
     # -- branching-order network -----------------------------------------
     def set_order_model(self, params: np.ndarray):
@@ -437,9 +485,10 @@ class Solver:
             raise RuntimeError(f"mcs_submit: {self.strerror(rc)} ({rc})")
         return int(t.value)
 
-    def poll(self, ticket: int) -> Optional[Result]:
+    def poll(self, ticket: int, raise_errors: bool = True) -> Optional[Result]:
         """None while the request runs; its Result once finished (the ticket is
-        then released)."""
+        then released).  A request lost by a failed server launch raises, or
+        with raise_errors=False returns a Result whose status is the error."""
         gi = np.zeros(MCS_MAX_N, np.int16)
         hi = np.zeros(MCS_MAX_N, np.int16)
         r = _Result()
@@ -448,7 +497,7 @@ class Solver:
         rc = self.lib.mcs_poll(self.ctx, ctypes.c_uint64(int(ticket)), ctypes.byref(r))
         if rc == MCS_PENDING:
             return None
-        if rc < 0 and rc != MCS_ERR_ARG:
+        if rc < 0 and rc != MCS_ERR_ARG and raise_errors:
             raise RuntimeError(f"mcs_poll: {self.strerror(rc)} ({rc})")
         if rc == MCS_ERR_ARG and r.status == 0 and r.size == 0:
             raise KeyError(f"unknown ticket {ticket}")
@@ -538,8 +587,8 @@ class HostBatch:
 class DeviceBatch:
     """A list of pairs laid out for the device entry points (torch tensors
     hold the device memory; flags carries MCS_DIRECTED when the pairs are
-    directed, and MCS_WORD32 when every graph has at most 32 vertices unless
-    word32=False)."""
+    directed, MCS_WORD32 when every graph has at most 32 vertices unless
+    word32=False, and MCS_WIDE when a graph has more than 64)."""
 
     def __init__(self, pairs, device=0, directed: bool = False, word32: Optional[bool] = None):
         import torch
@@ -552,6 +601,8 @@ class DeviceBatch:
             word32 = fits
         if word32:
             self.flags |= MCS_WORD32
+        if any(max(p.G.n, p.H.n) > 64 for p in pairs):
+            self.flags |= MCS_WIDE
         self.d_n = torch.from_numpy(h["n"]).to(self.device)
         self.d_adj_off = torch.from_numpy(h["adj_off"]).to(self.device)
         self.d_adj = torch.from_numpy(h["adj"]).to(self.device)

@@ -10,8 +10,9 @@ HERE = os.path.dirname(os.path.abspath(__file__))
 CSRC = os.path.join(HERE, "csrc")
 LIB = os.path.join(HERE, "libmcs.so")
 LIB_DEBUG = os.path.join(HERE, "libmcs_debug_bounds.so")
-SOURCES = ["mcs_kernels.cu", "mcs_api.cu", "mcs_noalloc.cu", "mcs_mlp.cu", "mcs_serve.cu"]
-HEADERS = ["mcs_internal.cuh", os.path.join("..", "..", "include", "mcs.h")]
+SOURCES = ["mcs_kernels.cu", "mcs_api.cu", "mcs_noalloc.cu", "mcs_mlp.cu", "mcs_serve.cu", "mcs_wide.cu",
+           "mcs_cpu.cpp"]
+HEADERS = ["mcs_internal.cuh", "mcs_cpu.h", os.path.join("..", "..", "include", "mcs.h")]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 
 
@@ -48,7 +49,7 @@ def build(force: bool = False, verbose: bool = False, extra=None, debug: bool = 
     # the translation units compile in parallel (the search kernel's
     # instantiations dominate; the others overlap with it)
     from concurrent.futures import ThreadPoolExecutor
-    objs = [os.path.join(build_dir, s.replace(".cu", ".o")) for s in SOURCES]
+    objs = [os.path.join(build_dir, os.path.splitext(s)[0] + ".o") for s in SOURCES]
     with ThreadPoolExecutor(max_workers=min(len(SOURCES), os.cpu_count() or 1)) as ex:
         jobs = [ex.submit(subprocess.check_call, [nvcc(), "-c", os.path.join(CSRC, s), "-o", o, *flags])
                 for s, o in zip(SOURCES, objs)]

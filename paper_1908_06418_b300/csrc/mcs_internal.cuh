@@ -18,11 +18,11 @@ typedef unsigned long long u64;
 
 // Per-pair packed graph data, produced by the pack kernel (renumbered by the
 // chosen vertex order; bit x of row v is vertex x in the new numbering).
+// The out- and in-row of a vertex are adjacent (one 16-byte pair), so that the
+// directed split reads one cache line per graph.
 struct PairGraph {
-    u64 gout[kMaxN];       // bit x: arc v -> x in G
-    u64 gin[kMaxN];        // bit x: arc x -> v in G (== gout when undirected)
-    u64 hout[kMaxN];
-    u64 hin[kMaxN];
+    u64 rows[4 * kMaxN];   // G: rows[2v] bit x = arc v -> x, rows[2v + 1] bit x = arc x -> v
+                           // (== the out-row when undirected); H: the same from 2 kMaxN
     ulonglong2 root[kMaxN];  // initial label classes (L mask, R mask)
     uint8_t permG[kMaxN];  // new number -> original number
     uint8_t permH[kMaxN];
@@ -153,6 +153,14 @@ struct SearchParams {
     int32_t dead_double;           // MCS_DEAD_END: 1 doubles the incumbent size, 0 adds one
     u64 restart_min;               // MCS_RESTART: no restart before this many nodes of a pair
     u64 restart_seed;              // MCS_RESTART: seed of the random order of spilled branches
+    int32_t lockstep;              // 1: searchers narrower than a warp advance in lockstep (plain batch mode)
+    // GPU + CPU race (MCS_RACE; null otherwise): words in mapped host memory
+    const volatile int32_t* race_cpu;   // best size found by the CPU search (read at polls)
+    volatile int32_t* race_gpu;         // best size found here (written on each new incumbent)
+    const volatile int32_t* race_stop;  // nonzero: the CPU search finished, stop
+    // failure injection (mcs_set_fault; 0 in normal runs)
+    uint32_t spin_limit;           // iterations of a ring-slot wait (0: kSpinLimit)
+    int32_t withhold_exit;         // exit tokens not posted when a launch's last pair ends
     // outputs
     int32_t* out_size;
     int32_t* out_status;
@@ -182,6 +190,7 @@ struct PackParams {
     u64* qseq;
     uint32_t qcap;
     const int32_t* order;          // processing order of the pairs (may be null)
+    int32_t block_ring;            // failure injection: non-root ring slots never become free
 };
 
 // Per-searcher shared memory layout (bytes from the searcher's base).  The
@@ -191,17 +200,24 @@ struct PackParams {
 constexpr int kSmAdjBytes = 4 * 64 * 8;          // gout, gin, hout, hin
 __host__ __device__ constexpr bool adj_in_smem(int gs) { return gs == 32; }
 __host__ __device__ constexpr int sm_adj_bytes(int gs) { return adj_in_smem(gs) ? kSmAdjBytes : 0; }
-constexpr int kSmRremOff = 0;                    // 65 * 8 -> 528   (offsets after the adjacency)
-constexpr int kSmInfoOff = 528;                  // 65 * 8 -> 528
-constexpr int kSmMOff = 1056;                    // 64 + 64
-constexpr int kSmCycOff = 1184;                  // busy, idle cycle counters, clock mark (3 x 8)
-constexpr int kSmClsOff = 1216;                  // 16-byte aligned
+// Row indices in PairGraph::rows (and in a whole-warp searcher's shared copy).
+__host__ __device__ constexpr int row_gout(int v) { return 2 * v; }
+__host__ __device__ constexpr int row_gin(int v) { return 2 * v + 1; }
+__host__ __device__ constexpr int row_hout(int u) { return 2 * kMaxN + 2 * u; }
+__host__ __device__ constexpr int row_hin(int u) { return 2 * kMaxN + 2 * u + 1; }
+// A searcher's levels: one 16-byte entry per depth d, {candidates still to
+// try, info}, info = base | C << 16 | v << 24 | flags << 32 | bound << 40 |
+// u << 48, where (v, u) is the pair matched at depth d once a deeper level
+// exists (the mapping prefix M is read from these entries).
+constexpr int kSmLvOff = 0;                      // 65 * 16 -> 1040 (offsets after the adjacency)
+constexpr int kSmCycOff = 1040;                  // busy, idle cycle counters, clock mark (3 x 8)
+constexpr int kSmClsOff = 1072;                  // 16-byte aligned
 static_assert(kSmClsOff % 16 == 0 && kSmAdjBytes % 16 == 0, "class cache must be 16-byte aligned");
 
 // Searchers of at most 4 lanes (8 or more per warp, up to 256 per SM) keep
 // their level arrays in their global region as well, after the class stack.
 __host__ __device__ constexpr bool levels_in_smem(int gs) { return gs >= 8; }
-constexpr int kLvEntries = 80;                   // 1,280 B >= kSmClsOff: level arrays in global
+constexpr int kLvEntries = 80;                   // 1,280 B >= kSmClsOff: level entries in global
 
 inline int warp_smem_bytes(int stack_entries, int gs = 32) {
     return sm_adj_bytes(gs) + (levels_in_smem(gs) ? kSmClsOff : 0) + 16 * stack_entries;
@@ -217,6 +233,18 @@ inline size_t gstack_entries(int stack_entries, int gs) {
 
 struct MlpState;
 struct ServeState;
+
+// Device arenas of the path for graphs of 65 to 256 vertices (mcs_wide.cu),
+// one set per word count (2 or 4 words per vertex set).
+struct WideArena {
+    void* graphs = nullptr; size_t graphs_cap = 0;
+    void* state = nullptr;  size_t state_cap = 0;
+    void* best = nullptr;   size_t best_cap = 0;
+    void* queue = nullptr;  size_t queue_cap = 0;
+    void* qseq = nullptr;   size_t qseq_cap = 0;
+    void* gstack = nullptr; size_t gstack_cap = 0;
+    void* ctl = nullptr;    size_t ctl_cap = 0;
+};
 
 // Host-side context behind the opaque mcs_ctx handle of include/mcs.h.
 struct mcs_ctx {
@@ -236,6 +264,7 @@ struct mcs_ctx {
     int serve_lanes = 32;         // lanes per searcher of the server launch: 32, 16 or 8
     int poll_nodes = 16;          // work-sharing poll interval (nodes, power of two)
     int steal_keep_q4 = 2;        // quarters of a donated level's candidates the donor keeps
+    int lockstep = 0;             // 1: plain batch searchers narrower than a warp run in lockstep
     long long dead_nodes = 1LL << 22;   // MCS_DEAD_END: nodes without a new incumbent before a raise
     int dead_double = 0;          // MCS_DEAD_END: 1 doubles the incumbent size, 0 adds one
     long long restart_min = 1LL << 20;   // MCS_RESTART: nodes of a pair before its first restart
@@ -261,7 +290,7 @@ struct mcs_ctx {
     uint8_t* d_out = nullptr; size_t d_out_cap = 0;
     uint8_t* h_out = nullptr; size_t h_out_cap = 0;
     cudaEvent_t ev0 = nullptr, ev1 = nullptr;
-    double stats[15] = {0};
+    double stats[17] = {0};
     bool ev_pending = false;       // ev0/ev1 recorded by a device call, not yet read
     Control h_ctl;
     struct MlpState* mlp = nullptr;   // ordering network (mcs_mlp.cu), created on first use
@@ -270,7 +299,29 @@ struct mcs_ctx {
     cudaGraphExec_t graph_exec = nullptr;
     cudaGraph_t graph = nullptr;
     uint64_t graph_key[16] = {0};
+    // graphs of 65 to 256 vertices (mcs_wide.cu)
+    WideArena wide[2];
+    void* wide_ctl = nullptr;      // control block of the last wide launch
+    bool last_wide = false;        // the last device batch ran on the multi-word path
+    // GPU + CPU race (MCS_RACE): three words of mapped host memory -- the CPU
+    // side's best size, the GPU side's, and the stop flag -- and their device views
+    int32_t* race_words = nullptr;
+    int32_t* race_words_dev = nullptr;
+    bool race_on = false;          // set while a racing solve is in flight
+    // failure injection (mcs_set_fault): test hooks, all 0 in normal use
+    long long fault_alloc_at = 0;  // the fault_alloc_at-th allocation from now fails (once)
+    int fault_cuda = 0;            // solve calls still to fail at the API boundary
+    long long fault_stall_ms = 0;  // idle-wait limit override
+    long long fault_spin = 0;      // ring-slot wait limit override (iterations)
+    int fault_withhold = 0;        // exit tokens withheld at the end of a launch
+    int fault_block_ring = 0;      // ring slots other than the roots never free up
 };
+
+// Failure injection: true when the allocation about to be made must fail.
+inline bool fault_alloc_now(mcs_ctx* c) {
+    if (c->fault_alloc_at <= 0) return false;
+    return --c->fault_alloc_at == 0;
+}
 
 // Work-sharing defaults for launches that do not take them from a context.
 constexpr uint32_t kPollMaskDefault = 15;
@@ -293,8 +344,15 @@ cudaError_t launch_search(const SearchParams& p, int blocks, int warps_per_block
 int search_max_blocks_per_sm(int warps_per_block, int smem_per_block, bool directed, bool learned,
                              int gs = 32, bool narrow = false);
 int serve_max_blocks_per_sm(int warps_per_block, int smem_per_block, int gs);
+// Loads the pack kernel and every whole-warp, degree-order batch
+// instantiation of the search kernel (both word widths, directed or not,
+// plain and goal-directed) on the current device and sets their dynamic
+// shared-memory limit to smem, so that later launches make no loading or
+// attribute call.
+cudaError_t warm_batch_variants(int smem);
 cudaError_t launch_popc_bench(unsigned long long* out, int blocks, int iters, cudaStream_t s);
-cudaError_t launch_serve_init(Control* ctl, u64* qseq, uint32_t qcap, int32_t* in_flight, cudaStream_t s);
+cudaError_t launch_serve_init(Control* ctl, u64* qseq, uint32_t qcap, int32_t* in_flight, int block_ring,
+                              cudaStream_t s);
 }
 
 // mcs_mlp.cu: learned candidate order
@@ -305,3 +363,9 @@ int mcs_order_ranks(mcs_ctx* c, int npairs, cudaStream_t s, const uint8_t** rank
 void mcs_order_free(mcs_ctx* c);
 // mcs_serve.cu
 void mcs_serve_free(mcs_ctx* c);
+// mcs_wide.cu: pairs of up to 256 vertices per graph
+int wide_run_device(mcs_ctx* c, int npairs, const int32_t* d_n, const int64_t* d_adj_off, const uint8_t* d_adj,
+                    const int64_t* d_lab_off, const int32_t* d_labels, const int32_t* d_order, uint32_t flags,
+                    double timeout_s, int max_n, int max_min_n, int32_t* d_size, int32_t* d_status,
+                    uint64_t* d_nodes, int16_t* d_map, float* d_usec, cudaStream_t s, bool timed);
+void wide_free(mcs_ctx* c);

@@ -242,7 +242,7 @@ __device__ void hr_positions(int n, const u64 (&orow)[2], const u64 (&icol)[2], 
 // graph is malformed.  hr: the static order of hr_positions instead of the
 // degree order (scratch: 64 words of shared memory).
 __device__ bool pack_graph(const GraphIn& g, bool directed, const float* key,
-                           u64* out_rows, u64* in_rows, uint8_t* perm,
+                           u64* rows /* 2 per vertex: out, in */, uint8_t* perm,
                            long long* vkey /* per lane: 2 entries */, int lane, bool hr, u64* scratch) {
     const int n = g.n;
     bool ok = (n >= 0 && n <= kMaxN);
@@ -330,8 +330,8 @@ __device__ bool pack_graph(const GraphIn& g, bool directed, const float* key,
             }
         }
         if (i < n) {
-            out_rows[rank[s]] = o;
-            in_rows[rank[s]] = directed ? in : o;
+            rows[2 * rank[s]] = o;
+            rows[2 * rank[s] + 1] = directed ? in : o;
             long long lab = g.lab ? (long long)g.lab[i] : 0;
             vkey[s] = lab * 2 + (g.a[i * n + i] ? 1 : 0);   // label + self-loop
         } else {
@@ -350,10 +350,9 @@ __device__ bool pack_pair_warp(const GraphIn (&g)[2], bool directed, const float
     long long vk[2][2];
     for (int side = 0; side < 2 && ok; ++side) {
         if (g[side].n < 0 || g[side].n > kMaxN) { ok = false; break; }
-        u64* orows = side ? pg.hout : pg.gout;
-        u64* irows = side ? pg.hin : pg.gin;
+        u64* rows = pg.rows + (side ? 2 * kMaxN : 0);
         uint8_t* perm = side ? pg.permH : pg.permG;
-        ok = pack_graph(g[side], directed, side ? key1 : key0, orows, irows, perm, vk[side], lane, hr,
+        ok = pack_graph(g[side], directed, side ? key1 : key0, rows, perm, vk[side], lane, hr,
                         reinterpret_cast<u64*>(skey));
     }
     __syncwarp();
@@ -417,7 +416,8 @@ __global__ void pack_kernel(PackParams P) {
             t->h.C = 0;
             P.qseq[i] = (u64)i + 1;
         } else {
-            P.qseq[i] = i;
+            // failure injection: a slot that never frees up (no ticket matches)
+            P.qseq[i] = P.block_ring ? ~0ull : (u64)i;
         }
     }
     if (blockIdx.x == 0 && threadIdx.x == 0) {
@@ -470,7 +470,7 @@ __global__ void pack_kernel(PackParams P) {
         if (P.out_usec) P.out_usec[p] = 0.f;
     }
     if (P.out_map)
-        for (int i = lane; i < kMaxN; i += 32) P.out_map[(size_t)p * kMaxN + i] = -1;
+        for (int i = lane; i < MCS_MAX_N; i += 32) P.out_map[(size_t)p * MCS_MAX_N + i] = -1;
 }
 
 cudaError_t launch_pack(const PackParams& p, cudaStream_t s) {
@@ -522,12 +522,14 @@ struct Grp {
 };
 
 struct WarpSmem {
-    const u64* adj; // rows gout | gin | hout | hin (64 each), shared or global
-    u64* rrem;      // per level: candidates still to try
-    u64* info;      // per level: base | C << 16 | v << 24 | flags << 32 | bound << 40
-    uint8_t* Mg; uint8_t* Mh;
+    const u64* adj;      // PairGraph::rows layout, shared or global
+    ulonglong2* lvl;     // per level: {candidates still to try, info} (kSmLvOff)
     ulonglong2* cls;
 };
+// The mapping prefix entry of depth i: (v << 8) | u of the pair matched there.
+__device__ __forceinline__ uint16_t m_entry(u64 info) {
+    return (uint16_t)((((info >> 24) & 0xff) << 8) | ((info >> 48) & 0xff));
+}
 
 // An adjacency row: shared-memory copy, or the packed pair in global memory
 // (read-only for the kernel's lifetime, so through the non-coherent cache).
@@ -663,9 +665,11 @@ __device__ __forceinline__ int learned_pick(const uint8_t* rk, u64 rrem, const G
     return (int)(g.umin(kk) & 63u);
 }
 
-// Bounded wait for a ring slot's sequence number.
-__device__ __forceinline__ bool wait_seq(const u64* seq, u64 want) {
-    for (int it = 0; it < kSpinLimit; ++it) {
+// Bounded wait for a ring slot's sequence number: `limit` iterations (0:
+// kSpinLimit; tests shorten it to make the wait expire).
+__device__ __forceinline__ bool wait_seq(const u64* seq, u64 want, uint32_t limit) {
+    const uint32_t lim = limit ? limit : (uint32_t)kSpinLimit;
+    for (uint32_t it = 0; it < lim; ++it) {
         if (vload(seq) == want) return true;
         if (it > 64) __nanosleep(64);
     }
@@ -677,14 +681,17 @@ __device__ void write_best(const SearchParams& P, int pair, const WarpSmem& w, i
                            const Grp<GS>& g) {
     if (!DBG_OK(P.ctl, d + 1 < kLevels && pair >= 0 && pair < P.npairs, 6, d)) return;
     uint16_t* slot = P.best + ((size_t)pair * kLevels + (d + 1)) * kMaxN;
-    for (int i = g.q; i < d; i += GS) slot[i] = (uint16_t)((w.Mg[i] << 8) | w.Mh[i]);
+    for (int i = g.q; i < d; i += GS) slot[i] = m_entry(w.lvl[i].y);
     if (g.q == 0) slot[d] = (uint16_t)((v << 8) | u);
 }
 
 // Posts `count` exit tokens (pair = -1) at the tail of the ring: every
 // searcher waiting on a ticket at or beyond the tail finds one and leaves.
+// (Failure injection withholds P.withhold_exit of them: the searchers left
+// without one give up at their idle-wait limit.)
 template <int GS>
 __device__ void post_exit_tokens(const SearchParams& P, int count, const Grp<GS>& g) {
+    count = max(0, count - P.withhold_exit);
     u64 t0 = 0;
     if (g.q == 0) t0 = atomicAdd(&P.ctl->q_tail, (u64)count);
     t0 = g.shfl64(t0, 0);
@@ -692,7 +699,9 @@ __device__ void post_exit_tokens(const SearchParams& P, int count, const Grp<GS>
     for (int i = g.q; i < count; i += GS) {
         const u64 t = t0 + i;
         Task* dst = P.queue + (t & (P.qcap - 1));
-        if (!wait_seq(P.qseq + (t & (P.qcap - 1)), t)) { ok = false; continue; }
+        // a slot that never frees up ends this lane's posting (one expired wait
+        // per lane at most; the error makes every waiting searcher leave)
+        if (!wait_seq(P.qseq + (t & (P.qcap - 1)), t, P.spin_limit)) { ok = false; break; }
         dst->h.pair = -1;
         __threadfence();
         P.qseq[t & (P.qcap - 1)] = t + 1;
@@ -756,7 +765,7 @@ __device__ __noinline__ bool requeue_goal(const SearchParams& P, int pair, int f
     __threadfence();
     const uint32_t qmask = P.qcap - 1;
     const u64 t = atomicAdd(&P.ctl->q_tail, 1ull);
-    if (!wait_seq(P.qseq + (t & qmask), t)) return false;
+    if (!wait_seq(P.qseq + (t & qmask), t, P.spin_limit)) return false;
     Task* dst = P.queue + (t & qmask);
     dst->h.pair = pair;
     dst->h.flags = kTaskFresh;
@@ -844,7 +853,7 @@ __device__ void finalize_pair(const SearchParams& P, int pair, const Grp<GS>& g,
                 uint16_t e = vload(slot + i);
                 if (!DBG_OK(P.ctl, (e >> 8) < kMaxN && (e & 0xff) < kMaxN, 8, e)) continue;
                 int gg = __ldcg(&pg.permG[e >> 8]), h = __ldcg(&pg.permH[e & 0xff]);
-                P.out_map[(size_t)pair * kMaxN + gg] = (int16_t)h;
+                P.out_map[(size_t)pair * MCS_MAX_N + gg] = (int16_t)h;
             }
         }
     } else {
@@ -996,7 +1005,7 @@ __device__ void serve_admit(const SearchParams& P, int lane, long long* skey, in
             serve_pack(P, slot, lane, skey);
             if (lane == 0) {
                 const u64 t = atomicAdd(&ctl->q_tail, 1ull);
-                if (wait_seq(P.qseq + (t & qmask), t)) {
+                if (wait_seq(P.qseq + (t & qmask), t, P.spin_limit)) {
                     Task* dst = P.queue + (t & qmask);
                     dst->h.pair = slot;
                     dst->h.flags = kTaskFresh;
@@ -1030,8 +1039,9 @@ __device__ void serve_admit(const SearchParams& P, int lane, long long* skey, in
 
 __device__ __forceinline__ void load_level(const WarpSmem& w, int d, Top& t) {
     if (d < 0 || d >= kLevels) d = 0;   // unreachable: callers test t.d >= d0 >= 0, depth <= 64
-    u64 inf = w.info[d];
-    t.rrem = w.rrem[d];
+    const ulonglong2 e = w.lvl[d];
+    const u64 inf = e.y;
+    t.rrem = e.x;
     t.base = (int)(inf & 0xffff);
     t.C = (int)((inf >> 16) & 0xff);
     t.v = (int)((inf >> 24) & 0xff);
@@ -1054,8 +1064,7 @@ __device__ __forceinline__ bool donate(const SearchParams& P, int pair, int d0, 
     const uint32_t qmask = P.qcap - 1;
     // flush the top cursor so that every level is in shared memory
     if (g.q == 0) {
-        w.rrem[t.d] = t.rrem;
-        w.info[t.d] = pack_info(t.base, t.C, t.v, t.flags, t.bound);
+        w.lvl[t.d] = make_ulonglong2(t.rrem, pack_info(t.base, t.C, t.v, t.flags, t.bound));
     }
     g.sync();
     int ds = -1;
@@ -1063,16 +1072,16 @@ __device__ __forceinline__ bool donate(const SearchParams& P, int pair, int d0, 
         const int d = off + g.q;
         bool open = false;
         if (d <= t.d) {
-            const u64 inf = w.info[d];
-            const int fl = (int)((inf >> 32) & 0xff), bd = (int)((inf >> 40) & 0xff);
-            open = (w.rrem[d] != 0 || (fl & kTaskPending)) && bd > inc;
+            const ulonglong2 e = w.lvl[d];
+            const int fl = (int)((e.y >> 32) & 0xff), bd = (int)((e.y >> 40) & 0xff);
+            open = (e.x != 0 || (fl & kTaskPending)) && bd > inc;
         }
         const unsigned m = g.ballot(open);
         if (m) ds = off + __ffs(m) - 1;
     }
     if (ds < 0) return true;
-    const u64 inf = w.info[ds];
-    const u64 rr = w.rrem[ds];
+    const u64 inf = w.lvl[ds].y;
+    const u64 rr = w.lvl[ds].x;
     const int fl = (int)((inf >> 32) & 0xff);
     const int k = __popcll(rr);
     u64 give;
@@ -1100,7 +1109,7 @@ __device__ __forceinline__ bool donate(const SearchParams& P, int pair, int d0, 
         // the ring for the next idle searcher.
         ticket = atomicAdd(&ctl->q_tail, 1ull);
         atomicAdd(&P.state[pair].open, 1);
-        ok = wait_seq(P.qseq + (ticket & qmask), ticket) ? 1 : -1;
+        ok = wait_seq(P.qseq + (ticket & qmask), ticket, P.spin_limit) ? 1 : -1;
     }
     ok = g.shfl(ok, 0);
     if (ok < 0) {
@@ -1113,7 +1122,11 @@ __device__ __forceinline__ bool donate(const SearchParams& P, int pair, int d0, 
     const int C = (int)((inf >> 16) & 0xff);
     const int bs = (int)(inf & 0xffff);
     for (int i = g.q; i < C; i += GS) dst->cls[i] = *st.at(bs + i);
-    for (int i = g.q; i < ds; i += GS) { dst->Mg[i] = w.Mg[i]; dst->Mh[i] = w.Mh[i]; }
+    for (int i = g.q; i < ds; i += GS) {
+        const uint16_t m = m_entry(w.lvl[i].y);
+        dst->Mg[i] = (uint8_t)(m >> 8);
+        dst->Mh[i] = (uint8_t)m;
+    }
     if (g.q == 0) {
         dst->h.pair = pair;
         dst->h.depth = ds;
@@ -1122,8 +1135,7 @@ __device__ __forceinline__ bool donate(const SearchParams& P, int pair, int d0, 
         dst->h.rrem = give;
         dst->h.flags = gflags;
         dst->h.bound = (int)((inf >> 40) & 0xff);
-        w.rrem[ds] = rr & ~give;
-        w.info[ds] = (inf & ~(0xffull << 32)) | ((u64)(fl & ~gflags) << 32);
+        w.lvl[ds] = make_ulonglong2(rr & ~give, (inf & ~(0xffull << 32)) | ((u64)(fl & ~gflags) << 32));
     }
     g.sync();
     __threadfence();
@@ -1163,8 +1175,7 @@ __device__ __noinline__ bool spill_all(const SearchParams& P, int pair, int d0, 
     Control* ctl = P.ctl;
     const uint32_t qmask = P.qcap - 1;
     if (g.q == 0) {
-        w.rrem[t.d] = t.rrem;
-        w.info[t.d] = pack_info(t.base, t.C, t.v, t.flags, t.bound);
+        w.lvl[t.d] = make_ulonglong2(t.rrem, pack_info(t.base, t.C, t.v, t.flags, t.bound));
     }
     g.sync();
     int nr = 0;
@@ -1178,8 +1189,8 @@ __device__ __noinline__ bool spill_all(const SearchParams& P, int pair, int d0, 
     for (int i = 0; i < m; ++i) {
         const int d = d0 + (int)((a * (unsigned)i + b) & (unsigned)(m - 1));
         if (d > t.d) continue;
-        const u64 inf = w.info[d];
-        const u64 rr = w.rrem[d];
+        const u64 inf = w.lvl[d].y;
+        const u64 rr = w.lvl[d].x;
         const int fl = (int)((inf >> 32) & 0xff), bd = (int)((inf >> 40) & 0xff);
         if (!((rr != 0 || (fl & kTaskPending)) && bd > inc)) continue;   // nothing left above the bound
         u64 ticket = 0;
@@ -1187,7 +1198,7 @@ __device__ __noinline__ bool spill_all(const SearchParams& P, int pair, int d0, 
         if (g.q == 0) {
             ticket = atomicAdd(&ctl->q_tail, 1ull);
             atomicAdd(&P.state[pair].open, 1);
-            ok = wait_seq(P.qseq + (ticket & qmask), ticket) ? 1 : -1;
+            ok = wait_seq(P.qseq + (ticket & qmask), ticket, P.spin_limit) ? 1 : -1;
         }
         ok = g.shfl(ok, 0);
         if (ok < 0) {
@@ -1199,7 +1210,11 @@ __device__ __noinline__ bool spill_all(const SearchParams& P, int pair, int d0, 
         const int C = (int)((inf >> 16) & 0xff);
         const int bs = (int)(inf & 0xffff);
         for (int i2 = g.q; i2 < C; i2 += GS) dst->cls[i2] = *st.at(bs + i2);
-        for (int i2 = g.q; i2 < d; i2 += GS) { dst->Mg[i2] = w.Mg[i2]; dst->Mh[i2] = w.Mh[i2]; }
+        for (int i2 = g.q; i2 < d; i2 += GS) {
+            const uint16_t m = m_entry(w.lvl[i2].y);
+            dst->Mg[i2] = (uint8_t)(m >> 8);
+            dst->Mh[i2] = (uint8_t)m;
+        }
         if (g.q == 0) {
             dst->h.pair = pair;
             dst->h.depth = d;
@@ -1252,10 +1267,7 @@ __global__ void __launch_bounds__(256, (GS == 32 ? MCS_SEARCH_MINB : MCS_GROUP_M
     WarpSmem w;
     u64* adj_sm = (u64*)base;                          // rows copied here when ADJ_SM
     w.adj = adj_sm;
-    w.rrem = (u64*)(lv + kSmRremOff);
-    w.info = (u64*)(lv + kSmInfoOff);
-    w.Mg = lv + kSmMOff;
-    w.Mh = lv + kSmMOff + kMaxN;
+    w.lvl = (ulonglong2*)(lv + kSmLvOff);
     w.cls = (ulonglong2*)(lv + kSmClsOff);
     constexpr bool STACK_SM = GS == 32;
     StackT<STACK_SM> st;
@@ -1266,17 +1278,14 @@ __global__ void __launch_bounds__(256, (GS == 32 ? MCS_SEARCH_MINB : MCS_GROUP_M
     if constexpr (!levels_in_smem(GS)) {
         // level arrays (and cycle counters) after the class stack, in global memory
         lv = reinterpret_cast<unsigned char*>(st.gm + kStackMax);
-        w.rrem = (u64*)(lv + kSmRremOff);
-        w.info = (u64*)(lv + kSmInfoOff);
-        w.Mg = lv + kSmMOff;
-        w.Mh = lv + kSmMOff + kMaxN;
+        w.lvl = (ulonglong2*)(lv + kSmLvOff);
     }
 #ifdef MCS_DEBUG_BOUNDS
     st.ctl = P.ctl;
 #endif
 
     Control* ctl = P.ctl;
-    int16_t* smap = reinterpret_cast<int16_t*>(lv + kSmRremOff);   // finalize scratch (levels unused then)
+    int16_t* smap = reinterpret_cast<int16_t*>(lv + kSmLvOff);     // finalize scratch (levels unused then)
     if constexpr (SERVE) {
         // warp 0 of the grid admits requests; its groups do not search
         if (blockIdx.x == 0 && wib == 0) {
@@ -1363,13 +1372,11 @@ __global__ void __launch_bounds__(256, (GS == 32 ? MCS_SEARCH_MINB : MCS_GROUP_M
         // slot is repacked while the kernel runs, so L1 may hold old lines)
         if (!ADJ_SM) {
             // rows read in place: written by the pack kernel before this launch
-            w.adj = pg.gout;                  // gout, gin, hout, hin are consecutive
+            w.adj = pg.rows;
         } else if (pair != cur_pair || SERVE) {
-            for (int i = g.q; i < kMaxN; i += GS) {
-                adj_sm[i] = __ldcg(&pg.gout[i]);
-                adj_sm[2 * kMaxN + i] = __ldcg(&pg.hout[i]);
-                if (DIR) { adj_sm[kMaxN + i] = __ldcg(&pg.gin[i]); adj_sm[3 * kMaxN + i] = __ldcg(&pg.hin[i]); }
-            }
+            // every row pair {out, in} of both graphs, one 16-byte load each
+            for (int i = g.q; i < 2 * kMaxN; i += GS)
+                reinterpret_cast<ulonglong2*>(adj_sm)[i] = ld_cg(reinterpret_cast<const ulonglong2*>(pg.rows) + i);
             cur_pair = SERVE ? -1 : pair;
         }
         // NARROW: every pair has at most 32 vertices per graph (checked by the pack kernel)
@@ -1391,7 +1398,9 @@ __global__ void __launch_bounds__(256, (GS == 32 ? MCS_SEARCH_MINB : MCS_GROUP_M
             t.flags = tflags;
             if (!DBG_OK(ctl, t.C >= 0 && t.C <= kMaxN, 3, t.C)) t.C = 0;
             if (!DBG_OK(ctl, t.d >= 0 && t.d < kMaxN, 4, t.d)) t.d = 0;
-            for (int i = g.q; i < t.d; i += GS) { w.Mg[i] = ld_cg(&task->Mg[i]); w.Mh[i] = ld_cg(&task->Mh[i]); }
+            // the mapping prefix: levels below the task's depth keep only their (v, u)
+            for (int i = g.q; i < t.d; i += GS)
+                w.lvl[i] = make_ulonglong2(0ull, ((u64)ld_cg(&task->Mg[i]) << 24) | ((u64)ld_cg(&task->Mh[i]) << 48));
             for (int i = g.q; i < t.C; i += GS) *st.at(i) = ld_cg(&task->cls[i]);
             ++stolen;
         } else {
@@ -1478,9 +1487,10 @@ __global__ void __launch_bounds__(256, (GS == 32 ? MCS_SEARCH_MINB : MCS_GROUP_M
                 cvisits += t.C;
                 const int v = t.v;
                 const W vb = (W)1 << v, ub = (W)1 << u;
-                const W gB = (W)adj_row<ADJ_SM, SERVE>(w.adj, v), hB = (W)adj_row<ADJ_SM, SERVE>(w.adj, 2 * kMaxN + u);
-                const W gA = DIR ? (W)adj_row<ADJ_SM, SERVE>(w.adj, kMaxN + v) : (W)0;
-                const W hA = DIR ? (W)adj_row<ADJ_SM, SERVE>(w.adj, 3 * kMaxN + u) : (W)0;
+                const W gB = (W)adj_row<ADJ_SM, SERVE>(w.adj, row_gout(v));
+                const W hB = (W)adj_row<ADJ_SM, SERVE>(w.adj, row_hout(u));
+                const W gA = DIR ? (W)adj_row<ADJ_SM, SERVE>(w.adj, row_gin(v)) : (W)0;
+                const W hA = DIR ? (W)adj_row<ADJ_SM, SERVE>(w.adj, row_hin(u)) : (W)0;
                 const int dm = t.d + 1;
                 const int cbase = t.base + t.C;
                 // parent and child both inside the shared-memory class cache:
@@ -1551,6 +1561,10 @@ __global__ void __launch_bounds__(256, (GS == 32 ? MCS_SEARCH_MINB : MCS_GROUP_M
                     if (old < dm) {
                         write_best<GS>(P, pair, w, t.d, v, u, g);
                         inc = dm;
+                        if (P.race_gpu && g.q == 0) {             // GPU + CPU race: publish the size
+                            *P.race_gpu = dm;
+                            __threadfence_system();
+                        }
                         if constexpr (GOAL) {
                             if (g.q == 0) {
                                 atomicMax(&ps.real, dm);        // a recorded mapping of size dm
@@ -1609,12 +1623,8 @@ __global__ void __launch_bounds__(256, (GS == 32 ? MCS_SEARCH_MINB : MCS_GROUP_M
                 }
                 if (pos > st.S) spilled += 1;
                 if (!DBG_OK(ctl, pos - cbase <= kMaxN && dm <= kMaxN, 5, (pos - cbase) * 1000 + dm)) pos = cbase;
-                if (g.q == 0) {
-                    w.Mg[t.d] = (uint8_t)v;
-                    w.Mh[t.d] = (uint8_t)u;
-                    w.rrem[t.d] = t.rrem;
-                    w.info[t.d] = pack_info(t.base, t.C, t.v, t.flags, t.bound);
-                }
+                if (g.q == 0)
+                    w.lvl[t.d] = make_ulonglong2(t.rrem, pack_info(t.base, t.C, t.v, t.flags, t.bound) | ((u64)u << 48));
                 g.sync();
                 t.d = dm;
                 t.base = cbase;
@@ -1636,6 +1646,15 @@ __global__ void __launch_bounds__(256, (GS == 32 ? MCS_SEARCH_MINB : MCS_GROUP_M
                     if constexpr (GOAL) atomicCAS(&ps.abort, 0, 1);   // time limit (a reached goal stays)
                     else ps.abort = 1;                 // per-pair time limit
                     p_abort = 1;
+                }
+                if (!GOAL && P.race_cpu) {
+                    // GPU + CPU race: prune against the CPU side's best size too,
+                    // and stop once the CPU side has finished its proof
+                    p_inc = max(p_inc, (int)*P.race_cpu);
+                    if (!p_abort && *P.race_stop) {
+                        ps.abort = 1;
+                        p_abort = 1;
+                    }
                 }
                 if (GOAL == 2 && (P.flags & MCS_RESTART) && p_abort == 0) {
                     // randomized restart (Section IV-A) once the pair's node count has
@@ -1709,6 +1728,397 @@ __global__ void __launch_bounds__(256, (GS == 32 ? MCS_SEARCH_MINB : MCS_GROUP_M
     }
 }
 
+// ---------------------------------------------------------------------------
+// lockstep searchers
+// ---------------------------------------------------------------------------
+// The same depth-first McSplit as search_kernel's plain batch mode (Algorithm
+// 1, Eq. 1, filterDomain of Table 1), for searchers narrower than a warp, with
+// the searchers of a warp advancing in lockstep: every pass of the warp's loop
+// expands one node of every searcher that has work, as one predicated
+// instruction stream.  The "v stays unmatched" step is the child step with
+// empty adjacency rows and no u (each class keeps one part, L \ {v} and R,
+// which is exactly the rescan of the level), so a node is one split pass, the
+// Eq. 1 reductions, and a second pass that writes a surviving child's classes.
+// Loops over class slots run to the warp's largest class count.  What is rare
+// per node -- taking a task, ending one, a new incumbent, work donation --
+// stays per searcher (divergent); the polls run on a tick shared by the warp.
+// Searchers that wait for work poll their ring slot once per pass instead of
+// sleeping on it.  Results, node counts of a lone searcher, and every bounded
+// wait are those of search_kernel.
+template <bool DIR, bool LEARNED, int GS, bool NARROW>
+__global__ void __launch_bounds__(256, MCS_GROUP_MINB) lockstep_kernel(SearchParams P) {
+    static_assert(GS == 2 || GS == 4 || GS == 8 || GS == 16, "lockstep searchers share a warp");
+    using W = typename std::conditional<NARROW, uint32_t, u64>::type;
+    extern __shared__ __align__(16) unsigned char smem[];
+    constexpr int GPW = 32 / GS;
+    constexpr int kNeed = 0, kRun = 1, kExit = 2;
+    const int lane = threadIdx.x & 31;
+    const int wib = threadIdx.x >> 5;
+    const Grp<GS> g(lane);
+    const int sid = (blockIdx.x * (blockDim.x >> 5) + wib) * GPW + (lane / GS);
+    // searchers beyond the limit take no work, but stay in the loop for the
+    // warp-wide votes until every searcher of the warp has left
+    int state = sid < P.max_warps ? kNeed : kExit;
+    unsigned char* lv = smem + (size_t)(wib * GPW + lane / GS) * P.warp_smem_bytes;
+    WarpSmem w;
+    w.adj = nullptr;
+    w.lvl = (ulonglong2*)(lv + kSmLvOff);
+    w.cls = nullptr;
+    StackT<false> st;
+    st.sm = nullptr;
+    st.S = 0;
+    const size_t gper = (size_t)kStackMax + (levels_in_smem(GS) ? 0 : kLvEntries);
+    st.gm = P.gstack + (size_t)(state == kExit ? 0 : sid) * gper;
+    if constexpr (!levels_in_smem(GS)) {
+        lv = reinterpret_cast<unsigned char*>(st.gm + kStackMax);
+        w.lvl = (ulonglong2*)(lv + kSmLvOff);
+    }
+#ifdef MCS_DEBUG_BOUNDS
+    st.ctl = P.ctl;
+#endif
+    Control* ctl = P.ctl;
+    int16_t* smap = reinterpret_cast<int16_t*>(lv + kSmLvOff);
+    const bool level_prune = (P.flags & MCS_NO_LEVEL_PRUNE) == 0;
+    const uint32_t qmask = P.qcap - 1;
+    u64 nodes = 0;
+    unsigned tick = 0;
+    unsigned spilled = 0, cvisits = 0, pruned = 0, donated = 0, stolen = 0;
+    u64* cyc = (u64*)(lv + kSmCycOff);
+    if (state != kExit && g.q == 0) { cyc[0] = 0; cyc[1] = 0; }
+    long long c_mark = clock64();
+    bool holding = false;
+    u64 qh = 0;
+    unsigned wait_it = 0, idle_ns = 128;
+    int pair = 0, d0 = 0, inc = 0;
+    int p_inc = 0, p_abort = 0, p_hungry = 0;
+    Top t;
+    t.d = -1; t.base = 0; t.C = 0; t.v = 0; t.flags = 0; t.bound = 0; t.rrem = 0;
+
+    while (__any_sync(FULL, state != kExit)) {
+        // ---------------- searchers without work: take a ticket, check its slot ----------------
+        if (state == kNeed) {
+            if (!holding) {
+                if (g.q == 0) qh = atomicAdd(&ctl->q_head, 1ull);
+                qh = g.shfl64(qh, 0);
+                holding = true;
+                wait_it = 0;
+            }
+            int got = 0;
+            if (g.q == 0) {
+                if (vload(P.qseq + (qh & qmask)) == qh + 1) {
+                    got = 1;
+                } else if ((++wait_it & 63) == 0) {
+                    if (vload(&ctl->error) != 0) {
+                        got = -1;
+                    } else {
+                        const u64 now = gtimer(), lp = vload(&ctl->last_progress);
+                        if (now > lp && now - lp > P.stall_ns) {
+                            atomicCAS(&ctl->error, 0, MCS_ERR_DEVICE_STALL);
+                            got = -1;
+                        }
+                    }
+                }
+            }
+            got = g.shfl(got, 0);
+            if (got < 0) state = kExit;
+            if (got > 0) {
+                holding = false;
+                __threadfence();
+                const Task* task = P.queue + (qh & qmask);
+                int tpair = 0, tflags = 0;
+                if (g.q == 0) { tpair = vload(&task->h.pair); tflags = vload(&task->h.flags); }
+                tpair = g.shfl(tpair, 0);
+                tflags = g.shfl(tflags, 0);
+                if (!DBG_OK(ctl, tpair < P.npairs, 2, tpair)) tpair = -1;
+                if (tpair < 0) {                                  // exit token
+                    g.sync();
+                    if (g.q == 0) P.qseq[qh & qmask] = qh + P.qcap;
+                    state = kExit;
+                } else {
+                    pair = tpair;
+                    // polled values belong to the task they were read for: a half
+                    // tick right after this install must not apply the previous
+                    // pair's incumbent or abort flag to this one
+                    p_inc = p_abort = p_hungry = 0;
+                    const bool fresh = (tflags & kTaskFresh) != 0;
+                    PairState& ps = P.state[pair];
+                    const PairGraph& pg = P.graphs[pair];
+                    int pstat = 0;
+                    if (g.q == 0) pstat = vload(&ps.status);
+                    pstat = g.shfl(pstat, 0);
+                    if (fresh && pstat != MCS_PENDING) {          // malformed input: report and skip
+                        g.sync();
+                        if (g.q == 0) { P.qseq[qh & qmask] = qh + P.qcap; ps.open = 0; }
+                        finalize_pair<false, GS, 0>(P, pair, g, smap);
+                    } else {
+                        if (fresh && g.q == 0) {
+                            const u64 now = gtimer();
+                            ps.t_start = now;
+                            ps.deadline = now + P.timeout_ns;
+                            atomicMax(&ctl->last_progress, now);
+                        }
+                        w.adj = pg.rows;                          // rows read in place
+                        if (!fresh) {
+                            int hd4[4] = {0, 0, 0, 0};
+                            u64 rr = 0;
+                            if (g.q == 0) {
+                                hd4[0] = vload(&task->h.depth);
+                                hd4[1] = vload(&task->h.C);
+                                hd4[2] = vload(&task->h.v);
+                                hd4[3] = vload(&task->h.bound);
+                                rr = vload(&task->h.rrem);
+                            }
+                            t.d = g.shfl(hd4[0], 0);
+                            t.C = g.shfl(hd4[1], 0);
+                            t.v = g.shfl(hd4[2], 0);
+                            t.bound = g.shfl(hd4[3], 0);
+                            t.rrem = g.shfl64(rr, 0);
+                            t.flags = tflags;
+                            if (!DBG_OK(ctl, t.C >= 0 && t.C <= kMaxN, 3, t.C)) t.C = 0;
+                            if (!DBG_OK(ctl, t.d >= 0 && t.d < kMaxN, 4, t.d)) t.d = 0;
+                            for (int i = g.q; i < t.d; i += GS)
+                                w.lvl[i] = make_ulonglong2(0ull, ((u64)ld_cg(&task->Mg[i]) << 24) |
+                                                                     ((u64)ld_cg(&task->Mh[i]) << 48));
+                            for (int i = g.q; i < t.C; i += GS) *st.at(i) = ld_cg(&task->cls[i]);
+                            ++stolen;
+                        } else {
+                            t.d = 0;
+                            t.C = __ldcg(&pg.C0);
+                            for (int i = g.q; i < t.C; i += GS) *st.at(i) = __ldcg(&pg.root[i]);
+                        }
+                        g.sync();
+                        if (g.q == 0) {
+                            __threadfence();
+                            P.qseq[qh & qmask] = qh + P.qcap;     // release the slot
+                        }
+                        t.base = 0;
+                        d0 = t.d;
+                        int ab0 = 0;
+                        if (g.q == 0) { inc = vload(&ps.inc); ab0 = vload(&ps.abort); }
+                        inc = g.shfl(inc, 0);
+                        ab0 = g.shfl(ab0, 0);
+                        if (g.q == 0) { const long long now = clock64(); cyc[1] += (u64)(now - c_mark); c_mark = now; }
+                        state = kRun;
+                        if (ab0) {
+                            t.d = d0 - 1;                         // ends below
+                        } else if (fresh) {
+                            // root node entry (Algorithm 1): bound of Eq. 1, then class choice
+                            ++nodes;
+                            cvisits += t.C;
+                            const Scan sc = scan_level<W, GS>(g, st, 0, t.C, -1);
+                            t.bound = sc.sum;
+                            if (t.bound <= inc) {
+                                t.d = d0 - 1;
+                            } else {
+                                t.v = sc.key & 63;
+                                t.rrem = sc.R;
+                                t.flags = kTaskPending;
+                            }
+                        }
+                    }
+                }
+            }
+        }
+        if (!__any_sync(FULL, state == kRun)) {
+            __nanosleep(idle_ns);
+            idle_ns = min(idle_ns * 2u, 8192u);
+            continue;
+        }
+        idle_ns = 128;
+        // ---------------- polls: one tick for the warp ----------------
+        ++tick;
+        if ((tick & P.poll_mask) == 0 && state == kRun && g.q == 0) {
+            PairState& ps = P.state[pair];
+            p_inc = vload(&ps.inc);
+            p_abort = vload(&ps.abort);
+            p_hungry = vload(&ctl->q_head) > vload(&ctl->q_tail);     // a searcher waits
+            if (!p_abort && (tick & 255) == 0 && gtimer() > vload(&ps.deadline)) {
+                ps.abort = 1;                                   // per-pair time limit
+                p_abort = 1;
+            }
+            if (cvisits >= (1u << 31)) { atomicAdd(&ctl->class_visits, (u64)cvisits); cvisits = 0; }
+            if (pruned >= (1u << 31)) { atomicAdd(&ctl->pruned, (u64)pruned); pruned = 0; }
+        }
+        if ((tick & P.poll_mask) == (P.poll_mask + 1) / 2 && state == kRun && t.d >= d0) {
+            const int g_inc = g.shfl(p_inc, 0);
+            const int ab = g.shfl(p_abort, 0);
+            const int hungry = g.shfl(p_hungry, 0);
+            inc = max(inc, g_inc);
+            if (ab) t.d = d0 - 1;                               // time limit: leave the task
+            else if (hungry && !donate<GS>(P, pair, d0, t, inc, w, st, g, donated)) t.d = d0 - 1;
+        }
+        // ---------------- pop exhausted or bounded levels ----------------
+        for (;;) {
+            const bool pop = state == kRun && t.d >= d0 &&
+                             ((level_prune && t.bound <= inc) || (t.rrem == 0 && !(t.flags & kTaskPending)));
+            if (!__any_sync(FULL, pop)) break;
+            if (pop) {
+                --t.d;
+                if (t.d >= d0) load_level(w, t.d, t);
+            }
+        }
+        if (state == kRun && t.d < d0) {                        // the task is done
+            end_task<false, GS, 0>(P, pair, nodes, g, smap);
+            if (g.q == 0) { const long long now = clock64(); cyc[0] += (u64)(now - c_mark); c_mark = now; }
+            state = kNeed;
+        }
+        // ---------------- one node of every searcher with work ----------------
+        const bool act = state == kRun;
+        const bool ch = act && t.rrem != 0;                     // child (v, u)
+        const bool um = act && t.rrem == 0;                     // "v stays unmatched"
+        int u = 0;
+        if constexpr (LEARNED) {
+            u = learned_pick<GS>(P.rank + ((size_t)pair * kMaxN + t.v) * kMaxN, ch ? t.rrem : 0ull, g);
+        } else {
+            u = ch ? __ffsll(t.rrem) - 1 : 0;
+        }
+        if (ch) t.rrem &= ~(1ull << u);
+        if (act) {
+            ++nodes;
+            cvisits += t.C;
+        }
+        const int v = t.v;
+        const W vb = act ? ((W)1 << v) : (W)0;
+        const W ub = ch ? ((W)1 << u) : (W)0;
+        W gB = 0, hB = 0, gA = 0, hA = 0;
+        if (ch) {
+            gB = (W)adj_row<false>(w.adj, row_gout(v));
+            hB = (W)adj_row<false>(w.adj, row_hout(u));
+            if (DIR) {
+                gA = (W)adj_row<false>(w.adj, row_gin(v));
+                hA = (W)adj_row<false>(w.adj, row_hin(u));
+            }
+        }
+        const int nsl = ((int)__reduce_max_sync(FULL, act ? (unsigned)t.C : 0u) + GS - 1) / GS;
+        int sum = 0;
+        unsigned best = kKeyNone;
+        W bestR = 0, L0 = 0, R0 = 0;
+        for (int sl = 0; sl < nsl; ++sl) {
+            const int i = sl * GS + g.q;
+            const bool have = act && i < t.C;
+            W L = 0, R = 0;
+            if (have) {
+                ulonglong2* ptr = st.at(t.base + i);
+                const ulonglong2 c = *ptr;
+                L = (W)c.x & ~vb;
+                R = (W)c.y & ~ub;
+                if (um && ((W)c.x & vb)) ptr->x = (u64)L;       // v leaves its class in place
+            }
+            if (sl == 0) { L0 = L; R0 = R; }
+            if (DIR) {
+                const W la = L & gA, lb = L & gB, ra = R & hA, rb = R & hB;
+                const W lp[4] = {(W)(L & ~(la | lb)), (W)(la & ~lb), (W)(lb & ~la), (W)(la & lb)};
+                const W rp[4] = {(W)(R & ~(ra | rb)), (W)(ra & ~rb), (W)(rb & ~ra), (W)(ra & rb)};
+#pragma unroll
+                for (int k = 0; k < 4; ++k) {
+                    const int a = Word<W>::popc(lp[k]), b = Word<W>::popc(rp[k]);
+                    const int m = min(a, b);
+                    sum += m;
+                    const unsigned key = m ? (((unsigned)max(a, b) << 6) | (unsigned)Word<W>::low(lp[k])) : kKeyNone;
+                    if (key < best) { best = key; bestR = rp[k]; }
+                }
+            } else {
+                const W l1 = L & gB, r1 = R & hB, l0 = L ^ l1, r0 = R ^ r1;
+                const int a1 = Word<W>::popc(l1), b1 = Word<W>::popc(r1), a0 = Word<W>::popc(l0), b0 = Word<W>::popc(r0);
+                const int m1 = min(a1, b1), m0 = min(a0, b0);
+                sum += m1 + m0;
+                const unsigned k1 = m1 ? (((unsigned)max(a1, b1) << 6) | (unsigned)Word<W>::low(l1)) : kKeyNone;
+                const unsigned k0 = m0 ? (((unsigned)max(a0, b0) << 6) | (unsigned)Word<W>::low(l0)) : kKeyNone;
+                if (k1 < best) { best = k1; bestR = r1; }
+                if (k0 < best) { best = k0; bestR = r0; }
+            }
+        }
+        sum = g.add(sum);
+        const int dm = t.d + 1;
+        // incumbent (Algorithm 1): |M u {(v,u)}| beats the best so far
+        if (ch && dm > inc) {
+            int old = 0;
+            if (g.q == 0) old = atomicMax(&P.state[pair].inc, dm);
+            old = g.shfl(old, 0);
+            if (old < dm) {
+                write_best<GS>(P, pair, w, t.d, v, u, g);
+                inc = dm;
+            } else {
+                inc = old;
+            }
+        }
+        const unsigned kmin = g.umin(best);
+        const unsigned win = g.ballot(best == kmin);
+        const u64 cR = g.shfl64((u64)bestR, win ? __ffs(win) - 1 : 0);
+        if (um) {
+            t.bound = t.d + sum;
+            if (t.bound <= inc) {
+                t.flags = 0;                                    // the level is exhausted and pops next
+            } else {
+                t.v = kmin & 63;
+                t.rrem = cR;
+                t.flags = kTaskPending;
+            }
+        }
+        const bool surv = ch && dm + sum > inc;
+        if (ch && !surv) ++pruned;                              // child pruned by Eq. 1
+        // descend: the surviving child's classes, compacted onto the stack
+        const int cbase = t.base + t.C;
+        int pos = cbase;
+        const int nsl2 = ((int)__reduce_max_sync(FULL, surv ? (unsigned)t.C : 0u) + GS - 1) / GS;
+        for (int sl = 0; sl < nsl2; ++sl) {
+            W L = 0, R = 0;
+            if (sl == 0) {
+                L = L0;
+                R = R0;
+            } else {
+                const int i = sl * GS + g.q;
+                if (surv && i < t.C) {
+                    const ulonglong2 c = *st.at(t.base + i);
+                    L = (W)c.x & ~vb;
+                    R = (W)c.y & ~ub;
+                }
+            }
+            if (!surv) { L = 0; R = 0; }
+            auto emit = [&](W l, W r) {
+                const bool keep = l && r;
+                const unsigned mk = g.ballot(keep);
+                if (keep) *st.at(pos + __popc(mk & g.lt())) = make_ulonglong2((u64)l, (u64)r);
+                pos += __popc(mk);
+            };
+            if (DIR) {
+                const W la = L & gA, lb = L & gB, ra = R & hA, rb = R & hB;
+                emit((W)(L & ~(la | lb)), (W)(R & ~(ra | rb)));
+                emit((W)(la & ~lb), (W)(ra & ~rb));
+                emit((W)(lb & ~la), (W)(rb & ~ra));
+                emit((W)(la & lb), (W)(ra & rb));
+            } else {
+                const W l1 = L & gB, r1 = R & hB;
+                emit(l1, r1);
+                emit((W)(L ^ l1), (W)(R ^ r1));
+            }
+        }
+        if (surv) {
+            if (pos > st.S) spilled += 1;
+            if (!DBG_OK(ctl, pos - cbase <= kMaxN && dm <= kMaxN, 5, (pos - cbase) * 1000 + dm)) pos = cbase;
+            if (g.q == 0)
+                w.lvl[t.d] = make_ulonglong2(t.rrem, pack_info(t.base, t.C, t.v, t.flags, t.bound) | ((u64)u << 48));
+            t.d = dm;
+            t.base = cbase;
+            t.C = pos - cbase;
+            t.v = kmin & 63;
+            t.rrem = cR;
+            t.flags = kTaskPending;
+            t.bound = dm + sum;
+        }
+        __syncwarp();
+    }
+    if (sid < P.max_warps && g.q == 0) {
+        if (spilled) atomicAdd(&ctl->spilled, (u64)spilled);
+        if (cvisits) atomicAdd(&ctl->class_visits, (u64)cvisits);
+        if (pruned) atomicAdd(&ctl->pruned, (u64)pruned);
+        if (donated) atomicAdd(&ctl->donated, (u64)donated);
+        if (stolen) atomicAdd(&ctl->stolen, (u64)stolen);
+        atomicAdd(&ctl->busy_cycles, cyc[0]);
+        atomicAdd(&ctl->idle_cycles, cyc[1]);
+    }
+}
+
 // Raises a kernel's dynamic shared-memory limit on the current device when a
 // launch needs more than was set before (one driver call per new maximum,
 // not one per launch).  Per kernel instantiation: `Tag` is unique to it.
@@ -1746,8 +2156,25 @@ static cudaError_t launch_t(const SearchParams& p, int blocks, int wpb, cudaStre
     return cudaGetLastError();
 }
 
+template <bool DIR, bool LEARNED, int GS, bool NARROW>
+static cudaError_t launch_l(const SearchParams& p, int blocks, int wpb, cudaStream_t s) {
+    size_t smem = (size_t)wpb * (32 / GS) * p.warp_smem_bytes;
+    auto* k = lockstep_kernel<DIR, LEARNED, GS, NARROW>;
+    if (!ensure_smem_limit<KernelTag<DIR, LEARNED, true, GS, NARROW, 99>>(k, (int)smem))
+        return cudaErrorInvalidValue;
+    k<<<blocks, wpb * 32, smem, s>>>(p);
+    return cudaGetLastError();
+}
+
 template <bool DIR, bool LEARNED, bool NARROW, int GOAL>
 static cudaError_t launch_g(const SearchParams& p, int blocks, int wpb, int gs, cudaStream_t s) {
+    if (GOAL == 0 && p.lockstep && gs < 32) {
+        // plain batch searches narrower than a warp: lockstep searchers
+        if (gs == 2) return launch_l<DIR, LEARNED, 2, NARROW>(p, blocks, wpb, s);
+        if (gs == 4) return launch_l<DIR, LEARNED, 4, NARROW>(p, blocks, wpb, s);
+        if (gs == 8) return launch_l<DIR, LEARNED, 8, NARROW>(p, blocks, wpb, s);
+        return launch_l<DIR, LEARNED, 16, NARROW>(p, blocks, wpb, s);
+    }
     if (gs == 2) return launch_t<DIR, LEARNED, false, 2, NARROW, GOAL>(p, blocks, wpb, s);
     if (gs == 4) return launch_t<DIR, LEARNED, false, 4, NARROW, GOAL>(p, blocks, wpb, s);
     if (gs == 8) return launch_t<DIR, LEARNED, false, 8, NARROW, GOAL>(p, blocks, wpb, s);
@@ -1782,6 +2209,29 @@ cudaError_t launch_search(const SearchParams& p, int blocks, int warps_per_block
                                  : launch_w<true, false>(p, blocks, warps_per_block, gs, narrow, s);
     return learned ? launch_w<false, true>(p, blocks, warps_per_block, gs, narrow, s)
                    : launch_w<false, false>(p, blocks, warps_per_block, gs, narrow, s);
+}
+
+// Loads one whole-warp batch instantiation on the current device and sets its
+// shared-memory limit (see warm_batch_variants).
+template <bool DIR, bool NARROW, int GOAL>
+static cudaError_t warm_t(int smem) {
+    auto* k = search_kernel<DIR, false, false, 32, NARROW, GOAL>;
+    if (!ensure_smem_limit<KernelTag<DIR, false, false, 32, NARROW, GOAL>>(k, smem)) return cudaErrorInvalidValue;
+    cudaFuncAttributes a;
+    return cudaFuncGetAttributes(&a, k);
+}
+
+cudaError_t warm_batch_variants(int smem) {
+    cudaFuncAttributes a;
+    cudaError_t e = cudaFuncGetAttributes(&a, pack_kernel);
+    const cudaError_t r[] = {e,
+        warm_t<false, false, 0>(smem), warm_t<false, true, 0>(smem), warm_t<true, false, 0>(smem),
+        warm_t<true, true, 0>(smem), warm_t<false, false, 1>(smem), warm_t<false, true, 1>(smem),
+        warm_t<true, false, 1>(smem), warm_t<true, true, 1>(smem), warm_t<false, false, 2>(smem),
+        warm_t<false, true, 2>(smem), warm_t<true, false, 2>(smem), warm_t<true, true, 2>(smem)};
+    for (cudaError_t x : r)
+        if (x != cudaSuccess) return x;
+    return cudaSuccess;
 }
 
 // Occupancy of the plain instantiation; the goal-directed one has the same
@@ -1827,9 +2277,9 @@ int serve_max_blocks_per_sm(int warps_per_block, int smem_per_block, int gs) {
 }
 
 // Serve mode: reset the control block and the ring before a server launch.
-__global__ void serve_init_kernel(Control* c, u64* qseq, uint32_t qcap, int32_t* in_flight) {
+__global__ void serve_init_kernel(Control* c, u64* qseq, uint32_t qcap, int32_t* in_flight, int block_ring) {
     for (uint32_t i = blockIdx.x * blockDim.x + threadIdx.x; i < qcap; i += gridDim.x * blockDim.x)
-        qseq[i] = i;
+        qseq[i] = block_ring ? ~0ull : (u64)i;       // failure injection: no slot ever frees up
     if (blockIdx.x == 0 && threadIdx.x == 0) {
         c->q_head = 0;
         c->q_tail = 0;
@@ -1843,8 +2293,9 @@ __global__ void serve_init_kernel(Control* c, u64* qseq, uint32_t qcap, int32_t*
     }
 }
 
-cudaError_t launch_serve_init(Control* ctl, u64* qseq, uint32_t qcap, int32_t* in_flight, cudaStream_t s) {
-    serve_init_kernel<<<64, 256, 0, s>>>(ctl, qseq, qcap, in_flight);
+cudaError_t launch_serve_init(Control* ctl, u64* qseq, uint32_t qcap, int32_t* in_flight, int block_ring,
+                              cudaStream_t s) {
+    serve_init_kernel<<<64, 256, 0, s>>>(ctl, qseq, qcap, in_flight, block_ring);
     return cudaGetLastError();
 }
 

@@ -52,7 +52,10 @@ unsigned char* g_ptr[kMaxDevices] = {};
 int g_sms[kMaxDevices] = {};
 
 // Once per device, with that device current: the device address of the
-// scratch and the SM count.  Returns 0 or an MCS_ERR_* code.
+// scratch, the SM count, and every kernel variant this entry point can
+// launch loaded with its shared-memory limit set (so that no later call, for
+// any flags, makes a loading or attribute call).  Returns 0 or an MCS_ERR_*
+// code.
 int setup_current_device(int dev, unsigned char** ptr, int* sms) {
     std::lock_guard<std::mutex> lock(g_mu);
     if (!g_ptr[dev]) {
@@ -61,6 +64,10 @@ int setup_current_device(int dev, unsigned char** ptr, int* sms) {
         int n = 0;
         if (cudaDeviceGetAttribute(&n, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess || n <= 0)
             return MCS_ERR_CUDA;
+        if (warm_batch_variants(kNaWarpsPerBlock * warp_smem_bytes(kNaStackSmem)) != cudaSuccess) {
+            cudaGetLastError();
+            return MCS_ERR_CUDA;
+        }
         g_ptr[dev] = (unsigned char*)p;
         g_sms[dev] = n;
     }
@@ -80,7 +87,7 @@ extern "C" int mcs_solve_batch_noalloc(int32_t npairs, const int32_t* d_n,
     if (npairs < 0 || npairs > kNaPairs) return MCS_ERR_ARG;     // beyond the fixed scratch
     if (npairs == 0) return 0;
     if (!d_n || !d_adj_off || !d_adj || !d_size || !d_status || !d_nodes) return MCS_ERR_ARG;
-    if (flags & MCS_ORDER_LEARNED) return MCS_ERR_UNSUPPORTED;
+    if (flags & (MCS_ORDER_LEARNED | MCS_WIDE | MCS_RACE)) return MCS_ERR_UNSUPPORTED;
     if ((flags & MCS_TOP_DOWN) && (flags & MCS_DEAD_END)) return MCS_ERR_ARG;
     if ((flags & MCS_RESTART) && (flags & (MCS_TOP_DOWN | MCS_DEAD_END))) return MCS_ERR_ARG;
     int dev = 0;

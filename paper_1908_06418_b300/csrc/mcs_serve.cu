@@ -74,7 +74,8 @@ struct ServeState {
     cudaStream_t stream = nullptr;
     cudaEvent_t done_ev = nullptr;
     bool running = false;
-    int last_error = 0;
+    int last_error = 0;                     // error of the last failed server launch
+    u64 failed_upto = 0;                    // ring entries below this were lost by it
     u64 written = 0;
     u64 next_ticket = 0;
     std::vector<int> free_slots;
@@ -144,17 +145,32 @@ int serve_state(mcs_ctx* c, ServeState** out) {
     return 0;
 }
 
+// False once the server launch has ended.  A launch that ended with an
+// error (a bounded device wait expired, or a CUDA error) loses the requests
+// published while it ran and not finished: they are marked failed (their
+// polls return the error) and are not admitted again; later requests start
+// a fresh launch.
 bool server_running(ServeState* S) {
     if (!S->running) return false;
     cudaError_t e = cudaEventQuery(S->done_ev);
     if (e == cudaErrorNotReady) return true;
     S->running = false;
-    if (e != cudaSuccess) S->last_error = MCS_ERR_CUDA;
+    int err = 0;
+    if (e != cudaSuccess) {
+        err = MCS_ERR_CUDA;
+    } else if (cudaMemcpy(&err, &S->ctl->error, sizeof(int), cudaMemcpyDeviceToHost) != cudaSuccess) {
+        err = MCS_ERR_CUDA;
+    }
+    if (err) {
+        S->last_error = err;
+        S->failed_upto = S->written;
+        *(volatile u64*)S->h_admitted = S->written;
+    }
     return false;
 }
 
 int launch_server(mcs_ctx* c, ServeState* S) {
-    CKS(launch_serve_init(S->ctl, S->qseq, S->qcap, S->in_flight, S->stream));
+    CKS(launch_serve_init(S->ctl, S->qseq, S->qcap, S->in_flight, c->fault_block_ring, S->stream));
     SearchParams sp;
     memset(&sp, 0, sizeof(sp));
     sp.poll_mask = kPollMaskDefault;
@@ -182,7 +198,10 @@ int launch_server(mcs_ctx* c, ServeState* S) {
     sp.npairs = kSlots;
     sp.flags = 0;
     sp.timeout_ns = (u64)(kMaxServeTimeout * 1e9);
-    sp.stall_ns = sp.timeout_ns + kLingerNs + 2000000000ull;
+    sp.stall_ns = c->fault_stall_ms > 0 ? (u64)c->fault_stall_ms * 1000000ull
+                                        : sp.timeout_ns + kLingerNs + 2000000000ull;
+    sp.spin_limit = (uint32_t)c->fault_spin;
+    sp.withhold_exit = c->fault_withhold;
     sp.graphs = S->graphs;
     sp.state = S->state;
     sp.best = S->best;
@@ -219,13 +238,15 @@ void place(ServeState* S, int slot, const Pending& p) {
 // Moves waiting requests into free slots and (re)launches the server when
 // published requests are not admitted yet and no server launch is running.
 int kick(mcs_ctx* c, ServeState* S) {
+    // first: a launch that failed is recorded before new requests are published
+    const bool running = server_running(S);
     while (!S->pending.empty() && !S->free_slots.empty()) {
         int slot = S->free_slots.back();
         S->free_slots.pop_back();
         place(S, slot, S->pending.front());
         S->pending.pop_front();
     }
-    if (!server_running(S)) {
+    if (!running) {
         const u64 admitted = *(volatile u64*)S->h_admitted;
         if (S->written > admitted) {
             *(volatile int32_t*)S->h_stop = 0;
@@ -237,6 +258,7 @@ int kick(mcs_ctx* c, ServeState* S) {
 
 int check_graph_s(const mcs_graph* g) {
     if (!g || g->n < 0 || g->n > MCS_MAX_N || (g->n > 0 && !g->adj)) return MCS_ERR_ARG;
+    if (g->n > kMaxN) return MCS_ERR_UNSUPPORTED;     // served requests: one-word bit sets
     return 0;
 }
 
@@ -261,8 +283,12 @@ extern "C" {
 
 int mcs_submit(mcs_ctx* c, const mcs_graph* G, const mcs_graph* H, uint32_t flags, double timeout_s,
                uint64_t* ticket) {
-    if (!c || !ticket || check_graph_s(G) || check_graph_s(H)) return MCS_ERR_ARG;
-    if (flags & (MCS_DIRECTED | MCS_ORDER_LEARNED | MCS_ORDER_HR | MCS_TOP_DOWN | MCS_DEAD_END | MCS_RESTART))
+    if (!c || !ticket) return MCS_ERR_ARG;
+    int chk = check_graph_s(G);
+    if (!chk) chk = check_graph_s(H);
+    if (chk) return chk;
+    if (flags & (MCS_DIRECTED | MCS_ORDER_LEARNED | MCS_ORDER_HR | MCS_TOP_DOWN | MCS_DEAD_END | MCS_RESTART |
+                 MCS_WIDE | MCS_RACE))
         return MCS_ERR_UNSUPPORTED;
     if (cudaSetDevice(c->device) != cudaSuccess) return MCS_ERR_CUDA;
     ServeState* S = nullptr;
@@ -302,13 +328,17 @@ int mcs_poll(mcs_ctx* c, uint64_t ticket, mcs_result* out) {
     const int slot = it->second.slot;
     ServeRes& r = S->h_res[slot];
     if (*(volatile u64*)&r.done != ticket) {
-        // a server launch that ended after admitting this request without
-        // finishing it failed (a bounded wait expired or a CUDA error)
-        if (!server_running(S) && *(volatile u64*)S->h_admitted > it->second.ring_pos &&
-            *(volatile u64*)&r.done != ticket) {
+        // published while a server launch ran that then failed (a bounded
+        // wait expired or a CUDA error), and not finished by it
+        if (!server_running(S) && it->second.ring_pos < S->failed_upto && *(volatile u64*)&r.done != ticket) {
             S->active.erase(it);
             S->free_slots.push_back(slot);
-            return S->last_error ? S->last_error : MCS_ERR_DEVICE_STALL;
+            out->size = 0;
+            out->status = S->last_error ? S->last_error : MCS_ERR_DEVICE_STALL;
+            out->npairs = 0;
+            out->nodes = 0;
+            out->seconds = 0.0;
+            return out->status;
         }
         return MCS_PENDING;
     }

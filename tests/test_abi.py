@@ -46,6 +46,7 @@ def test_strerror_and_argument_checks_without_gpu():
     assert lib.mcs_set_launch(None, 4, 0, 0) == m.MCS_ERR_ARG
     assert lib.mcs_set_search_group(None, 8) == m.MCS_ERR_ARG
     assert lib.mcs_set_steal(None, 16, 2) == m.MCS_ERR_ARG
+    assert lib.mcs_set_fault(None, m.MCS_FAULT_ALLOC, 1) == m.MCS_ERR_ARG
 
 
 def test_create_without_device_returns_null():

@@ -83,10 +83,48 @@ def test_features_equal_reference(solver):
         assert np.array_equal(out[i, 0, :20], mlp.vertex_features(p.G.adj, directed=True).astype(np.float32))
 
 
-def test_forward_and_gradient_match_reference(solver):
+U16 = 2.0 ** -11          # unit roundoff of fp16
+
+
+def _grad_tolerance(theta, x, y, w):
+    """Element-wise tolerance of the device gradient against the fp64
+    reference, from the device's arithmetic.  The backward pass rounds dz2 and
+    dz1 to fp16 (unit roundoff u = 2^-11) and accumulates in fp32, so each
+    gradient element g_i = sum_r t_ri can differ by a few u times
+    A_i = sum_r |t_ri| (the absolute-sum of its terms; for W1 and b1 the terms
+    of dz1 are bounded by sum_o |dz2| |W2|).  The bound is 16 u A_i.  A
+    pre-activation that lies within fp32 rounding of zero (|z| <= 2^-18 times
+    the absolute-sum of its own terms) may take either ReLU branch on the
+    device; such rows add their full term F_i to the bound (none is expected
+    on these inputs, but the bound must not depend on luck)."""
+    W1, b1, W2, b2, w3, b3 = mlp.unpack(theta)
+    B = len(y)
+    s, (x, z1, h1, z2, h2) = mlp.forward(theta, x, round_h1_fp16=True)
+    ds = w * (1.0 / (1.0 + np.exp(-s)) - y) / B
+    near1 = np.abs(z1) <= 2.0 ** -18 * (np.abs(x) @ np.abs(W1) + np.abs(b1))
+    near2 = np.abs(z2) <= 2.0 ** -18 * (np.abs(h1) @ np.abs(W2) + np.abs(b2))
+    full2 = np.abs(np.outer(ds, w3))                     # |dz2| on either branch
+    adz2 = full2 * ((z2 > 0) | near2)
+    fl2 = full2 * near2                                  # terms a flipped z2 mask adds or drops
+    full1 = adz2 @ np.abs(W2).T                          # bound of |dz1| on either branch
+    adz1 = full1 * ((z1 > 0) | near1)
+    fl1 = full1 * near1 + (fl2 @ np.abs(W2).T) * ((z1 > 0) | near1)
+    ax, ah1, ah2, ads = np.abs(x), np.abs(h1), np.abs(h2), np.abs(ds)
+    A = np.concatenate([(ax.T @ adz1).ravel(), adz1.sum(0), (ah1.T @ adz2).ravel(), adz2.sum(0),
+                        ah2.T @ ads, [ads.sum()]])
+    F = np.concatenate([(ax.T @ fl1).ravel(), fl1.sum(0), (ah1.T @ fl2).ravel(), fl2.sum(0),
+                        np.zeros(mlp.H), [0.0]])
+    return 16.0 * U16 * A + F, int(near1.sum() + near2.sum())
+
+
+@pytest.mark.parametrize("npairs,per_pair", [(6, 60), (16, 70)])
+def test_forward_and_gradient_match_reference(solver, npairs, per_pair):
+    """Logits, loss and every gradient element of the tensor-core backward
+    against oracle/mlp.py on the same fp16-rounded parameters: 360 rows (three
+    128-row tiles, the last ragged) and 1,120 rows (nine tiles)."""
     from paper_1908_06418_b300 import DeviceBatch
-    pairs = _pairs(6, 21)
-    rows, y = _rows(pairs, 60, 5)
+    pairs = _pairs(npairs, 21 + npairs)
+    rows, y = _rows(pairs, per_pair, 5 + npairs)
     w = np.random.default_rng(3).uniform(0.5, 2.0, len(y)).astype(np.float32)
     theta = (mlp.init_params(9) + np.random.default_rng(4).normal(0, 0.02, mlp.N_PARAMS))
     theta[mlp.D_IN * mlp.H:mlp.D_PAD * mlp.H] = 0.0       # padded inputs stay zero
@@ -101,14 +139,15 @@ def test_forward_and_gradient_match_reference(solver):
     assert np.max(np.abs(got["scores"] - s_ref)) <= 2e-3 * max(1.0, np.max(np.abs(s_ref)))
     assert abs(got["loss"] - loss_ref) <= 1e-3 * abs(loss_ref) + 1e-5
     g = got["grad"].astype(np.float64)
-    # backward keeps dz in fp16: agreement to ~1e-2 relative, blockwise
-    blocks = [(0, mlp.D_PAD * mlp.H), (mlp.D_PAD * mlp.H, mlp.H), (mlp.D_PAD * mlp.H + mlp.H, mlp.H * mlp.H),
-              (mlp.D_PAD * mlp.H + mlp.H + mlp.H * mlp.H, mlp.H),
-              (mlp.N_PARAMS - mlp.H - 1, mlp.H), (mlp.N_PARAMS - 1, 1)]
-    for o, n in blocks:
-        ref = g_ref[o:o + n]
-        err = np.linalg.norm(g[o:o + n] - ref)
-        assert err <= 1e-2 * np.linalg.norm(ref) + 1e-7, (o, n, err, np.linalg.norm(ref))
+    tol, nflip = _grad_tolerance(th, x, y.astype(np.float64), w.astype(np.float64))
+    err = np.abs(g - g_ref)
+    bad = np.nonzero(err > tol + 1e-12)[0]
+    print(f"\ngradient: {len(g)} elements, max err/tol {np.max(err / (tol + 1e-30)):.3f}, "
+          f"boundary units {nflip}")
+    assert len(bad) == 0, [(int(i), g[i], g_ref[i], tol[i]) for i in bad[:8]]
+    # the comparison is not vacuous: the tolerance is small against the gradient itself
+    big = np.abs(g_ref) > 1e-3 * np.max(np.abs(g_ref))
+    assert np.median(tol[big] / np.abs(g_ref[big])) < 0.05
 
 
 def test_forward_many_tiles_matches_reference(solver):
@@ -190,26 +229,111 @@ def test_learned_order_stays_exact(solver, directed, labelled):
         assert oracle.verify(p.G.adj, p.H.adj, b.g_idx, b.h_idx, p.G.labels, p.H.labels) == 1
 
 
-def test_trained_network_gain_is_measured(solver, capsys):
-    """What the trained network changes: the learned candidate order must give
-    the same (exact) sizes; it is reported here with its node counts.  On the
-    planted-core bounded-valence family the difference stays within the
-    run-to-run spread of the parallel search (a few per cent either way): the
-    proof of optimality dominates these searches, and a candidate order cannot
-    shorten a proof that must visit every node above the bound."""
+def _golden(name):
+    import json
     import os
-    from paper_1908_06418_b300 import MCS_ORDER_LEARNED
+    import sys
+    here = os.path.dirname(os.path.abspath(__file__))
+    path = os.path.join(here, "golden", name)
+    if not os.path.exists(path):
+        pytest.skip(f"{name} not generated")
+    sys.path.insert(0, os.path.join(here, "golden"))
+    from make_oracle_golden import pair_digest
+    return [json.loads(x) for x in open(path)], pair_digest
+
+
+def _model(name):
+    import os
     path = os.path.join(os.path.dirname(os.path.dirname(os.path.abspath(__file__))),
-                        "paper_1908_06418_b300", "data", "order_mlp_planted.npy")
-    solver.set_order_model(np.load(path).astype(np.float32))
+                        "paper_1908_06418_b300", "data", name)
+    return np.load(path).astype(np.float32)
+
+
+@pytest.mark.parametrize("model", ["order_mlp_bvg.npy", "order_mlp_planted.npy"])
+@pytest.mark.parametrize("workload", ["directed", "labelled", "undirected"])
+def test_trained_network_order_matches_the_oracle(solver, model, workload):
+    """The shipped, trained ordering networks drive the search
+    (MCS_ORDER_LEARNED) and every proven size equals the CPU oracle's, with
+    verified mappings: the 96 directed G(36, p) hard pairs and 1,024 of the
+    labelled batch (stored oracle optima), and undirected unlabelled pairs
+    (64 G(20, 0.3) pairs solved by the oracle here, plus the stored planted-
+    core pairs when present)."""
+    from paper_1908_06418_b300 import MCS_ORDER_LEARNED
+    solver.set_order_model(_model(model))
+    solver.reset_launch()
+    if workload == "directed":
+        rows, digest = _golden("c2_oracle.jsonl")
+        pairs = synth.config2_pairs()[:96]
+        want = [(r["size"], r["complete"]) for r in rows[:96]]
+        assert all(r["digest"] == digest(p) for r, p in zip(rows, pairs))
+    elif workload == "labelled":
+        rows, digest = _golden("c3_oracle.jsonl")
+        allp = synth.config3_pairs()
+        idx = list(range(0, 4096, 4))
+        pairs = [allp[i] for i in idx]
+        want = [(rows[i]["size"], rows[i]["complete"]) for i in idx]
+        assert all(rows[i]["digest"] == digest(allp[i]) for i in idx[:64])
+    else:
+        pairs = synth.config1_like(64)
+        want = [(oracle.mcs(p.G.adj, p.H.adj).size, True) for p in pairs]
+        try:
+            rows, digest = _golden("planted_oracle.jsonl")
+        except pytest.skip.Exception:
+            rows = []
+        for r in rows[:64]:
+            p = synth.planted_bvg_pair(r["idx"], 24, 34, cid=47)
+            assert r["digest"] == digest(p)
+            pairs.append(p)
+            want.append((r["size"], r["complete"]))
+    directed = workload == "directed"
+    res = solver.solve_batch(pairs, flags=MCS_ORDER_LEARNED, directed=directed, timeout_s=300)
+    compared = 0
+    for i, (p, r, (k, complete)) in enumerate(zip(pairs, res, want)):
+        assert r.status == 0, (i, r.status)
+        assert oracle.verify(p.G.adj, p.H.adj, r.g_idx, r.h_idx, p.G.labels, p.H.labels) == 1, i
+        if complete:
+            assert r.size == k, (i, r.size, k)
+            compared += 1
+        else:
+            assert r.size >= k, (i, r.size, k)
+    assert compared >= 0.9 * len(pairs)
+
+
+def test_trained_network_effect_is_measured(solver, capsys):
+    """What the trained network changes, measured: the 160 held-out
+    planted-core pairs (n 24-34) are solved three times with the degree order
+    and three times with the learned order; sizes must be identical (and equal
+    the stored oracle optima when present), and the median summed node count
+    of each order is printed with its spread.  The multi-searcher node count
+    varies from run to run (the parallel search finds incumbents at different
+    times), so one run proves nothing either way; the measured median ratio is
+    recorded beside the network in the design notes.  This test asserts
+    exactness only: it does not claim a gain."""
+    from paper_1908_06418_b300 import MCS_ORDER_LEARNED
+    solver.set_order_model(_model("order_mlp_planted.npy"))
+    solver.reset_launch()
     pairs = [synth.planted_bvg_pair(i, 24, 34, cid=47) for i in range(160)]
-    plain = solver.solve_batch(pairs, timeout_s=60)
-    learned = solver.solve_batch(pairs, flags=MCS_ORDER_LEARNED, timeout_s=60)
-    assert all(a.status == b.status == 0 for a, b in zip(plain, learned))
-    assert [a.size for a in plain] == [b.size for b in learned]
-    n_plain = sum(r.nodes for r in plain)
-    n_learned = sum(r.nodes for r in learned)
+    want = None
+    try:
+        rows, digest = _golden("planted_oracle.jsonl")
+        want = {r["idx"]: r["size"] for r in rows if r["complete"]}
+    except pytest.skip.Exception:
+        pass
+    tot = {"plain": [], "learned": []}
+    sizes = None
+    for rep in range(3):
+        for name, flags in (("plain", 0), ("learned", MCS_ORDER_LEARNED)):
+            res = solver.solve_batch(pairs, flags=flags, timeout_s=60)
+            assert all(r.status == 0 for r in res)
+            sz = [r.size for r in res]
+            if sizes is None:
+                sizes = sz
+            assert sz == sizes, name
+            tot[name].append(sum(r.nodes for r in res))
+    if want:
+        for i, k in want.items():
+            assert sizes[i] == k, (i, sizes[i], k)
+    mp, ml = float(np.median(tot["plain"])), float(np.median(tot["learned"]))
     with capsys.disabled():
-        print(f"\nlearned order: {n_learned} nodes vs {n_plain} plain "
-              f"({100.0 * (n_learned / n_plain - 1):+.1f} %)")
-    assert n_learned <= 1.10 * n_plain
+        print(f"\nlearned order: median {ml:.4g} nodes (runs {tot['learned']}) vs plain {mp:.4g} "
+              f"(runs {tot['plain']}): {100.0 * (ml / mp - 1):+.1f} %")

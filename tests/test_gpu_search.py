@@ -4,6 +4,7 @@ Sizes must match bit-exactly; every returned mapping must pass the oracle's
 verifier (several optimal mappings may exist, so mappings are verified rather
 than compared)."""
 import json
+import sys
 import os
 
 import numpy as np
@@ -11,6 +12,7 @@ import pytest
 
 import oracle
 import synth
+from paper_1908_06418_b300 import MCS_MAX_N
 
 pytestmark = pytest.mark.gpu
 HERE = os.path.dirname(os.path.abspath(__file__))
@@ -163,7 +165,7 @@ def test_invalid_inputs_are_reported_per_pair(solver):
     bad_entry = good.G.adj.copy(); bad_entry[0, 1] = 2; bad_entry[1, 0] = 2
     asym = good.G.adj.copy(); asym[0, 1] = 1 - asym[1, 0]
     neg = np.full(20, -1, np.int32)
-    big = np.zeros((65, 65), np.uint8)
+    big = np.zeros((MCS_MAX_N + 1, MCS_MAX_N + 1), np.uint8)      # more vertices than any path takes
     pairs = [(good.G.adj, good.H.adj, None, None), (bad_entry, good.H.adj, None, None),
              (asym, good.H.adj, None, None), (good.G.adj, good.H.adj, neg, None),
              (big, good.H.adj, None, None), (good.G.adj, good.H.adj, None, None)]
@@ -258,13 +260,13 @@ def test_graph_replay_matches_direct_launch(solver):
     def run(flags):
         o = [torch.full((n,), -9, dtype=torch.int32, device=b.device) for _ in range(2)]
         nodes = torch.zeros(n, dtype=torch.int64, device=b.device)
-        mp = torch.zeros(n * 64, dtype=torch.int16, device=b.device)
+        mp = torch.zeros(n * MCS_MAX_N, dtype=torch.int16, device=b.device)
         rc = solver.solve_batch_device(n, b.d_n, b.d_adj_off, b.d_adj, b.d_lab_off, b.d_labels,
                                        o[0], o[1], nodes, mp, flags=flags, timeout_s=60,
                                        stream=stream.cuda_stream)
         stream.synchronize()
         assert rc == 0
-        return o[0].cpu().numpy(), o[1].cpu().numpy(), mp.cpu().numpy().reshape(n, 64)
+        return o[0].cpu().numpy(), o[1].cpu().numpy(), mp.cpu().numpy().reshape(n, MCS_MAX_N)
 
     s0, st0, _ = run(0)
     for rep in range(3):
@@ -403,13 +405,13 @@ def test_full_workload_in_the_tuned_launch_shape(solver, workload):
             size = torch.zeros(n, dtype=torch.int32, device=b.device)
             status = torch.zeros(n, dtype=torch.int32, device=b.device)
             nodes = torch.zeros(n, dtype=torch.int64, device=b.device)
-            mp = torch.zeros(n * 64, dtype=torch.int16, device=b.device)
+            mp = torch.zeros(n * MCS_MAX_N, dtype=torch.int16, device=b.device)
             rc = solver.solve_batch_device(n, b.d_n, b.d_adj_off, b.d_adj, b.d_lab_off, b.d_labels,
                                            size, status, nodes, mp, flags=b.flags, timeout_s=600)
             torch.cuda.synchronize()
             assert rc == 0
             sz, st = size.cpu().numpy(), status.cpu().numpy()
-            mp = mp.cpu().numpy().reshape(n, 64)
+            mp = mp.cpu().numpy().reshape(n, MCS_MAX_N)
             for j, i in enumerate(idx):
                 g = rows[i]
                 assert st[j] == 0, (i, st[j])
@@ -446,14 +448,14 @@ def test_bounded_valence_batch_in_the_tuned_launch_shape(solver, learned):
         size = torch.zeros(n, dtype=torch.int32, device=b.device)
         status = torch.zeros(n, dtype=torch.int32, device=b.device)
         nodes = torch.zeros(n, dtype=torch.int64, device=b.device)
-        mp = torch.zeros(n * 64, dtype=torch.int16, device=b.device)
+        mp = torch.zeros(n * MCS_MAX_N, dtype=torch.int16, device=b.device)
         rc = solver.solve_batch_device(n, b.d_n, b.d_adj_off, b.d_adj, b.d_lab_off, b.d_labels,
                                        size, status, nodes, mp,
                                        flags=b.flags | (MCS_ORDER_LEARNED if learned else 0), timeout_s=0.2)
         torch.cuda.synchronize()
         assert rc in (MCS_OK, MCS_TIMEOUT)
         sz, st = size.cpu().numpy(), status.cpu().numpy()
-        mp = mp.cpu().numpy().reshape(n, 64)
+        mp = mp.cpu().numpy().reshape(n, MCS_MAX_N)
         assert set(np.unique(st)) <= {MCS_OK, MCS_TIMEOUT}
         for j, p in enumerate(pairs):
             gi = np.nonzero(mp[j] >= 0)[0]
@@ -462,6 +464,61 @@ def test_bounded_valence_batch_in_the_tuned_launch_shape(solver, learned):
             if not learned:
                 first = oracle.mcs(p.G.adj, p.H.adj, node_limit=65).size
                 assert sz[j] >= first, (j, sz[j], first)
+    finally:
+        solver.reset_launch()
+
+
+@pytest.mark.parametrize("learned", [False, True])
+def test_bounded_valence_planted_core_exact_in_the_tuned_launch_shape(solver, learned):
+    """The exact check of the bounded-valence workload: 96 pairs of the same
+    family and sizes (n 40-64, 3-regular or mesh structure, undirected,
+    unlabelled) whose graphs share a planted common induced core of 90 % of n,
+    the way the ARG mcsXX pairs are built.  The oracle proved their optima
+    (stored); the GPU solves them in the launch shape the bench applies to the
+    bounded-valence batch (4-lane searchers), with the degree order and with
+    the trained network's order, and every size it proves must equal the
+    oracle's, with a verified mapping."""
+    import torch
+    from paper_1908_06418_b300 import DeviceBatch, MCS_OK, MCS_ORDER_LEARNED
+    rows = _golden("c4p_oracle.jsonl")
+    sys.path.insert(0, os.path.join(HERE, "golden"))
+    from make_oracle_golden import c4p_pairs, pair_digest
+    pairs = c4p_pairs()
+    for r in rows:
+        assert r["digest"] == pair_digest(pairs[r["idx"]])
+    if learned:
+        solver.set_order_model(np.load(os.path.join(os.path.dirname(HERE), "paper_1908_06418_b300", "data",
+                                                    "order_mlp_bvg.npy")).astype(np.float32))
+    try:
+        e = solver.apply_tuned(synth.config4_pairs(8))
+        assert e is not None and e["search_group"] == 4
+        b = DeviceBatch(pairs)
+        n = len(pairs)
+        size = torch.zeros(n, dtype=torch.int32, device=b.device)
+        status = torch.zeros(n, dtype=torch.int32, device=b.device)
+        nodes = torch.zeros(n, dtype=torch.int64, device=b.device)
+        mp = torch.zeros(n * MCS_MAX_N, dtype=torch.int16, device=b.device)
+        rc = solver.solve_batch_device(n, b.d_n, b.d_adj_off, b.d_adj, b.d_lab_off, b.d_labels,
+                                       size, status, nodes, mp,
+                                       flags=b.flags | (MCS_ORDER_LEARNED if learned else 0), timeout_s=120)
+        torch.cuda.synchronize()
+        assert rc in (0, 1)
+        sz, st = size.cpu().numpy(), status.cpu().numpy()
+        mp = mp.cpu().numpy().reshape(n, MCS_MAX_N)
+        compared = 0
+        for r in rows:
+            j = r["idx"]
+            p = pairs[j]
+            gi = np.nonzero(mp[j] >= 0)[0]
+            assert len(gi) == sz[j], j
+            assert oracle.verify(p.G.adj, p.H.adj, gi, mp[j][gi]) == 1, j
+            if r["complete"] and st[j] == MCS_OK:
+                assert sz[j] == r["size"], (j, sz[j], r["size"])
+                compared += 1
+            elif st[j] == MCS_OK:
+                assert sz[j] >= r["size"], (j, sz[j], r["size"])
+        proven = sum(1 for r in rows if r["complete"])
+        assert compared >= 0.95 * proven, (compared, proven)
     finally:
         solver.reset_launch()
 

@@ -1,6 +1,8 @@
 """Searchers narrower than a warp (16, 8, 4 or 2 lanes: two to sixteen independent
 depth-first searches per warp) against the CPU oracle: sizes bit-exact,
-mappings verified, and a lone searcher walks the oracle's search tree."""
+mappings verified, and a lone searcher walks the oracle's search tree.  Every
+test runs in both ways the searchers of a warp can share it: in lockstep (one
+predicated node step for all of them per pass) and free-running."""
 import numpy as np
 import pytest
 
@@ -10,13 +12,14 @@ import synth
 pytestmark = pytest.mark.gpu
 
 
-@pytest.fixture(scope="module")
-def solver():
+@pytest.fixture(scope="module", params=["lockstep", "free"])
+def solver(request):
     import torch
     if not torch.cuda.is_available():
         pytest.skip("no CUDA device")
-    from paper_1908_06418_b300 import Solver
+    from paper_1908_06418_b300 import Solver, MCS_MODE_LOCKSTEP, MCS_MODE_FREE
     s = Solver(0)
+    s.set_search_mode(MCS_MODE_LOCKSTEP if request.param == "lockstep" else MCS_MODE_FREE)
     yield s
     s.close()
 
