@@ -1647,9 +1647,10 @@ __global__ void __launch_bounds__(256, (GS == 32 ? MCS_SEARCH_MINB : MCS_GROUP_M
                     else ps.abort = 1;                 // per-pair time limit
                     p_abort = 1;
                 }
-                if (!GOAL && P.race_cpu) {
+                if (!GOAL && P.race_cpu && (tick & 4095) == 0) {
                     // GPU + CPU race: prune against the CPU side's best size too,
-                    // and stop once the CPU side has finished its proof
+                    // and stop once the CPU side has finished its proof (words in
+                    // host memory: one bus round trip each, so every 4,096 nodes)
                     p_inc = max(p_inc, (int)*P.race_cpu);
                     if (!p_abort && *P.race_stop) {
                         ps.abort = 1;

@@ -90,16 +90,17 @@ def _c5_golden():
 
 
 def test_served_stream_matches_the_oracle_over_the_whole_size_range(solver):
-    """The first 800 requests of the serving stream itself (n log-uniform in
-    16..56, 0-8 label classes), served together in waves with the oracle's
-    own 60 s budget per request: every request the oracle proved (stored) is
-    proven by the server with the same size and a verified mapping, including
-    requests of 37..56 vertices;
-    requests the oracle could not prove are verified and, when proven, at
-    least its best size.  The proven requests of 37 or more vertices are then
+    """The requests among the first 800 of the serving stream itself (n
+    log-uniform in 16..56, 0-8 label classes) that the oracle proved within
+    60 s -- 710, 375 of them with more than 36 vertices -- served together in
+    waves with the oracle's own 60 s budget per request: each is proven by
+    the server with the same size and a verified mapping.  (The 90 requests
+    the oracle could not prove would hold searchers for the whole limit and
+    say nothing exact.)  The proven requests of 37 or more vertices are then
     served again one at a time: alone equals in the mix."""
-    from paper_1908_06418_b300 import MCS_OK, MCS_TIMEOUT
+    from paper_1908_06418_b300 import MCS_OK
     rows, pairs = _c5_golden()
+    rows = [r for r in rows if r["complete"]]
     tickets = []
     for i in range(0, len(rows), 100):
         for r in rows[i:i + 100]:
@@ -107,25 +108,19 @@ def test_served_stream_matches_the_oracle_over_the_whole_size_range(solver):
             tickets.append(solver.submit(p.G.adj, p.H.adj, p.G.labels, p.H.labels, timeout_s=60))
         time.sleep(0.005)
     served = _wait(solver, tickets, limit_s=900)
-    compared = big = 0
+    big = 0
     for r, res in zip(rows, served):
         p = pairs[r["idx"]]
-        assert res.status in (MCS_OK, MCS_TIMEOUT), (r["idx"], res.status)
+        assert res.status == MCS_OK, (r["idx"], res.status)
+        assert res.size == r["size"], (r["idx"], res.size, r["size"])
         assert oracle.verify(p.G.adj, p.H.adj, res.g_idx, res.h_idx, p.G.labels, p.H.labels) == 1
-        if r["complete"]:
-            assert res.status == MCS_OK, (r["idx"], res.status)
-            assert res.size == r["size"], (r["idx"], res.size, r["size"])
-            compared += 1
-            big += int(max(p.G.n, p.H.n) > 36)
-        elif res.status == MCS_OK:
-            assert res.size >= r["size"], (r["idx"], res.size, r["size"])
-    assert compared >= 0.9 * len(rows)
-    assert big >= 20, big
+        big += int(max(p.G.n, p.H.n) > 36)
+    assert big >= 300, big
     alone_rows = [(r, res) for r, res in zip(rows, served)
-                  if r["complete"] and max(pairs[r["idx"]].G.n, pairs[r["idx"]].H.n) > 36][:40]
+                  if max(pairs[r["idx"]].G.n, pairs[r["idx"]].H.n) > 36][:40]
     for r, res in alone_rows:
         p = pairs[r["idx"]]
-        t = solver.submit(p.G.adj, p.H.adj, p.G.labels, p.H.labels, timeout_s=20)
+        t = solver.submit(p.G.adj, p.H.adj, p.G.labels, p.H.labels, timeout_s=60)
         a = _wait(solver, [t])[0]
         assert a.status == MCS_OK and a.size == res.size == r["size"]
 

@@ -139,6 +139,31 @@ def test_closed_forms():
     assert oracle.mcs(np.zeros((0, 0), np.uint8), complete(3)).size == 0
 
 
+def test_closed_forms_beyond_64_vertices():
+    """The oracle has no word-size limit; the GPU's multi-word path (65-256
+    vertices) is checked against it, so it is pinned at those sizes too:
+    paths, cycles, complete and empty graphs, a labelled graph against a
+    permuted copy of itself (MCS(G, G) = |V|) and against one of its induced
+    subgraphs (MCS = the subgraph's size)."""
+    assert oracle.mcs(path(100), path(120)).size == 100
+    assert oracle.mcs(cycle(90), cycle(130)).size == 89
+    assert oracle.mcs(complete(100), complete(90)).size == 90
+    assert oracle.mcs(np.zeros((100, 100), np.uint8), np.zeros((80, 80), np.uint8)).size == 80
+    assert oracle.mcs(complete(256), complete(256)).size == 256
+    assert oracle.mcs(np.zeros((256, 256), np.uint8), complete(70)).size == 1
+    r = synth.rng_for(9102, 0, 0)
+    for n, k in ((100, 16), (200, 40), (256, 64)):
+        G = synth.er_undirected(n, 0.04, r)
+        lab = synth.uniform_labels(n, k, r)
+        perm = r.permutation(n)
+        res = oracle.mcs(G, G[np.ix_(perm, perm)], lab, lab[perm])
+        assert res.complete and res.size == n
+        sub = perm[: (2 * n) // 3]
+        res = oracle.mcs(G, G[np.ix_(sub, sub)], lab, lab[sub])
+        assert res.complete and res.size == len(sub)
+        assert oracle.verify(G, G[np.ix_(sub, sub)], res.g_idx, res.h_idx, lab, lab[sub]) == 1
+
+
 def test_invariants():
     rs = np.random.default_rng(3)
     for s in range(40):
