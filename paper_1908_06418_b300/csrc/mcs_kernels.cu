@@ -541,6 +541,14 @@ __device__ __forceinline__ u64 adj_row(const u64* rows, int i) {
     else if constexpr (COHERENT) return __ldcg(rows + i);
     else return __ldg(rows + i);
 }
+// Both rows {out, in} of a vertex in one 16-byte load (i = row_gout or row_hout).
+template <bool SM, bool COHERENT = false>
+__device__ __forceinline__ ulonglong2 adj_row_pair(const u64* rows, int i) {
+    const ulonglong2* p = reinterpret_cast<const ulonglong2*>(rows + i);
+    if constexpr (SM) return *p;
+    else if constexpr (COHERENT) return __ldcg(p);
+    else return __ldg(p);
+}
 
 __device__ __forceinline__ u64 pack_info(int base, int C, int v, int flags, int bound) {
     return (u64)base | ((u64)C << 16) | ((u64)v << 24) | ((u64)flags << 32) | ((u64)bound << 40);
@@ -605,24 +613,28 @@ __device__ __forceinline__ Scan scan_level(const Grp<GS>& g, const Stack& st, in
     unsigned best = kKeyNone;
     W bestR = 0;
     const W vb = remove_v >= 0 ? ((W)1 << remove_v) : (W)0;
-    for (int i0 = 0; i0 < C; i0 += GS) {
-        const int i = i0 + g.q;
-        if (i < C) {
-            ulonglong2* ptr = st.at(base + i);
-            const ulonglong2 c = *ptr;
-            W L = (W)c.x;
-            const W R = (W)c.y;
-            if (L & vb) {
-                L &= ~vb;
-                ptr->x = L;
-            }
-            if (L) {
-                const int a = Word<W>::popc(L), b = Word<W>::popc(R);
-                sum += min(a, b);
-                const unsigned key = ((unsigned)max(a, b) << 6) | (unsigned)Word<W>::low(L);
-                if (key < best) { best = key; bestR = R; }
-            }
+    auto one = [&](int i, bool have) {
+        ulonglong2* ptr = st.at(base + (have ? i : 0));
+        const ulonglong2 c = *ptr;
+        W L = have ? (W)c.x : (W)0;
+        const W R = have ? (W)c.y : (W)0;
+        if (L & vb) {
+            L &= ~vb;
+            ptr->x = L;
         }
+        if (L) {
+            const int a = Word<W>::popc(L), b = Word<W>::popc(R);
+            sum += min(a, b);
+            const unsigned key = ((unsigned)max(a, b) << 6) | (unsigned)Word<W>::low(L);
+            if (key < best) { best = key; bestR = R; }
+        }
+    };
+    // slot 0 straight-line (lanes beyond the class count read entry 0 of the
+    // level and contribute nothing), further slots when classes outnumber lanes
+    one(g.q, g.q < C);
+    for (int i0 = GS; i0 < C; i0 += GS) {
+        const int i = i0 + g.q;
+        if (i < C) one(i, true);
     }
     Scan r;
     r.sum = g.add(sum);
@@ -1262,6 +1274,15 @@ __global__ void __launch_bounds__(256, (GS == 32 ? MCS_SEARCH_MINB : MCS_GROUP_M
     const int sid = (blockIdx.x * (blockDim.x >> 5) + wib) * GPW + (lane / GS);
     if (sid >= P.max_warps) return;
     constexpr bool ADJ_SM = adj_in_smem(GS);
+    // Choose a surviving child's branching class in the pass that writes its
+    // classes (lazy) or while summing Eq. 1 for every child (eager).
+#if defined(MCS_KEYS_MODE) && MCS_KEYS_MODE == 0
+    constexpr bool LAZY_KEYS = true;
+#elif defined(MCS_KEYS_MODE) && MCS_KEYS_MODE == 1
+    constexpr bool LAZY_KEYS = false;
+#else
+    constexpr bool LAZY_KEYS = DIR;
+#endif
     unsigned char* base = smem + (size_t)(wib * GPW + lane / GS) * P.warp_smem_bytes;
     unsigned char* lv = base + sm_adj_bytes(GS);       // level arrays and class cache
     WarpSmem w;
@@ -1487,10 +1508,15 @@ __global__ void __launch_bounds__(256, (GS == 32 ? MCS_SEARCH_MINB : MCS_GROUP_M
                 cvisits += t.C;
                 const int v = t.v;
                 const W vb = (W)1 << v, ub = (W)1 << u;
-                const W gB = (W)adj_row<ADJ_SM, SERVE>(w.adj, row_gout(v));
-                const W hB = (W)adj_row<ADJ_SM, SERVE>(w.adj, row_hout(u));
-                const W gA = DIR ? (W)adj_row<ADJ_SM, SERVE>(w.adj, row_gin(v)) : (W)0;
-                const W hA = DIR ? (W)adj_row<ADJ_SM, SERVE>(w.adj, row_hin(u)) : (W)0;
+                W gB, hB, gA = 0, hA = 0;
+                if constexpr (DIR) {
+                    const ulonglong2 gv = adj_row_pair<ADJ_SM, SERVE>(w.adj, row_gout(v));
+                    const ulonglong2 hu = adj_row_pair<ADJ_SM, SERVE>(w.adj, row_hout(u));
+                    gB = (W)gv.x; gA = (W)gv.y; hB = (W)hu.x; hA = (W)hu.y;
+                } else {
+                    gB = (W)adj_row<ADJ_SM, SERVE>(w.adj, row_gout(v));
+                    hB = (W)adj_row<ADJ_SM, SERVE>(w.adj, row_hout(u));
+                }
                 const int dm = t.d + 1;
                 const int cbase = t.base + t.C;
                 // parent and child both inside the shared-memory class cache:
@@ -1501,56 +1527,77 @@ __global__ void __launch_bounds__(256, (GS == 32 ? MCS_SEARCH_MINB : MCS_GROUP_M
                 W bestR = 0;
                 int pos = cbase;
                 // Appends the part (l, r) to the child level when both sides are
-                // non-empty (group-wide ballot compaction, order kept).
+                // non-empty (group-wide ballot compaction, order kept), and
+                // offers it as the child's branching class: key max(|l|, |r|)
+                // << 6 | lowest l vertex, the smallest key wins.
                 auto emit = [&](W l, W r, bool keep) {
                     const unsigned mk = g.ballot(keep);
                     if (keep) {
                         const int q2 = pos + __popc(mk & g.lt());
                         if (in_sm) st.sm[q2] = make_ulonglong2((u64)l, (u64)r);
                         else *st.at(q2) = make_ulonglong2((u64)l, (u64)r);
+                        if constexpr (LAZY_KEYS) {
+                            const unsigned key = ((unsigned)max(Word<W>::popc(l), Word<W>::popc(r)) << 6) |
+                                                 (unsigned)Word<W>::low(l);
+                            if (key < best) { best = key; bestR = r; }
+                        }
                     }
                     pos += __popc(mk);
                 };
-                // The child's classes are written only once it survives Eq. 1, in
-                // a second pass over the classes kept in registers (both slots of
-                // a whole warp, slot 0 of a narrow searcher; further slots of a
-                // narrow searcher are re-read).
+                // The child's classes are written, and its branching class chosen,
+                // only once it survives Eq. 1 (55-60 % of children do not), in a
+                // second pass over the classes kept in registers (both slots of a
+                // whole warp, slot 0 of a narrow searcher; further slots of a
+                // narrow searcher are re-read).  The first pass only sums Eq. 1.
                 W Ls[2], Rs[2];
-    #pragma unroll (GS == 32 ? 2 : 1)
-                for (int sl = 0; sl < kMaxN / GS; ++sl) {
-                    const int i0 = sl * GS;
-                    if (i0 >= t.C) break;
-                    const int i = i0 + g.q;
+                // Eq. 1 terms of one class slot: min(|L'|, |R'|) over its parts
+                // (with eager keys the branching class is chosen here as well;
+                // with lazy keys only survivors choose it, in the second pass)
+                auto part_sum = [&](W L, W R) -> int {
+                    auto term = [&](W l, W r) -> int {
+                        const int a = Word<W>::popc(l), b = Word<W>::popc(r), m = min(a, b);
+                        if constexpr (!LAZY_KEYS) {
+                            const unsigned key = m ? (((unsigned)max(a, b) << 6) | (unsigned)Word<W>::low(l)) : kKeyNone;
+                            if (key < best) { best = key; bestR = r; }
+                        }
+                        return m;
+                    };
+                    if (DIR) {
+                        const W la = L & gA, lb = L & gB, ra = R & hA, rb = R & hB;
+                        const W lp[4] = {(W)(L & ~(la | lb)), (W)(la & ~lb), (W)(lb & ~la), (W)(la & lb)};
+                        const W rp[4] = {(W)(R & ~(ra | rb)), (W)(ra & ~rb), (W)(rb & ~ra), (W)(ra & rb)};
+                        int s4 = 0;
+    #pragma unroll
+                        for (int k = 0; k < 4; ++k) s4 += term(lp[k], rp[k]);
+                        return s4;
+                    } else {
+                        const W l1 = L & gB, r1 = R & hB;
+                        return term(l1, r1) + term((W)(L ^ l1), (W)(R ^ r1));
+                    }
+                };
+                {
+                    // slot 0, straight-line (a child's level holds at least the
+                    // class of v and u, so t.C >= 1): lanes beyond the class count
+                    // read the level's first class and contribute nothing
+                    const bool have = g.q < t.C;
+                    const int i = have ? g.q : 0;
+                    const ulonglong2 c = in_sm ? st.sm[t.base + i] : *st.at(t.base + i);
+                    const W L = have ? ((W)c.x & ~vb) : (W)0;
+                    const W R = have ? ((W)c.y & ~ub) : (W)0;
+                    Ls[0] = L;
+                    Rs[0] = R;
+                    sum += part_sum(L, R);
+                }
+                for (int sl = 1; sl * GS < t.C; ++sl) {      // further slots: more classes than lanes
+                    const int i = sl * GS + g.q;
                     W L = 0, R = 0;
                     if (i < t.C) {
                         const ulonglong2 c = in_sm ? st.sm[t.base + i] : *st.at(t.base + i);
                         L = (W)c.x & ~vb;
                         R = (W)c.y & ~ub;
                     }
-                    if constexpr (GS == 32) { Ls[sl] = L; Rs[sl] = R; }
-                    else if (sl == 0) { Ls[0] = L; Rs[0] = R; }
-                    if (DIR) {
-                        const W la = L & gA, lb = L & gB, ra = R & hA, rb = R & hB;
-                        const W lp[4] = {(W)(L & ~(la | lb)), (W)(la & ~lb), (W)(lb & ~la), (W)(la & lb)};
-                        const W rp[4] = {(W)(R & ~(ra | rb)), (W)(ra & ~rb), (W)(rb & ~ra), (W)(ra & rb)};
-    #pragma unroll
-                        for (int k = 0; k < 4; ++k) {
-                            const int a = Word<W>::popc(lp[k]), b = Word<W>::popc(rp[k]);
-                            const int m = min(a, b);
-                            sum += m;
-                            const unsigned key = m ? (((unsigned)max(a, b) << 6) | (unsigned)Word<W>::low(lp[k])) : kKeyNone;
-                            if (key < best) { best = key; bestR = rp[k]; }
-                        }
-                    } else {
-                        const W l1 = L & gB, r1 = R & hB, l0 = L ^ l1, r0 = R ^ r1;
-                        const int a1 = Word<W>::popc(l1), b1 = Word<W>::popc(r1), a0 = Word<W>::popc(l0), b0 = Word<W>::popc(r0);
-                        const int m1 = min(a1, b1), m0 = min(a0, b0);
-                        sum += m1 + m0;
-                        const unsigned k1 = m1 ? (((unsigned)max(a1, b1) << 6) | (unsigned)Word<W>::low(l1)) : kKeyNone;
-                        const unsigned k0 = m0 ? (((unsigned)max(a0, b0) << 6) | (unsigned)Word<W>::low(l0)) : kKeyNone;
-                        if (k1 < best) { best = k1; bestR = r1; }
-                        if (k0 < best) { best = k0; bestR = r0; }
-                    }
+                    if constexpr (GS == 32) { Ls[1] = L; Rs[1] = R; }
+                    sum += part_sum(L, R);
                 }
                 sum = g.add(sum);
                 // incumbent (Algorithm 1): |M u {(v,u)}| beats the best so far
@@ -1590,25 +1637,8 @@ __global__ void __launch_bounds__(256, (GS == 32 ? MCS_SEARCH_MINB : MCS_GROUP_M
                     }
                 }
                 if (dm + sum <= inc) { ++pruned; return; }    // child pruned by Eq. 1
-                const unsigned kmin = g.umin(best);
-                const unsigned win = g.ballot(best == kmin);
-                const u64 cR = g.shfl64((u64)bestR, __ffs(win) - 1);
                 // descend: compact the child's classes onto the stack
-#pragma unroll (GS == 32 ? 2 : 1)
-                for (int sl = 0; sl < kMaxN / GS; ++sl) {
-                    if (sl * GS >= t.C) break;
-                    W L = 0, R = 0;
-                    if (GS == 32 || sl == 0) {
-                        L = Ls[GS == 32 ? sl : 0];
-                        R = Rs[GS == 32 ? sl : 0];
-                    } else {
-                        const int i = sl * GS + g.q;
-                        if (i < t.C) {
-                            const ulonglong2 c = *st.at(t.base + i);
-                            L = (W)c.x & ~vb;
-                            R = (W)c.y & ~ub;
-                        }
-                    }
+                auto emit_parts = [&](W L, W R) {
                     if (DIR) {
                         const W la = L & gA, lb = L & gB, ra = R & hA, rb = R & hB;
                         const W lp[4] = {(W)(L & ~(la | lb)), (W)(la & ~lb), (W)(lb & ~la), (W)(la & lb)};
@@ -1620,7 +1650,26 @@ __global__ void __launch_bounds__(256, (GS == 32 ? MCS_SEARCH_MINB : MCS_GROUP_M
                         emit(l1, r1, l1 && r1);
                         emit(l0, r0, l0 && r0);
                     }
+                };
+                emit_parts(Ls[0], Rs[0]);                  // slot 0 from registers
+                for (int sl = 1; sl * GS < t.C; ++sl) {
+                    W L = 0, R = 0;
+                    if (GS == 32) {
+                        L = Ls[1];
+                        R = Rs[1];
+                    } else {
+                        const int i = sl * GS + g.q;
+                        if (i < t.C) {
+                            const ulonglong2 c = *st.at(t.base + i);
+                            L = (W)c.x & ~vb;
+                            R = (W)c.y & ~ub;
+                        }
+                    }
+                    emit_parts(L, R);
                 }
+                const unsigned kmin = g.umin(best);
+                const unsigned win = g.ballot(best == kmin);
+                const u64 cR = g.shfl64((u64)bestR, __ffs(win) - 1);
                 if (pos > st.S) spilled += 1;
                 if (!DBG_OK(ctl, pos - cbase <= kMaxN && dm <= kMaxN, 5, (pos - cbase) * 1000 + dm)) pos = cbase;
                 if (g.q == 0)
