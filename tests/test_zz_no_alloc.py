@@ -131,7 +131,9 @@ def test_noalloc_flags_match_the_oracle(case):
     torch.cuda.set_device(dev)
     rs = np.random.default_rng(31415)
     directed = case.startswith("directed")
-    nmax = 32 if "word32" in case else 40
+    # unlabelled pairs of more than about 30 vertices can take the CPU oracle
+    # minutes each, so the unlabelled cases stay below that
+    nmax = 28 if case in ("directed", "top-down") else 32
     k = 3 if case == "word32-labelled" else 0
     pairs = []
     for i in range(40):
