@@ -45,11 +45,12 @@ METRIC = "MCS pairs solved/sec (exact) on 1 B300"
 # the dominant search kernel, from a single-pass ncu capture of this
 # workload's launch:
 #   ncu --metrics dram__bytes_read.sum,dram__bytes_write.sum --clock-control none
-#       -k regex:search_kernel -s <warm-up launches> -c 1
-#       python bench.py --workload <w> --steps 1 --warmup 1 --no-cpu-baseline --no-single
+#       -k regex:search_kernel -s <search launches before the timed one> -c 1
+#       python bench.py --workload <w> --steps 2 --warmup 1 --no-cpu-baseline --no-single
+#       --no-batched --no-served --no-race
 # Reported only while the kernel source is the one the capture was taken with.
-TRAFFIC = {"c2": {"kernel_sha1": "de3f4df5bb2549c2", "bytes": 1.19e9 + 5.28e9},
-           "c3": {"kernel_sha1": "de3f4df5bb2549c2", "bytes": 99.89e6 + 197.09e6}}
+TRAFFIC = {"c2": {"kernel_sha1": "6422e082133504d4", "bytes": 1128680960 + 1438386688},
+           "c3": {"kernel_sha1": "6422e082133504d4", "bytes": 111085568 + 205210112}}
 UNIT = "pairs/s"
 
 

@@ -1756,8 +1756,8 @@ __global__ void __launch_bounds__(256, (GS == 32 ? MCS_SEARCH_MINB : MCS_GROUP_M
                 if (hungry && !donate<GS>(P, pair, d0, t, inc, w, st, g, donated)) break;
             }
             // level prune: every node below this level has bound <= this one
-#ifdef MCS_TIGHT_POP
-            // pop every exhausted or bounded level in one go, then expand a node
+            // pop every exhausted or bounded level in one go (without a trip
+            // through the poll checks per level), then expand a node
             if ((level_prune && t.bound <= inc) || (t.rrem == 0 && !(t.flags & kTaskPending))) {
                 do {
                     --t.d;
@@ -1766,13 +1766,6 @@ __global__ void __launch_bounds__(256, (GS == 32 ? MCS_SEARCH_MINB : MCS_GROUP_M
                 } while ((level_prune && t.bound <= inc) || (t.rrem == 0 && !(t.flags & kTaskPending)));
                 if (t.d < d0) break;
             }
-#else
-            if ((level_prune && t.bound <= inc) || (t.rrem == 0 && !(t.flags & kTaskPending))) {
-                --t.d;
-                if (t.d >= d0) load_level(w, t.d, t);
-                continue;
-            }
-#endif
             if constexpr (NARROW) node_step(uint32_t{});
             else node_step(u64{});
         }
