@@ -380,8 +380,9 @@ int mcs_set_restart(mcs_ctx* ctx, long long min_nodes, unsigned long long seed);
  * microseconds (for mcs_solve_batch_device: once its stream has passed the
  * launch, else the previous value), out[1] total nodes (host API calls only),
  * out[2] donated tasks, out[3] donated tasks taken up, out[4] child levels
- * that spilled past the shared-memory class cache (searchers narrower than a
- * warp keep the whole stack in global memory: every child level counts),
+ * that spilled past the shared-memory class cache of whole-warp searchers (0
+ * for searchers narrower than a warp, which keep the whole stack in global
+ * memory),
  * out[5] searchers launched,
  * out[6] bytes copied host to device, out[7] bytes copied device to host
  * (out[6..7]: host API calls only), out[8] label classes read by node

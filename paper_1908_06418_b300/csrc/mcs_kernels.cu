@@ -893,12 +893,12 @@ __device__ void finalize_pair(const SearchParams& P, int pair, const Grp<GS>& g,
 
 // A task of `pair` ended: publish node count, drop the open count and finalise
 // the pair if this was its last task.
-template <bool SERVE, int GS, int GOAL>
-__device__ __forceinline__ void end_task(const SearchParams& P, int pair, u64& nodes, const Grp<GS>& g,
+template <bool SERVE, int GS, int GOAL, typename N>
+__device__ __forceinline__ void end_task(const SearchParams& P, int pair, N& nodes, const Grp<GS>& g,
                                          int16_t* smap) {
     int last = 0;
     if (g.q == 0) {
-        if (nodes) atomicAdd(&P.state[pair].nodes, nodes);
+        if (nodes) atomicAdd(&P.state[pair].nodes, (u64)nodes);
         __threadfence();
         last = atomicSub(&P.state[pair].open, 1) == 1;
     }
@@ -1306,7 +1306,13 @@ __global__ void __launch_bounds__(256, (GS == 32 ? MCS_SEARCH_MINB : MCS_GROUP_M
 #endif
 
     Control* ctl = P.ctl;
-    int16_t* smap = reinterpret_cast<int16_t*>(lv + kSmLvOff);     // finalize scratch (levels unused then)
+    // finalize scratch (the level entries are unused then) and the busy / idle
+    // / mark clock words, addressed from the level entries when needed
+    // rather than held in registers through the search loop
+    auto smap = [&]() { return reinterpret_cast<int16_t*>(w.lvl); };
+    auto cyc = [&]() {
+        return reinterpret_cast<u64*>(reinterpret_cast<unsigned char*>(w.lvl) + (kSmCycOff - kSmLvOff));
+    };
     if constexpr (SERVE) {
         // warp 0 of the grid admits requests; its groups do not search
         if (blockIdx.x == 0 && wib == 0) {
@@ -1317,13 +1323,12 @@ __global__ void __launch_bounds__(256, (GS == 32 ? MCS_SEARCH_MINB : MCS_GROUP_M
     const bool level_prune = (P.flags & MCS_NO_LEVEL_PRUNE) == 0;
     const uint32_t qmask = P.qcap - 1;
     int cur_pair = -1;
-    u64 nodes = 0;
+    unsigned nodes = 0;     // of the current task; flushed to the pair before it can wrap
     unsigned tick = 0;
     // statistics, meaningful in lane 0 of the group (32-bit: flushed to the
     // control block before they can wrap, and when the searcher leaves)
-    unsigned spilled = 0, cvisits = 0, pruned = 0, donated = 0, stolen = 0;
-    u64* cyc = (u64*)(lv + kSmCycOff);                  // busy, idle clock cycles
-    if (g.q == 0) { cyc[0] = 0; cyc[1] = 0; }
+    unsigned spilled = 0, cvisits = 0, pruned = 0, donated = 0;
+    if (g.q == 0) { cyc()[0] = 0; cyc()[1] = 0; }
 
     while (true) {
         // ------------------------------------------------------------------
@@ -1377,7 +1382,7 @@ __global__ void __launch_bounds__(256, (GS == 32 ? MCS_SEARCH_MINB : MCS_GROUP_M
             if (pstat != MCS_PENDING) {                   // malformed input: report and skip
                 g.sync();
                 if (g.q == 0) { P.qseq[qh & qmask] = qh + P.qcap; ps.open = 0; }
-                finalize_pair<SERVE, GS, GOAL>(P, pair, g, smap);
+                finalize_pair<SERVE, GS, GOAL>(P, pair, g, smap());
                 continue;
             }
             if (g.q == 0) {
@@ -1423,7 +1428,7 @@ __global__ void __launch_bounds__(256, (GS == 32 ? MCS_SEARCH_MINB : MCS_GROUP_M
             for (int i = g.q; i < t.d; i += GS)
                 w.lvl[i] = make_ulonglong2(0ull, ((u64)ld_cg(&task->Mg[i]) << 24) | ((u64)ld_cg(&task->Mh[i]) << 48));
             for (int i = g.q; i < t.C; i += GS) *st.at(i) = ld_cg(&task->cls[i]);
-            ++stolen;
+            if (g.q == 0) atomicAdd(&ctl->stolen, 1ull);   // rare: counted in place
         } else {
             t.d = 0;
             t.C = __ldcg(&pg.C0);
@@ -1447,11 +1452,16 @@ __global__ void __launch_bounds__(256, (GS == 32 ? MCS_SEARCH_MINB : MCS_GROUP_M
         }
         inc = g.shfl(inc, 0);
         ab0 = g.shfl(ab0, 0);
-        const long long c_busy = clock64();
-        if (g.q == 0) cyc[1] += (u64)(c_busy - c_idle);
+        // the start of the busy period is kept in memory (cyc()[2]), not in a
+        // register that would stay live through the search loop
+        if (g.q == 0) {
+            const long long c_busy = clock64();
+            cyc()[1] += (u64)(c_busy - c_idle);
+            cyc()[2] = (u64)c_busy;
+        }
         if (ab0) {
-            end_task<SERVE, GS, GOAL>(P, pair, nodes, g, smap);
-            if (g.q == 0) cyc[0] += (u64)(clock64() - c_busy);
+            end_task<SERVE, GS, GOAL>(P, pair, nodes, g, smap());
+            if (g.q == 0) cyc()[0] += (u64)(clock64() - (long long)cyc()[2]);
             continue;
         }
         if (fresh) {
@@ -1461,8 +1471,8 @@ __global__ void __launch_bounds__(256, (GS == 32 ? MCS_SEARCH_MINB : MCS_GROUP_M
             const Scan sc = scan_level<typename std::conditional<NARROW, uint32_t, u64>::type, GS>(g, st, 0, t.C, -1);
             t.bound = sc.sum;
             if (t.bound <= inc) {
-                end_task<SERVE, GS, GOAL>(P, pair, nodes, g, smap);
-                if (g.q == 0) cyc[0] += (u64)(clock64() - c_busy);
+                end_task<SERVE, GS, GOAL>(P, pair, nodes, g, smap());
+                if (g.q == 0) cyc()[0] += (u64)(clock64() - (long long)cyc()[2]);
                 continue;
             }
             t.v = sc.key & 63;
@@ -1670,7 +1680,7 @@ __global__ void __launch_bounds__(256, (GS == 32 ? MCS_SEARCH_MINB : MCS_GROUP_M
                 const unsigned kmin = g.umin(best);
                 const unsigned win = g.ballot(best == kmin);
                 const u64 cR = g.shfl64((u64)bestR, __ffs(win) - 1);
-                if (pos > st.S) spilled += 1;
+                if (STACK_SM && pos > st.S) spilled += 1;   // narrow searchers have no shared part
                 if (!DBG_OK(ctl, pos - cbase <= kMaxN && dm <= kMaxN, 5, (pos - cbase) * 1000 + dm)) pos = cbase;
                 if (g.q == 0)
                     w.lvl[t.d] = make_ulonglong2(t.rrem, pack_info(t.base, t.C, t.v, t.flags, t.bound) | ((u64)u << 48));
@@ -1684,13 +1694,15 @@ __global__ void __launch_bounds__(256, (GS == 32 ? MCS_SEARCH_MINB : MCS_GROUP_M
                 t.bound = dm + sum;
         };
 
-        int p_inc = 0, p_abort = 0, p_hungry = 0, p_restart = 0;
+        // polled values of lane 0, packed in one word until their use:
+        // incumbent << 2 | hungry << 1 | abort
+        int p_word = 0, p_restart = 0;
         while (t.d >= d0) {
             ++tick;
             if ((tick & P.poll_mask) == 0 && g.q == 0) {
-                p_inc = vload(&ps.inc);
-                p_abort = vload(&ps.abort);
-                p_hungry = vload(&ctl->q_head) > vload(&ctl->q_tail);   // a searcher waits
+                int p_inc = vload(&ps.inc);
+                int p_abort = vload(&ps.abort);
+                const int p_hungry = vload(&ctl->q_head) > vload(&ctl->q_tail);   // a searcher waits
                 if (!p_abort && (tick & 255) == 0 && gtimer() > vload(&ps.deadline)) {
                     if constexpr (GOAL) atomicCAS(&ps.abort, 0, 1);   // time limit (a reached goal stays)
                     else ps.abort = 1;                 // per-pair time limit
@@ -1736,12 +1748,15 @@ __global__ void __launch_bounds__(256, (GS == 32 ? MCS_SEARCH_MINB : MCS_GROUP_M
                     }
                 }
                 if (cvisits >= (1u << 31)) { atomicAdd(&ctl->class_visits, (u64)cvisits); cvisits = 0; }
+                if (nodes >= (1u << 31)) { atomicAdd(&ps.nodes, (u64)nodes); nodes = 0; }
                 if (pruned >= (1u << 31)) { atomicAdd(&ctl->pruned, (u64)pruned); pruned = 0; }
+                p_word = (p_inc << 2) | (p_hungry << 1) | (p_abort != 0);
             }
             if ((tick & P.poll_mask) == (P.poll_mask + 1) / 2) {
-                const int g_inc = g.shfl(p_inc, 0);
-                const int ab = g.shfl(p_abort, 0);
-                const int hungry = g.shfl(p_hungry, 0);
+                const int pw = g.shfl(p_word, 0);
+                const int g_inc = pw >> 2;
+                const int ab = pw & 1;
+                const int hungry = (pw >> 1) & 1;
                 inc = max(inc, g_inc);
                 if (ab) break;
                 if constexpr (GOAL == 2) {
@@ -1753,7 +1768,12 @@ __global__ void __launch_bounds__(256, (GS == 32 ? MCS_SEARCH_MINB : MCS_GROUP_M
                     }
                 }
                 // ---- donate the shallowest open level to a waiting searcher ----
-                if (hungry && !donate<GS>(P, pair, d0, t, inc, w, st, g, donated)) break;
+                if (hungry) {
+                    const bool ok = donate<GS>(P, pair, d0, t, inc, w, st, g, donated);
+                    if (g.q == 0 && donated) atomicAdd(&ctl->donated, (u64)donated);   // rare: counted in place
+                    donated = 0;
+                    if (!ok) break;
+                }
             }
             // level prune: every node below this level has bound <= this one
             // pop every exhausted or bounded level in one go (without a trip
@@ -1769,17 +1789,15 @@ __global__ void __launch_bounds__(256, (GS == 32 ? MCS_SEARCH_MINB : MCS_GROUP_M
             if constexpr (NARROW) node_step(uint32_t{});
             else node_step(u64{});
         }
-        end_task<SERVE, GS, GOAL>(P, pair, nodes, g, smap);
-        if (g.q == 0) cyc[0] += (u64)(clock64() - c_busy);
+        end_task<SERVE, GS, GOAL>(P, pair, nodes, g, smap());
+        if (g.q == 0) cyc()[0] += (u64)(clock64() - (long long)cyc()[2]);
     }
     if (g.q == 0) {
         if (spilled) atomicAdd(&ctl->spilled, (u64)spilled);
         if (cvisits) atomicAdd(&ctl->class_visits, (u64)cvisits);
         if (pruned) atomicAdd(&ctl->pruned, (u64)pruned);
-        if (donated) atomicAdd(&ctl->donated, (u64)donated);
-        if (stolen) atomicAdd(&ctl->stolen, (u64)stolen);
-        atomicAdd(&ctl->busy_cycles, cyc[0]);
-        atomicAdd(&ctl->idle_cycles, cyc[1]);
+        atomicAdd(&ctl->busy_cycles, cyc()[0]);
+        atomicAdd(&ctl->idle_cycles, cyc()[1]);
     }
 }
 
