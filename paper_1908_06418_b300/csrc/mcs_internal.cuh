@@ -210,7 +210,7 @@ __host__ __device__ constexpr int row_hin(int u) { return 2 * kMaxN + 2 * u + 1;
 // u << 48, where (v, u) is the pair matched at depth d once a deeper level
 // exists (the mapping prefix M is read from these entries).
 constexpr int kSmLvOff = 0;                      // 65 * 16 -> 1040 (offsets after the adjacency)
-constexpr int kSmCycOff = 1040;                  // busy, idle cycle counters, clock mark (3 x 8)
+constexpr int kSmCycOff = 1040;                  // busy, idle cycles, clock mark, held ticket (4 x 8)
 constexpr int kSmClsOff = 1072;                  // 16-byte aligned
 static_assert(kSmClsOff % 16 == 0 && kSmAdjBytes % 16 == 0, "class cache must be 16-byte aligned");
 

@@ -1699,80 +1699,85 @@ __global__ void __launch_bounds__(256, (GS == 32 ? MCS_SEARCH_MINB : MCS_GROUP_M
         int p_word = 0, p_restart = 0;
         while (t.d >= d0) {
             ++tick;
-            if ((tick & P.poll_mask) == 0 && g.q == 0) {
-                int p_inc = vload(&ps.inc);
-                int p_abort = vload(&ps.abort);
-                const int p_hungry = vload(&ctl->q_head) > vload(&ctl->q_tail);   // a searcher waits
-                if (!p_abort && (tick & 255) == 0 && gtimer() > vload(&ps.deadline)) {
-                    if constexpr (GOAL) atomicCAS(&ps.abort, 0, 1);   // time limit (a reached goal stays)
-                    else ps.abort = 1;                 // per-pair time limit
-                    p_abort = 1;
-                }
-                if (!GOAL && P.race_cpu && (tick & 4095) == 0) {
-                    // GPU + CPU race: prune against the CPU side's best size too,
-                    // and stop once the CPU side has finished its proof (words in
-                    // host memory: one bus round trip each, so every 4,096 nodes)
-                    p_inc = max(p_inc, (int)*P.race_cpu);
-                    if (!p_abort && *P.race_stop) {
-                        ps.abort = 1;
-                        p_abort = 1;
+            // twice per poll interval (one test per node): lane 0 loads the
+            // polled values, and half an interval later the group uses them
+            if ((tick & (P.poll_mask >> 1)) == 0) {
+                if ((tick & P.poll_mask) == 0) {
+                    if (g.q == 0) {
+                        int p_inc = vload(&ps.inc);
+                        int p_abort = vload(&ps.abort);
+                        const int p_hungry = vload(&ctl->q_head) > vload(&ctl->q_tail);   // a searcher waits
+                        if (!p_abort && (tick & 255) == 0 && gtimer() > vload(&ps.deadline)) {
+                            if constexpr (GOAL) atomicCAS(&ps.abort, 0, 1);   // time limit (a reached goal stays)
+                            else ps.abort = 1;                 // per-pair time limit
+                            p_abort = 1;
+                        }
+                        if (!GOAL && P.race_cpu && (tick & 4095) == 0) {
+                            // GPU + CPU race: prune against the CPU side's best size too,
+                            // and stop once the CPU side has finished its proof (words in
+                            // host memory: one bus round trip each, so every 4,096 nodes)
+                            p_inc = max(p_inc, (int)*P.race_cpu);
+                            if (!p_abort && *P.race_stop) {
+                                ps.abort = 1;
+                                p_abort = 1;
+                            }
+                        }
+                        if (GOAL == 2 && (P.flags & MCS_RESTART) && p_abort == 0) {
+                            // randomized restart (Section IV-A) once the pair's node count has
+                            // doubled since its last new incumbent (and passed restart_min); the
+                            // searcher whose poll wins the mark update restarts
+                            const u64 step = (u64)P.poll_mask + 1;
+                            const u64 now = atomicAdd((unsigned long long*)&ps.live, (unsigned long long)step) + step;
+                            const u64 mk = vload(&ps.mark);
+                            // room for a whole stack of spilled branches: unclaimed tasks stay
+                            // under half the ring (else this restart waits for the next doubling)
+                            const long long pend = (long long)vload(&ctl->q_tail) - (long long)vload(&ctl->q_head);
+                            if (now >= P.restart_min && now >= 2 * mk && pend + 2 * kLevels < (long long)(P.qcap / 2) &&
+                                atomicCAS((unsigned long long*)&ps.mark, (unsigned long long)mk, (unsigned long long)now) == mk)
+                                p_restart = 1;
+                        }
+                        if (GOAL == 2 && (P.flags & MCS_DEAD_END) && p_abort == 0) {
+                            // dead-end forecast (Section IV): the searcher whose poll takes the
+                            // pair's count of nodes without a new incumbent past the threshold
+                            // raises the incumbent size, as if a mapping of that size were known
+                            const u64 step = (u64)P.poll_mask + 1;
+                            const u64 before = atomicAdd((unsigned long long*)&ps.dead, (unsigned long long)step);
+                            if (before < P.dead_nodes && before + step >= P.dead_nodes && vload(&ps.cap) == kNoCap) {
+                                const int cur = vload(&ps.inc);
+                                const int r = min(P.dead_double ? max(cur + 1, 2 * cur) : cur + 1, kMaxN);
+                                atomicMax(&ps.floor, r);
+                                atomicMax(&ps.inc, r);
+                                atomicExch((unsigned long long*)&ps.dead, 0ull);
+                                p_inc = max(p_inc, r);
+                            }
+                        }
+                        if (cvisits >= (1u << 31)) { atomicAdd(&ctl->class_visits, (u64)cvisits); cvisits = 0; }
+                        if (nodes >= (1u << 31)) { atomicAdd(&ps.nodes, (u64)nodes); nodes = 0; }
+                        if (pruned >= (1u << 31)) { atomicAdd(&ctl->pruned, (u64)pruned); pruned = 0; }
+                        p_word = (p_inc << 2) | (p_hungry << 1) | (p_abort != 0);
                     }
-                }
-                if (GOAL == 2 && (P.flags & MCS_RESTART) && p_abort == 0) {
-                    // randomized restart (Section IV-A) once the pair's node count has
-                    // doubled since its last new incumbent (and passed restart_min); the
-                    // searcher whose poll wins the mark update restarts
-                    const u64 step = (u64)P.poll_mask + 1;
-                    const u64 now = atomicAdd((unsigned long long*)&ps.live, (unsigned long long)step) + step;
-                    const u64 mk = vload(&ps.mark);
-                    // room for a whole stack of spilled branches: unclaimed tasks stay
-                    // under half the ring (else this restart waits for the next doubling)
-                    const long long pend = (long long)vload(&ctl->q_tail) - (long long)vload(&ctl->q_head);
-                    if (now >= P.restart_min && now >= 2 * mk && pend + 2 * kLevels < (long long)(P.qcap / 2) &&
-                        atomicCAS((unsigned long long*)&ps.mark, (unsigned long long)mk, (unsigned long long)now) == mk)
-                        p_restart = 1;
-                }
-                if (GOAL == 2 && (P.flags & MCS_DEAD_END) && p_abort == 0) {
-                    // dead-end forecast (Section IV): the searcher whose poll takes the
-                    // pair's count of nodes without a new incumbent past the threshold
-                    // raises the incumbent size, as if a mapping of that size were known
-                    const u64 step = (u64)P.poll_mask + 1;
-                    const u64 before = atomicAdd((unsigned long long*)&ps.dead, (unsigned long long)step);
-                    if (before < P.dead_nodes && before + step >= P.dead_nodes && vload(&ps.cap) == kNoCap) {
-                        const int cur = vload(&ps.inc);
-                        const int r = min(P.dead_double ? max(cur + 1, 2 * cur) : cur + 1, kMaxN);
-                        atomicMax(&ps.floor, r);
-                        atomicMax(&ps.inc, r);
-                        atomicExch((unsigned long long*)&ps.dead, 0ull);
-                        p_inc = max(p_inc, r);
+                } else {
+                    const int pw = g.shfl(p_word, 0);
+                    const int g_inc = pw >> 2;
+                    const int ab = pw & 1;
+                    const int hungry = (pw >> 1) & 1;
+                    inc = max(inc, g_inc);
+                    if (ab) break;
+                    if constexpr (GOAL == 2) {
+                        const int rst = g.shfl(p_restart, 0);
+                        p_restart = 0;
+                        if (rst) {                         // restart: every open level to the ring
+                            spill_all<GS>(P, pair, d0, t, inc, w, st, g);
+                            break;
+                        }
                     }
-                }
-                if (cvisits >= (1u << 31)) { atomicAdd(&ctl->class_visits, (u64)cvisits); cvisits = 0; }
-                if (nodes >= (1u << 31)) { atomicAdd(&ps.nodes, (u64)nodes); nodes = 0; }
-                if (pruned >= (1u << 31)) { atomicAdd(&ctl->pruned, (u64)pruned); pruned = 0; }
-                p_word = (p_inc << 2) | (p_hungry << 1) | (p_abort != 0);
-            }
-            if ((tick & P.poll_mask) == (P.poll_mask + 1) / 2) {
-                const int pw = g.shfl(p_word, 0);
-                const int g_inc = pw >> 2;
-                const int ab = pw & 1;
-                const int hungry = (pw >> 1) & 1;
-                inc = max(inc, g_inc);
-                if (ab) break;
-                if constexpr (GOAL == 2) {
-                    const int rst = g.shfl(p_restart, 0);
-                    p_restart = 0;
-                    if (rst) {                         // restart: every open level to the ring
-                        spill_all<GS>(P, pair, d0, t, inc, w, st, g);
-                        break;
+                    // ---- donate the shallowest open level to a waiting searcher ----
+                    if (hungry) {
+                        const bool ok = donate<GS>(P, pair, d0, t, inc, w, st, g, donated);
+                        if (g.q == 0 && donated) atomicAdd(&ctl->donated, (u64)donated);   // rare: counted in place
+                        donated = 0;
+                        if (!ok) break;
                     }
-                }
-                // ---- donate the shallowest open level to a waiting searcher ----
-                if (hungry) {
-                    const bool ok = donate<GS>(P, pair, d0, t, inc, w, st, g, donated);
-                    if (g.q == 0 && donated) atomicAdd(&ctl->donated, (u64)donated);   // rare: counted in place
-                    donated = 0;
-                    if (!ok) break;
                 }
             }
             // level prune: every node below this level has bound <= this one
@@ -1850,34 +1855,40 @@ __global__ void __launch_bounds__(256, MCS_GROUP_MINB) lockstep_kernel(SearchPar
     st.ctl = P.ctl;
 #endif
     Control* ctl = P.ctl;
-    int16_t* smap = reinterpret_cast<int16_t*>(lv + kSmLvOff);
+    // finalize scratch and the busy / idle / mark clock words, addressed from
+    // the level entries rather than held in registers (as in search_kernel)
+    auto smap = [&]() { return reinterpret_cast<int16_t*>(w.lvl); };
+    auto cyc = [&]() {
+        return reinterpret_cast<u64*>(reinterpret_cast<unsigned char*>(w.lvl) + (kSmCycOff - kSmLvOff));
+    };
     const bool level_prune = (P.flags & MCS_NO_LEVEL_PRUNE) == 0;
     const uint32_t qmask = P.qcap - 1;
-    u64 nodes = 0;
+    unsigned nodes = 0;      // of the current task; flushed to the pair before it can wrap
     unsigned tick = 0;
-    unsigned spilled = 0, cvisits = 0, pruned = 0, donated = 0, stolen = 0;
-    u64* cyc = (u64*)(lv + kSmCycOff);
-    if (state != kExit && g.q == 0) { cyc[0] = 0; cyc[1] = 0; }
-    long long c_mark = clock64();
-    bool holding = false;
-    u64 qh = 0;
+    unsigned cvisits = 0, pruned = 0, donated = 0;
+    if (state != kExit && g.q == 0) { cyc()[0] = 0; cyc()[1] = 0; cyc()[2] = (u64)clock64(); }
+    bool holding = false;    // the ticket taken is kept in cyc()[3] while waiting for its slot
     unsigned wait_it = 0, idle_ns = 128;
     int pair = 0, d0 = 0, inc = 0;
-    int p_inc = 0, p_abort = 0, p_hungry = 0;
+    int p_word = 0;          // lane 0's polled values: incumbent << 2 | hungry << 1 | abort
     Top t;
     t.d = -1; t.base = 0; t.C = 0; t.v = 0; t.flags = 0; t.bound = 0; t.rrem = 0;
 
     while (__any_sync(FULL, state != kExit)) {
         // ---------------- searchers without work: take a ticket, check its slot ----------------
         if (state == kNeed) {
+            u64 qh = 0;
             if (!holding) {
-                if (g.q == 0) qh = atomicAdd(&ctl->q_head, 1ull);
-                qh = g.shfl64(qh, 0);
+                if (g.q == 0) {
+                    qh = atomicAdd(&ctl->q_head, 1ull);
+                    cyc()[3] = qh;
+                }
                 holding = true;
                 wait_it = 0;
             }
             int got = 0;
             if (g.q == 0) {
+                qh = cyc()[3];
                 if (vload(P.qseq + (qh & qmask)) == qh + 1) {
                     got = 1;
                 } else if ((++wait_it & 63) == 0) {
@@ -1895,6 +1906,7 @@ __global__ void __launch_bounds__(256, MCS_GROUP_MINB) lockstep_kernel(SearchPar
             got = g.shfl(got, 0);
             if (got < 0) state = kExit;
             if (got > 0) {
+                qh = g.shfl64(qh, 0);
                 holding = false;
                 __threadfence();
                 const Task* task = P.queue + (qh & qmask);
@@ -1912,7 +1924,7 @@ __global__ void __launch_bounds__(256, MCS_GROUP_MINB) lockstep_kernel(SearchPar
                     // polled values belong to the task they were read for: a half
                     // tick right after this install must not apply the previous
                     // pair's incumbent or abort flag to this one
-                    p_inc = p_abort = p_hungry = 0;
+                    p_word = 0;
                     const bool fresh = (tflags & kTaskFresh) != 0;
                     PairState& ps = P.state[pair];
                     const PairGraph& pg = P.graphs[pair];
@@ -1922,7 +1934,7 @@ __global__ void __launch_bounds__(256, MCS_GROUP_MINB) lockstep_kernel(SearchPar
                     if (fresh && pstat != MCS_PENDING) {          // malformed input: report and skip
                         g.sync();
                         if (g.q == 0) { P.qseq[qh & qmask] = qh + P.qcap; ps.open = 0; }
-                        finalize_pair<false, GS, 0>(P, pair, g, smap);
+                        finalize_pair<false, GS, 0>(P, pair, g, smap());
                     } else {
                         if (fresh && g.q == 0) {
                             const u64 now = gtimer();
@@ -1930,7 +1942,6 @@ __global__ void __launch_bounds__(256, MCS_GROUP_MINB) lockstep_kernel(SearchPar
                             ps.deadline = now + P.timeout_ns;
                             atomicMax(&ctl->last_progress, now);
                         }
-                        w.adj = pg.rows;                          // rows read in place
                         if (!fresh) {
                             int hd4[4] = {0, 0, 0, 0};
                             u64 rr = 0;
@@ -1953,7 +1964,7 @@ __global__ void __launch_bounds__(256, MCS_GROUP_MINB) lockstep_kernel(SearchPar
                                 w.lvl[i] = make_ulonglong2(0ull, ((u64)ld_cg(&task->Mg[i]) << 24) |
                                                                      ((u64)ld_cg(&task->Mh[i]) << 48));
                             for (int i = g.q; i < t.C; i += GS) *st.at(i) = ld_cg(&task->cls[i]);
-                            ++stolen;
+                            if (g.q == 0) atomicAdd(&ctl->stolen, 1ull);   // rare: counted in place
                         } else {
                             t.d = 0;
                             t.C = __ldcg(&pg.C0);
@@ -1970,7 +1981,11 @@ __global__ void __launch_bounds__(256, MCS_GROUP_MINB) lockstep_kernel(SearchPar
                         if (g.q == 0) { inc = vload(&ps.inc); ab0 = vload(&ps.abort); }
                         inc = g.shfl(inc, 0);
                         ab0 = g.shfl(ab0, 0);
-                        if (g.q == 0) { const long long now = clock64(); cyc[1] += (u64)(now - c_mark); c_mark = now; }
+                        if (g.q == 0) {
+                            const long long now = clock64();
+                            cyc()[1] += (u64)(now - (long long)cyc()[2]);
+                            cyc()[2] = (u64)now;
+                        }
                         state = kRun;
                         if (ab0) {
                             t.d = d0 - 1;                         // ends below
@@ -2002,23 +2017,29 @@ __global__ void __launch_bounds__(256, MCS_GROUP_MINB) lockstep_kernel(SearchPar
         ++tick;
         if ((tick & P.poll_mask) == 0 && state == kRun && g.q == 0) {
             PairState& ps = P.state[pair];
-            p_inc = vload(&ps.inc);
-            p_abort = vload(&ps.abort);
-            p_hungry = vload(&ctl->q_head) > vload(&ctl->q_tail);     // a searcher waits
+            const int p_inc = vload(&ps.inc);
+            int p_abort = vload(&ps.abort);
+            const int p_hungry = vload(&ctl->q_head) > vload(&ctl->q_tail);     // a searcher waits
             if (!p_abort && (tick & 255) == 0 && gtimer() > vload(&ps.deadline)) {
                 ps.abort = 1;                                   // per-pair time limit
                 p_abort = 1;
             }
             if (cvisits >= (1u << 31)) { atomicAdd(&ctl->class_visits, (u64)cvisits); cvisits = 0; }
             if (pruned >= (1u << 31)) { atomicAdd(&ctl->pruned, (u64)pruned); pruned = 0; }
+            if (nodes >= (1u << 31)) { atomicAdd(&ps.nodes, (u64)nodes); nodes = 0; }
+            p_word = (p_inc << 2) | (p_hungry << 1) | (p_abort != 0);
         }
         if ((tick & P.poll_mask) == (P.poll_mask + 1) / 2 && state == kRun && t.d >= d0) {
-            const int g_inc = g.shfl(p_inc, 0);
-            const int ab = g.shfl(p_abort, 0);
-            const int hungry = g.shfl(p_hungry, 0);
-            inc = max(inc, g_inc);
-            if (ab) t.d = d0 - 1;                               // time limit: leave the task
-            else if (hungry && !donate<GS>(P, pair, d0, t, inc, w, st, g, donated)) t.d = d0 - 1;
+            const int pw = g.shfl(p_word, 0);
+            inc = max(inc, pw >> 2);
+            if (pw & 1) {
+                t.d = d0 - 1;                                   // time limit: leave the task
+            } else if ((pw >> 1) & 1) {
+                const bool ok = donate<GS>(P, pair, d0, t, inc, w, st, g, donated);
+                if (g.q == 0 && donated) atomicAdd(&ctl->donated, (u64)donated);   // rare: counted in place
+                donated = 0;
+                if (!ok) t.d = d0 - 1;
+            }
         }
         // ---------------- pop exhausted or bounded levels ----------------
         for (;;) {
@@ -2031,8 +2052,12 @@ __global__ void __launch_bounds__(256, MCS_GROUP_MINB) lockstep_kernel(SearchPar
             }
         }
         if (state == kRun && t.d < d0) {                        // the task is done
-            end_task<false, GS, 0>(P, pair, nodes, g, smap);
-            if (g.q == 0) { const long long now = clock64(); cyc[0] += (u64)(now - c_mark); c_mark = now; }
+            end_task<false, GS, 0>(P, pair, nodes, g, smap());
+            if (g.q == 0) {
+                const long long now = clock64();
+                cyc()[0] += (u64)(now - (long long)cyc()[2]);
+                cyc()[2] = (u64)now;
+            }
             state = kNeed;
         }
         // ---------------- one node of every searcher with work ----------------
@@ -2055,11 +2080,11 @@ __global__ void __launch_bounds__(256, MCS_GROUP_MINB) lockstep_kernel(SearchPar
         const W ub = ch ? ((W)1 << u) : (W)0;
         W gB = 0, hB = 0, gA = 0, hA = 0;
         if (ch) {
-            gB = (W)adj_row<false>(w.adj, row_gout(v));
-            hB = (W)adj_row<false>(w.adj, row_hout(u));
+            gB = (W)adj_row<false>(P.graphs[pair].rows, row_gout(v));
+            hB = (W)adj_row<false>(P.graphs[pair].rows, row_hout(u));
             if (DIR) {
-                gA = (W)adj_row<false>(w.adj, row_gin(v));
-                hA = (W)adj_row<false>(w.adj, row_hin(u));
+                gA = (W)adj_row<false>(P.graphs[pair].rows, row_gin(v));
+                hA = (W)adj_row<false>(P.graphs[pair].rows, row_hin(u));
             }
         }
         const int nsl = ((int)__reduce_max_sync(FULL, act ? (unsigned)t.C : 0u) + GS - 1) / GS;
@@ -2167,7 +2192,6 @@ __global__ void __launch_bounds__(256, MCS_GROUP_MINB) lockstep_kernel(SearchPar
             }
         }
         if (surv) {
-            if (pos > st.S) spilled += 1;
             if (!DBG_OK(ctl, pos - cbase <= kMaxN && dm <= kMaxN, 5, (pos - cbase) * 1000 + dm)) pos = cbase;
             if (g.q == 0)
                 w.lvl[t.d] = make_ulonglong2(t.rrem, pack_info(t.base, t.C, t.v, t.flags, t.bound) | ((u64)u << 48));
@@ -2182,13 +2206,10 @@ __global__ void __launch_bounds__(256, MCS_GROUP_MINB) lockstep_kernel(SearchPar
         __syncwarp();
     }
     if (sid < P.max_warps && g.q == 0) {
-        if (spilled) atomicAdd(&ctl->spilled, (u64)spilled);
         if (cvisits) atomicAdd(&ctl->class_visits, (u64)cvisits);
         if (pruned) atomicAdd(&ctl->pruned, (u64)pruned);
-        if (donated) atomicAdd(&ctl->donated, (u64)donated);
-        if (stolen) atomicAdd(&ctl->stolen, (u64)stolen);
-        atomicAdd(&ctl->busy_cycles, cyc[0]);
-        atomicAdd(&ctl->idle_cycles, cyc[1]);
+        atomicAdd(&ctl->busy_cycles, cyc()[0]);
+        atomicAdd(&ctl->idle_cycles, cyc()[1]);
     }
 }
 
