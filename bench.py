@@ -49,8 +49,8 @@ METRIC = "MCS pairs solved/sec (exact) on 1 B300"
 #       python bench.py --workload <w> --steps 2 --warmup 1 --no-cpu-baseline --no-single
 #       --no-batched --no-served --no-race
 # Reported only while the kernel source is the one the capture was taken with.
-TRAFFIC = {"c2": {"kernel_sha1": "6422e082133504d4", "bytes": 1128680960 + 1438386688},
-           "c3": {"kernel_sha1": "6422e082133504d4", "bytes": 111085568 + 205210112}}
+TRAFFIC = {"c2": {"kernel_sha1": "bfc9a84d6fb9f8a0", "bytes": 992815360 + 979917568},
+           "c3": {"kernel_sha1": "bfc9a84d6fb9f8a0", "bytes": 102537728 + 191992576}}
 UNIT = "pairs/s"
 
 
