@@ -58,7 +58,7 @@ extern "C" {
 #define MCS_ERR_NOMEM         -2   /* device or pinned allocation failed              */
 #define MCS_ERR_CUDA          -3   /* a CUDA runtime call failed                      */
 #define MCS_ERR_DEVICE_STALL  -4   /* a bounded device-side wait expired              */
-#define MCS_ERR_UNSUPPORTED   -5   /* option not available in this build              */
+#define MCS_ERR_UNSUPPORTED   -5   /* option not supported for these flags or inputs  */
 
 /* flags */
 #define MCS_DIRECTED          0x1u  /* arcs are ordered pairs (4-way class split)      */
