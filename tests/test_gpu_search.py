@@ -357,6 +357,10 @@ def test_work_sharing_settings_give_same_sizes(solver, steal):
         solver.reset_launch()
     assert [r.size for r in res] == ref and all(r.status == 0 for r in res)
     assert st["donated"] > 0
+    # a batch ends only once every task is done: each donated task was taken up
+    assert st["stolen"] == st["donated"], st
+    # searchers narrower than a warp have no shared-memory part of the class stack
+    assert st["spilled"] == 0, st
 
 
 def test_work_sharing_values_out_of_range_are_rejected(solver):
