@@ -57,28 +57,32 @@ UNIT = "pairs/s"
 # ---------------------------------------------------------------------------
 # workloads
 # ---------------------------------------------------------------------------
-def workload(name: str):
+def workload(name: str, shard: int = 0):
+    """The named workload's pairs and config.  Under several ranks each rank
+    solves shard `shard` = its rank: the same recipe (sizes, densities,
+    labels) drawn from seeds of its own, so no pair is solved twice."""
     import synth
+    sc = lambda cid: synth.shard_cid(cid, shard)
     if name == "c2":
-        return synth.config2_pairs(), dict(
+        return synth.config2_pairs(cid=sc(2)), dict(
             workload="hard single pairs: 96 directed G(36,p), p in {0.05,0.1,0.3} x 32 seeds "
                      "+ 6x6 grid pair with 10% edges deleted", pairs=97)
     if name == "c2s":     # small case of the same kernel for profiler captures
-        return synth.config2_pairs()[0:96:4], dict(
+        return synth.config2_pairs(cid=sc(2))[0:96:4], dict(
             workload="24 directed G(36,p) pairs (every 4th of the hard single pairs)", pairs=24)
     if name == "c3":
-        return synth.config3_pairs(), dict(
+        return synth.config3_pairs(cid=sc(3)), dict(
             workload="batched: 4096 undirected pairs, n U{10..40}, p U[0.05,0.4], 4 labels",
             pairs=4096)
     if name == "c1":
         return [synth.config1_pair()], dict(workload="single pair G(20,0.3) x G(20,0.3)", pairs=1)
     if name == "c4":
-        return synth.config4_pairs(2048), dict(
+        return synth.config4_pairs(2048, cid=sc(4)), dict(
             workload="learned ordering: 2048 bounded-valence pairs (random 3-/4-regular and perturbed "
                      "2D meshes, n U{40..64}), order network data/order_mlp_bvg.npy (per-pair limit: timeout_s)",
             pairs=2048)
     if name == "td":
-        return [synth.planted_bvg_pair(i, 40, 64, cid=62) for i in range(4, 480, 5)], dict(
+        return [synth.planted_bvg_pair(i, 40, 64, cid=sc(62)) for i in range(4, 480, 5)], dict(
             workload="top-down strategy (Section IV-A): 96 bounded-valence pairs with a planted common "
                      "core of 90% of n (3-regular or mesh core), n U{40..64}; MCS_TOP_DOWN", pairs=96)
     raise SystemExit(f"unknown workload {name}")
@@ -208,7 +212,7 @@ def oracle_sample(name: str, n_pairs: int, budget: float, offset: int = 0):
 
 
 def combine_ranks(total_ms, solved, nodes, dist=None, device="cpu"):
-    """Whole-job figures of a multi-rank run (one replica per rank): after a
+    """Whole-job figures of a multi-rank run (one shard of pairs per rank): after a
     barrier, the slowest rank's timed milliseconds and the work of all ranks
     summed.  dist: torch.distributed (any backend) or None for one rank."""
     if not dist:
@@ -370,7 +374,7 @@ def main():
     line = measure(a, a.workload, solver, local, rank, world, dist)
     # the default run (one GPU) also measures the batched form (the 4,096
     # labelled pairs) and the served form (the Poisson stream of requests);
-    # under several ranks only the replicated headline workload runs
+    # under several ranks only the sharded headline workload runs
     if world == 1 and a.workload == "c2" and not a.no_batched:
         b = copy.copy(a)
         b.workload = "c3"
@@ -400,8 +404,9 @@ def measure(a, name, solver, local, rank, world, dist):
     from paper_1908_06418_b300 import (pack_host, MCS_DIRECTED, MCS_OK, MCS_WORD32, MCS_ORDER_LEARNED,
                                        MCS_TOP_DOWN, MCS_DEAD_END, MCS_ORDER_HR, MCS_RESTART)
 
-    pairs, cfg = workload(name)
-    gold = golden_sizes(name)
+    # each rank its own shard of pairs; the stored oracle sizes cover shard 0
+    pairs, cfg = workload(name, shard=rank)
+    gold = golden_sizes(name) if rank == 0 else {}
     dev = torch.device("cuda", local)
     learned = name == "c4" and a.order == "degree"
     hr = a.order == "hr"
@@ -413,7 +418,7 @@ def measure(a, name, solver, local, rank, world, dist):
     # it is given, and CUDA events recorded on that same stream time it
     stream = torch.cuda.Stream(dev)
 
-    # device-resident inputs, one group per flag set (replicas on every rank);
+    # device-resident inputs, one group per flag set (this rank's shard);
     # a group whose graphs all have at most 32 vertices takes the 32-bit node step
     groups = []
     for directed in (True, False):
@@ -587,7 +592,8 @@ def measure(a, name, solver, local, rank, world, dist):
             "p50_latency_ms": float(np.percentile(lats, 50)) if lats else None,
             "p99_latency_ms": float(np.percentile(lats, 99)) if lats else None,
             "solved_per_step": solved_tot / a.steps / world,
-            "config": dict(cfg, parallelism=f"replicas x{world}", l2="flushed between steps (512 MB write)",
+            "config": dict(cfg, parallelism=f"pair shards x{world} (one shard of distinct pairs per rank, "
+                                            "same recipe)", l2="flushed between steps (512 MB write)",
                            vertex_order=("learned" if learned else a.order),
                            timeout_s=a.timeout, launch_shapes=shapes),
             "gpu_launches": launches_per_step * a.steps,

@@ -183,23 +183,30 @@ def config1_like(count: int, n: int = 20, p: float = 0.3, cid: int = 11) -> List
 
 
 def config2_pairs(seeds: int = 32, n: int = 36, ps=(0.05, 0.1, 0.3),
-                  with_grid: bool = True) -> List[Pair]:
+                  with_grid: bool = True, cid: int = 2) -> List[Pair]:
     """Directed unlabelled G(n, p) pairs, ``seeds`` per p, plus one pair of
     undirected 6x6 grids each losing round(0.1 * 60) = 6 random edges."""
     out = []
     idx = 0
     for p in ps:
         for s in range(seeds):
-            out.append(Pair(Graph(er_directed(n, p, rng_for(2, idx, 0))),
-                            Graph(er_directed(n, p, rng_for(2, idx, 1))),
+            out.append(Pair(Graph(er_directed(n, p, rng_for(cid, idx, 0))),
+                            Graph(er_directed(n, p, rng_for(cid, idx, 1))),
                             True, f"c2-p{p}-s{s}"))
             idx += 1
     if with_grid:
         g = grid(6, 6)
-        out.append(Pair(Graph(delete_edges(g, 6, rng_for(2, 1000, 0))),
-                        Graph(delete_edges(g, 6, rng_for(2, 1000, 1))),
+        out.append(Pair(Graph(delete_edges(g, 6, rng_for(cid, 1000, 0))),
+                        Graph(delete_edges(g, 6, rng_for(cid, 1000, 1))),
                         False, "c2-grid6x6"))
     return out
+
+
+def shard_cid(cid: int, shard: int) -> int:
+    """Config id of a workload's shard: shard 0 is the workload itself; shard
+    r > 0 draws the same recipe from seeds of its own (config ids from
+    100,000 up, disjoint from every other generator's)."""
+    return cid if shard == 0 else 100000 + 1000 * int(shard) + int(cid)
 
 
 def config3_pairs(count: int = 4096, nmin: int = 10, nmax: int = 40,
